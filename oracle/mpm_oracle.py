@@ -1,0 +1,350 @@
+"""Plain FP64 CPU oracle driver for the implicit-MPM Newton step.
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this module.  It
+does not import the CUDA package, and the CUDA package never imports it.
+
+The per-particle and per-node arithmetic is in ``oracle.cpp`` (compiled to
+``oracle/_build/liboracle.so`` by :func:`build`).  This module holds the
+Newton loop of the paper's Sec. 2.2:
+
+* residual r(u^{n+1,k}) = assembled f_int - f_ext;
+* Newton update  -J du = r  with J = dr/du (exact, from the oracle's tangent),
+  solved by a sparse direct factorisation (SciPy's SuperLU, a library step);
+* stop when ||r^k|| / ||r^0|| <= tol (paper's convergence criterion), with
+  r^0 taken after the prescribed boundary increment is applied;
+* commit of the particle state after convergence.
+
+Readings (the paper is silent on these):
+* active DOFs are those of nodes with nodal mass M_i > ACTIVE_REL * max_p m_p;
+* a prescribed DOF takes its increment at k = 0; its row and column of J are
+  replaced by the identity and its residual entry is excluded from the norm;
+* a prescribed DOF on an inactive node is ignored.
+
+It also provides the coloured central finite-difference Jacobian used to pin
+the exact tangent: the seeding pattern of the paper's sparse differentiation
+(Algorithm 2, block size b = 5 for quadratic B-splines, Table 1) with a
+central difference in place of a reverse-mode pass.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB = os.path.join(HERE, "_build", "liboracle.so")
+ACTIVE_REL = 1e-12
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+_L = ctypes.POINTER(ctypes.c_long)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.cpp with g++ (-O2, no FMA contraction)."""
+    src = os.path.join(HERE, "oracle.cpp")
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(src):
+        tmp = LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, src])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(LIB)
+        L.orc_stencil.argtypes = [_I, _D, _D, _L, _D, _D]
+        L.orc_eig.argtypes = [_D, _D, _D]
+        L.orc_return_map.argtypes = [ctypes.c_int, _D, _D, ctypes.c_double, _D, _D, _I, _D, _D]
+        L.orc_particle.argtypes = [ctypes.c_int, _D, _D, ctypes.c_double, _D, ctypes.c_double,
+                                   _D, _D, _D, _I, _D, _D]
+        L.orc_residual.argtypes = [_I, _D, _D, ctypes.c_int, _D, _D, _D, _I, _D, _D, _D, _D,
+                                   _D, _D, _I]
+        L.orc_jacobian.argtypes = [_I, _D, ctypes.c_int, _D, _D, _I, _D, _D, _D, _D,
+                                   ctypes.c_long, _L, _L, _D]
+        L.orc_commit.argtypes = [_I, _D, ctypes.c_int, _D, _D, _I, _D, _D, _D, _D, _D]
+        _lib = L
+    return _lib
+
+
+def _p(a, t=_D):
+    return a.ctypes.data_as(t)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+# --------------------------------------------------------------------------
+# single-particle entry points (used by the pins)
+# --------------------------------------------------------------------------
+
+def stencil(dim, n, h, origin, xp):
+    gi = np.array([dim, n[0], n[1], n[2] if dim == 3 else 0], dtype=np.int32)
+    gd = _f64([h, origin[0], origin[1], origin[2]])
+    node = np.zeros(27, dtype=np.int64)
+    w = np.zeros(27)
+    g = np.zeros(81)
+    c = lib().orc_stencil(_p(gi, _I), _p(gd), _p(_f64(xp)), _p(node, _L), _p(w), _p(g))
+    if c < 0:
+        raise OracleError("particle outside the grid")
+    return node[:c], w[:c], g[:3 * c].reshape(c, 3)
+
+
+def eig(a):
+    a = _f64(a).reshape(9)
+    lam = np.zeros(3)
+    Q = np.zeros(9)
+    lib().orc_eig(_p(a), _p(lam), _p(Q))
+    return lam, Q.reshape(3, 3)
+
+
+def return_map(model, params, etr, pcn=-1e5):
+    eps = np.zeros(3)
+    pc = np.zeros(1)
+    mode = np.zeros(1, dtype=np.int32)
+    deps = np.zeros(9)
+    dg = np.zeros(1)
+    rc = lib().orc_return_map(int(model), _p(_f64(params)), _p(_f64(etr)), float(pcn), _p(eps),
+                              _p(pc), _p(mode, _I), _p(deps), _p(dg))
+    if rc:
+        raise OracleError(f"return map failed ({rc})")
+    return eps, float(pc[0]), int(mode[0]), deps.reshape(3, 3), float(dg[0])
+
+
+def particle(model, params, be6, pcn, dF, V0=1.0, tangent=True):
+    """Stress update of one particle. Returns dict(tau, be, pc, mode, P, A)
+    with A[a,c,b,e] = dP[a,c]/d dF[b,e]."""
+    tau = np.zeros(9)
+    be = np.zeros(6)
+    pc = np.zeros(1)
+    mode = np.zeros(1, dtype=np.int32)
+    P = np.zeros(9)
+    A = np.zeros(81) if tangent else None
+    rc = lib().orc_particle(int(model), _p(_f64(params)), _p(_f64(be6)), float(pcn),
+                            _p(_f64(np.asarray(dF).reshape(9))), float(V0), _p(tau), _p(be),
+                            _p(pc), _p(mode, _I), _p(P), _p(A) if tangent else None)
+    if rc:
+        raise OracleError(f"particle update failed ({rc})")
+    return dict(tau=tau.reshape(3, 3), be=be, pc=float(pc[0]), mode=int(mode[0]),
+                P=P.reshape(3, 3), A=A.reshape(3, 3, 3, 3) if tangent else None)
+
+
+# --------------------------------------------------------------------------
+# scene-level oracle
+# --------------------------------------------------------------------------
+
+class OracleScene:
+    """Particle state plus grid, evolved load step by load step."""
+
+    def __init__(self, dim, n, h, origin, x, vol0, mass, model, params, pc0):
+        self.dim = int(dim)
+        self.n = (int(n[0]), int(n[1]), int(n[2]) if dim == 3 else 0)
+        self.h = float(h)
+        self.origin = tuple(float(o) for o in origin)
+        self.gi = np.array([self.dim, *self.n], dtype=np.int32)
+        self.gd = _f64([self.h, *self.origin])
+        self.x = _f64(x).copy()
+        self.V0 = _f64(vol0).copy()
+        self.m = _f64(mass).copy()
+        self.model = np.ascontiguousarray(model, dtype=np.int32).copy()
+        self.params = _f64(params).copy()
+        self.np = self.x.shape[0]
+        self.be = np.zeros((self.np, 6))
+        self.be[:, :3] = 1.0
+        self.pc = _f64(pc0).copy()
+        self.F = np.tile(np.eye(3).reshape(9), (self.np, 1))
+        self.gravity = np.zeros(3)
+        nn = 1
+        for a in range(self.dim):
+            nn *= self.n[a] + 1
+        self.nnode = nn
+
+    @classmethod
+    def from_scene(cls, sc):
+        model, params, pc0 = sc.particle_params()
+        return cls(sc.dim, sc.n, sc.h, sc.origin, sc.x, sc.vol0, sc.mass, model, params, pc0)
+
+    # ---- residual / Jacobian -------------------------------------------
+    def residual(self, du, with_mode=False):
+        du = _f64(du)
+        r = np.zeros(self.nnode * self.dim)
+        M = np.zeros(self.nnode)
+        mode = np.zeros(self.np, dtype=np.int32)
+        rc = lib().orc_residual(_p(self.gi, _I), _p(self.gd), _p(_f64(self.gravity)), self.np,
+                                _p(self.x), _p(self.V0), _p(self.m), _p(self.model, _I),
+                                _p(self.params), _p(self.be), _p(self.pc), _p(du), _p(r), _p(M),
+                                _p(mode, _I))
+        if rc:
+            raise OracleError(f"residual failed ({rc})")
+        return (r, M, mode) if with_mode else (r, M)
+
+    def jacobian_blocks(self, du):
+        """Node-pair blocks (bi, bj, val[nb, d, d]) of J = dr/du, summed."""
+        d = self.dim
+        cap = self.nnode * (5 ** d)
+        bi = np.zeros(cap, dtype=np.int64)
+        bj = np.zeros(cap, dtype=np.int64)
+        val = np.zeros(cap * d * d)
+        nb = lib().orc_jacobian(_p(self.gi, _I), _p(self.gd), self.np, _p(self.x), _p(self.V0),
+                                _p(self.model, _I), _p(self.params), _p(self.be), _p(self.pc),
+                                _p(_f64(du)), cap, _p(bi, _L), _p(bj, _L), _p(val))
+        if nb < 0:
+            raise OracleError(f"jacobian failed ({nb})")
+        return bi[:nb], bj[:nb], val[:nb * d * d].reshape(nb, d, d)
+
+    def jacobian(self, du):
+        """J over the dense DOF space as a scipy CSR matrix."""
+        d = self.dim
+        bi, bj, val = self.jacobian_blocks(du)
+        rows = (bi[:, None, None] * d + np.arange(d)[None, :, None]) + 0 * np.arange(d)[None, None, :]
+        cols = (bj[:, None, None] * d + np.arange(d)[None, None, :]) + 0 * np.arange(d)[None, :, None]
+        N = self.nnode * d
+        return sp.csr_matrix((val.ravel(), (rows.ravel(), cols.ravel())), shape=(N, N))
+
+    def active_dofs(self, M):
+        act = M > ACTIVE_REL * self.m.max()
+        return np.repeat(act, self.dim)
+
+    # ---- Newton (paper Sec. 2.2) ------------------------------------------
+    def solve_step(self, dof, value, gravity, tol=1e-12, maxit=25, commit=True):
+        """One load step.  Returns dict(du, hist, iters, converged, r0)."""
+        self.gravity = _f64(gravity).copy()
+        N = self.nnode * self.dim
+        du = np.zeros(N)
+        r, M = self.residual(du)
+        act = self.active_dofs(M)
+        fixed = np.zeros(N, dtype=bool)
+        dof = np.asarray(dof, dtype=np.int64)
+        keep = act[dof]
+        fixed[dof[keep]] = True
+        du[dof[keep]] = np.asarray(value, dtype=np.float64)[keep]
+        free = act & ~fixed
+        fidx = np.nonzero(free)[0]
+        r, M = self.residual(du)
+        r0 = np.linalg.norm(r[free])
+        hist = [1.0]
+        it = 0
+        conv = r0 == 0.0
+        while not conv and it < maxit:
+            J = self.jacobian(du)[fidx][:, fidx].tocsc()
+            delta = spla.spsolve(J, -r[fidx])
+            du[fidx] += delta
+            r, M = self.residual(du)
+            it += 1
+            rel = np.linalg.norm(r[free]) / r0
+            hist.append(rel)
+            conv = rel <= tol
+        out = dict(du=du, hist=np.array(hist), iters=it, converged=bool(conv), r0=r0,
+                   free=free, fixed=fixed, active=act, r=r, mass=M)
+        if commit:
+            self.commit(du)
+        return out
+
+    def commit(self, du):
+        rc = lib().orc_commit(_p(self.gi, _I), _p(self.gd), self.np, _p(self.x), _p(self.V0),
+                              _p(self.model, _I), _p(self.params), _p(self.be), _p(self.pc),
+                              _p(self.F), _p(_f64(du)))
+        if rc:
+            raise OracleError(f"commit failed ({rc})")
+
+    # ---- state helpers -----------------------------------------------------
+    def stresses(self, du=None):
+        """Kirchhoff stress (np,3,3) and mode of each particle at increment du
+        (zero increment by default: the committed state)."""
+        if du is None:
+            du = np.zeros(self.nnode * self.dim)
+        out = np.zeros((self.np, 3, 3))
+        modes = np.zeros(self.np, dtype=np.int32)
+        for p in range(self.np):
+            node, w, g = stencil(self.dim, self.n, self.h, self.origin, self.x[p])
+            dF = np.eye(3)
+            for l in range(len(node)):
+                for a in range(self.dim):
+                    for c in range(self.dim):
+                        dF[a, c] += du[node[l] * self.dim + a] * g[l, c]
+            o = particle(self.model[p], self.params[p], self.be[p], self.pc[p], dF,
+                         self.V0[p], tangent=False)
+            out[p] = o["tau"]
+            modes[p] = o["mode"]
+        return out, modes
+
+    def snapshot(self):
+        return dict(x=self.x.copy(), be=self.be.copy(), pc=self.pc.copy(), F=self.F.copy())
+
+    def restore(self, s):
+        self.x[:] = s["x"]
+        self.be[:] = s["be"]
+        self.pc[:] = s["pc"]
+        self.F[:] = s["F"]
+
+
+def node_ijk(sc: OracleScene, node):
+    nx1 = sc.n[0] + 1
+    ny1 = sc.n[1] + 1
+    ix = node % nx1
+    iy = (node // nx1) % ny1
+    iz = node // (nx1 * ny1)
+    return ix, iy, iz
+
+
+def fd_jacobian_colored(sc: OracleScene, du, eps, b=5):
+    """Central-difference Jacobian with the sparse-differentiation colouring:
+    one colour per (local_x, local_y[, local_z], component) with block size b,
+    seeding every DOF of that colour at once; each seeded column is read off
+    the rows within +-2 nodes of its node.  Returns a dense (N, N) array."""
+    d = sc.dim
+    N = sc.nnode * d
+    nodes = np.arange(sc.nnode)
+    ix, iy, iz = node_ijk(sc, nodes)
+    J = np.zeros((N, N))
+    locs = [(lx, ly, lz) for lz in (range(b) if d == 3 else [0]) for ly in range(b) for lx in range(b)]
+    for (lx, ly, lz) in locs:
+        sel = (ix % b == lx) & (iy % b == ly) & ((iz % b == lz) if d == 3 else True)
+        seeded = nodes[sel]
+        for comp in range(d):
+            e = np.zeros(N)
+            e[seeded * d + comp] = 1.0
+            rp, _ = sc.residual(du + eps * e)
+            rm, _ = sc.residual(du - eps * e)
+            col = (rp - rm) / (2 * eps)
+            for j in seeded:
+                jx, jy, jz = ix[j], iy[j], iz[j]
+                near = (np.abs(ix - jx) <= 2) & (np.abs(iy - jy) <= 2)
+                if d == 3:
+                    near &= np.abs(iz - jz) <= 2
+                rows = nodes[near]
+                for a in range(d):
+                    J[rows * d + a, j * d + comp] = col[rows * d + a]
+    return J
+
+
+def fd_jacobian_plain(sc: OracleScene, du, eps, cols):
+    """Central-difference columns of J, one DOF at a time (the dense
+    differentiation of the paper's Algorithm 1 with a difference in place of a
+    reverse pass).  Returns (N, len(cols))."""
+    N = sc.nnode * sc.dim
+    out = np.zeros((N, len(cols)))
+    for k, j in enumerate(cols):
+        e = np.zeros(N)
+        e[j] = 1.0
+        rp, _ = sc.residual(du + eps * e)
+        rm, _ = sc.residual(du - eps * e)
+        out[:, k] = (rp - rm) / (2 * eps)
+    return out

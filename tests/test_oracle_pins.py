@@ -1,0 +1,356 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics
+(no GPU).  Each test names what it checks and why a plausible mistake in the
+oracle would fail it.
+
+* B-spline: partition of unity, zero gradient sum, linear reproduction
+  (a wrong node offset, a dropped 1/h or a sign error fails these).
+* Eigen-decomposition against LAPACK (an independent library routine).
+* G2P patch test: an affine nodal field gives dF = 1 + A exactly.
+* Zero-strain tangent equals the isotropic elasticity tensor (closed form).
+* Per-particle tangent against central differences of the oracle's own
+  stress, elastic, plastic, apex and repeated-eigenvalue states.
+* Return maps: consistency f = 0, flow rule, hardening law.
+* P2G: linear and angular momentum balance of the internal force; gravity
+  sums to the total weight (a transposed dF^-T breaks the angular balance).
+* Global Jacobian against the coloured central-difference Jacobian, and the
+  coloured difference equal, bit for bit, to one-DOF-at-a-time differences
+  (the paper's sparse = dense Jacobian check, Sec. 4.3).
+* Newton converges quadratically (paper Sec. 4.2/4.1 observation).
+* Block compression: exact homogeneous closed form at every load step.
+* Bar under self-weight (paper Sec. 4.2): error against
+  sigma_yy = -rho0 g (l0 - Y) decreases monotonically with refinement and the
+  height tends to the closed-form height.
+"""
+import numpy as np
+import pytest
+
+from paper_2507_09435_gb300 import scenes as S
+
+RNG = np.random.default_rng(20250709)
+
+
+def _mat(model, **kw):
+    base = dict(E=1e6, nu=0.3, phi=30.0, psi=0.0, c=2e3, M=1.2, lambda_cc=0.1, kappa_cc=0.02)
+    base.update(kw)
+    return np.array([base[k] for k in ("E", "nu", "phi", "psi", "c", "M", "lambda_cc", "kappa_cc")])
+
+
+def _lame(E, nu):
+    return E / (2 * (1 + nu)), E * nu / ((1 + nu) * (1 - 2 * nu))
+
+
+# ---------------------------------------------------------------- B-splines
+@pytest.mark.parametrize("dim", [2, 3])
+def test_bspline_reproduction(oracle, dim):
+    n = (10, 9, 8 if dim == 3 else 0)
+    h, o = 0.37, (0.3, -0.2, 0.1)
+    for _ in range(50):
+        xp = np.array([o[a] + h * RNG.uniform(0.5, n[a] - 0.5) if a < dim else 0.0 for a in range(3)])
+        node, w, g = oracle.stencil(dim, n, h, o, xp)
+        assert len(node) == 3 ** dim
+        nx1, ny1 = n[0] + 1, n[1] + 1
+        xi = np.stack([node % nx1, (node // nx1) % ny1, node // (nx1 * ny1)], 1) * h + np.array(o)
+        assert abs(w.sum() - 1) < 1e-14
+        assert np.abs(g.sum(0)).max() < 1e-12
+        assert np.abs((w[:, None] * xi).sum(0)[:dim] - xp[:dim]).max() < 1e-13
+        G = xi[:, :dim].T @ g[:, :dim]
+        assert np.abs(G - np.eye(dim)).max() < 1e-13
+        assert (w >= 0).all()
+
+
+def test_bspline_outside_grid_is_rejected(oracle):
+    with pytest.raises(oracle.OracleError):
+        oracle.stencil(2, (4, 4, 0), 1.0, (0, 0, 0), np.array([0.4, 2.0, 0.0]))
+    with pytest.raises(oracle.OracleError):
+        oracle.stencil(2, (4, 4, 0), 1.0, (0, 0, 0), np.array([2.0, 3.6, 0.0]))
+
+
+# ---------------------------------------------------------------- eigen
+def test_eig_matches_lapack(oracle):
+    cases = []
+    for _ in range(30):
+        a = RNG.standard_normal((3, 3))
+        cases.append(a + a.T)
+    cases.append(np.eye(3))
+    cases.append(np.diag([2.0, 2.0, 1.0]))
+    q, _ = np.linalg.qr(RNG.standard_normal((3, 3)))
+    cases.append(q @ np.diag([1.5, 1.5, 0.7]) @ q.T)
+    cases.append(np.array([[1.0, 1e-9, 0.0], [1e-9, 1.0, 0.0], [0.0, 0.0, 1.0]]))
+    for a in cases:
+        lam, Q = oracle.eig(a)
+        assert np.abs(np.sort(lam) - np.linalg.eigvalsh(a)).max() < 1e-13 * max(1, np.abs(a).max())
+        assert np.abs(Q @ np.diag(lam) @ Q.T - a).max() < 1e-13 * max(1, np.abs(a).max())
+        assert np.abs(Q.T @ Q - np.eye(3)).max() < 1e-14
+
+
+# ---------------------------------------------------------------- G2P patch
+@pytest.mark.parametrize("dim", [2, 3])
+def test_g2p_patch_affine_field(oracle, dim):
+    sc = S.tiny_scene(dim, S.MODEL_NH, seed=1, ncell=2)
+    orc = oracle.OracleScene.from_scene(sc)
+    A = np.zeros((3, 3))
+    A[:dim, :dim] = 1e-3 * RNG.standard_normal((dim, dim))
+    X = sc.node_coords()
+    du = (X @ A.T)[:, :dim].ravel()
+    x0 = orc.x.copy()
+    orc.commit(du)
+    F = orc.F.reshape(-1, 3, 3)
+    assert np.abs(F - (np.eye(3) + A)[None]).max() < 1e-15
+    assert np.abs(orc.x - (x0 + x0 @ A.T)).max() < 1e-15
+
+
+# ---------------------------------------------------------------- tangents
+def test_zero_strain_tangent_is_isotropic_elasticity(oracle):
+    for model in (S.MODEL_NH, S.MODEL_NH_DP, S.MODEL_NH_MCC):
+        p = _mat(model, E=2e6, nu=0.25)
+        o = oracle.particle(model, p, [1, 1, 1, 0, 0, 0], -1e5, np.eye(3), V0=0.5)
+        assert np.abs(o["tau"]).max() < 1e-9
+        mu, lam = _lame(2e6, 0.25)
+        d = np.eye(3)
+        C = 0.5 * (mu * (np.einsum("ab,ce->acbe", d, d) + np.einsum("ae,cb->acbe", d, d))
+                   + lam * np.einsum("ac,be->acbe", d, d))
+        assert np.abs(o["A"] - C).max() < 1e-9 * mu  # C already carries V0 = 0.5
+
+
+def _fd_A(oracle, model, p, be6, pcn, dF, V0, delta=1e-6):
+    A = np.zeros((3, 3, 3, 3))
+    for b in range(3):
+        for e in range(3):
+            dp = dF.copy(); dp[b, e] += delta
+            dm = dF.copy(); dm[b, e] -= delta
+            Pp = oracle.particle(model, p, be6, pcn, dp, V0, tangent=False)["P"]
+            Pm = oracle.particle(model, p, be6, pcn, dm, V0, tangent=False)["P"]
+            A[:, :, b, e] = (Pp - Pm) / (2 * delta)
+    return A
+
+
+def _spd6(scale):
+    a = RNG.standard_normal((3, 3)) * scale
+    s = 0.5 * (a + a.T)
+    w, V = np.linalg.eigh(s)
+    B = V @ np.diag(np.exp(2 * w)) @ V.T
+    return np.array([B[0, 0], B[1, 1], B[2, 2], B[0, 1], B[1, 2], B[0, 2]])
+
+
+TANGENT_CASES = [
+    # (model, params, be6, pcn, dF, expected mode)
+    ("nh_random", S.MODEL_NH, {}, "spd", -1e5, "rand0.05", 0),
+    ("nh_zero", S.MODEL_NH, {}, "eye", -1e5, np.eye(3), 0),
+    ("nh_repeated", S.MODEL_NH, {}, "eye", -1e5, np.diag([1.01, 1.01, 1.0]), 0),
+    ("dp_elastic", S.MODEL_NH_DP, dict(c=2e5), "eye", -1e5, "rand0.01", 0),
+    ("dp_plastic", S.MODEL_NH_DP, {}, "eye", -1e5, "shear", 1),
+    ("dp_plastic_dilatant", S.MODEL_NH_DP, dict(psi=10.0), "eye", -1e5, "shear", 1),
+    ("dp_plastic_repeated", S.MODEL_NH_DP, {}, "eye", -1e5, np.diag([0.97, 1.015, 1.015]), 1),
+    ("dp_plastic_prestrained", S.MODEL_NH_DP, {}, "spd", -1e5, "shear", 1),
+    ("dp_apex", S.MODEL_NH_DP, {}, "eye", -1e5, np.diag([1.02, 1.02, 1.01]), 2),
+    ("mcc_elastic", S.MODEL_NH_MCC, {}, "eye", -1e6, "rand0.001c", 0),
+    ("mcc_compaction", S.MODEL_NH_MCC, {}, "eye", -2e4, "compress", 1),
+    ("mcc_repeated", S.MODEL_NH_MCC, {}, "eye", -2e4, np.diag([0.96, 0.99, 0.99]), 1),
+    ("mcc_prestrained", S.MODEL_NH_MCC, {}, "spd", -2e4, "compress", 1),
+]
+
+
+def _make_dF(spec):
+    if isinstance(spec, np.ndarray):
+        return spec.copy()
+    if spec == "rand0.05":
+        return np.eye(3) + 0.05 * RNG.standard_normal((3, 3))
+    if spec == "rand0.01":
+        return np.eye(3) + 0.01 * RNG.standard_normal((3, 3))
+    if spec == "rand0.001c":
+        return np.eye(3) * 0.999 + 0.001 * RNG.standard_normal((3, 3))
+    if spec == "shear":
+        return np.eye(3) + np.array([[0.01, 0.04, 0], [0.01, -0.02, 0.0], [0, 0.005, 0.0]]) \
+            + 0.003 * RNG.standard_normal((3, 3))
+    if spec == "compress":
+        return np.eye(3) * 0.97 + np.array([[0, 0.03, 0], [0.0, -0.01, 0.0], [0, 0, 0]]) \
+            + 0.003 * RNG.standard_normal((3, 3))
+    raise ValueError(spec)
+
+
+@pytest.mark.parametrize("case", TANGENT_CASES, ids=[c[0] for c in TANGENT_CASES])
+def test_particle_tangent_matches_central_differences(oracle, case):
+    _, model, kw, be_spec, pcn, dF_spec, mode = case
+    p = _mat(model, **kw)
+    be6 = np.array([1, 1, 1, 0, 0, 0.0]) if be_spec == "eye" else _spd6(0.01)
+    dF = _make_dF(dF_spec)
+    o = oracle.particle(model, p, be6, pcn, dF, V0=0.3)
+    assert o["mode"] == mode
+    Afd = _fd_A(oracle, model, p, be6, pcn, dF, 0.3)
+    scale = np.abs(o["A"]).max()
+    assert np.abs(o["A"] - Afd).max() < 2e-7 * scale
+
+
+# ---------------------------------------------------------------- return maps
+def test_dp_return_consistency_and_flow(oracle):
+    for psi in (0.0, 8.0):
+        p = _mat(S.MODEL_NH_DP, psi=psi)
+        mu, lam = _lame(p[0], p[1])
+        tp, ts = np.tan(np.radians(30.0)), np.tan(np.radians(psi))
+        eta, xi = 3 * tp / np.sqrt(9 + 12 * tp ** 2), 3 / np.sqrt(9 + 12 * tp ** 2)
+        etab = 3 * ts / np.sqrt(9 + 12 * ts ** 2)
+        for _ in range(20):
+            etr = RNG.standard_normal(3) * 0.02 - 0.01
+            eps, pc, mode, _, dg = oracle.return_map(S.MODEL_NH_DP, p, etr)
+            tau = mu * (np.exp(2 * eps) - 1) + lam * eps.sum()
+            pr = tau.mean()
+            s = tau - pr
+            rJ2 = np.sqrt(0.5 * (s ** 2).sum())
+            f = rJ2 + eta * pr - xi * 2e3
+            if mode == 0:
+                assert f <= 1e-9 * mu and np.array_equal(eps, etr)
+            elif mode == 1:
+                assert abs(f) < 1e-9 * 2e3
+                assert dg > 0
+                flow = s / (2 * rJ2) + etab / 3
+                assert np.abs((etr - eps) - dg * flow).max() < 1e-13
+                if psi == 0.0:
+                    assert abs(eps.sum() - etr.sum()) < 1e-15
+            else:
+                assert np.abs(tau - xi * 2e3 / eta).max() < 1e-8 * 2e3
+
+
+def test_mcc_return_consistency_flow_and_hardening(oracle):
+    p = _mat(S.MODEL_NH_MCC)
+    mu, lam = _lame(p[0], p[1])
+    M, lmk = 1.2, 0.08
+    nplastic = 0
+    for _ in range(30):
+        pcn = -2e4 * np.exp(0.2 * RNG.standard_normal())
+        etr = RNG.standard_normal(3) * 0.01 - 0.01
+        eps, pc, mode, _, dg = oracle.return_map(S.MODEL_NH_MCC, p, etr, pcn)
+        tau = mu * (np.exp(2 * eps) - 1) + lam * eps.sum()
+        pr = tau.mean()
+        s = tau - pr
+        q2 = 1.5 * (s ** 2).sum()
+        f = q2 / M ** 2 + pr * (pr - pc)
+        if mode == 0:
+            assert f <= 0 and pc == pcn
+        else:
+            nplastic += 1
+            assert abs(f) < 1e-9 * pcn ** 2
+            assert abs(pc - pcn * np.exp(-(etr - eps).sum() / lmk)) < 1e-12 * abs(pcn)
+            flow = 3 * s / M ** 2 + (2 * pr - pc) / 3
+            assert np.abs((etr - eps) - dg * flow).max() < 1e-13
+    assert nplastic > 5
+
+
+# ---------------------------------------------------------------- P2G balances
+@pytest.mark.parametrize("dim,model", [(2, S.MODEL_NH), (2, S.MODEL_NH_DP), (3, S.MODEL_NH_MCC)])
+def test_internal_force_momentum_balance(oracle, dim, model):
+    sc = S.tiny_scene(dim, model, seed=3, ncell=3)
+    orc = oracle.OracleScene.from_scene(sc)
+    du = S.random_increment(sc, 0.01, seed=4)
+    orc.gravity = np.zeros(3)
+    r, M = orc.residual(du)
+    f = r.reshape(-1, dim)
+    scale = np.abs(f).max()
+    assert np.abs(f.sum(0)).max() < 1e-12 * scale * len(f)
+    y = sc.node_coords()[:, :dim] + du.reshape(-1, dim)
+    if dim == 2:
+        mom = (y[:, 0] * f[:, 1] - y[:, 1] * f[:, 0]).sum()
+        assert abs(mom) < 1e-12 * scale * np.abs(y).max() * len(f)
+    else:
+        mom = np.cross(y, f).sum(0)
+        assert np.abs(mom).max() < 1e-12 * scale * np.abs(y).max() * len(f)
+    g = np.array([0.3, -9.81, 1.2])
+    orc.gravity = g
+    r2, M2 = orc.residual(du)
+    fg = (r2 - r).reshape(-1, dim).sum(0)
+    assert np.allclose(-fg, sc.mass.sum() * g[:dim], rtol=1e-13)
+    assert abs(M2.sum() - sc.mass.sum()) < 1e-13 * sc.mass.sum()
+
+
+# ---------------------------------------------------------------- global Jacobian
+JAC_CASES = [(2, S.MODEL_NH, 0.02), (2, S.MODEL_NH_DP, 0.03), (3, S.MODEL_NH_MCC, 0.01)]
+
+
+@pytest.mark.parametrize("dim,model,amp", JAC_CASES)
+def test_jacobian_matches_colored_central_differences(oracle, dim, model, amp):
+    sc = S.tiny_scene(dim, model, seed=7, ncell=3 if dim == 2 else 2)
+    orc = oracle.OracleScene.from_scene(sc)
+    orc.gravity = np.array([0.0, -9.81, 0.0])
+    du = S.random_increment(sc, amp, seed=8)
+    r, M, modes = orc.residual(du, with_mode=True)
+    if model != S.MODEL_NH:
+        assert (modes > 0).sum() >= 4, "case should drive particles plastic"
+    J = orc.jacobian(du).toarray()
+    Jfd = oracle.fd_jacobian_colored(orc, du, eps=1e-6 * sc.h)
+    act = orc.active_dofs(M)
+    Ja, Jf = J[np.ix_(act, act)], Jfd[np.ix_(act, act)]
+    assert np.abs(Ja - Jf).max() < 1e-6 * np.abs(Ja).max()
+    assert np.abs(J[~act]).max() == 0 and np.abs(J[:, ~act]).max() == 0
+
+
+def test_colored_fd_equals_plain_fd_bitwise(oracle):
+    sc = S.tiny_scene(2, S.MODEL_NH_DP, seed=9, ncell=3)
+    orc = oracle.OracleScene.from_scene(sc)
+    du = S.random_increment(sc, 0.02, seed=10)
+    eps = 1e-6 * sc.h
+    Jc = oracle.fd_jacobian_colored(orc, du, eps)
+    _, M = orc.residual(du)
+    act = np.nonzero(orc.active_dofs(M))[0]
+    cols = act[:: max(1, len(act) // 12)]
+    Jp = oracle.fd_jacobian_plain(orc, du, eps, cols)
+    for k, j in enumerate(cols):
+        nz = Jc[:, j] != 0
+        assert np.array_equal(Jc[nz, j], Jp[nz, k])
+        assert np.abs(Jp[~nz, k]).max() == 0.0
+
+
+# ---------------------------------------------------------------- Newton and closed forms
+def test_block_compression_homogeneous_closed_form_and_quadratic_newton(oracle):
+    sc = S.block_compression()
+    orc = oracle.OracleScene.from_scene(sc)
+    mu, lam = _lame(1e6, 0.3)
+    for k, st in enumerate(sc.steps):
+        out = orc.solve_step(st.dof, st.value, st.gravity, tol=1e-12)
+        assert out["converged"] and out["iters"] <= 4
+        h = out["hist"]
+        for a, b in zip(h[1:-1], h[2:]):
+            assert b <= 50 * a * a + 1e-13
+        l2 = (1 - sc.meta["strain_per_step"]) ** (k + 1)
+        l1 = 1.0
+        for _ in range(50):
+            g = mu * (l1 * l1 - 1) + lam * np.log(l1 * l2)
+            l1 -= g / (2 * mu * l1 + lam / l1)
+        F = orc.F.reshape(-1, 3, 3)
+        assert np.abs(F - np.diag([l1, l2, 1.0])[None]).max() < 1e-11
+        tau, _ = orc.stresses()
+        assert np.abs(tau[:, 0, 0]).max() < 1e-9 * mu
+        J = l1 * l2
+        assert np.abs(tau[:, 1, 1] - (mu * (l2 * l2 - 1) + lam * np.log(J))).max() < 1e-9 * mu
+
+
+def test_self_weight_bar_converges_to_closed_form(oracle):
+    """Paper Sec. 4.2: sigma_yy(Y) = -rho0 g (l0 - Y) for the bar under
+    self-weight; error metric of the paper (volume-weighted |sigma_yy -
+    sigma_a| over rho0 g l0).  With quadratic B-splines and fixed ghost nodes
+    at the base the error has a first-order boundary layer, so the pin is
+    monotone decrease at a rate of at least 0.6 per halving, plus convergence
+    of the bar height to the closed-form height."""
+    rho0, g, l0, mu = 80.0, 9.81, 50.0, 5e3
+    Yq = np.linspace(0, l0, 20001)
+    q = rho0 * g * (l0 - Yq)
+    lam_q = (-q + np.sqrt(q * q + 4 * mu * mu)) / (2 * mu)
+    H = np.trapezoid(lam_q, Yq)
+    errs, herr = [], []
+    for nc in (4, 8, 16, 32):
+        sc = S.self_weight_column(nc)
+        orc = oracle.OracleScene.from_scene(sc)
+        Y = sc.x[:, 1] - sc.meta["y_base"]
+        for st in sc.steps:
+            out = orc.solve_step(st.dof, st.value, st.gravity, tol=1e-11)
+            assert out["converged"] and out["iters"] <= 6
+        tau, _ = orc.stresses()
+        J = np.linalg.det(orc.F.reshape(-1, 3, 3))
+        sig = tau[:, 1, 1] / J
+        sa = -rho0 * g * (l0 - Y)
+        errs.append(np.sum(np.abs(sig - sa) * orc.V0) / (g * rho0 * l0 * orc.V0.sum()))
+        top = orc.x[:, 1].max() - sc.meta["y_base"] + 0.25 * sc.h * lam_q[-1]
+        herr.append(abs(top - H) / H)
+    errs = np.array(errs)
+    assert (np.diff(errs) < 0).all()
+    assert (np.log2(errs[:-1] / errs[1:]) > 0.6).all()
+    assert errs[-1] < 0.04
+    assert herr[-1] < 0.06 and herr[-1] < herr[0]
