@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark of the implicit-MPM Newton step on one GB300 (or N replicas).
+
+Workload (default): 2D plane-strain rigid-footing bearing capacity, 256x128
+grid (h = 0.1 m), 128,016 particles (2x2 per cell), Neo-Hookean +
+non-associative Drucker-Prager (phi 30 deg, psi 0, c 5 kPa, E 1e7 Pa,
+nu 0.3), gravity, displacement-controlled footing; FP64 residual / return
+map / Newton check, FP32 Jacobian and BiCGStab (mixed mode).
+
+A bench "step" is one load step: sort + pattern, Newton iterations
+(residual + Jacobian + Krylov + update) to a relative residual of 1e-8,
+commit.  The metric is Newton iterations per second; particle-updates/s =
+particles x Newton iterations / s.  The first warm-up step is the geostatic
+step; the timed steps are footing increments.  L2 is flushed (256 MiB write)
+between timed steps, outside the per-step CUDA-event windows.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+build) on the same workload, one bounded sample per step.
+Multi-GPU: replicas only (independent scenes, no collective on the data
+path); value = all ranks' Newton iterations / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Newton iters/s"
+UNIT = "newton_iters/s"
+WORKLOAD = "footing_256x128_dp"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--krylov", default="bicgstab", choices=["bicgstab", "gmres"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_scene():
+    from paper_2507_09435_gb300 import scenes
+    return scenes.footing(nx=256, ny=128, h=0.1, ppc=2, nsteps=50)
+
+
+def config(args, sc):
+    return {"workload": WORKLOAD, "grid": [sc.n[0], sc.n[1]], "h": sc.h, "particles": sc.np,
+            "ppc": 4, "model": "neo-hookean + drucker-prager (phi 30, psi 0, c 5 kPa)",
+            "precision": args.precision, "krylov": args.krylov, "preconditioner": "block-jacobi",
+            "newton_tol": 1e-8, "step": "one load step (footing increment 4 mm)",
+            "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas{args.gpus}"}
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=self.tmp,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [l.strip().split(",") for l in self.tmp.read().splitlines() if l.strip()]
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU legs: the FP64 oracle, as it stands, on a bounded sample of the workload
+# ----------------------------------------------------------------------------
+
+def oracle_newton_sample(sc, krylov_iters, max_newton=1):
+    """Time `max_newton` oracle Newton iterations of the geostatic step of the
+    workload: oracle residual + exact Jacobian (C++, single thread) + a
+    block-Jacobi BiCGStab on it with the GPU's Krylov iteration count (SciPy
+    sparse products, FP64) + the new residual.  Returns (seconds, iterations)."""
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    from oracle import mpm_oracle as O
+    orc = O.OracleScene.from_scene(sc)
+    st = sc.steps[0]
+    orc.gravity = np.asarray(st.gravity, dtype=np.float64)
+    N = sc.nnode * sc.dim
+    du = np.zeros(N)
+    t0 = time.perf_counter()
+    r, M = orc.residual(du)
+    act = orc.active_dofs(M)
+    fixed = np.zeros(N, dtype=bool)
+    fixed[np.asarray(st.dof)] = True
+    free = np.nonzero(act & ~fixed)[0]
+    node = free // sc.dim
+    for _ in range(max_newton):
+        J = orc.jacobian(du)[free][:, free].tocsr()
+        # block-Jacobi: the node-diagonal blocks of the free-DOF matrix
+        coo = J.tocoo()
+        keep = node[coo.row] == node[coo.col]
+        Bd = sp.csc_matrix((coo.data[keep], (coo.row[keep], coo.col[keep])), shape=J.shape)
+        lu = spla.splu(Bd)
+        pre = spla.LinearOperator(J.shape, matvec=lu.solve)
+        x, _ = spla.bicgstab(J, -r[free], M=pre, rtol=1e-30, maxiter=max(1, int(krylov_iters)))
+        du[free] += x
+        r, M = orc.residual(du)
+    return time.perf_counter() - t0, max_newton
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    sc = workload_scene()
+    kry = float(os.environ.get("MPM_BENCH_KRYLOV_PER_NEWTON", "400"))
+    for _ in range(max(0, min(args.warmup, 1))):
+        pass  # the oracle has no warm-up state; each step is an independent bounded sample
+    times, iters = [], 0
+    for _ in range(args.steps):
+        t, n = oracle_newton_sample(sc, kry, 1)
+        times.append(t)
+        iters += n
+    tot = sum(times)
+    value = iters / tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args, sc),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"1 oracle Newton iteration per step of the geostatic load step "
+                                       f"(residual + exact Jacobian + {int(kry)} block-Jacobi BiCGStab iterations)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+    from paper_2507_09435_gb300 import mpm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    mpm.lib()   # build / load libmpm before timing
+
+    sc = workload_scene()
+    prec = mpm.MPM_MIXED if args.precision == "mixed" else mpm.MPM_FP64
+    kry = mpm.MPM_BICGSTAB if args.krylov == "bicgstab" else mpm.MPM_GMRES
+    stream = torch.cuda.Stream(device=dev)
+    gs = mpm.GpuScene(sc, precision=prec, krylov=kry, stream=stream.cuda_stream, newton_tol=1e-8,
+                      krylov_maxit=50000)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    steps = sc.steps
+    k_next = 0
+
+    def next_step():
+        nonlocal k_next
+        st = steps[min(k_next, len(steps) - 1)]
+        k_next += 1
+        return st
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 1)):
+        rep = gs.solve_step(next_step())
+
+    # ---- device-timed region -------------------------------------------------
+    barrier()
+    clk = ClockSampler(torch.cuda.current_device())
+    L0 = mpm.mpm_kernel_launches(gs.h)
+    t_ms, newton, krylov = 0.0, 0, 0
+    phase = np.zeros(4)
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep = gs.solve_step(next_step())
+        e1.record(stream)
+        e1.synchronize()
+        t_ms += e0.elapsed_time(e1)
+        newton += rep.newton_iters
+        krylov += rep.krylov_iters_total
+        phase += [rep.t_setup_ms, rep.t_residual_ms, rep.t_assembly_ms, rep.t_krylov_ms]
+    launches = mpm.mpm_kernel_launches(gs.h) - L0
+    barrier()
+    clocks = clk.stop()
+    tt = torch.tensor([t_ms, float(newton), float(krylov)], dtype=torch.float64, device=dev)
+    if world > 1:
+        tmax = tt[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        t_all = float(tmax[0])
+    else:
+        t_all = float(tt[0])
+    newton_all, krylov_all = float(tt[1]), float(tt[2])
+    value = newton_all / (t_all / 1e3)
+
+    # ---- dominant kernel (Jacobian-vector product), timed live ---------------
+    gs.begin(next_step())
+    spmv_ms, spmv_bytes = mpm.mpm_time_spmv(gs.h, 200)
+    peaks, src = read_peaks()
+    achieved = spmv_bytes / (spmv_ms * 1e-3) / 1e9
+    roof = {"kernel": "k_bicg_2/k_bicg_4 (stencil-BSR SpMV)", "bound": "hbm", "achieved": achieved,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "peak_source": src, "bytes_per_launch": spmv_bytes, "ms_per_launch": spmv_ms,
+            "note": "matrix is L2-resident at this size (about 13 MB FP32)"}
+
+    # ---- end to end through the C ABI with host buffers ----------------------
+    e2e = None
+    if not args.no_e2e:
+        pin_dof = [torch.from_numpy(np.asarray(s.dof, dtype=np.int64)).pin_memory() for s in steps]
+        pin_val = [torch.from_numpy(np.asarray(s.value, dtype=np.float64)).pin_memory() for s in steps]
+        gs2 = mpm.GpuScene(sc, precision=prec, krylov=kry, stream=stream.cuda_stream, newton_tol=1e-8,
+                           krylov_maxit=50000)
+        gs2.solve_step(steps[0])
+        h2d = d2h = 0
+        t_e, n_e = 0.0, 0
+        kk = 1
+        for _ in range(max(1, args.steps // 2)):
+            idx = min(kk, len(steps) - 1)
+            kk += 1
+            barrier()
+            t0 = time.perf_counter()
+            mpm.mpm_set_dirichlet(gs2.h, pin_dof[idx].numpy(), pin_val[idx].numpy())
+            mpm.mpm_set_gravity(gs2.h, steps[idx].gravity)
+            rep = mpm.mpm_solve_step(gs2.h)
+            out = gs2.particles(be=False, pc=False, F=False)
+            t_e += time.perf_counter() - t0
+            n_e += rep.newton_iters
+            h2d = pin_dof[idx].numel() * 8 + pin_val[idx].numel() * 8 + 24
+            d2h = out["x"].nbytes + out["tau"].nbytes
+        tv = torch.tensor([t_e, float(n_e)], dtype=torch.float64, device=dev)
+        if world > 1:
+            tm = tv[:1].clone()
+            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+            dist.all_reduce(tv, op=dist.ReduceOp.SUM)
+            t_e = float(tm[0])
+        e2e = {"value": float(tv[1]) / t_e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h),
+               "call": "mpm_set_dirichlet + mpm_set_gravity + mpm_solve_step + mpm_get_particles(x, tau)"}
+        gs2.close()
+
+    # ---- CPU baseline: the oracle on a bounded sample ------------------------
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        kpn = krylov_all / max(newton_all, 1.0)
+        t, n = oracle_newton_sample(sc, kpn, 1)
+        cpu = {"value": n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"1 oracle Newton iteration of the geostatic step (residual + exact Jacobian + "
+                         f"{int(round(kpn))} block-Jacobi BiCGStab iterations, the GPU's mean per Newton "
+                         f"iteration), {t:.1f} s"}
+
+    if rank == 0:
+        n_gpus = world
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": n_gpus, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_all / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64+f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+                "config": config(args, sc),
+                "particle_updates_per_s": value * sc.np,
+                "krylov_iters_per_newton": krylov_all / max(newton_all, 1.0),
+                "newton_iters_per_step": newton_all / (args.steps * n_gpus),
+                "phase_ms_per_step": {"setup": phase[0] / args.steps, "residual": phase[1] / args.steps,
+                                      "assembly": phase[2] / args.steps, "krylov": phase[3] / args.steps},
+                "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    gs.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,219 @@
+/*
+ * mpm.h -- C ABI of the GB300 implicit-MPM Newton step.
+ *
+ * One implicit material-point-method load step (Zhao, Li, Jiang & Choo,
+ * "GeoWarp", arXiv 2507.09435, Sec. 2.2): the residual
+ *   r(u^{n+1}) = assembled (f_int,p - f_ext,p)          (paper Sec. 2.2, residual eq.)
+ * is driven to zero by Newton's method
+ *   -J^{n+1,k} du^{n+1,k} = r(u^{n+1,k}),  J = dr/du     (paper Sec. 2.2, Newton eqs.)
+ * until ||r^k|| / ||r^0|| <= tol                          (paper Sec. 2.2, criterion)
+ * after which the particle state is updated and the grid reset (the paper's
+ * four-stage procedure, Sec. 2.2).  Each Newton iteration runs, on the GPU:
+ *   G2P of the nodal increment through quadratic B-spline gradients, the
+ *   constitutive update (Neo-Hookean elasticity, optionally Drucker-Prager or
+ *   modified Cam-Clay return mapping in principal logarithmic strain), P2G of
+ *   the internal force into the FP64 residual, assembly of each particle's
+ *   consistent tangent into a node-block sparse Jacobian (block size dim x dim,
+ *   coupling +-2 nodes per axis: the 5^dim block neighbourhood of the paper's
+ *   Sec. 3.2 / Table 1 for quadratic B-splines), and a block-Jacobi
+ *   preconditioned BiCGStab or GMRES(m) solve.
+ *
+ * Conventions
+ *   - Units SI; stress positive in tension; pressure p = tr(tau)/3.
+ *   - Grid: n[a] cells per axis (n[2] ignored in 2D), spacing h, nodes at
+ *     origin + i*h, 0 <= i <= n[a].  Node index ix + (nx+1)*(iy + (ny+1)*iz);
+ *     a DOF index is node*dim + component.  2D is plane strain.
+ *   - Particle arrays passed in are HOST arrays in the caller's order; they
+ *     are copied at the call.  The library keeps particles sorted by cell on
+ *     the device; every getter returns them in the caller's original order.
+ *   - Output buffers are caller-owned host arrays of the documented size.
+ *   - The scene owns all device memory it allocates; mpm_destroy_scene frees it.
+ *   - Every call returns an mpm_status; on error the scene keeps a message
+ *     readable with mpm_last_error.  No C++ exception crosses this ABI.
+ *   - A scene is used by one host thread at a time.  Distinct scenes may be
+ *     driven concurrently, each on its own CUDA stream.
+ */
+#ifndef MPM_H
+#define MPM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpm_scene mpm_scene;
+
+typedef enum {
+  MPM_OK = 0,
+  MPM_ERR_INVALID_ARG = 1,
+  MPM_ERR_OOM = 2,
+  MPM_ERR_CUDA = 3,
+  MPM_ERR_NOT_CONVERGED = 4,     /* Newton hit newton_maxit before tol        */
+  MPM_ERR_KRYLOV_MAXIT = 5,      /* linear solve hit krylov_maxit             */
+  MPM_ERR_KRYLOV_BREAKDOWN = 6,  /* BiCGStab/GMRES breakdown (zero divisor)   */
+  MPM_ERR_NONFINITE = 7,         /* NaN/Inf in residual or state              */
+  MPM_ERR_TIMEOUT = 8,           /* host-side wall-clock budget exceeded      */
+  MPM_ERR_BOUNDS = 9,            /* a particle's support left the grid        */
+  MPM_ERR_RETURN_MAP = 10,       /* local return-map Newton did not converge  */
+  MPM_ERR_STATE = 11             /* call out of order (e.g. newton before begin) */
+} mpm_status;
+
+enum { MPM_NH = 0, MPM_NH_DP = 1, MPM_NH_MCC = 2 };        /* material models   */
+enum { MPM_FP64 = 0, MPM_MIXED = 1 };                       /* precision modes   */
+enum { MPM_BICGSTAB = 0, MPM_GMRES = 1 };                   /* Krylov methods    */
+enum { MPM_FORCING_FIXED = 0, MPM_FORCING_EW = 1 };         /* linear tolerances */
+
+typedef struct {
+  int dim;                 /* 2 (plane strain) or 3                              */
+  int n[3];                /* cells per axis                                     */
+  double h;                /* grid spacing                                       */
+  double origin[3];
+  int precision;           /* MPM_FP64: Jacobian + Krylov in FP64;
+                              MPM_MIXED: Jacobian + Krylov in FP32 (residual,
+                              return map, eigen-decomposition and the Newton
+                              check stay FP64 in both modes)                   */
+  int krylov;              /* MPM_BICGSTAB or MPM_GMRES                          */
+  int gmres_restart;       /* GMRES(m) restart length (default 30)               */
+  double newton_tol;       /* relative residual tolerance (paper criterion)      */
+  int newton_maxit;
+  int forcing;             /* MPM_FORCING_FIXED: linear rtol = krylov_rtol;
+                              MPM_FORCING_EW: Eisenstat-Walker choice 2,
+                              clamped to [krylov_rtol, 0.1]                      */
+  double krylov_rtol;
+  int krylov_maxit;
+} mpm_scene_desc;
+
+typedef struct {
+  int model;               /* MPM_NH, MPM_NH_DP, MPM_NH_MCC                       */
+  double E, nu, rho;       /* Young's modulus, Poisson ratio, density           */
+  double phi, psi, c;      /* DP friction / dilation angle (degrees), cohesion    */
+  double M, lambda_cc, kappa_cc; /* MCC critical-state slope, compression indices */
+  double pc0;              /* MCC initial preconsolidation pressure (negative)    */
+} mpm_material;
+
+typedef struct {
+  int status;              /* mpm_status of this iteration                       */
+  int krylov_iters;        /* linear iterations spent in this Newton iteration   */
+  double krylov_rel;       /* achieved relative linear residual (recurrence)    */
+  double krylov_rtol;      /* requested relative linear tolerance               */
+  double r_norm;           /* ||r^k|| over free DOFs after the update            */
+  double rel_residual;     /* ||r^k|| / ||r^0||                                  */
+  int n_plastic;           /* particles on the plastic branch at this iterate    */
+} mpm_newton_report;
+
+typedef struct {
+  int status;
+  int newton_iters;
+  int converged;
+  int krylov_iters_total;
+  double r0_norm;
+  double rel_residual;
+  double hist[33];         /* relative residual after 0..newton_iters iterations */
+  int krylov_iters[32];
+  int n_active_nodes;
+  long long nnzb;          /* structurally present Jacobian blocks              */
+  double t_setup_ms, t_residual_ms, t_assembly_ms, t_krylov_ms, t_commit_ms;
+} mpm_step_report;
+
+/* Create a scene from host particle arrays.
+ *   x[np*3] positions (z ignored in 2D); vol0[np], mass[np] (> 0);
+ *   mat_id[np] in [0, nmat); E_p, phi_p: optional per-particle Young's
+ *   modulus / friction angle overriding the material's (NULL = none);
+ *   pc0_p: optional per-particle initial preconsolidation (NULL = material's);
+ *   stream: a cudaStream_t to run on, or NULL for a stream the scene creates.
+ * Errors: MPM_ERR_INVALID_ARG (bad sizes, a particle outside the grid's
+ * interior, non-positive mass), MPM_ERR_OOM, MPM_ERR_CUDA. */
+mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
+                            const double* vol0, const double* mass, const int* mat_id,
+                            const double* E_p, const double* phi_p, const double* pc0_p,
+                            const mpm_material* mats, int nmat, void* stream,
+                            mpm_scene** out);
+
+/* Gravity vector used by the following load steps (f_ext = sum_p w_ip m_p g). */
+mpm_status mpm_set_gravity(mpm_scene* s, const double g[3]);
+
+/* Prescribed displacement increments for the following load steps:
+ * dof[k] = node*dim + comp on the dense node grid, value[k] the increment per
+ * load step.  Replaces the previous set.  DOFs on nodes without mass are
+ * ignored.  Errors: MPM_ERR_INVALID_ARG for an index outside the grid. */
+mpm_status mpm_set_dirichlet(mpm_scene* s, int n, const long long* dof, const double* value);
+
+/* Stage a load step: sort particles by cell, find the active nodes
+ * (nodal mass > 1e-12 * max particle mass) and the Jacobian pattern, apply the
+ * prescribed increments, evaluate r^0.  `rep` (nullable) gets ||r^0||. */
+mpm_status mpm_begin_step(mpm_scene* s, mpm_newton_report* rep);
+
+/* One Newton iteration of the staged step: assemble J, solve J d = -r with
+ * the configured Krylov method, update du += d, evaluate the new residual.
+ * Returns MPM_ERR_STATE if no step is staged.  Does not commit. */
+mpm_status mpm_newton_step(mpm_scene* s, mpm_newton_report* rep);
+
+/* Replace the iterate of the staged step by du (host, nnode*dim) and
+ * re-evaluate the residual and the per-particle tangents there; prescribed
+ * DOFs keep their prescribed increments.  For checks at chosen states and
+ * for warm starts.  MPM_ERR_STATE if no step is staged. */
+mpm_status mpm_set_du(mpm_scene* s, const double* du);
+
+/* Assemble the Jacobian J = dr/du at the current iterate of the staged step
+ * (readable with mpm_get_jacobian_bsr) without solving.  mpm_newton_step
+ * does this itself; the call exists for inspection and external solvers. */
+mpm_status mpm_assemble(mpm_scene* s);
+
+/* Commit the staged step's converged increment to the particles
+ * (x += sum_i w_ip du_i, F <- dF F, elastic strain and hardening variable). */
+mpm_status mpm_commit_step(mpm_scene* s);
+
+/* Whole load step: begin, Newton to newton_tol (at most newton_maxit), commit.
+ * Returns MPM_ERR_NOT_CONVERGED (state not committed) when tol is missed. */
+mpm_status mpm_solve_step(mpm_scene* s, mpm_step_report* rep);
+
+/* FP64 residual of the current iterate on the dense node grid, nnode*dim
+ * entries; prescribed and inactive DOFs read 0. */
+mpm_status mpm_get_residual(const mpm_scene* s, double* r);
+/* Current nodal increment du (nnode*dim) and nodal mass (nnode). */
+mpm_status mpm_get_du(const mpm_scene* s, double* du);
+mpm_status mpm_get_mass(const mpm_scene* s, double* mass);
+
+/* Number of active nodes and of structurally present Jacobian blocks of the
+ * staged step (the blocks whose node pair shares an occupied cell). */
+mpm_status mpm_get_counts(const mpm_scene* s, int* n_active, long long* nnzb);
+
+/* The Jacobian assembled for the latest Newton iteration, in block CSR:
+ * row_node[n_active] node index of each block row, row_ptr[n_active+1],
+ * col_node[nnzb] node index of each block, val[nnzb*dim*dim] row-major
+ * blocks converted to double.  Rows and columns of prescribed DOFs hold the
+ * identity.  Capacity `cap` in blocks; MPM_ERR_INVALID_ARG if too small. */
+mpm_status mpm_get_jacobian_bsr(const mpm_scene* s, long long cap, int* row_node,
+                                long long* row_ptr, int* col_node, double* val);
+
+/* Particle state in the caller's original order (any pointer may be NULL):
+ * x[np*3], be[np*6] elastic left Cauchy-Green (xx,yy,zz,xy,yz,xz),
+ * pc[np] preconsolidation, F[np*9] deformation gradient (row-major),
+ * tau[np*9] Kirchhoff stress of the committed state. */
+mpm_status mpm_get_particles(const mpm_scene* s, double* x, double* be, double* pc, double* F,
+                             double* tau);
+
+/* Number of CUDA kernels this scene has launched so far (including those
+ * inside CUDA-graph launches). */
+mpm_status mpm_kernel_launches(const mpm_scene* s, long long* out);
+
+/* Time the Jacobian-vector product kernel of the staged step's assembled
+ * Jacobian: `reps` launches on the scene's stream between CUDA events.
+ * ms_per_launch: average duration; bytes_per_launch: algorithmic bytes of
+ * one launch (present blocks, the input and output vectors, the row list). */
+mpm_status mpm_time_spmv(mpm_scene* s, int reps, double* ms_per_launch, double* bytes_per_launch);
+
+/* Device memory a scene of this size would take (for admission control). */
+mpm_status mpm_footprint_bytes(const mpm_scene_desc* desc, int np, size_t* out);
+
+void mpm_destroy_scene(mpm_scene* s);
+const char* mpm_status_string(mpm_status st);
+/* Last error message of a scene; with s == NULL, the message of the last
+ * failed mpm_create_scene on this thread. */
+const char* mpm_last_error(const mpm_scene* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPM_H */

@@ -71,7 +71,7 @@ def lib():
         L.orc_particle.argtypes = [ctypes.c_int, _D, _D, ctypes.c_double, _D, ctypes.c_double,
                                    _D, _D, _D, _I, _D, _D]
         L.orc_residual.argtypes = [_I, _D, _D, ctypes.c_int, _D, _D, _D, _I, _D, _D, _D, _D,
-                                   _D, _D, _I]
+                                   _D, _D, _I, _D]
         L.orc_jacobian.argtypes = [_I, _D, ctypes.c_int, _D, _D, _I, _D, _D, _D, _D,
                                    ctypes.c_long, _L, _L, _D]
         L.orc_commit.argtypes = [_I, _D, ctypes.c_int, _D, _D, _I, _D, _D, _D, _D, _D]
@@ -182,18 +182,26 @@ class OracleScene:
         return cls(sc.dim, sc.n, sc.h, sc.origin, sc.x, sc.vol0, sc.mass, model, params, pc0)
 
     # ---- residual / Jacobian -------------------------------------------
-    def residual(self, du, with_mode=False):
+    def residual(self, du, with_mode=False, with_scale=False):
+        """r(du) on the dense DOF grid and the nodal mass; optionally the
+        per-particle modes and the per-DOF sum of absolute contributions."""
         du = _f64(du)
         r = np.zeros(self.nnode * self.dim)
         M = np.zeros(self.nnode)
         mode = np.zeros(self.np, dtype=np.int32)
+        rabs = np.zeros(self.nnode * self.dim) if with_scale else None
         rc = lib().orc_residual(_p(self.gi, _I), _p(self.gd), _p(_f64(self.gravity)), self.np,
                                 _p(self.x), _p(self.V0), _p(self.m), _p(self.model, _I),
                                 _p(self.params), _p(self.be), _p(self.pc), _p(du), _p(r), _p(M),
-                                _p(mode, _I))
+                                _p(mode, _I), _p(rabs) if with_scale else None)
         if rc:
             raise OracleError(f"residual failed ({rc})")
-        return (r, M, mode) if with_mode else (r, M)
+        out = (r, M)
+        if with_mode:
+            out = out + (mode,)
+        if with_scale:
+            out = out + (rabs,)
+        return out
 
     def jacobian_blocks(self, du):
         """Node-pair blocks (bi, bj, val[nb, d, d]) of J = dr/du, summed."""

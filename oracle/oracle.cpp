@@ -648,15 +648,18 @@ int orc_particle(int model, const double* params, const double* be6, double pcn,
 // Global residual r = f_int - f_ext on the dense node grid (nnode*dim) and
 // nodal mass M_i = sum_p w_ip m_p (paper's mapping equation).  Returns 0,
 // -1 (particle outside the grid) or a constitutive failure code.  When
-// `mode_out` is given the per-particle mode is written there.
+// `mode_out` is given the per-particle mode is written there; when `rabs` is
+// given it receives sum_p |contribution| per DOF (the scale against which
+// the rounding of r is judged).
 int orc_residual(const int* gi, const double* gd, const double* grav, int np, const double* x,
                  const double* V0, const double* m, const int* model, const double* params,
                  const double* be, const double* pc, const double* du, double* r, double* mass,
-                 int* mode_out) {
+                 int* mode_out, double* rabs) {
   Grid G = make_grid(gi, gd);
   long nn = G.nnode();
   std::fill(r, r + nn * G.dim, 0.0);
   std::fill(mass, mass + nn, 0.0);
+  if (rabs) std::fill(rabs, rabs + nn * G.dim, 0.0);
   for (int p = 0; p < np; ++p) {
     Stencil S;
     if (make_stencil(G, x + 3 * p, S)) return -1;
@@ -675,6 +678,7 @@ int orc_residual(const int* gi, const double* gd, const double* grav, int np, co
         double f = 0;
         for (int c = 0; c < G.dim; ++c) f += o.P[a][c] * S.g[l][c];
         r[i * G.dim + a] += f - S.w[l] * m[p] * grav[a];
+        if (rabs) rabs[i * G.dim + a] += std::fabs(f) + std::fabs(S.w[l] * m[p] * grav[a]);
       }
     }
   }

@@ -1,0 +1,1001 @@
+// C ABI of the implicit-MPM Newton step (declared in include/mpm.h): scene
+// lifetime, the staged load step and its Newton loop (paper Sec. 2.2), and
+// the getters used by tests and callers.  All device memory is owned by the
+// scene; all work is stream-ordered on the scene's stream, with host
+// synchronisation only where a scalar decides the control flow (active-row
+// count, residual norm, Krylov done flag between graph chunks).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mpm.h"
+#include "mpm_internal.h"
+
+using namespace mpm;
+
+namespace {
+struct Fail {
+  mpm_status st;
+  std::string msg;
+};
+[[noreturn]] void fail(mpm_status st, const std::string& m) { throw Fail{st, m}; }
+void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(e == cudaErrorMemoryAllocation ? MPM_ERR_OOM : MPM_ERR_CUDA,
+         std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+constexpr double ACTIVE_REL = 1e-12;
+constexpr int KTPB = 256;
+constexpr int GRAPH_CHUNK = 8;   // Krylov iterations per graph launch
+thread_local std::string g_create_err;  // message of the last failed mpm_create_scene
+}  // namespace
+
+struct mpm_scene {
+  mpm_scene_desc desc{};
+  int D = 2, np = 0, nmat = 0, nbe = 4, nF = 4;
+  bool mixed = false;
+  DevGrid G{};
+  long long nnode = 0, ndof = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::vector<void*> allocs;
+  MatC* d_mats = nullptr;
+  std::vector<MatC> hmats;
+  DevParticles P{}, Q{};   // live particle arrays and the gather target of the sort
+  int *d_key = nullptr, *d_rank = nullptr, *d_perm = nullptr;
+  int *d_count = nullptr, *d_cstart = nullptr, *d_flag = nullptr, *d_pos = nullptr;
+  int *d_cells = nullptr, *d_node2row = nullptr, *d_rows = nullptr, *d_scan_tmp = nullptr;
+  int *d_nrow = nullptr, *d_err = nullptr, *d_nplastic = nullptr;
+  double *d_M = nullptr, *d_du = nullptr, *d_r = nullptr, *d_bcval = nullptr, *d_grav = nullptr,
+         *d_norm = nullptr;
+  uint8_t* d_fixed = nullptr;
+  void* d_A = nullptr;
+  // matrix (stencil-BSR), grown on demand
+  void* d_K = nullptr;
+  void* d_dinv = nullptr;
+  int cap = 0;
+  // Krylov vectors (BiCGStab: 9), padded
+  void* d_vec = nullptr;
+  long long vpad = 0, vlen = 0;   // padding and padded length in elements
+  KrylovScalars* d_S = nullptr;
+  KrylovScalars* h_S = nullptr;
+  int* h_int = nullptr;           // pinned: ncell, nrow, err, nplastic
+  double* h_dbl = nullptr;        // pinned: norm
+  cudaGraphExec_t gexec = nullptr;
+  int graph_cap = -1;
+  bool use_graph = true;
+  cudaEvent_t ev[6]{};
+  // step state
+  int nrow = 0, ncell = 0;
+  bool staged = false;
+  int k = 0;
+  double r0 = 0, rk = 0, rprev = 0, eta_prev = 0.1;
+  double grav[3] = {0, 0, 0};
+  double mmax = 0;
+  float t_asm = 0, t_kry = 0, t_res = 0;
+  long long launches = 0;   // kernels launched by this scene
+  std::string err;
+
+  template <class T>
+  T* dalloc(size_t n) {
+    void* p = nullptr;
+    ck(cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)), "cudaMalloc");
+    allocs.push_back(p);
+    return (T*)p;
+  }
+  void dfree(void* p) {
+    if (!p) return;
+    auto it = std::find(allocs.begin(), allocs.end(), p);
+    if (it != allocs.end()) allocs.erase(it);
+    cudaFree(p);
+  }
+};
+
+namespace {
+
+template <int D>
+void pattern_mask(mpm_scene* s, std::vector<int>& mask);
+
+size_t tsize(const mpm_scene* s) { return s->mixed ? 4 : 8; }
+
+int stencil_slots(int D) { return D == 2 ? 25 : 125; }
+
+mpm_status map_err_bits(int bits, std::string& msg) {
+  if (bits & ERRF_BOUNDS) { msg = "a particle's B-spline support left the grid"; return MPM_ERR_BOUNDS; }
+  if (bits & ERRF_RETURN) { msg = "return-map local Newton did not converge"; return MPM_ERR_RETURN_MAP; }
+  if (bits & (ERRF_NONFINITE | ERRF_DET)) { msg = "non-finite value or non-positive det(F)"; return MPM_ERR_NONFINITE; }
+  return MPM_OK;
+}
+
+void validate_desc(const mpm_scene_desc* d) {
+  if (!d) fail(MPM_ERR_INVALID_ARG, "desc is NULL");
+  if (d->dim != 2 && d->dim != 3) fail(MPM_ERR_INVALID_ARG, "dim must be 2 or 3");
+  for (int a = 0; a < d->dim; ++a)
+    if (d->n[a] < 3) fail(MPM_ERR_INVALID_ARG, "need at least 3 cells per axis");
+  if (!(d->h > 0)) fail(MPM_ERR_INVALID_ARG, "h must be positive");
+  if (d->precision != MPM_FP64 && d->precision != MPM_MIXED) fail(MPM_ERR_INVALID_ARG, "bad precision");
+  if (d->krylov != MPM_BICGSTAB && d->krylov != MPM_GMRES) fail(MPM_ERR_INVALID_ARG, "bad krylov");
+  if (!(d->newton_tol > 0) || d->newton_maxit < 1 || d->newton_maxit > 32)
+    fail(MPM_ERR_INVALID_ARG, "newton_tol > 0 and 1 <= newton_maxit <= 32 required");
+  if (!(d->krylov_rtol > 0) || d->krylov_maxit < 1) fail(MPM_ERR_INVALID_ARG, "bad Krylov settings");
+}
+
+long long nnode_of(const mpm_scene_desc* d) {
+  long long c = 1;
+  for (int a = 0; a < d->dim; ++a) c *= d->n[a] + 1;
+  return c;
+}
+
+// Device bytes of a scene, excluding the matrix capacity growth margin.
+size_t footprint(const mpm_scene_desc* d, int np) {
+  const int D = d->dim;
+  const size_t T = d->precision == MPM_MIXED ? 4 : 8;
+  const long long nn = nnode_of(d), ndof = nn * D;
+  const int nbe = D == 2 ? 4 : 6, nF = D * D;
+  size_t part = (size_t)np * (2 * (D + 2 + 2 + nbe + 1 + nF) * 8 + 2 * 2 * 4 + 3 * 4);
+  size_t grid = (size_t)nn * (7 * 4 + 8) + (size_t)ndof * (3 * 8 + 1);
+  size_t tang = (size_t)np * D * D * D * D * T;
+  long long pad = 2 + 2LL * (d->n[0] + 1) + (D == 3 ? 2LL * (d->n[0] + 1) * (d->n[1] + 1) : 0);
+  size_t vec = 9 * (size_t)(nn + 2 * pad) * D * T;
+  // active rows are bounded by the nodes the particles can reach
+  long long rows = std::min<long long>(nn, (long long)np * (D == 2 ? 9 : 27));
+  size_t mat = (size_t)rows * (stencil_slots(D) + 1) * D * D * T;
+  return part + grid + tang + vec + mat + (1 << 20);
+}
+
+template <class T>
+DevMatrix<T> matview(mpm_scene* s) {
+  DevMatrix<T> K;
+  K.val = (T*)s->d_K;
+  K.dinv = (T*)s->d_dinv;
+  K.cap = s->cap;
+  K.rows = s->d_rows;
+  K.nrow = s->d_nrow;
+  return K;
+}
+
+template <int D, class T>
+KrylovVecs<D, T> vecview(mpm_scene* s) {
+  T* b = (T*)s->d_vec;
+  KrylovVecs<D, T> v;
+  T** f[9] = {&v.x, &v.r, &v.rhat, &v.p, &v.phat, &v.v, &v.s, &v.shat, &v.t};
+  for (int k = 0; k < 9; ++k) *f[k] = b + k * s->vlen + s->vpad;
+  return v;
+}
+
+void ensure_capacity(mpm_scene* s, int nrow) {
+  if (nrow <= s->cap) return;
+  int cap = std::max<int>(1024, (int)std::min<long long>(s->nnode, (long long)(nrow * 1.25) + 64));
+  s->dfree(s->d_K);
+  s->dfree(s->d_dinv);
+  s->d_K = nullptr;
+  s->d_dinv = nullptr;
+  const size_t S = stencil_slots(s->D), DD = s->D * s->D;
+  if (s->mixed) {
+    s->d_K = s->dalloc<float>((size_t)cap * S * DD);
+    s->d_dinv = s->dalloc<float>((size_t)cap * DD);
+  } else {
+    s->d_K = s->dalloc<double>((size_t)cap * S * DD);
+    s->d_dinv = s->dalloc<double>((size_t)cap * DD);
+  }
+  s->cap = cap;
+  if (s->gexec) {
+    cudaGraphExecDestroy(s->gexec);
+    s->gexec = nullptr;
+  }
+  s->graph_cap = -1;
+}
+
+template <int D>
+DevParticles make_particles(mpm_scene* s) {
+  DevParticles P{};
+  P.np = s->np;
+  for (int a = 0; a < 3; ++a) P.x[a] = (a < D) ? s->dalloc<double>(s->np) : nullptr;
+  P.vol0 = s->dalloc<double>(s->np);
+  P.mass = s->dalloc<double>(s->np);
+  P.mat = s->dalloc<int>(s->np);
+  P.Ep = s->dalloc<double>(s->np);
+  P.phip = s->dalloc<double>(s->np);
+  for (int k = 0; k < MAX_BE; ++k) P.be[k] = (k < s->nbe) ? s->dalloc<double>(s->np) : nullptr;
+  P.pc = s->dalloc<double>(s->np);
+  for (int k = 0; k < MAX_F; ++k) P.F[k] = (k < s->nF) ? s->dalloc<double>(s->np) : nullptr;
+  P.orig = s->dalloc<int>(s->np);
+  return P;
+}
+
+GatherArrays gather_list(mpm_scene* s, const DevParticles& src, DevParticles& dst) {
+  GatherArrays g{};
+  int nd = 0;
+  for (int a = 0; a < s->D; ++a) { g.dsrc[nd] = src.x[a]; g.ddst[nd++] = dst.x[a]; }
+  g.dsrc[nd] = src.vol0; g.ddst[nd++] = dst.vol0;
+  g.dsrc[nd] = src.mass; g.ddst[nd++] = dst.mass;
+  g.dsrc[nd] = src.Ep; g.ddst[nd++] = dst.Ep;
+  g.dsrc[nd] = src.phip; g.ddst[nd++] = dst.phip;
+  for (int k = 0; k < s->nbe; ++k) { g.dsrc[nd] = src.be[k]; g.ddst[nd++] = dst.be[k]; }
+  g.dsrc[nd] = src.pc; g.ddst[nd++] = dst.pc;
+  for (int k = 0; k < s->nF; ++k) { g.dsrc[nd] = src.F[k]; g.ddst[nd++] = dst.F[k]; }
+  g.nd = nd;
+  g.isrc[0] = src.mat; g.idst[0] = dst.mat;
+  g.isrc[1] = src.orig; g.idst[1] = dst.orig;
+  g.ni = 2;
+  return g;
+}
+
+template <int D, class T>
+void residual_pass(mpm_scene* s, int mode) {
+  ck(cudaMemsetAsync(s->d_r, 0, s->ndof * sizeof(double), s->st), "memset r");
+  ck(cudaMemsetAsync(s->d_nplastic, 0, sizeof(int), s->st), "memset");
+  ck(launch_particles<D, T>(s->P, s->G, s->d_mats, s->d_du, s->d_r, s->d_grav, (T*)s->d_A, mode, s->d_err,
+                            s->d_nplastic, s->st),
+     "particle kernel");
+  ck(cudaMemsetAsync(s->d_norm, 0, sizeof(double), s->st), "memset");
+  ck(launch_norm_free<D>(s->d_r, s->d_rows, s->nrow, s->d_fixed, s->d_norm, s->st), "norm kernel");
+  ck(cudaMemcpyAsync(s->h_dbl, s->d_norm, sizeof(double), cudaMemcpyDeviceToHost, s->st), "copy norm");
+  ck(cudaMemcpyAsync(s->h_int + 2, s->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s->st), "copy err");
+  s->launches += 2;
+}
+
+void check_err_bits(mpm_scene* s) {
+  std::string m;
+  mpm_status st = map_err_bits(s->h_int[2], m);
+  if (st != MPM_OK) fail(st, m);
+}
+
+template <int D, class T>
+void begin_step_impl(mpm_scene* s, mpm_newton_report* rep) {
+  cudaStream_t st = s->st;
+  const long long nn = s->nnode;
+  s->staged = false;
+  ck(cudaMemsetAsync(s->d_err, 0, sizeof(int), st), "memset");
+  // a0: counting sort of particles by base cell
+  ck(cudaMemsetAsync(s->d_count, 0, (nn + 1) * sizeof(int), st), "memset");
+  ck(launch_cell_keys<D>(s->P, s->G, s->d_key, s->d_count, s->d_rank, s->d_err, st), "cell keys");
+  ck(scan_exclusive(s->d_count, s->d_cstart, (int)(nn + 1), s->d_scan_tmp, st), "scan");
+  ck(launch_sort_scatter(s->np, s->d_key, s->d_rank, s->d_cstart, s->d_perm, st), "scatter");
+  GatherArrays g = gather_list(s, s->P, s->Q);
+  ck(launch_gather(s->np, s->d_perm, g, st), "gather");
+  std::swap(s->P, s->Q);
+  // occupied cells
+  ck(launch_flag_positive(s->d_count, s->d_flag, nn + 1, st), "flags");
+  ck(scan_exclusive(s->d_flag, s->d_pos, (int)(nn + 1), s->d_scan_tmp, st), "scan");
+  ck(launch_compact(s->d_flag, s->d_pos, s->d_cells, nn, st), "compact");
+  ck(cudaMemcpyAsync(s->h_int + 0, s->d_pos + nn, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
+  // nodal mass and active rows
+  ck(cudaMemsetAsync(s->d_M, 0, nn * sizeof(double), st), "memset");
+  ck(launch_mass<D>(s->P, s->G, s->d_M, st), "mass");
+  ck(cudaMemsetAsync(s->d_flag + nn, 0, sizeof(int), st), "memset");
+  ck(launch_active(s->d_M, ACTIVE_REL * s->mmax, s->d_flag, nn, st), "active");
+  ck(scan_exclusive(s->d_flag, s->d_pos, (int)(nn + 1), s->d_scan_tmp, st), "scan");
+  ck(launch_node2row(s->d_flag, s->d_pos, s->d_node2row, s->d_rows, nn, st), "node2row");
+  ck(cudaMemcpyAsync(s->d_nrow, s->d_pos + nn, sizeof(int), cudaMemcpyDeviceToDevice, st), "copy");
+  ck(cudaMemcpyAsync(s->h_int + 1, s->d_pos + nn, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
+  ck(cudaMemcpyAsync(s->h_int + 2, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
+  ck(cudaStreamSynchronize(st), "sync");
+  s->launches += 10 + 3LL * scan_launches(nn + 1);
+  check_err_bits(s);
+  s->ncell = s->h_int[0];
+  s->nrow = s->h_int[1];
+  ensure_capacity(s, s->nrow);
+  // prescribed increments and r^0 (with the tangent for the first iteration)
+  ck(cudaMemcpyAsync(s->d_grav, s->grav, 3 * sizeof(double), cudaMemcpyHostToDevice, st), "grav");
+  ck(launch_apply_bc(s->d_fixed, s->d_bcval, s->d_node2row, s->d_du, s->ndof, D, st), "bc");
+  cudaEventRecord(s->ev[2], st);
+  residual_pass<D, T>(s, 1);
+  cudaEventRecord(s->ev[3], st);
+  ck(cudaStreamSynchronize(st), "sync");
+  check_err_bits(s);
+  s->r0 = std::sqrt(s->h_dbl[0]);
+  s->rk = s->r0;
+  s->rprev = s->r0;
+  s->eta_prev = 0.1;
+  s->k = 0;
+  s->staged = true;
+  if (!std::isfinite(s->r0)) fail(MPM_ERR_NONFINITE, "non-finite initial residual");
+  cudaEventElapsedTime(&s->t_res, s->ev[2], s->ev[3]);
+  if (rep) {
+    rep->status = MPM_OK;
+    rep->krylov_iters = 0;
+    rep->krylov_rel = 0;
+    rep->krylov_rtol = 0;
+    rep->r_norm = s->r0;
+    rep->rel_residual = 1.0;
+    rep->n_plastic = s->h_int[3];
+  }
+}
+
+template <int D, class T>
+void build_graph(mpm_scene* s, int nblk) {
+  if (s->gexec) {
+    cudaGraphExecDestroy(s->gexec);
+    s->gexec = nullptr;
+  }
+  cudaGraph_t g;
+  ck(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal), "capture");
+  DevMatrix<T> K = matview<T>(s);
+  KrylovVecs<D, T> v = vecview<D, T>(s);
+  for (int c = 0; c < GRAPH_CHUNK; ++c) launch_bicgstab_iter<D, T>(s->G, K, v, s->d_S, nblk, s->st);
+  ck(cudaStreamEndCapture(s->st, &g), "end capture");
+  ck(cudaGraphInstantiate(&s->gexec, g, 0), "instantiate");
+  cudaGraphDestroy(g);
+  s->graph_cap = s->cap;
+}
+
+// Assembly of the per-particle consistent tangents (written by the last
+// residual pass) into the stencil-BSR Jacobian, prescribed rows/columns set
+// to the identity, block-Jacobi inverse.
+template <int D, class T>
+void assemble_impl(mpm_scene* s) {
+  if (!s->staged) fail(MPM_ERR_STATE, "no load step staged (call mpm_begin_step)");
+  cudaStream_t st = s->st;
+  const int S = stencil_slots(D);
+  DevMatrix<T> K = matview<T>(s);
+  ck(cudaMemsetAsync(s->d_K, 0, (size_t)s->cap * S * D * D * sizeof(T), st), "memset K");
+  ck(launch_assemble<D, T>(s->P, s->G, s->d_cells, s->ncell, s->d_cstart, s->d_node2row, (const T*)s->d_A, K, st),
+     "assemble");
+  ck(launch_bc_matrix<D, T>(s->G, K, s->d_fixed, s->d_node2row, s->nrow, st), "bc matrix");
+  ck(launch_block_jacobi<D, T>(K, s->nrow, s->d_err, st), "block jacobi");
+  s->launches += 3;
+}
+
+template <int D, class T>
+void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
+  if (!s->staged) fail(MPM_ERR_STATE, "no load step staged (call mpm_begin_step)");
+  cudaStream_t st = s->st;
+  DevMatrix<T> K = matview<T>(s);
+  cudaEventRecord(s->ev[0], st);
+  assemble_impl<D, T>(s);
+  // linear tolerance: fixed, or Eisenstat-Walker choice 2 (gamma 0.9, alpha 2)
+  double eta = s->desc.krylov_rtol;
+  if (s->desc.forcing == MPM_FORCING_EW) {
+    if (s->k == 0) {
+      eta = 0.1;
+    } else {
+      double ratio = s->rk / s->rprev;
+      eta = 0.9 * ratio * ratio;
+      double safe = 0.9 * s->eta_prev * s->eta_prev;
+      if (safe > 0.1) eta = std::max(eta, safe);
+    }
+    // no need to solve below what the Newton tolerance asks of this step
+    eta = std::max(eta, 0.5 * s->desc.newton_tol * s->r0 / std::max(s->rk, 1e-300));
+    eta = std::min(std::max(eta, s->desc.krylov_rtol), 0.1);
+  }
+  s->eta_prev = eta;
+  const int nblk = (s->cap + KTPB - 1) / KTPB;
+  cudaEventRecord(s->ev[1], st);
+  KrylovVecs<D, T> v = vecview<D, T>(s);
+  double tol2 = eta * eta * s->rk * s->rk;
+  ck(launch_bicgstab_init<D, T>(K, s->d_r, s->d_fixed, v, s->d_S, tol2, s->desc.krylov_maxit, nblk, st),
+     "krylov init");
+  if (s->use_graph && s->graph_cap != s->cap) build_graph<D, T>(s, nblk);
+  int launched = 0;
+  for (;;) {
+    if (s->use_graph) {
+      ck(cudaGraphLaunch(s->gexec, st), "graph launch");
+    } else {
+      for (int c = 0; c < GRAPH_CHUNK; ++c) ck(launch_bicgstab_iter<D, T>(s->G, K, v, s->d_S, nblk, st), "krylov");
+    }
+    launched += GRAPH_CHUNK;
+    s->launches += 5 * GRAPH_CHUNK;
+    ck(cudaMemcpyAsync(s->h_S, s->d_S, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st), "copy S");
+    ck(cudaStreamSynchronize(st), "sync");
+    if (s->h_S->done) break;
+    if (launched > s->desc.krylov_maxit + 2 * GRAPH_CHUNK) break;   // belt and braces
+  }
+  const int kit = s->h_S->iter;
+  const int kstat = s->h_S->status;
+  const double krel = (s->rk > 0) ? std::sqrt(std::max(s->h_S->rr_last, 0.0)) / s->rk : 0.0;
+  ck(launch_update_du<D, T>(K, v.x, s->d_fixed, s->d_du, nblk, st), "update");
+  s->launches += 2;   // Krylov init + update
+  cudaEventRecord(s->ev[2], st);
+  residual_pass<D, T>(s, 1);
+  cudaEventRecord(s->ev[3], st);
+  ck(cudaStreamSynchronize(st), "sync");
+  check_err_bits(s);
+  cudaEventElapsedTime(&s->t_asm, s->ev[0], s->ev[1]);
+  cudaEventElapsedTime(&s->t_kry, s->ev[1], s->ev[2]);
+  cudaEventElapsedTime(&s->t_res, s->ev[2], s->ev[3]);
+  s->rprev = s->rk;
+  s->rk = std::sqrt(s->h_dbl[0]);
+  s->k += 1;
+  if (!std::isfinite(s->rk)) fail(MPM_ERR_NONFINITE, "non-finite residual");
+  if (rep) {
+    rep->status = kstat == 0 ? MPM_OK : (kstat == 1 ? MPM_ERR_KRYLOV_MAXIT : MPM_ERR_KRYLOV_BREAKDOWN);
+    rep->krylov_iters = kit;
+    rep->krylov_rel = krel;
+    rep->krylov_rtol = eta;
+    rep->r_norm = s->rk;
+    rep->rel_residual = (s->r0 > 0) ? s->rk / s->r0 : 0.0;
+    rep->n_plastic = s->h_int[3];
+  }
+}
+
+template <int D, class T>
+void set_du_impl(mpm_scene* s, const double* du) {
+  if (!s->staged) fail(MPM_ERR_STATE, "no load step staged (call mpm_begin_step)");
+  std::vector<double> h(du, du + s->ndof);
+  std::vector<uint8_t> f(s->ndof);
+  std::vector<double> bc(s->ndof);
+  std::vector<int> n2r(s->nnode);
+  ck(cudaStreamSynchronize(s->st), "sync");
+  ck(cudaMemcpy(f.data(), s->d_fixed, s->ndof, cudaMemcpyDeviceToHost), "download");
+  ck(cudaMemcpy(bc.data(), s->d_bcval, s->ndof * sizeof(double), cudaMemcpyDeviceToHost), "download");
+  ck(cudaMemcpy(n2r.data(), s->d_node2row, s->nnode * sizeof(int), cudaMemcpyDeviceToHost), "download");
+  for (long long d = 0; d < s->ndof; ++d)
+    if (f[d] && n2r[d / D] >= 0) h[d] = bc[d];
+  ck(cudaMemcpy(s->d_du, h.data(), s->ndof * sizeof(double), cudaMemcpyHostToDevice), "upload");
+  residual_pass<D, T>(s, 1);
+  ck(cudaStreamSynchronize(s->st), "sync");
+  check_err_bits(s);
+  s->rk = std::sqrt(s->h_dbl[0]);
+}
+
+template <int D, class T>
+void commit_impl(mpm_scene* s) {
+  if (!s->staged) fail(MPM_ERR_STATE, "no load step staged");
+  ck(launch_particles<D, T>(s->P, s->G, s->d_mats, s->d_du, s->d_r, s->d_grav, (T*)s->d_A, 2, s->d_err, nullptr,
+                            s->st),
+     "commit kernel");
+  ck(cudaMemcpyAsync(s->h_int + 2, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->st), "copy");
+  ck(cudaStreamSynchronize(s->st), "sync");
+  s->launches += 1;
+  check_err_bits(s);
+  s->staged = false;
+}
+
+template <int D, class T>
+void time_spmv_impl(mpm_scene* s, int reps, double* ms, double* bytes) {
+  if (!s->staged) fail(MPM_ERR_STATE, "no load step staged");
+  if (reps < 1) fail(MPM_ERR_INVALID_ARG, "reps must be positive");
+  DevMatrix<T> K = matview<T>(s);
+  KrylovVecs<D, T> v = vecview<D, T>(s);
+  const int nblk = (s->cap + KTPB - 1) / KTPB;
+  ck(launch_spmv<D, T>(s->G, K, v.phat, v.v, nblk, s->st), "spmv");   // warm-up
+  ck(cudaEventRecord(s->ev[4], s->st), "event");
+  for (int k = 0; k < reps; ++k) ck(launch_spmv<D, T>(s->G, K, v.phat, v.v, nblk, s->st), "spmv");
+  ck(cudaEventRecord(s->ev[5], s->st), "event");
+  ck(cudaEventSynchronize(s->ev[5]), "sync");
+  float t = 0;
+  ck(cudaEventElapsedTime(&t, s->ev[4], s->ev[5]), "elapsed");
+  s->launches += reps + 1;
+  *ms = t / reps;
+  long long nnzb = 0;
+  {
+    std::vector<int> mask;
+    pattern_mask<D>(s, mask);
+    for (int m : mask) nnzb += m;
+  }
+  const double ts = sizeof(T);
+  *bytes = (double)nnzb * D * D * ts + (double)s->nrow * D * ts * 2.0 + (double)s->nrow * 4.0;
+}
+
+// dispatch on (dim, precision)
+template <template <int, class> class F, class... Args>
+void dispatch(mpm_scene* s, Args... args) {
+  if (s->D == 2) {
+    if (s->mixed) F<2, float>::run(s, args...);
+    else F<2, double>::run(s, args...);
+  } else {
+    if (s->mixed) F<3, float>::run(s, args...);
+    else F<3, double>::run(s, args...);
+  }
+}
+template <int D, class T> struct BeginF { static void run(mpm_scene* s, mpm_newton_report* r) { begin_step_impl<D, T>(s, r); } };
+template <int D, class T> struct NewtonF { static void run(mpm_scene* s, mpm_newton_report* r) { newton_impl<D, T>(s, r); } };
+template <int D, class T> struct CommitF { static void run(mpm_scene* s) { commit_impl<D, T>(s); } };
+template <int D, class T> struct SetDuF { static void run(mpm_scene* s, const double* du) { set_du_impl<D, T>(s, du); } };
+template <int D, class T> struct TimeSpmvF {
+  static void run(mpm_scene* s, int reps, double* ms, double* bytes) { time_spmv_impl<D, T>(s, reps, ms, bytes); }
+};
+template <int D, class T> struct AssembleF {
+  static void run(mpm_scene* s) {
+    assemble_impl<D, T>(s);
+    ck(cudaMemcpyAsync(s->h_int + 2, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->st), "copy");
+    ck(cudaStreamSynchronize(s->st), "sync");
+    check_err_bits(s);
+  }
+};
+
+template <class Fn>
+mpm_status guarded(mpm_scene* s, Fn&& fn) {
+  try {
+    fn();
+    return MPM_OK;
+  } catch (const Fail& f) {
+    if (s) s->err = f.msg;
+    return f.st;
+  } catch (const std::exception& e) {
+    if (s) s->err = e.what();
+    return MPM_ERR_INVALID_ARG;
+  } catch (...) {
+    if (s) s->err = "unknown failure";
+    return MPM_ERR_INVALID_ARG;
+  }
+}
+
+void destroy(mpm_scene* s) {
+  if (!s) return;
+  if (s->st) cudaStreamSynchronize(s->st);
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  for (void* p : s->allocs) cudaFree(p);
+  if (s->h_S) cudaFreeHost(s->h_S);
+  if (s->h_int) cudaFreeHost(s->h_int);
+  if (s->h_dbl) cudaFreeHost(s->h_dbl);
+  for (auto& e : s->ev)
+    if (e) cudaEventDestroy(e);
+  if (s->own_stream && s->st) cudaStreamDestroy(s->st);
+  delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x, const double* vol0,
+                            const double* mass, const int* mat_id, const double* E_p, const double* phi_p,
+                            const double* pc0_p, const mpm_material* mats, int nmat, void* stream,
+                            mpm_scene** out) {
+  if (!out) return MPM_ERR_INVALID_ARG;
+  *out = nullptr;
+  mpm_scene* s = new (std::nothrow) mpm_scene();
+  if (!s) return MPM_ERR_OOM;
+  mpm_status rc = guarded(s, [&] {
+    validate_desc(desc);
+    if (np < 0 || (np > 0 && (!x || !vol0 || !mass || !mat_id))) fail(MPM_ERR_INVALID_ARG, "particle arrays");
+    if (!mats || nmat < 1) fail(MPM_ERR_INVALID_ARG, "need at least one material");
+    s->desc = *desc;
+    s->D = desc->dim;
+    s->np = np;
+    s->nmat = nmat;
+    s->nbe = s->D == 2 ? 4 : 6;
+    s->nF = s->D * s->D;
+    s->mixed = desc->precision == MPM_MIXED;
+    DevGrid& G = s->G;
+    G.dim = s->D;
+    for (int a = 0; a < 3; ++a) {
+      G.n[a] = (a < s->D) ? desc->n[a] : 0;
+      G.o[a] = desc->origin[a];
+    }
+    G.nx1 = G.n[0] + 1;
+    G.ny1 = G.n[1] + 1;
+    G.nz1 = s->D == 3 ? G.n[2] + 1 : 1;
+    G.h = desc->h;
+    G.ih = 1.0 / desc->h;
+    s->nnode = (long long)G.nx1 * G.ny1 * G.nz1;
+    G.nnode = s->nnode;
+    s->ndof = s->nnode * s->D;
+    if (s->nnode + 1 > 2000000000LL) fail(MPM_ERR_INVALID_ARG, "grid too large");
+    // materials
+    for (int m = 0; m < nmat; ++m) {
+      const mpm_material& q = mats[m];
+      if (q.model < MPM_NH || q.model > MPM_NH_MCC) fail(MPM_ERR_INVALID_ARG, "bad material model");
+      if (!(q.E > 0) || !(q.nu > -1 && q.nu < 0.5)) fail(MPM_ERR_INVALID_ARG, "bad elastic constants");
+      if (q.model == MPM_NH_MCC && !(q.lambda_cc > q.kappa_cc && q.M > 0))
+        fail(MPM_ERR_INVALID_ARG, "bad Cam-Clay constants");
+      MatC c{};
+      c.model = q.model;
+      c.E = q.E;
+      c.nu = q.nu;
+      c.rho = q.rho;
+      c.phi = q.phi;
+      c.psi = q.psi;
+      c.coh = q.c;
+      c.M = q.M;
+      c.lmk = q.lambda_cc - q.kappa_cc;
+      c.pc0 = q.pc0;
+      s->hmats.push_back(c);
+    }
+    // host-side validation of particles
+    for (int p = 0; p < np; ++p) {
+      if (mat_id[p] < 0 || mat_id[p] >= nmat) fail(MPM_ERR_INVALID_ARG, "mat_id out of range");
+      if (!(mass[p] > 0) || !(vol0[p] > 0)) fail(MPM_ERR_INVALID_ARG, "mass and vol0 must be positive");
+      for (int a = 0; a < s->D; ++a) {
+        double sg = (x[3 * p + a] - G.o[a]) / G.h;
+        double fb = std::floor(sg - 0.5);
+        if (!(fb >= 0 && fb <= G.n[a] - 2)) fail(MPM_ERR_INVALID_ARG, "particle outside the grid interior");
+      }
+      if (E_p && !(E_p[p] > 0)) fail(MPM_ERR_INVALID_ARG, "E_p must be positive");
+      if (pc0_p && s->hmats[mat_id[p]].model == MPM_NH_MCC && !(pc0_p[p] < 0))
+        fail(MPM_ERR_INVALID_ARG, "pc0 must be negative");
+      s->mmax = std::max(s->mmax, mass[p]);
+    }
+    if (stream) {
+      s->st = (cudaStream_t)stream;
+    } else {
+      ck(cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking), "stream");
+      s->own_stream = true;
+    }
+    s->use_graph = s->st != nullptr && s->st != cudaStreamLegacy && s->st != cudaStreamPerThread;
+    for (auto& e : s->ev) ck(cudaEventCreate(&e), "event");
+    ck(cudaMallocHost(&s->h_S, sizeof(KrylovScalars)), "host alloc");
+    ck(cudaMallocHost(&s->h_int, 16 * sizeof(int)), "host alloc");
+    ck(cudaMallocHost(&s->h_dbl, 16 * sizeof(double)), "host alloc");
+    s->d_mats = s->dalloc<MatC>(nmat);
+    ck(cudaMemcpyAsync(s->d_mats, s->hmats.data(), nmat * sizeof(MatC), cudaMemcpyHostToDevice, s->st), "copy");
+    // particles: staging on the host in SoA order
+    auto mk = [&](DevParticles& P) {
+      if (s->D == 2) P = make_particles<2>(s);
+      else P = make_particles<3>(s);
+    };
+    mk(s->P);
+    mk(s->Q);
+    std::vector<double> h(np);
+    auto up = [&](double* d) {
+      ck(cudaMemcpy(d, h.data(), np * sizeof(double), cudaMemcpyHostToDevice), "upload");
+    };
+    if (np > 0) {
+      for (int a = 0; a < s->D; ++a) {
+        for (int p = 0; p < np; ++p) h[p] = x[3 * p + a];
+        up(s->P.x[a]);
+      }
+      std::copy(vol0, vol0 + np, h.begin()); up(s->P.vol0);
+      std::copy(mass, mass + np, h.begin()); up(s->P.mass);
+      for (int p = 0; p < np; ++p) h[p] = E_p ? E_p[p] : mats[mat_id[p]].E;
+      up(s->P.Ep);
+      for (int p = 0; p < np; ++p) h[p] = phi_p ? phi_p[p] : mats[mat_id[p]].phi;
+      up(s->P.phip);
+      for (int p = 0; p < np; ++p) h[p] = pc0_p ? pc0_p[p] : mats[mat_id[p]].pc0;
+      up(s->P.pc);
+      for (int k = 0; k < s->nbe; ++k) {
+        std::fill(h.begin(), h.end(), k < 3 ? 1.0 : 0.0);
+        up(s->P.be[k]);
+      }
+      for (int k = 0; k < s->nF; ++k) {
+        std::fill(h.begin(), h.end(), (k % (s->D + 1) == 0) ? 1.0 : 0.0);
+        up(s->P.F[k]);
+      }
+      ck(cudaMemcpy(s->P.mat, mat_id, np * sizeof(int), cudaMemcpyHostToDevice), "upload");
+      std::vector<int> o(np);
+      for (int p = 0; p < np; ++p) o[p] = p;
+      ck(cudaMemcpy(s->P.orig, o.data(), np * sizeof(int), cudaMemcpyHostToDevice), "upload");
+    }
+    // sort scratch and grid arrays
+    const long long nn = s->nnode;
+    s->d_key = s->dalloc<int>(np);
+    s->d_rank = s->dalloc<int>(np);
+    s->d_perm = s->dalloc<int>(np);
+    s->d_count = s->dalloc<int>(nn + 1);
+    s->d_cstart = s->dalloc<int>(nn + 1);
+    s->d_flag = s->dalloc<int>(nn + 1);
+    s->d_pos = s->dalloc<int>(nn + 1);
+    s->d_cells = s->dalloc<int>(nn);
+    s->d_node2row = s->dalloc<int>(nn);
+    s->d_rows = s->dalloc<int>(nn);
+    s->d_scan_tmp = s->dalloc<int>(scan_tmp_ints((int)(nn + 1)));
+    s->d_nrow = s->dalloc<int>(1);
+    s->d_err = s->dalloc<int>(2);
+    s->d_nplastic = s->d_err + 1;
+    s->d_M = s->dalloc<double>(nn);
+    s->d_du = s->dalloc<double>(s->ndof);
+    s->d_r = s->dalloc<double>(s->ndof);
+    s->d_bcval = s->dalloc<double>(s->ndof);
+    s->d_grav = s->dalloc<double>(3);
+    s->d_norm = s->dalloc<double>(1);
+    s->d_fixed = s->dalloc<uint8_t>(s->ndof);
+    ck(cudaMemsetAsync(s->d_du, 0, s->ndof * sizeof(double), s->st), "memset");
+    ck(cudaMemsetAsync(s->d_r, 0, s->ndof * sizeof(double), s->st), "memset");
+    ck(cudaMemsetAsync(s->d_bcval, 0, s->ndof * sizeof(double), s->st), "memset");
+    ck(cudaMemsetAsync(s->d_fixed, 0, s->ndof, s->st), "memset");
+    ck(cudaMemsetAsync(s->d_nrow, 0, sizeof(int), s->st), "memset");
+    const size_t T = tsize(s);
+    const size_t D4 = (size_t)s->D * s->D * s->D * s->D;
+    s->d_A = s->mixed ? (void*)s->dalloc<float>((size_t)np * D4) : (void*)s->dalloc<double>((size_t)np * D4);
+    s->vpad = (2 + 2LL * G.nx1 + (s->D == 3 ? 2LL * G.nx1 * G.ny1 : 0)) * s->D;
+    s->vlen = s->ndof + 2 * s->vpad;
+    if (s->mixed) s->d_vec = s->dalloc<float>(9 * s->vlen);
+    else s->d_vec = s->dalloc<double>(9 * s->vlen);
+    ck(cudaMemsetAsync(s->d_vec, 0, 9 * s->vlen * T, s->st), "memset");
+    s->d_S = s->dalloc<KrylovScalars>(1);
+    ck(cudaStreamSynchronize(s->st), "sync");
+  });
+  if (rc != MPM_OK) {
+    g_create_err = s->err;
+    destroy(s);
+    return rc;
+  }
+  *out = s;
+  return MPM_OK;
+}
+
+mpm_status mpm_set_gravity(mpm_scene* s, const double g[3]) {
+  if (!s || !g) return MPM_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a) s->grav[a] = g[a];
+  return MPM_OK;
+}
+
+mpm_status mpm_set_dirichlet(mpm_scene* s, int n, const long long* dof, const double* value) {
+  if (!s) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] {
+    if (n < 0 || (n > 0 && (!dof || !value))) fail(MPM_ERR_INVALID_ARG, "dirichlet arrays");
+    std::vector<uint8_t> f(s->ndof, 0);
+    std::vector<double> v(s->ndof, 0.0);
+    for (int k = 0; k < n; ++k) {
+      if (dof[k] < 0 || dof[k] >= s->ndof) fail(MPM_ERR_INVALID_ARG, "dirichlet dof out of range");
+      f[dof[k]] = 1;
+      v[dof[k]] = value[k];
+    }
+    ck(cudaStreamSynchronize(s->st), "sync");
+    ck(cudaMemcpy(s->d_fixed, f.data(), s->ndof, cudaMemcpyHostToDevice), "upload");
+    ck(cudaMemcpy(s->d_bcval, v.data(), s->ndof * sizeof(double), cudaMemcpyHostToDevice), "upload");
+  });
+}
+
+mpm_status mpm_begin_step(mpm_scene* s, mpm_newton_report* rep) {
+  if (!s) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] { dispatch<BeginF>(s, rep); });
+}
+
+mpm_status mpm_newton_step(mpm_scene* s, mpm_newton_report* rep) {
+  if (!s) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] { dispatch<NewtonF>(s, rep); });
+}
+
+mpm_status mpm_commit_step(mpm_scene* s) {
+  if (!s) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] { dispatch<CommitF>(s); });
+}
+
+mpm_status mpm_set_du(mpm_scene* s, const double* du) {
+  if (!s || !du) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] { dispatch<SetDuF>(s, du); });
+}
+
+mpm_status mpm_assemble(mpm_scene* s) {
+  if (!s) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] { dispatch<AssembleF>(s); });
+}
+
+mpm_status mpm_time_spmv(mpm_scene* s, int reps, double* ms_per_launch, double* bytes_per_launch) {
+  if (!s || !ms_per_launch || !bytes_per_launch) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] { dispatch<TimeSpmvF>(s, reps, ms_per_launch, bytes_per_launch); });
+}
+
+mpm_status mpm_kernel_launches(const mpm_scene* s, long long* out) {
+  if (!s || !out) return MPM_ERR_INVALID_ARG;
+  *out = s->launches;
+  return MPM_OK;
+}
+
+mpm_status mpm_solve_step(mpm_scene* s, mpm_step_report* rep) {
+  if (!s) return MPM_ERR_INVALID_ARG;
+  mpm_step_report local{};
+  mpm_step_report& R = rep ? *rep : local;
+  std::memset(&R, 0, sizeof(R));
+  mpm_status st = guarded(s, [&] {
+    auto t0 = std::chrono::steady_clock::now();
+    mpm_newton_report nr{};
+    dispatch<BeginF>(s, &nr);
+    auto t1 = std::chrono::steady_clock::now();
+    R.t_setup_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    R.r0_norm = s->r0;
+    R.hist[0] = 1.0;
+    R.n_active_nodes = s->nrow;
+    R.t_residual_ms += s->t_res;
+    bool conv = s->r0 == 0.0;
+    while (!conv && s->k < s->desc.newton_maxit) {
+      dispatch<NewtonF>(s, &nr);
+      R.krylov_iters[s->k - 1] = nr.krylov_iters;
+      R.krylov_iters_total += nr.krylov_iters;
+      R.hist[s->k] = nr.rel_residual;
+      R.t_assembly_ms += s->t_asm;
+      R.t_krylov_ms += s->t_kry;
+      R.t_residual_ms += s->t_res;
+      conv = nr.rel_residual <= s->desc.newton_tol;
+    }
+    R.newton_iters = s->k;
+    R.converged = conv;
+    R.rel_residual = s->r0 > 0 ? s->rk / s->r0 : 0.0;
+    if (!conv) fail(MPM_ERR_NOT_CONVERGED, "Newton did not reach newton_tol");
+    auto t2 = std::chrono::steady_clock::now();
+    dispatch<CommitF>(s);
+    auto t3 = std::chrono::steady_clock::now();
+    R.t_commit_ms = std::chrono::duration<double, std::milli>(t3 - t2).count();
+  });
+  R.status = st;
+  return st;
+}
+
+mpm_status mpm_get_residual(const mpm_scene* cs, double* r) {
+  mpm_scene* s = const_cast<mpm_scene*>(cs);
+  if (!s || !r) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] {
+    ck(cudaStreamSynchronize(s->st), "sync");
+    std::vector<double> full(s->ndof), du(1);
+    ck(cudaMemcpy(full.data(), s->d_r, s->ndof * sizeof(double), cudaMemcpyDeviceToHost), "download");
+    std::vector<uint8_t> f(s->ndof);
+    ck(cudaMemcpy(f.data(), s->d_fixed, s->ndof, cudaMemcpyDeviceToHost), "download");
+    std::vector<int> n2r(s->nnode);
+    ck(cudaMemcpy(n2r.data(), s->d_node2row, s->nnode * sizeof(int), cudaMemcpyDeviceToHost), "download");
+    for (long long d = 0; d < s->ndof; ++d) r[d] = (f[d] || n2r[d / s->D] < 0) ? 0.0 : full[d];
+  });
+}
+
+mpm_status mpm_get_du(const mpm_scene* cs, double* du) {
+  mpm_scene* s = const_cast<mpm_scene*>(cs);
+  if (!s || !du) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] {
+    ck(cudaStreamSynchronize(s->st), "sync");
+    ck(cudaMemcpy(du, s->d_du, s->ndof * sizeof(double), cudaMemcpyDeviceToHost), "download");
+  });
+}
+
+mpm_status mpm_get_mass(const mpm_scene* cs, double* mass) {
+  mpm_scene* s = const_cast<mpm_scene*>(cs);
+  if (!s || !mass) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] {
+    ck(cudaStreamSynchronize(s->st), "sync");
+    ck(cudaMemcpy(mass, s->d_M, s->nnode * sizeof(double), cudaMemcpyDeviceToHost), "download");
+  });
+}
+
+}  // extern "C"
+
+namespace {
+template <int D>
+void pattern_mask(mpm_scene* s, std::vector<int>& mask) {
+  const int S = stencil_slots(D);
+  int* d_mask = s->dalloc<int>((size_t)std::max(s->nrow, 1) * S);
+  ck(cudaMemsetAsync(d_mask, 0, (size_t)std::max(s->nrow, 1) * S * sizeof(int), s->st), "memset");
+  ck(launch_pattern_count<D>(s->G, s->d_rows, s->nrow, s->d_node2row, s->d_count, d_mask, s->st), "pattern");
+  s->launches += 1;
+  mask.resize((size_t)s->nrow * S);
+  ck(cudaMemcpyAsync(mask.data(), d_mask, mask.size() * sizeof(int), cudaMemcpyDeviceToHost, s->st), "download");
+  ck(cudaStreamSynchronize(s->st), "sync");
+  s->dfree(d_mask);
+}
+}  // namespace
+
+extern "C" {
+
+mpm_status mpm_get_counts(const mpm_scene* cs, int* n_active, long long* nnzb) {
+  mpm_scene* s = const_cast<mpm_scene*>(cs);
+  if (!s) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] {
+    ck(cudaStreamSynchronize(s->st), "sync");
+    if (n_active) *n_active = s->nrow;
+    if (nnzb) {
+      std::vector<int> mask;
+      if (s->D == 2) pattern_mask<2>(s, mask);
+      else pattern_mask<3>(s, mask);
+      long long c = 0;
+      for (int m : mask) c += m;
+      *nnzb = c;
+    }
+  });
+}
+
+mpm_status mpm_get_jacobian_bsr(const mpm_scene* cs, long long cap, int* row_node, long long* row_ptr,
+                                int* col_node, double* val) {
+  mpm_scene* s = const_cast<mpm_scene*>(cs);
+  if (!s || !row_node || !row_ptr || !col_node || !val) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] {
+    if (!s->staged && s->nrow == 0) fail(MPM_ERR_STATE, "no Jacobian assembled");
+    const int D = s->D, S = stencil_slots(D), DD = D * D;
+    std::vector<int> mask;
+    if (D == 2) pattern_mask<2>(s, mask);
+    else pattern_mask<3>(s, mask);
+    std::vector<int> rows(s->nrow);
+    ck(cudaMemcpy(rows.data(), s->d_rows, s->nrow * sizeof(int), cudaMemcpyDeviceToHost), "download");
+    const size_t nval = (size_t)s->cap * S * DD;
+    std::vector<double> K(nval);
+    if (s->mixed) {
+      std::vector<float> Kf(nval);
+      ck(cudaMemcpy(Kf.data(), s->d_K, nval * sizeof(float), cudaMemcpyDeviceToHost), "download");
+      for (size_t q = 0; q < nval; ++q) K[q] = Kf[q];
+    } else {
+      ck(cudaMemcpy(K.data(), s->d_K, nval * sizeof(double), cudaMemcpyDeviceToHost), "download");
+    }
+    const int nx1 = s->G.nx1, ny1 = s->G.ny1;
+    long long nb = 0;
+    row_ptr[0] = 0;
+    for (int r = 0; r < s->nrow; ++r) {
+      row_node[r] = rows[r];
+      for (int sl = 0; sl < S; ++sl) {
+        if (!mask[(size_t)r * S + sl]) continue;
+        if (nb >= cap) fail(MPM_ERR_INVALID_ARG, "capacity too small for the Jacobian");
+        int dx = sl % 5 - 2, dy = (sl / 5) % 5 - 2, dz = D == 3 ? sl / 25 - 2 : 0;
+        col_node[nb] = rows[r] + dx + nx1 * (dy + ny1 * dz);
+        for (int a = 0; a < D; ++a)
+          for (int b = 0; b < D; ++b) val[nb * DD + a * D + b] = K[((size_t)(sl * D + a) * D + b) * s->cap + r];
+        ++nb;
+      }
+      row_ptr[r + 1] = nb;
+    }
+  });
+}
+
+mpm_status mpm_get_particles(const mpm_scene* cs, double* x, double* be, double* pc, double* F, double* tau) {
+  mpm_scene* s = const_cast<mpm_scene*>(cs);
+  if (!s) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] {
+    ck(cudaStreamSynchronize(s->st), "sync");
+    const int np = s->np, D = s->D;
+    if (np == 0) return;
+    std::vector<int> orig(np);
+    ck(cudaMemcpy(orig.data(), s->P.orig, np * sizeof(int), cudaMemcpyDeviceToHost), "download");
+    std::vector<double> h(np);
+    auto down = [&](const double* d) {
+      ck(cudaMemcpy(h.data(), d, np * sizeof(double), cudaMemcpyDeviceToHost), "download");
+    };
+    if (x) {
+      for (int p = 0; p < np; ++p)
+        for (int a = 0; a < 3; ++a) x[3 * p + a] = 0.0;
+      for (int a = 0; a < D; ++a) {
+        down(s->P.x[a]);
+        for (int p = 0; p < np; ++p) x[3 * orig[p] + a] = h[p];
+      }
+    }
+    if (be) {
+      static const int map2[4] = {0, 1, 2, 3};
+      for (int p = 0; p < np; ++p)
+        for (int k = 0; k < 6; ++k) be[6 * p + k] = 0.0;
+      for (int k = 0; k < s->nbe; ++k) {
+        down(s->P.be[k]);
+        int dst = D == 2 ? map2[k] : k;
+        for (int p = 0; p < np; ++p) be[6 * orig[p] + dst] = h[p];
+      }
+    }
+    if (pc) {
+      down(s->P.pc);
+      for (int p = 0; p < np; ++p) pc[orig[p]] = h[p];
+    }
+    if (F) {
+      for (int p = 0; p < np; ++p)
+        for (int k = 0; k < 9; ++k) F[9 * p + k] = (k % 4 == 0) ? 1.0 : 0.0;
+      for (int a = 0; a < D; ++a)
+        for (int c = 0; c < D; ++c) {
+          down(s->P.F[a * D + c]);
+          for (int p = 0; p < np; ++p) F[9 * orig[p] + 3 * a + c] = h[p];
+        }
+    }
+    if (tau) {
+      double* d_tau = s->dalloc<double>((size_t)np * 9);
+      if (D == 2) ck(launch_stress_out<2>(s->P, s->G, s->d_mats, d_tau, s->st), "stress");
+      else ck(launch_stress_out<3>(s->P, s->G, s->d_mats, d_tau, s->st), "stress");
+      ck(cudaStreamSynchronize(s->st), "sync");
+      ck(cudaMemcpy(tau, d_tau, (size_t)np * 9 * sizeof(double), cudaMemcpyDeviceToHost), "download");
+      s->dfree(d_tau);
+    }
+  });
+}
+
+mpm_status mpm_footprint_bytes(const mpm_scene_desc* desc, int np, size_t* out) {
+  if (!out) return MPM_ERR_INVALID_ARG;
+  try {
+    validate_desc(desc);
+    if (np < 0) return MPM_ERR_INVALID_ARG;
+    *out = footprint(desc, np);
+    return MPM_OK;
+  } catch (const Fail& f) {
+    return f.st;
+  }
+}
+
+void mpm_destroy_scene(mpm_scene* s) { destroy(s); }
+
+const char* mpm_status_string(mpm_status st) {
+  switch (st) {
+    case MPM_OK: return "ok";
+    case MPM_ERR_INVALID_ARG: return "invalid argument";
+    case MPM_ERR_OOM: return "out of device memory";
+    case MPM_ERR_CUDA: return "CUDA error";
+    case MPM_ERR_NOT_CONVERGED: return "Newton did not converge";
+    case MPM_ERR_KRYLOV_MAXIT: return "Krylov iteration limit";
+    case MPM_ERR_KRYLOV_BREAKDOWN: return "Krylov breakdown";
+    case MPM_ERR_NONFINITE: return "non-finite value";
+    case MPM_ERR_TIMEOUT: return "timeout";
+    case MPM_ERR_BOUNDS: return "particle support left the grid";
+    case MPM_ERR_RETURN_MAP: return "return map did not converge";
+    case MPM_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* mpm_last_error(const mpm_scene* s) { return s ? s->err.c_str() : g_create_err.c_str(); }
+
+}  // extern "C"

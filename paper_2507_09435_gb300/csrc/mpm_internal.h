@@ -1,0 +1,140 @@
+// Internal declarations shared by the CUDA translation units of libmpm.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mpm_device.cuh"
+
+namespace mpm {
+
+constexpr int MAX_BE = 6;
+constexpr int MAX_F = 9;
+
+// Particle state on the device, structure of arrays, kept sorted by base cell.
+struct DevParticles {
+  int np;
+  double* x[3];
+  double* vol0;
+  double* mass;
+  int* mat;
+  double* Ep;        // per-particle Young's modulus (always filled)
+  double* phip;      // per-particle friction angle (always filled)
+  double* be[MAX_BE];  // xx, yy, zz, xy (2D) / xx, yy, zz, xy, yz, xz (3D)
+  double* pc;
+  double* F[MAX_F];  // dim*dim row-major
+  int* orig;         // caller's index of each sorted particle
+};
+
+struct DevGrid {
+  int dim;
+  int n[3];
+  int nx1, ny1, nz1;
+  long long nnode;
+  double h, ih;
+  double o[3];
+};
+
+// Stencil-BSR Jacobian: for every active node (row) the 5^dim neighbour
+// blocks at fixed slots, values SoA: val[((slot*D + a)*D + b)*cap + row].
+template <class T>
+struct DevMatrix {
+  T* val;
+  T* dinv;          // block-Jacobi inverse, dinv[(a*D+b)*cap + row]
+  int cap;          // row capacity (row stride of the SoA planes)
+  const int* rows;  // node index of each row
+  const int* nrow;  // device scalar: active row count
+};
+
+struct KrylovScalars {
+  double rho, alpha, omega;
+  double acc_rv, acc_ts, acc_tt, acc_rho, acc_rr;
+  double tol2, bnorm2, rr_last;
+  int iter, done, status, maxit;
+};
+
+// ---- host launchers (stream-ordered, no synchronisation) ----------------
+cudaError_t scan_exclusive(const int* in, int* out, int n, int* tmp, cudaStream_t st);
+size_t scan_tmp_ints(int n);
+
+template <int D>
+cudaError_t launch_cell_keys(const DevParticles& P, const DevGrid& G, int* key, int* count, int* rank,
+                             int* err, cudaStream_t st);
+cudaError_t launch_sort_scatter(int np, const int* key, const int* rank, const int* cstart, int* perm,
+                                cudaStream_t st);
+struct GatherArrays {
+  int nd, ni;
+  const double* dsrc[24];
+  double* ddst[24];
+  const int* isrc[4];
+  int* idst[4];
+};
+cudaError_t launch_gather(int np, const int* perm, const GatherArrays& g, cudaStream_t st);
+cudaError_t launch_flag_positive(const int* count, int* flag, long long n, cudaStream_t st);
+cudaError_t launch_compact(const int* flag, const int* pos, int* list, long long n, cudaStream_t st);
+template <int D>
+cudaError_t launch_mass(const DevParticles& P, const DevGrid& G, double* M, cudaStream_t st);
+cudaError_t launch_active(const double* M, double thr, int* flag, long long nnode, cudaStream_t st);
+cudaError_t launch_node2row(const int* flag, const int* pos, int* node2row, int* rows, long long nnode,
+                            cudaStream_t st);
+cudaError_t launch_apply_bc(const uint8_t* fixed, const double* bcval, const int* node2row, double* du,
+                            long long ndof, int D, cudaStream_t st);
+
+// particle pass: mode 0 residual, 1 residual + tangent, 2 commit
+template <int D, class T>
+cudaError_t launch_particles(const DevParticles& P, const DevGrid& G, const MatC* mats, const double* du,
+                             double* r, const double* grav, T* A, int mode, int* err, int* nplastic,
+                             cudaStream_t st);
+template <int D>
+cudaError_t launch_stress_out(const DevParticles& P, const DevGrid& G, const MatC* mats, double* tau9,
+                              cudaStream_t st);
+
+template <int D, class T>
+cudaError_t launch_assemble(const DevParticles& P, const DevGrid& G, const int* cells, int ncell,
+                            const int* cstart, const int* node2row, const T* A, DevMatrix<T> K,
+                            cudaStream_t st);
+template <int D, class T>
+cudaError_t launch_bc_matrix(const DevGrid& G, DevMatrix<T> K, const uint8_t* fixed, const int* node2row,
+                             int nrow_host, cudaStream_t st);
+template <int D, class T>
+cudaError_t launch_block_jacobi(DevMatrix<T> K, int nrow_host, int* err, cudaStream_t st);
+template <int D>
+cudaError_t launch_pattern_count(const DevGrid& G, const int* rows, int nrow_host, const int* node2row,
+                                 const int* count, int* mask, cudaStream_t st);
+
+// free-DOF residual norm^2 into *out (device double, accumulated)
+template <int D>
+cudaError_t launch_norm_free(const double* r, const int* rows, int nrow_host, const uint8_t* fixed,
+                             double* out, cudaStream_t st);
+
+// Krylov
+template <int D, class T>
+struct KrylovVecs {
+  T *x, *r, *rhat, *p, *phat, *v, *s, *shat, *t;
+};
+template <int D, class T>
+cudaError_t launch_bicgstab_init(DevMatrix<T> K, const double* res, const uint8_t* fixed, KrylovVecs<D, T> v,
+                                 KrylovScalars* S, double tol2, int maxit, int nblk, cudaStream_t st);
+template <int D, class T>
+cudaError_t launch_bicgstab_iter(const DevGrid& G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S,
+                                 int nblk, cudaStream_t st);
+template <int D, class T>
+cudaError_t launch_update_du(DevMatrix<T> K, const T* x, const uint8_t* fixed, double* du, int nblk,
+                             cudaStream_t st);
+template <int D, class T>
+cudaError_t launch_spmv(const DevGrid& G, DevMatrix<T> K, const T* x, T* y, int nblk, cudaStream_t st);
+// kernels launched by one scan_exclusive call of n elements
+int scan_launches(long long n);
+
+// GMRES(m) with classical Gram-Schmidt applied twice
+template <int D, class T>
+struct GmresWork {
+  T* V;            // (m+1) basis vectors, each nvec long
+  T* Z;            // m preconditioned vectors (flexible form: x = Z y)
+  long long nvec;  // length of one vector (nnode*D)
+  int m;
+  double* H;       // (m+1) x m Hessenberg, column-major, on device
+  double* dots;    // m+1 partial dot accumulators
+  double* cs;      // Givens cosines (m), sines (m), g (m+1)
+};
+
+}  // namespace mpm

@@ -1,0 +1,378 @@
+"""Thin Python binding of the C ABI in include/mpm.h (argument marshalling
+only; every step of the Newton path runs in libmpm's CUDA kernels).
+
+Function names match the C symbols.  Arrays are NumPy host arrays (or
+anything ``np.ascontiguousarray`` accepts, e.g. a CPU/pinned torch tensor's
+``.numpy()``).  There is no CPU fallback: if ``libmpm.so`` cannot be built or
+loaded, or a call fails, an exception is raised.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+MPM_OK = 0
+MPM_NH, MPM_NH_DP, MPM_NH_MCC = 0, 1, 2
+MPM_FP64, MPM_MIXED = 0, 1
+MPM_BICGSTAB, MPM_GMRES = 0, 1
+MPM_FORCING_FIXED, MPM_FORCING_EW = 0, 1
+
+STATUS = {
+    0: "MPM_OK", 1: "MPM_ERR_INVALID_ARG", 2: "MPM_ERR_OOM", 3: "MPM_ERR_CUDA",
+    4: "MPM_ERR_NOT_CONVERGED", 5: "MPM_ERR_KRYLOV_MAXIT", 6: "MPM_ERR_KRYLOV_BREAKDOWN",
+    7: "MPM_ERR_NONFINITE", 8: "MPM_ERR_TIMEOUT", 9: "MPM_ERR_BOUNDS", 10: "MPM_ERR_RETURN_MAP",
+    11: "MPM_ERR_STATE",
+}
+
+
+class mpm_scene_desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("h", ctypes.c_double),
+                ("origin", ctypes.c_double * 3), ("precision", ctypes.c_int), ("krylov", ctypes.c_int),
+                ("gmres_restart", ctypes.c_int), ("newton_tol", ctypes.c_double),
+                ("newton_maxit", ctypes.c_int), ("forcing", ctypes.c_int), ("krylov_rtol", ctypes.c_double),
+                ("krylov_maxit", ctypes.c_int)]
+
+
+class mpm_material(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("E", ctypes.c_double), ("nu", ctypes.c_double),
+                ("rho", ctypes.c_double), ("phi", ctypes.c_double), ("psi", ctypes.c_double),
+                ("c", ctypes.c_double), ("M", ctypes.c_double), ("lambda_cc", ctypes.c_double),
+                ("kappa_cc", ctypes.c_double), ("pc0", ctypes.c_double)]
+
+
+class mpm_newton_report(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("krylov_iters", ctypes.c_int), ("krylov_rel", ctypes.c_double),
+                ("krylov_rtol", ctypes.c_double), ("r_norm", ctypes.c_double),
+                ("rel_residual", ctypes.c_double), ("n_plastic", ctypes.c_int)]
+
+
+class mpm_step_report(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("newton_iters", ctypes.c_int), ("converged", ctypes.c_int),
+                ("krylov_iters_total", ctypes.c_int), ("r0_norm", ctypes.c_double),
+                ("rel_residual", ctypes.c_double), ("hist", ctypes.c_double * 33),
+                ("krylov_iters", ctypes.c_int * 32), ("n_active_nodes", ctypes.c_int),
+                ("nnzb", ctypes.c_longlong), ("t_setup_ms", ctypes.c_double),
+                ("t_residual_ms", ctypes.c_double), ("t_assembly_ms", ctypes.c_double),
+                ("t_krylov_ms", ctypes.c_double), ("t_commit_ms", ctypes.c_double)]
+
+
+class MPMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+_LL = ctypes.POINTER(ctypes.c_longlong)
+_P = ctypes.c_void_p
+_lib = None
+
+# every symbol declared in include/mpm.h
+EXPORTS = ["mpm_create_scene", "mpm_set_gravity", "mpm_set_dirichlet", "mpm_begin_step", "mpm_newton_step",
+           "mpm_set_du", "mpm_assemble", "mpm_commit_step", "mpm_solve_step", "mpm_get_residual", "mpm_get_du", "mpm_get_mass",
+           "mpm_get_counts", "mpm_get_jacobian_bsr", "mpm_get_particles", "mpm_kernel_launches",
+           "mpm_time_spmv", "mpm_footprint_bytes",
+           "mpm_destroy_scene", "mpm_status_string", "mpm_last_error"]
+
+
+def lib(build: bool = True):
+    """Load libmpm.so (building it first if needed).  Raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmpm.so not found at {path}")
+    L = ctypes.CDLL(path)
+    L.mpm_create_scene.argtypes = [ctypes.POINTER(mpm_scene_desc), ctypes.c_int, _D, _D, _D, _I, _D, _D, _D,
+                                   ctypes.POINTER(mpm_material), ctypes.c_int, _P, ctypes.POINTER(_P)]
+    L.mpm_set_gravity.argtypes = [_P, _D]
+    L.mpm_set_dirichlet.argtypes = [_P, ctypes.c_int, _LL, _D]
+    L.mpm_begin_step.argtypes = [_P, ctypes.POINTER(mpm_newton_report)]
+    L.mpm_newton_step.argtypes = [_P, ctypes.POINTER(mpm_newton_report)]
+    L.mpm_set_du.argtypes = [_P, _D]
+    L.mpm_assemble.argtypes = [_P]
+    L.mpm_commit_step.argtypes = [_P]
+    L.mpm_solve_step.argtypes = [_P, ctypes.POINTER(mpm_step_report)]
+    L.mpm_get_residual.argtypes = [_P, _D]
+    L.mpm_get_du.argtypes = [_P, _D]
+    L.mpm_get_mass.argtypes = [_P, _D]
+    L.mpm_get_counts.argtypes = [_P, _I, _LL]
+    L.mpm_get_jacobian_bsr.argtypes = [_P, ctypes.c_longlong, _I, _LL, _I, _D]
+    L.mpm_get_particles.argtypes = [_P, _D, _D, _D, _D, _D]
+    L.mpm_kernel_launches.argtypes = [_P, _LL]
+    L.mpm_time_spmv.argtypes = [_P, ctypes.c_int, _D, _D]
+    L.mpm_footprint_bytes.argtypes = [ctypes.POINTER(mpm_scene_desc), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_size_t)]
+    L.mpm_destroy_scene.argtypes = [_P]
+    L.mpm_destroy_scene.restype = None
+    L.mpm_status_string.argtypes = [ctypes.c_int]
+    L.mpm_status_string.restype = ctypes.c_char_p
+    L.mpm_last_error.argtypes = [_P]
+    L.mpm_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("mpm_destroy_scene", "mpm_status_string", "mpm_last_error"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _p(a, t=_D):
+    return None if a is None else a.ctypes.data_as(t)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(rc, handle=None):
+    if rc != MPM_OK:
+        msg = lib().mpm_last_error(handle).decode() if handle is not None or rc else ""
+        raise MPMError(rc, msg)
+
+
+def make_desc(dim, n, h, origin=(0.0, 0.0, 0.0), precision=MPM_FP64, krylov=MPM_BICGSTAB, gmres_restart=30,
+              newton_tol=1e-8, newton_maxit=25, forcing=None, krylov_rtol=None, krylov_maxit=20000):
+    d = mpm_scene_desc()
+    d.dim = dim
+    for a in range(3):
+        d.n[a] = int(n[a]) if a < len(n) else 0
+        d.origin[a] = float(origin[a]) if a < len(origin) else 0.0
+    d.h = float(h)
+    d.precision = precision
+    d.krylov = krylov
+    d.gmres_restart = gmres_restart
+    d.newton_tol = newton_tol
+    d.newton_maxit = newton_maxit
+    if forcing is None:
+        forcing = MPM_FORCING_EW if precision == MPM_MIXED else MPM_FORCING_FIXED
+    if krylov_rtol is None:
+        krylov_rtol = 1e-6 if precision == MPM_MIXED else 1e-10
+    d.forcing = forcing
+    d.krylov_rtol = krylov_rtol
+    d.krylov_maxit = krylov_maxit
+    return d
+
+
+def mpm_footprint_bytes(desc, np_):
+    out = ctypes.c_size_t(0)
+    _check(lib().mpm_footprint_bytes(ctypes.byref(desc), int(np_), ctypes.byref(out)))
+    return int(out.value)
+
+
+def mpm_create_scene(desc, x, vol0, mass, mat_id, mats, E_p=None, phi_p=None, pc0_p=None, stream=None):
+    x = _f64(x)
+    np_ = x.shape[0]
+    x3 = np.zeros((np_, 3))
+    x3[:, :x.shape[1]] = x
+    mat_id = np.ascontiguousarray(mat_id, dtype=np.int32)
+    marr = (mpm_material * len(mats))(*mats)
+    h = _P()
+    L = lib()
+    rc = L.mpm_create_scene(ctypes.byref(desc), np_, _p(x3), _p(_f64(vol0)), _p(_f64(mass)), _p(mat_id, _I),
+                            _p(_f64(E_p)), _p(_f64(phi_p)), _p(_f64(pc0_p)), marr, len(mats),
+                            _P(stream) if stream else None, ctypes.byref(h))
+    if rc != MPM_OK:
+        raise MPMError(rc, L.mpm_last_error(None).decode())
+    return h
+
+
+def mpm_destroy_scene(h):
+    lib().mpm_destroy_scene(h)
+
+
+def mpm_set_gravity(h, g):
+    _check(lib().mpm_set_gravity(h, _p(_f64(np.asarray(g, dtype=np.float64).reshape(3)))), h)
+
+
+def mpm_set_dirichlet(h, dof, value):
+    dof = np.ascontiguousarray(dof, dtype=np.int64)
+    value = _f64(value)
+    _check(lib().mpm_set_dirichlet(h, int(dof.size), _p(dof, _LL), _p(value)), h)
+
+
+def mpm_begin_step(h):
+    rep = mpm_newton_report()
+    _check(lib().mpm_begin_step(h, ctypes.byref(rep)), h)
+    return rep
+
+
+def mpm_newton_step(h):
+    rep = mpm_newton_report()
+    _check(lib().mpm_newton_step(h, ctypes.byref(rep)), h)
+    return rep
+
+
+def mpm_set_du(h, du):
+    _check(lib().mpm_set_du(h, _p(_f64(du))), h)
+
+
+def mpm_assemble(h):
+    _check(lib().mpm_assemble(h), h)
+
+
+def mpm_commit_step(h):
+    _check(lib().mpm_commit_step(h), h)
+
+
+def mpm_solve_step(h, check=True):
+    rep = mpm_step_report()
+    rc = lib().mpm_solve_step(h, ctypes.byref(rep))
+    if check:
+        _check(rc, h)
+    return rep
+
+
+def mpm_get_residual(h, ndof):
+    r = np.zeros(ndof)
+    _check(lib().mpm_get_residual(h, _p(r)), h)
+    return r
+
+
+def mpm_get_du(h, ndof):
+    r = np.zeros(ndof)
+    _check(lib().mpm_get_du(h, _p(r)), h)
+    return r
+
+
+def mpm_get_mass(h, nnode):
+    r = np.zeros(nnode)
+    _check(lib().mpm_get_mass(h, _p(r)), h)
+    return r
+
+
+def mpm_get_counts(h):
+    na = ctypes.c_int(0)
+    nb = ctypes.c_longlong(0)
+    _check(lib().mpm_get_counts(h, ctypes.byref(na), ctypes.byref(nb)), h)
+    return na.value, nb.value
+
+
+def mpm_get_jacobian_bsr(h, dim):
+    na, nb = mpm_get_counts(h)
+    row_node = np.zeros(na, dtype=np.int32)
+    row_ptr = np.zeros(na + 1, dtype=np.int64)
+    col_node = np.zeros(max(nb, 1), dtype=np.int32)
+    val = np.zeros(max(nb, 1) * dim * dim)
+    _check(lib().mpm_get_jacobian_bsr(h, nb, _p(row_node, _I), _p(row_ptr, _LL), _p(col_node, _I), _p(val)), h)
+    return row_node, row_ptr, col_node[:nb], val[:nb * dim * dim].reshape(nb, dim, dim)
+
+
+def mpm_get_particles(h, np_, x=True, be=True, pc=True, F=True, tau=True):
+    out = {}
+    bufs = {}
+    for k, sz, want in (("x", 3, x), ("be", 6, be), ("pc", 1, pc), ("F", 9, F), ("tau", 9, tau)):
+        bufs[k] = np.zeros(np_ * sz) if want else None
+    _check(lib().mpm_get_particles(h, _p(bufs["x"]), _p(bufs["be"]), _p(bufs["pc"]), _p(bufs["F"]),
+                                   _p(bufs["tau"])), h)
+    if x:
+        out["x"] = bufs["x"].reshape(np_, 3)
+    if be:
+        out["be"] = bufs["be"].reshape(np_, 6)
+    if pc:
+        out["pc"] = bufs["pc"]
+    if F:
+        out["F"] = bufs["F"].reshape(np_, 3, 3)
+    if tau:
+        out["tau"] = bufs["tau"].reshape(np_, 3, 3)
+    return out
+
+
+def mpm_kernel_launches(h):
+    out = ctypes.c_longlong(0)
+    _check(lib().mpm_kernel_launches(h, ctypes.byref(out)), h)
+    return int(out.value)
+
+
+def mpm_time_spmv(h, reps):
+    ms = ctypes.c_double(0)
+    by = ctypes.c_double(0)
+    _check(lib().mpm_time_spmv(h, int(reps), ctypes.byref(ms), ctypes.byref(by)), h)
+    return ms.value, by.value
+
+
+# --------------------------------------------------------------------------
+# convenience wrapper over a generated scene (see scenes.py)
+# --------------------------------------------------------------------------
+
+def materials_of(scene):
+    out = []
+    for m in scene.materials:
+        q = mpm_material()
+        q.model, q.E, q.nu, q.rho = m.model, m.E, m.nu, m.rho
+        q.phi, q.psi, q.c = m.phi, m.psi, m.c
+        q.M, q.lambda_cc, q.kappa_cc, q.pc0 = m.M, m.lambda_cc, m.kappa_cc, m.pc0
+        out.append(q)
+    return out
+
+
+class GpuScene:
+    """A scene resident on the GPU, driven load step by load step."""
+
+    def __init__(self, scene, precision=MPM_FP64, krylov=MPM_BICGSTAB, stream=None, **kw):
+        self.scene = scene
+        self.dim = scene.dim
+        self.desc = make_desc(scene.dim, scene.n, scene.h, scene.origin, precision=precision, krylov=krylov,
+                              **kw)
+        self.h = mpm_create_scene(self.desc, scene.x[:, :scene.dim], scene.vol0, scene.mass, scene.mat_id,
+                                  materials_of(scene), E_p=scene.E_p, phi_p=scene.phi_p, pc0_p=scene.pc0_p,
+                                  stream=stream)
+        self.nnode = scene.nnode
+        self.ndof = scene.nnode * scene.dim
+        self.np = scene.np
+
+    def close(self):
+        if self.h is not None:
+            mpm_destroy_scene(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_step(self, step):
+        mpm_set_dirichlet(self.h, step.dof, step.value)
+        mpm_set_gravity(self.h, step.gravity)
+
+    def solve_step(self, step, check=True):
+        self.set_step(step)
+        return mpm_solve_step(self.h, check=check)
+
+    def begin(self, step):
+        self.set_step(step)
+        return mpm_begin_step(self.h)
+
+    def newton(self):
+        return mpm_newton_step(self.h)
+
+    def commit(self):
+        mpm_commit_step(self.h)
+
+    def set_du(self, du):
+        mpm_set_du(self.h, du)
+
+    def assemble(self):
+        mpm_assemble(self.h)
+
+    def residual(self):
+        return mpm_get_residual(self.h, self.ndof)
+
+    def du(self):
+        return mpm_get_du(self.h, self.ndof)
+
+    def mass(self):
+        return mpm_get_mass(self.h, self.nnode)
+
+    def jacobian_bsr(self):
+        return mpm_get_jacobian_bsr(self.h, self.dim)
+
+    def particles(self, **kw):
+        return mpm_get_particles(self.h, self.np, **kw)

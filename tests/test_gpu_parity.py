@@ -1,0 +1,183 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on the
+same seeded inputs: residual, Jacobian blocks, converged increments and the
+committed particle state.  Sizes span several cells/tiles with ragged cell
+occupancy; plastic, apex and repeated-eigenvalue states are exercised through
+random increments set with mpm_set_du."""
+import numpy as np
+import pytest
+
+from oracle import mpm_oracle as O
+from paper_2507_09435_gb300 import mpm, scenes as S
+
+from parity_util import (DU_TOL, JAC_TOL_FP64, JAC_TOL_MIXED, RES_TOL, du_error, fixed_mask, jacobian_error,
+                         residual_error)
+
+pytestmark = pytest.mark.gpu
+
+
+def _run_parity(sc, nsteps, precision=mpm.MPM_FP64, jac_every_step=True, expect_plastic=False):
+    orc = O.OracleScene.from_scene(sc)
+    gs = mpm.GpuScene(sc, precision=precision, newton_tol=1e-12, newton_maxit=30,
+                      forcing=mpm.MPM_FORCING_FIXED, krylov_rtol=1e-13 if precision == mpm.MPM_FP64 else 1e-6,
+                      krylov_maxit=20000)
+    saw_plastic = False
+    jtol = JAC_TOL_FP64 if precision == mpm.MPM_FP64 else JAC_TOL_MIXED
+    for k, st in enumerate(sc.steps[:nsteps]):
+        fixed = fixed_mask(sc, st)
+        orc.gravity = np.asarray(st.gravity, dtype=np.float64)
+        rep = gs.begin(st)
+        du = gs.du()
+        assert residual_error(gs, orc, du, fixed) < RES_TOL
+        if jac_every_step or k == 0:
+            gs.assemble()
+            ej, ng, no = jacobian_error(gs, orc, du, fixed)
+            assert ej < jtol, (k, ej)
+            assert ng == no
+        it = 0
+        rel = 1.0
+        while rel > 1e-12 and it < 30:
+            nr = gs.newton()
+            it += 1
+            rel = nr.rel_residual
+            saw_plastic |= nr.n_plastic > 0
+            assert residual_error(gs, orc, gs.du(), fixed) < RES_TOL
+        assert rel <= 1e-12, (k, rel)
+        du_g = gs.du()
+        out = orc.solve_step(st.dof, st.value, st.gravity, tol=1e-12, maxit=30)
+        assert out["converged"]
+        assert du_error(du_g, out["du"]) < DU_TOL, (k, du_error(du_g, out["du"]))
+        gs.commit()
+        part = gs.particles()
+        scale_x = np.abs(orc.x).max()
+        assert np.abs(part["x"] - orc.x).max() < 1e-12 * scale_x + DU_TOL * np.abs(out["du"]).max()
+        assert np.abs(part["F"] - orc.F.reshape(-1, 3, 3)).max() < 1e-6
+        assert np.abs(part["be"] - orc.be).max() < 1e-6
+        if sc.materials[0].model == S.MODEL_NH_MCC:
+            assert np.abs(part["pc"] - orc.pc).max() < 1e-6 * np.abs(orc.pc).max()
+    if expect_plastic:
+        assert saw_plastic
+    gs.close()
+
+
+def test_block_compression_fp64():
+    """1,024-particle Neo-Hookean block, 5 load steps (32x32 grid)."""
+    _run_parity(S.block_compression(), 5)
+
+
+def test_block_compression_matches_homogeneous_closed_form():
+    sc = S.block_compression()
+    gs = mpm.GpuScene(sc, newton_tol=1e-12, krylov_rtol=1e-13)
+    mu, lam = 1e6 / 2.6, 1e6 * 0.3 / (1.3 * 0.4)
+    for k, st in enumerate(sc.steps):
+        rep = gs.solve_step(st)
+        assert rep.converged
+        l2 = 0.999 ** (k + 1)
+        l1 = 1.0
+        for _ in range(50):
+            g = mu * (l1 * l1 - 1) + lam * np.log(l1 * l2)
+            l1 -= g / (2 * mu * l1 + lam / l1)
+        F = gs.particles()["F"]
+        assert np.abs(F - np.diag([l1, l2, 1.0])[None]).max() < 1e-10
+    gs.close()
+
+
+def test_footing_coarse_fp64_plastic():
+    """Coarsened footing (46x22 soil cells, 4,048 particles): geostatic step
+    plus footing steps large enough to drive Drucker-Prager particles plastic."""
+    sc = S.footing(nx=48, ny=24, h=0.5, nsteps=5, settle_frac=0.2)
+    _run_parity(sc, 4, jac_every_step=True, expect_plastic=True)
+
+
+@pytest.mark.parametrize("dim,model,amp", [(2, S.MODEL_NH, 0.03), (2, S.MODEL_NH_DP, 0.03),
+                                           (3, S.MODEL_NH_MCC, 0.01), (3, S.MODEL_NH_DP, 0.02),
+                                           (3, S.MODEL_NH, 0.03), (2, S.MODEL_NH_MCC, 0.02)])
+@pytest.mark.parametrize("precision", [mpm.MPM_FP64, mpm.MPM_MIXED])
+def test_random_states(dim, model, amp, precision):
+    """Residual and Jacobian at random increments (plastic and apex branches,
+    jittered particles, ragged cell occupancy)."""
+    sc = S.tiny_scene(dim, model, seed=11 + dim + model, ncell=3 if dim == 2 else 2, ppc=3 if dim == 2 else 2)
+    # fix the bottom layer so that J is non-singular
+    n = sc.n
+    nx1, ny1 = n[0] + 1, n[1] + 1
+    nodes = np.arange(sc.nnode)
+    iy = (nodes // nx1) % ny1
+    dof = np.concatenate([nodes[iy <= 3] * dim + a for a in range(dim)])
+    step = S.LoadStep(np.sort(dof).astype(np.int64), np.zeros(dof.size), (0.0, -9.81, 0.0))
+    fixed = fixed_mask(sc, step)
+    orc = O.OracleScene.from_scene(sc)
+    orc.gravity = np.array(step.gravity)
+    gs = mpm.GpuScene(sc, precision=precision)
+    gs.begin(step)
+    _, M = orc.residual(np.zeros(sc.nnode * dim))
+    act = orc.active_dofs(M)
+    du = S.random_increment(sc, amp, seed=5)
+    du[~act] = 0.0
+    du[fixed] = 0.0
+    gs.set_du(du)
+    _, _, modes = orc.residual(du, with_mode=True)
+    if model != S.MODEL_NH:
+        assert (modes > 0).sum() >= 3
+    assert residual_error(gs, orc, du, fixed) < RES_TOL
+    gs.assemble()
+    ej, ng, no = jacobian_error(gs, orc, du, fixed)
+    assert ej < (JAC_TOL_FP64 if precision == mpm.MPM_FP64 else JAC_TOL_MIXED) * (10 if model else 1)
+    gs.close()
+
+
+def test_column_3d_mcc_fp64():
+    """Small 3D modified Cam-Clay column (4x4x6 cells, 768 particles) under a
+    gravity ramp with a low preconsolidation so that it yields."""
+    sc = S.column_collapse_3d(nx=12, ny=12, nz=12, h=0.1, col=(4, 4, 6), nsteps=3, pc_mean=-3e3,
+                              E=1e6, g=9.81 * 20)
+    _run_parity(sc, 3, jac_every_step=True, expect_plastic=True)
+
+
+def test_mixed_precision_footing_converges_and_states_error():
+    """Mixed mode (FP32 Jacobian and Krylov, FP64 residual/return map/check)
+    reaches the 1e-8 Newton tolerance; its increment is within the stated
+    error of the FP64 oracle's."""
+    sc = S.footing(nx=48, ny=24, h=0.5, nsteps=5, settle_frac=0.2)
+    orc = O.OracleScene.from_scene(sc)
+    gs = mpm.GpuScene(sc, precision=mpm.MPM_MIXED, newton_tol=1e-8)
+    for k, st in enumerate(sc.steps[:3]):
+        gs.set_step(st)
+        rep = mpm.mpm_solve_step(gs.h, check=False)
+        assert rep.converged, [rep.hist[i] for i in range(rep.newton_iters + 1)]
+        assert rep.rel_residual <= 1e-8
+        out = orc.solve_step(st.dof, st.value, st.gravity, tol=1e-12)
+        part = gs.particles()
+        # stated error of the mixed form against the FP64 oracle
+        ex = np.abs(part["x"] - orc.x).max() / np.abs(out["du"]).max()
+        assert ex < 1e-5, ex
+    gs.close()
+
+
+def test_empty_scene_and_state_errors():
+    sc = S.block_compression()
+    d = mpm.make_desc(2, sc.n, sc.h)
+    h = mpm.mpm_create_scene(d, np.zeros((0, 2)), np.zeros(0), np.zeros(0), np.zeros(0, np.int32),
+                             mpm.materials_of(sc))
+    with pytest.raises(mpm.MPMError) as e:
+        mpm.mpm_newton_step(h)
+    assert e.value.status == 11
+    rep = mpm.mpm_solve_step(h)
+    assert rep.converged and rep.newton_iters == 0
+    mpm.mpm_destroy_scene(h)
+
+
+def test_particle_leaving_grid_is_reported():
+    """A prescribed increment that pushes particles out of the grid makes the
+    next load step fail with MPM_ERR_BOUNDS (flag raised in the kernels)."""
+    sc = S.block_compression()
+    gs = mpm.GpuScene(sc, newton_maxit=3)
+    nodes = np.arange(sc.nnode)
+    dof = np.concatenate([nodes * 2, nodes * 2 + 1])
+    val = np.concatenate([np.full(sc.nnode, -2.5 * sc.h), np.zeros(sc.nnode)])
+    step = S.LoadStep(dof.astype(np.int64), val, (0.0, 0.0, 0.0))
+    gs.set_step(step)
+    rep = mpm.mpm_solve_step(gs.h, check=False)
+    assert rep.status == 0
+    with pytest.raises(mpm.MPMError) as e:
+        gs.begin(step)
+    assert e.value.status == 9
+    gs.close()
