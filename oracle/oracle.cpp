@@ -365,10 +365,18 @@ int return_map(const Mat& m, const double etr[3], double pcn, double eps[3],
   double p = (tau[0] + tau[1] + tau[2]) / 3.0;
   double s[3] = {tau[0] - p, tau[1] - p, tau[2] - p};
   double J2 = 0.5 * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
-  double f;
-  if (m.model == MODEL_NH_DP) f = std::sqrt(J2) + m.eta * p - m.xi * m.coh;
-  else f = 3.0 * J2 / (m.M * m.M) + p * (p - pcn);
-  if (!(f > 0.0)) return 0;  // elastic
+  double f, ftol;
+  if (m.model == MODEL_NH_DP) {
+    f = std::sqrt(J2) + m.eta * p - m.xi * m.coh;
+    ftol = 1e-10 * m.mu;
+  } else {
+    f = 3.0 * J2 / (m.M * m.M) + p * (p - pcn);
+    ftol = 1e-10 * m.mu * std::fabs(pcn);
+  }
+  // Reading: a trial state within a rounding-level tolerance of the yield
+  // surface is elastic (e.g. a state committed on the surface, re-evaluated
+  // at zero increment), so the branch does not hang on the last bit of f.
+  if (!(f > ftol)) return 0;  // elastic
 
   if (m.model == MODEL_NH_DP && m.eta > 0.0) {
     // Apex test (reading): the deviatoric return keeps the trial volume
@@ -400,21 +408,35 @@ int return_map(const Mat& m, const double etr[3], double pcn, double eps[3],
     }
   }
 
-  // local Newton on the four return-map equations from the trial state
+  // local Newton on the four return-map equations from the trial state,
+  // with step halving while the step does not reduce ||R|| (a safeguard;
+  // the root it converges to is the same)
   double x[4] = {etr[0], etr[1], etr[2], 0.0};
   int conv = 0;
   for (int it = 0; it < 100; ++it) {
     double R[4], Jx[4][4], Je[4][3];
     model_res(x, etr, m, pcn, R);
+    double n0 = std::sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2] + R[3] * R[3]);
     res_jacobians(x, etr, m, pcn, Jx, Je);
-    if (solve_small(4, Jx, R) != 0) return -2;
+    double dx[4] = {R[0], R[1], R[2], R[3]};
+    if (solve_small(4, Jx, dx) != 0) return -2;
+    double alpha = 1.0;
+    for (int ls = 0; ls < 30; ++ls) {
+      double xt[4], Rt[4];
+      for (int i = 0; i < 4; ++i) xt[i] = x[i] - alpha * dx[i];
+      model_res(xt, etr, m, pcn, Rt);
+      double n1 = std::sqrt(Rt[0] * Rt[0] + Rt[1] * Rt[1] + Rt[2] * Rt[2] + Rt[3] * Rt[3]);
+      // accept a sufficient decrease, or any step once ||R|| is at rounding level
+      if (std::isfinite(n1) && (n1 <= (1.0 - 1e-4 * alpha) * n0 || n1 <= 1e-12)) break;
+      alpha *= 0.5;
+    }
     double big = 0;
     for (int i = 0; i < 4; ++i) {
-      x[i] -= R[i];
-      big = std::max(big, std::fabs(R[i]) / (1.0 + std::fabs(x[i])));
+      x[i] -= alpha * dx[i];
+      big = std::max(big, std::fabs(alpha * dx[i]) / (1.0 + std::fabs(x[i])));
     }
     if (!std::isfinite(big)) return -2;
-    if (big <= 1e-13) { conv = 1; break; }  // quadratic: the error left is ~1e-26
+    if (alpha == 1.0 && big <= 1e-13) { conv = 1; break; }  // quadratic: the error left is ~1e-26
   }
   if (!conv) return -2;
   // implicit-function theorem: dx/detr = -(dR/dx)^-1 dR/detr

@@ -181,6 +181,20 @@ def test_particle_tangent_matches_central_differences(oracle, case):
     assert np.abs(o["A"] - Afd).max() < 2e-7 * scale
 
 
+@pytest.mark.parametrize("model", [S.MODEL_NH_DP, S.MODEL_NH_MCC])
+def test_committed_plastic_state_is_elastic_at_zero_increment(oracle, model):
+    """A state returned to the yield surface, re-evaluated with dF = 1, takes
+    the elastic branch (yield tolerance reading) and keeps its stress."""
+    p = _mat(model)
+    pcn = -2e4
+    dF = _make_dF("shear" if model == S.MODEL_NH_DP else "compress")
+    o = oracle.particle(model, p, [1, 1, 1, 0, 0, 0], pcn, dF)
+    assert o["mode"] == 1
+    o2 = oracle.particle(model, p, o["be"], o["pc"], np.eye(3))
+    assert o2["mode"] == 0
+    assert np.abs(o2["tau"] - o["tau"]).max() < 1e-9 * np.abs(o["tau"]).max()
+
+
 # ---------------------------------------------------------------- return maps
 def test_dp_return_consistency_and_flow(oracle):
     for psi in (0.0, 8.0):
