@@ -204,6 +204,14 @@ mpm_status mpm_kernel_launches(const mpm_scene* s, long long* out);
  * one launch (present blocks, the input and output vectors, the row list). */
 mpm_status mpm_time_spmv(mpm_scene* s, int reps, double* ms_per_launch, double* bytes_per_launch);
 
+/* Overwrite the committed particle state (caller's particle order, host
+ * arrays; any pointer may be NULL to keep that field): be[np*6] elastic left
+ * Cauchy-Green (xx,yy,zz,xy,yz,xz), pc[np] preconsolidation, F[np*9].  With
+ * mpm_get_particles this checkpoints and resumes a scene; it also sets an
+ * initial (e.g. geostatic) stress state.  Unstages a staged step.
+ * MPM_ERR_INVALID_ARG for a non-positive-definite be or det(F) <= 0. */
+mpm_status mpm_set_particles(mpm_scene* s, const double* be, const double* pc, const double* F);
+
 /* Device memory a scene of this size would take (for admission control). */
 mpm_status mpm_footprint_bytes(const mpm_scene_desc* desc, int np, size_t* out);
 

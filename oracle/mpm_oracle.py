@@ -179,7 +179,10 @@ class OracleScene:
     @classmethod
     def from_scene(cls, sc):
         model, params, pc0 = sc.particle_params()
-        return cls(sc.dim, sc.n, sc.h, sc.origin, sc.x, sc.vol0, sc.mass, model, params, pc0)
+        o = cls(sc.dim, sc.n, sc.h, sc.origin, sc.x, sc.vol0, sc.mass, model, params, pc0)
+        if getattr(sc, "be0", None) is not None:
+            o.be[:] = sc.be0
+        return o
 
     # ---- residual / Jacobian -------------------------------------------
     def residual(self, du, with_mode=False, with_scale=False):

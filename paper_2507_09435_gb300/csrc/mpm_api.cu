@@ -80,6 +80,8 @@ struct mpm_scene {
   double mmax = 0;
   float t_asm = 0, t_kry = 0, t_res = 0;
   long long launches = 0;   // kernels launched by this scene
+  long long halvings = 0;   // Newton steps halved after a return-map failure
+  double* d_duprev = nullptr;
   std::string err;
 
   template <class T>
@@ -139,7 +141,7 @@ size_t footprint(const mpm_scene_desc* d, int np) {
   const long long nn = nnode_of(d), ndof = nn * D;
   const int nbe = D == 2 ? 4 : 6, nF = D * D;
   size_t part = (size_t)np * (2 * (D + 2 + 2 + nbe + 1 + nF) * 8 + 2 * 2 * 4 + 3 * 4);
-  size_t grid = (size_t)nn * (7 * 4 + 8) + (size_t)ndof * (3 * 8 + 1);
+  size_t grid = (size_t)nn * (7 * 4 + 8) + (size_t)ndof * (4 * 8 + 1);
   size_t tang = (size_t)np * D * D * D * D * T;
   long long pad = 2 + 2LL * (d->n[0] + 1) + (D == 3 ? 2LL * (d->n[0] + 1) * (d->n[1] + 1) : 0);
   size_t vec = 9 * (size_t)(nn + 2 * pad) * D * T;
@@ -390,12 +392,24 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
   const int kit = s->h_S->iter;
   const int kstat = s->h_S->status;
   const double krel = (s->rk > 0) ? std::sqrt(std::max(s->h_S->rr_last, 0.0)) / s->rk : 0.0;
+  ck(cudaMemcpyAsync(s->d_duprev, s->d_du, s->ndof * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy du");
   ck(launch_update_du<D, T>(K, v.x, s->d_fixed, s->d_du, nblk, st), "update");
   s->launches += 2;   // Krylov init + update
   cudaEventRecord(s->ev[2], st);
   residual_pass<D, T>(s, 1);
   cudaEventRecord(s->ev[3], st);
   ck(cudaStreamSynchronize(st), "sync");
+  // a full step that drives a return map out of its domain (or to a
+  // non-finite state) is halved, at most four times, before giving up
+  for (int half = 1; half <= 4 && (s->h_int[2] & (ERRF_RETURN | ERRF_NONFINITE | ERRF_DET)); ++half) {
+    ck(cudaMemsetAsync(s->d_err, 0, sizeof(int), st), "memset");
+    ck(launch_step_du<D, T>(K, v.x, s->d_fixed, s->d_duprev, s->d_du, std::ldexp(1.0, -half), nblk, st), "step");
+    s->launches += 1;
+    residual_pass<D, T>(s, 1);
+    cudaEventRecord(s->ev[3], st);
+    ck(cudaStreamSynchronize(st), "sync");
+    s->halvings += 1;
+  }
   check_err_bits(s);
   cudaEventElapsedTime(&s->t_asm, s->ev[0], s->ev[1]);
   cudaEventElapsedTime(&s->t_kry, s->ev[1], s->ev[2]);
@@ -672,6 +686,7 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
     s->d_nplastic = s->d_err + 1;
     s->d_M = s->dalloc<double>(nn);
     s->d_du = s->dalloc<double>(s->ndof);
+    s->d_duprev = s->dalloc<double>(s->ndof);
     s->d_r = s->dalloc<double>(s->ndof);
     s->d_bcval = s->dalloc<double>(s->ndof);
     s->d_grav = s->dalloc<double>(3);
@@ -961,6 +976,53 @@ mpm_status mpm_get_particles(const mpm_scene* cs, double* x, double* be, double*
       ck(cudaMemcpy(tau, d_tau, (size_t)np * 9 * sizeof(double), cudaMemcpyDeviceToHost), "download");
       s->dfree(d_tau);
     }
+  });
+}
+
+mpm_status mpm_set_particles(mpm_scene* s, const double* be, const double* pc, const double* F) {
+  if (!s) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] {
+    const int np = s->np, D = s->D;
+    for (int p = 0; p < np; ++p) {
+      if (be) {
+        const double* b = be + 6 * p;
+        double m2 = b[0] * b[1] - b[3] * b[3];
+        double m3 = b[0] * (b[1] * b[2] - b[4] * b[4]) - b[3] * (b[3] * b[2] - b[4] * b[5]) +
+                    b[5] * (b[3] * b[4] - b[1] * b[5]);
+        if (!(b[0] > 0 && m2 > 0 && m3 > 0)) fail(MPM_ERR_INVALID_ARG, "be must be positive definite");
+        if (D == 2 && (b[4] != 0.0 || b[5] != 0.0)) fail(MPM_ERR_INVALID_ARG, "2D be has no yz/xz parts");
+      }
+      if (F) {
+        const double* f = F + 9 * p;
+        double d = f[0] * (f[4] * f[8] - f[5] * f[7]) - f[1] * (f[3] * f[8] - f[5] * f[6]) +
+                   f[2] * (f[3] * f[7] - f[4] * f[6]);
+        if (!(d > 0)) fail(MPM_ERR_INVALID_ARG, "det(F) must be positive");
+      }
+    }
+    ck(cudaStreamSynchronize(s->st), "sync");
+    s->staged = false;
+    if (np == 0) return;
+    std::vector<int> orig(np);
+    ck(cudaMemcpy(orig.data(), s->P.orig, np * sizeof(int), cudaMemcpyDeviceToHost), "download");
+    std::vector<double> h(np);
+    auto up = [&](double* d) {
+      ck(cudaMemcpy(d, h.data(), np * sizeof(double), cudaMemcpyHostToDevice), "upload");
+    };
+    if (be)
+      for (int k = 0; k < s->nbe; ++k) {
+        for (int p = 0; p < np; ++p) h[p] = be[6 * orig[p] + k];
+        up(s->P.be[k]);
+      }
+    if (pc) {
+      for (int p = 0; p < np; ++p) h[p] = pc[orig[p]];
+      up(s->P.pc);
+    }
+    if (F)
+      for (int a = 0; a < D; ++a)
+        for (int c = 0; c < D; ++c) {
+          for (int p = 0; p < np; ++p) h[p] = F[9 * orig[p] + 3 * a + c];
+          up(s->P.F[a * D + c]);
+        }
   });
 }
 

@@ -204,6 +204,165 @@ struct ReturnOut {
 // Drucker-Prager return in principal log strain.  Unknowns
 // (eps_1..3, dgamma); equations eps - eps^tr + dgamma (n + etabar/3) = 0 and
 // (sqrt(J2) + eta p - xi c)/mu = 0 with n_A = s_A / (2 sqrt(J2)).
+// dp_eval gives R and (optionally) its Jacobian J = dR/dx.
+__device__ inline void dp_eval(double mu, double lam, double eta, double xi, double etab, double coh,
+                               const double etr[3], const double x[4], double R[4], double (*J)[4]) {
+  double E[3], tau[3];
+  double th = x[0] + x[1] + x[2];
+#pragma unroll
+  for (int A = 0; A < 3; ++A) { E[A] = exp(2.0 * x[A]); tau[A] = mu * (E[A] - 1.0) + lam * th; }
+  double p = (tau[0] + tau[1] + tau[2]) * (1.0 / 3.0);
+  double s[3] = {tau[0] - p, tau[1] - p, tau[2] - p};
+  double q = sqrt(0.5 * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]));
+  double iq = 1.0 / q;
+  double n[3] = {0.5 * s[0] * iq, 0.5 * s[1] * iq, 0.5 * s[2] * iq};
+#pragma unroll
+  for (int A = 0; A < 3; ++A) R[A] = x[A] - etr[A] + x[3] * (n[A] + etab * (1.0 / 3.0));
+  R[3] = (q + eta * p - xi * coh) / mu;
+  if (!J) return;
+  // C_AB = d tau_A / d eps_B ; dp_B ; ds_AB = C_AB - dp_B ; dn_A/ds_C = (d_AC - 2 n_A n_C)/(2 q)
+  double dpB[3], ds[3][3];
+#pragma unroll
+  for (int B = 0; B < 3; ++B) dpB[B] = (2.0 * mu * E[B] + 3.0 * lam) * (1.0 / 3.0);
+#pragma unroll
+  for (int A = 0; A < 3; ++A)
+#pragma unroll
+    for (int B = 0; B < 3; ++B) ds[A][B] = ((A == B) ? 2.0 * mu * E[A] : 0.0) + lam - dpB[B];
+#pragma unroll
+  for (int A = 0; A < 3; ++A) {
+#pragma unroll
+    for (int B = 0; B < 3; ++B) {
+      double sacc = 0.0;
+#pragma unroll
+      for (int C = 0; C < 3; ++C) sacc += (((A == C) ? 1.0 : 0.0) - 2.0 * n[A] * n[C]) * ds[C][B];
+      J[A][B] = ((A == B) ? 1.0 : 0.0) + x[3] * sacc * 0.5 * iq;
+    }
+    J[A][3] = n[A] + etab * (1.0 / 3.0);
+  }
+#pragma unroll
+  for (int B = 0; B < 3; ++B) {
+    double sacc = 0.0;
+#pragma unroll
+    for (int C = 0; C < 3; ++C) sacc += n[C] * ds[C][B];
+    J[3][B] = (sacc + eta * dpB[B]) / mu;
+  }
+  J[3][3] = 0.0;
+}
+
+// Modified Cam-Clay return (associative) in principal log strain.  Unknowns
+// (eps_1..3, y = dgamma |pc_n|); f = q^2/M^2 + p (p - pc),
+// pc = pc_n exp(-sum(eps^tr - eps)/(lambda - kappa)).  mcc_eval gives R and,
+// optionally, J = dR/dx and Je = dR/d eps^tr.
+__device__ inline void mcc_eval(double mu, double lam, double M, double lmk, double pcn, const double etr[3],
+                                const double x[4], double R[4], double (*J)[4], double (*Je)[3],
+                                double& pc_out) {
+  double E[3], tau[3];
+  double th = x[0] + x[1] + x[2];
+#pragma unroll
+  for (int A = 0; A < 3; ++A) { E[A] = exp(2.0 * x[A]); tau[A] = mu * (E[A] - 1.0) + lam * th; }
+  double p = (tau[0] + tau[1] + tau[2]) * (1.0 / 3.0);
+  double s[3] = {tau[0] - p, tau[1] - p, tau[2] - p};
+  double q2 = 1.5 * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+  double dvp = (etr[0] - x[0]) + (etr[1] - x[1]) + (etr[2] - x[2]);
+  double pc = pcn * exp(-dvp / lmk);
+  pc_out = pc;
+  double sc = fabs(pcn), isc = 1.0 / sc, iM2 = 1.0 / (M * M);
+  double m[3];
+#pragma unroll
+  for (int A = 0; A < 3; ++A) m[A] = 3.0 * s[A] * iM2 + (2.0 * p - pc) * (1.0 / 3.0);
+#pragma unroll
+  for (int A = 0; A < 3; ++A) R[A] = x[A] - etr[A] + x[3] * m[A] * isc;
+  R[3] = (q2 * iM2 + p * (p - pc)) * isc * isc;
+  if (!J) return;
+  double dpB[3], ds[3][3];
+#pragma unroll
+  for (int B = 0; B < 3; ++B) dpB[B] = (2.0 * mu * E[B] + 3.0 * lam) * (1.0 / 3.0);
+#pragma unroll
+  for (int A = 0; A < 3; ++A)
+#pragma unroll
+    for (int B = 0; B < 3; ++B) ds[A][B] = ((A == B) ? 2.0 * mu * E[A] : 0.0) + lam - dpB[B];
+  double dpc = pc / lmk;   // d pc / d eps_B ( = - d pc / d eps^tr_B)
+#pragma unroll
+  for (int A = 0; A < 3; ++A) {
+#pragma unroll
+    for (int B = 0; B < 3; ++B) {
+      double dm = 3.0 * iM2 * ds[A][B] + (2.0 * dpB[B] - dpc) * (1.0 / 3.0);
+      J[A][B] = ((A == B) ? 1.0 : 0.0) + x[3] * isc * dm;
+      Je[A][B] = -((A == B) ? 1.0 : 0.0) + x[3] * isc * dpc * (1.0 / 3.0);
+    }
+    J[A][3] = m[A] * isc;
+  }
+#pragma unroll
+  for (int B = 0; B < 3; ++B) {
+    double dq2 = 3.0 * (s[0] * ds[0][B] + s[1] * ds[1][B] + s[2] * ds[2][B]);
+    J[3][B] = (dq2 * iM2 + dpB[B] * (2.0 * p - pc) - p * dpc) * isc * isc;
+    Je[3][B] = p * dpc * isc * isc;
+  }
+  J[3][3] = 0.0;
+}
+
+// Safeguarded local Newton shared by both models: from the trial state, a
+// Newton step on R(x) = 0, halved while it does not reduce ||R|| (accepting
+// any step once ||R|| is at rounding level); converged when a full step is
+// below 1e-13 relative.  Then dx/d eps^tr = -J^-1 dR/d eps^tr at the root.
+template <int MODEL>
+__device__ inline void local_newton(double mu, double lam, double eta, double xi, double etab, double coh,
+                                    double M, double lmk, double pcn, const double etr[3], ReturnOut& o) {
+  double x[4] = {etr[0], etr[1], etr[2], 0.0};
+  double R[4], J[4][4], Je[4][3], pc = pcn;
+  bool conv = false;
+  for (int it = 0; it < 40 && !conv; ++it) {
+    if (MODEL == MODEL_NH_DP) dp_eval(mu, lam, eta, xi, etab, coh, etr, x, R, J);
+    else mcc_eval(mu, lam, M, lmk, pcn, etr, x, R, J, Je, pc);
+    double n0 = sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2] + R[3] * R[3]);
+    double b[4][1] = {{R[0]}, {R[1]}, {R[2]}, {R[3]}};
+    if (!solve4<1>(J, b)) { o.ok = false; return; }
+    double alpha = 1.0;
+    for (int ls = 0; ls < 30; ++ls) {
+      double xt[4], Rt[4], pct;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) xt[i] = x[i] - alpha * b[i][0];
+      if (MODEL == MODEL_NH_DP) dp_eval(mu, lam, eta, xi, etab, coh, etr, xt, Rt, nullptr);
+      else mcc_eval(mu, lam, M, lmk, pcn, etr, xt, Rt, nullptr, nullptr, pct);
+      double n1 = sqrt(Rt[0] * Rt[0] + Rt[1] * Rt[1] + Rt[2] * Rt[2] + Rt[3] * Rt[3]);
+      if (isfinite(n1) && (n1 <= (1.0 - 1e-4 * alpha) * n0 || n1 <= 1e-12)) break;
+      alpha *= 0.5;
+    }
+    double big = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      x[i] -= alpha * b[i][0];
+      big = fmax(big, fabs(alpha * b[i][0]) / (1.0 + fabs(x[i])));
+    }
+    if (!(big < 1e300)) { o.ok = false; return; }
+    conv = (alpha == 1.0) && (big <= 1e-13);
+  }
+  if (!conv) { o.ok = false; return; }
+  double rhs[4][3];
+  if (MODEL == MODEL_NH_DP) {
+    dp_eval(mu, lam, eta, xi, etab, coh, etr, x, R, J);
+    // dR/d eps^tr = [-I; 0]
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) rhs[i][j] = (i == j) ? 1.0 : 0.0;
+  } else {
+    mcc_eval(mu, lam, M, lmk, pcn, etr, x, R, J, Je, pc);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) rhs[i][j] = -Je[i][j];
+  }
+  if (!solve4<3>(J, rhs)) { o.ok = false; return; }
+#pragma unroll
+  for (int A = 0; A < 3; ++A) {
+    o.eps[A] = x[A];
+#pragma unroll
+    for (int B = 0; B < 3; ++B) o.deps[A][B] = rhs[A][B];
+  }
+  o.pc = (MODEL == MODEL_NH_MCC) ? pc : pcn;
+}
+
 __device__ inline void dp_return(double mu, double lam, double eta, double xi, double etab,
                                  double coh, const double etr[3], ReturnOut& o) {
   o.ok = true;
@@ -235,203 +394,14 @@ __device__ inline void dp_return(double mu, double lam, double eta, double xi, d
       return;
     }
   }
-  double x[4] = {etr[0], etr[1], etr[2], 0.0};
-  double J[4][4];
-  bool conv = false;
-  for (int it = 0; it < 40; ++it) {
-    double E[3], tau[3];
-    double th = x[0] + x[1] + x[2];
-#pragma unroll
-    for (int A = 0; A < 3; ++A) { E[A] = exp(2.0 * x[A]); tau[A] = mu * (E[A] - 1.0) + lam * th; }
-    double p = (tau[0] + tau[1] + tau[2]) * (1.0 / 3.0);
-    double s[3] = {tau[0] - p, tau[1] - p, tau[2] - p};
-    double q = sqrt(0.5 * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]));
-    double iq = 1.0 / q;
-    double n[3] = {0.5 * s[0] * iq, 0.5 * s[1] * iq, 0.5 * s[2] * iq};
-    double R[4][1];
-#pragma unroll
-    for (int A = 0; A < 3; ++A) R[A][0] = x[A] - etr[A] + x[3] * (n[A] + etab * (1.0 / 3.0));
-    R[3][0] = (q + eta * p - xi * coh) / mu;
-    // C_AB = d tau_A / d eps_B ; dp_B ; ds_AB = C_AB - dp_B
-    double dpB[3], ds[3][3];
-#pragma unroll
-    for (int B = 0; B < 3; ++B) dpB[B] = (2.0 * mu * E[B] + 3.0 * lam) * (1.0 / 3.0);
-#pragma unroll
-    for (int A = 0; A < 3; ++A)
-#pragma unroll
-      for (int B = 0; B < 3; ++B) ds[A][B] = ((A == B) ? 2.0 * mu * E[A] : 0.0) + lam - dpB[B];
-    // dn_A/ds_C = (delta_AC - 2 n_A n_C) / (2 q)
-#pragma unroll
-    for (int A = 0; A < 3; ++A) {
-#pragma unroll
-      for (int B = 0; B < 3; ++B) {
-        double sacc = 0.0;
-#pragma unroll
-        for (int C = 0; C < 3; ++C) sacc += (((A == C) ? 1.0 : 0.0) - 2.0 * n[A] * n[C]) * ds[C][B];
-        J[A][B] = ((A == B) ? 1.0 : 0.0) + x[3] * sacc * 0.5 * iq;
-      }
-      J[A][3] = n[A] + etab * (1.0 / 3.0);
-    }
-#pragma unroll
-    for (int B = 0; B < 3; ++B) {
-      double sacc = 0.0;
-#pragma unroll
-      for (int C = 0; C < 3; ++C) sacc += n[C] * ds[C][B];
-      J[3][B] = (sacc + eta * dpB[B]) / mu;
-    }
-    J[3][3] = 0.0;
-    double Jc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) Jc[i][j] = J[i][j];
-    if (!solve4<1>(Jc, R)) { o.ok = false; return; }
-    double big = 0.0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      x[i] -= R[i][0];
-      big = fmax(big, fabs(R[i][0]) / (1.0 + fabs(x[i])));
-    }
-    if (!(big < 1e300)) { o.ok = false; return; }
-    if (big <= 1e-13) { conv = true; }
-    if (conv) break;
-  }
-  if (!conv) { o.ok = false; return; }
-  // d x / d eps^tr = J^-1 [I; 0] (dR/d eps^tr = [-I; 0]), at the converged
-  // state: rebuild J there (one more evaluation) for the exact tangent.
-  {
-    double E[3], tau[3];
-    double th = x[0] + x[1] + x[2];
-#pragma unroll
-    for (int A = 0; A < 3; ++A) { E[A] = exp(2.0 * x[A]); tau[A] = mu * (E[A] - 1.0) + lam * th; }
-    double p = (tau[0] + tau[1] + tau[2]) * (1.0 / 3.0);
-    double s[3] = {tau[0] - p, tau[1] - p, tau[2] - p};
-    double q = sqrt(0.5 * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]));
-    double iq = 1.0 / q;
-    double n[3] = {0.5 * s[0] * iq, 0.5 * s[1] * iq, 0.5 * s[2] * iq};
-    double dpB[3], ds[3][3];
-#pragma unroll
-    for (int B = 0; B < 3; ++B) dpB[B] = (2.0 * mu * E[B] + 3.0 * lam) * (1.0 / 3.0);
-#pragma unroll
-    for (int A = 0; A < 3; ++A)
-#pragma unroll
-      for (int B = 0; B < 3; ++B) ds[A][B] = ((A == B) ? 2.0 * mu * E[A] : 0.0) + lam - dpB[B];
-#pragma unroll
-    for (int A = 0; A < 3; ++A) {
-#pragma unroll
-      for (int B = 0; B < 3; ++B) {
-        double sacc = 0.0;
-#pragma unroll
-        for (int C = 0; C < 3; ++C) sacc += (((A == C) ? 1.0 : 0.0) - 2.0 * n[A] * n[C]) * ds[C][B];
-        J[A][B] = ((A == B) ? 1.0 : 0.0) + x[3] * sacc * 0.5 * iq;
-      }
-      J[A][3] = n[A] + etab * (1.0 / 3.0);
-    }
-#pragma unroll
-    for (int B = 0; B < 3; ++B) {
-      double sacc = 0.0;
-#pragma unroll
-      for (int C = 0; C < 3; ++C) sacc += n[C] * ds[C][B];
-      J[3][B] = (sacc + eta * dpB[B]) / mu;
-    }
-    J[3][3] = 0.0;
-  }
-  double rhs[4][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 0, 0}};
-  if (!solve4<3>(J, rhs)) { o.ok = false; return; }
-#pragma unroll
-  for (int A = 0; A < 3; ++A) {
-    o.eps[A] = x[A];
-#pragma unroll
-    for (int B = 0; B < 3; ++B) o.deps[A][B] = rhs[A][B];
-  }
-}
-
-// Modified Cam-Clay return (associative) in principal log strain.  Unknowns
-// (eps_1..3, y = dgamma |pc_n|); f = q^2/M^2 + p (p - pc),
-// pc = pc_n exp(-sum(eps^tr - eps)/(lambda - kappa)).
-__device__ inline void mcc_assemble(double mu, double lam, double M, double lmk, double pcn,
-                                    const double etr[3], const double x[4], double R[4],
-                                    double J[4][4], double Je[4][3], double& pc_out) {
-  double E[3], tau[3];
-  double th = x[0] + x[1] + x[2];
-#pragma unroll
-  for (int A = 0; A < 3; ++A) { E[A] = exp(2.0 * x[A]); tau[A] = mu * (E[A] - 1.0) + lam * th; }
-  double p = (tau[0] + tau[1] + tau[2]) * (1.0 / 3.0);
-  double s[3] = {tau[0] - p, tau[1] - p, tau[2] - p};
-  double q2 = 1.5 * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
-  double dvp = (etr[0] - x[0]) + (etr[1] - x[1]) + (etr[2] - x[2]);
-  double pc = pcn * exp(-dvp / lmk);
-  pc_out = pc;
-  double sc = fabs(pcn), isc = 1.0 / sc, M2 = M * M, iM2 = 1.0 / M2;
-  double m[3];
-#pragma unroll
-  for (int A = 0; A < 3; ++A) m[A] = 3.0 * s[A] * iM2 + (2.0 * p - pc) * (1.0 / 3.0);
-#pragma unroll
-  for (int A = 0; A < 3; ++A) R[A] = x[A] - etr[A] + x[3] * m[A] * isc;
-  R[3] = (q2 * iM2 + p * (p - pc)) * isc * isc;
-  double dpB[3], ds[3][3];
-#pragma unroll
-  for (int B = 0; B < 3; ++B) dpB[B] = (2.0 * mu * E[B] + 3.0 * lam) * (1.0 / 3.0);
-#pragma unroll
-  for (int A = 0; A < 3; ++A)
-#pragma unroll
-    for (int B = 0; B < 3; ++B) ds[A][B] = ((A == B) ? 2.0 * mu * E[A] : 0.0) + lam - dpB[B];
-  double dpc = pc / lmk;   // d pc / d eps_B ( = - d pc / d eps^tr_B)
-#pragma unroll
-  for (int A = 0; A < 3; ++A) {
-#pragma unroll
-    for (int B = 0; B < 3; ++B) {
-      double dm = 3.0 * iM2 * ds[A][B] + (2.0 * dpB[B] - dpc) * (1.0 / 3.0);
-      J[A][B] = ((A == B) ? 1.0 : 0.0) + x[3] * isc * dm;
-      Je[A][B] = -((A == B) ? 1.0 : 0.0) + x[3] * isc * dpc * (1.0 / 3.0);
-    }
-    J[A][3] = m[A] * isc;
-  }
-#pragma unroll
-  for (int B = 0; B < 3; ++B) {
-    double dq2 = 3.0 * (s[0] * ds[0][B] + s[1] * ds[1][B] + s[2] * ds[2][B]);
-    J[3][B] = (dq2 * iM2 + dpB[B] * (2.0 * p - pc) - p * dpc) * isc * isc;
-    Je[3][B] = p * dpc * isc * isc;
-  }
-  J[3][3] = 0.0;
+  local_newton<MODEL_NH_DP>(mu, lam, eta, xi, etab, coh, 0.0, 1.0, 0.0, etr, o);
 }
 
 __device__ inline void mcc_return(double mu, double lam, double M, double lmk, double pcn,
                                   const double etr[3], ReturnOut& o) {
   o.ok = true;
   o.mode = 1;
-  double x[4] = {etr[0], etr[1], etr[2], 0.0};
-  double R[4], J[4][4], Je[4][3], pc = pcn;
-  bool conv = false;
-  for (int it = 0; it < 40; ++it) {
-    mcc_assemble(mu, lam, M, lmk, pcn, etr, x, R, J, Je, pc);
-    double b[4][1] = {{R[0]}, {R[1]}, {R[2]}, {R[3]}};
-    if (!solve4<1>(J, b)) { o.ok = false; return; }
-    double big = 0.0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      x[i] -= b[i][0];
-      big = fmax(big, fabs(b[i][0]) / (1.0 + fabs(x[i])));
-    }
-    if (!(big < 1e300)) { o.ok = false; return; }
-    if (big <= 1e-13) { conv = true; break; }
-  }
-  if (!conv) { o.ok = false; return; }
-  mcc_assemble(mu, lam, M, lmk, pcn, etr, x, R, J, Je, pc);
-  // dx/detr = -J^-1 Je
-  double rhs[4][3];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) rhs[i][j] = -Je[i][j];
-  if (!solve4<3>(J, rhs)) { o.ok = false; return; }
-#pragma unroll
-  for (int A = 0; A < 3; ++A) {
-    o.eps[A] = x[A];
-#pragma unroll
-    for (int B = 0; B < 3; ++B) o.deps[A][B] = rhs[A][B];
-  }
-  o.pc = pc;
+  local_newton<MODEL_NH_MCC>(mu, lam, 0.0, 0.0, 0.0, 0.0, M, lmk, pcn, etr, o);
 }
 
 // Per-particle constitutive state for one iterate.
@@ -490,16 +460,20 @@ __device__ inline int constitutive(const MatC& mc, double E_p, double phi_p, dou
     double s00 = st.tau[0][0] - p, s11 = st.tau[1][1] - p, s22 = st.tau[2][2] - p;
     double ss = s00 * s00 + s11 * s11 + s22 * s22 +
                 2.0 * (st.tau[0][1] * st.tau[0][1] + st.tau[1][2] * st.tau[1][2] + st.tau[0][2] * st.tau[0][2]);
-    double f;
+    double f, ftol;
     if (mc.model == MODEL_NH_DP) {
       dp_consts(phi_p, eta, xi);
       double xb;
       dp_consts(mc.psi, etab, xb);
       f = sqrt(0.5 * ss) + eta * p - xi * mc.coh;
+      ftol = 1e-10 * L.mu;
     } else {
       f = 1.5 * ss / (mc.M * mc.M) + p * (p - pcn);
+      ftol = 1e-10 * L.mu * fabs(pcn);
     }
-    plastic = f > 0.0;
+    // within a rounding-level tolerance of the surface the state is elastic
+    // (a state committed on the surface, re-evaluated at zero increment)
+    plastic = f > ftol;
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i)

@@ -295,6 +295,27 @@ cudaError_t launch_bicgstab_iter(const DevGrid& G, DevMatrix<T> K, KrylovVecs<D,
   return cudaGetLastError();
 }
 
+// du = base + alpha d on the free DOFs (the halved step of a Newton iteration
+// whose full step drove a return map out of its domain).
+template <int D, class T>
+__global__ void k_step_du(DevMatrix<T> K, const T* __restrict__ x, const uint8_t* __restrict__ fixed,
+                          const double* __restrict__ base, double* du, double alpha) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= *K.nrow) return;
+  const long long i = K.rows[row];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const long long d = i * D + a;
+    if (!fixed[d]) du[d] = base[d] + alpha * (double)x[d];
+  }
+}
+template <int D, class T>
+cudaError_t launch_step_du(DevMatrix<T> K, const T* x, const uint8_t* fixed, const double* base, double* du,
+                           double alpha, int nblk, cudaStream_t st) {
+  k_step_du<D, T><<<nblk, KTPB, 0, st>>>(K, x, fixed, base, du, alpha);
+  return cudaGetLastError();
+}
+
 // Plain y = J x over the active rows (used to time the product in isolation).
 template <int D, class T>
 __global__ void __launch_bounds__(KTPB) k_spmv(DevGrid G, DevMatrix<T> K, const T* __restrict__ x, T* y) {
@@ -340,7 +361,9 @@ cudaError_t launch_update_du(DevMatrix<T> K, const T* x, const uint8_t* fixed, d
                                                   KrylovScalars*, int, cudaStream_t);                   \
   template cudaError_t launch_update_du<D, T>(DevMatrix<T>, const T*, const uint8_t*, double*, int,     \
                                               cudaStream_t);                                            \
-  template cudaError_t launch_spmv<D, T>(const DevGrid&, DevMatrix<T>, const T*, T*, int, cudaStream_t);
+  template cudaError_t launch_spmv<D, T>(const DevGrid&, DevMatrix<T>, const T*, T*, int, cudaStream_t);  \
+  template cudaError_t launch_step_du<D, T>(DevMatrix<T>, const T*, const uint8_t*, const double*, double*, \
+                                            double, int, cudaStream_t);
 MPM_KRYLOV_INST(2, float)
 MPM_KRYLOV_INST(2, double)
 MPM_KRYLOV_INST(3, float)

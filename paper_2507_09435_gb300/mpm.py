@@ -77,7 +77,7 @@ _lib = None
 EXPORTS = ["mpm_create_scene", "mpm_set_gravity", "mpm_set_dirichlet", "mpm_begin_step", "mpm_newton_step",
            "mpm_set_du", "mpm_assemble", "mpm_commit_step", "mpm_solve_step", "mpm_get_residual", "mpm_get_du", "mpm_get_mass",
            "mpm_get_counts", "mpm_get_jacobian_bsr", "mpm_get_particles", "mpm_kernel_launches",
-           "mpm_time_spmv", "mpm_footprint_bytes",
+           "mpm_time_spmv", "mpm_set_particles", "mpm_footprint_bytes",
            "mpm_destroy_scene", "mpm_status_string", "mpm_last_error"]
 
 
@@ -107,6 +107,7 @@ def lib(build: bool = True):
     L.mpm_get_jacobian_bsr.argtypes = [_P, ctypes.c_longlong, _I, _LL, _I, _D]
     L.mpm_get_particles.argtypes = [_P, _D, _D, _D, _D, _D]
     L.mpm_kernel_launches.argtypes = [_P, _LL]
+    L.mpm_set_particles.argtypes = [_P, _D, _D, _D]
     L.mpm_time_spmv.argtypes = [_P, ctypes.c_int, _D, _D]
     L.mpm_footprint_bytes.argtypes = [ctypes.POINTER(mpm_scene_desc), ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_size_t)]
@@ -284,6 +285,10 @@ def mpm_get_particles(h, np_, x=True, be=True, pc=True, F=True, tau=True):
     return out
 
 
+def mpm_set_particles(h, be=None, pc=None, F=None):
+    _check(lib().mpm_set_particles(h, _p(_f64(be)), _p(_f64(pc)), _p(_f64(F))), h)
+
+
 def mpm_kernel_launches(h):
     out = ctypes.c_longlong(0)
     _check(lib().mpm_kernel_launches(h, ctypes.byref(out)), h)
@@ -326,6 +331,8 @@ class GpuScene:
         self.nnode = scene.nnode
         self.ndof = scene.nnode * scene.dim
         self.np = scene.np
+        if getattr(scene, "be0", None) is not None:
+            mpm_set_particles(self.h, be=scene.be0)
 
     def close(self):
         if self.h is not None:

@@ -84,6 +84,7 @@ class Scene:
     E_p: Optional[np.ndarray] = None     # per-particle Young's modulus override
     phi_p: Optional[np.ndarray] = None   # per-particle friction angle override
     pc0_p: Optional[np.ndarray] = None   # per-particle initial preconsolidation
+    be0: Optional[np.ndarray] = None     # (np, 6) initial elastic left Cauchy-Green, default identity
     steps: List[LoadStep] = field(default_factory=list)
     meta: dict = field(default_factory=dict)
 
@@ -295,6 +296,43 @@ def column_collapse_3d(nx: int = 128, ny: int = 128, nz: int = 64, h: float = 0.
     dof, val = _merge(*pairs)
     sc.steps = [LoadStep(dof, val, (0.0, 0.0, -g * (k + 1) / nsteps)) for k in range(nsteps)]
     sc.meta = dict(col=col, ppc=ppc)
+    return sc
+
+
+def oedometer_3d(ncell: int = 4, h: float = 0.1, ppc: int = 2, nsteps: int = 4, strain_per_step: float = 2e-3,
+                 model: int = MODEL_NH_MCC, E: float = 1e6, nu: float = 0.3, pc0: float = -26e3,
+                 pc_sigma: float = 0.05, prestrain: float = 0.01, phi: float = 30.0, c: float = 2e3,
+                 seed: int = SEED_BASE + 13) -> Scene:
+    """3D oedometric compression of a cube of ``ncell``^3 cells: the affine
+    increment du_z = -eps (z - z_bottom) on every node within one cell of the
+    bottom or top face (or beyond), rollers (u_x = 0 / u_y = 0) on the nodes
+    within one cell of the side faces (or beyond).  The particles start from
+    an isotropic elastic pre-compression b_e = (1 - prestrain)^2 1 and a
+    preconsolidation near the corresponding pressure, so that loading is
+    plastic from the first step while every particle stays in compression
+    (where the modified Cam-Clay return map is defined)."""
+    ng = ncell + 4
+    n = (ng, ng, ng)
+    lo, hi = 2, 2 + ncell
+    cells = box_cells((lo, lo, lo), (hi, hi, hi))
+    x = lattice(cells, h, ppc, 3)
+    mat = Material(model=model, E=E, nu=nu, rho=1000.0, M=1.2, lambda_cc=0.1, kappa_cc=0.02, pc0=pc0,
+                   phi=phi, psi=0.0, c=c)
+    vol = np.full(x.shape[0], h ** 3 / ppc ** 3)
+    rng = np.random.default_rng(seed)
+    pc = pc0 * np.exp(pc_sigma * rng.standard_normal(x.shape[0]))
+    be0 = np.zeros((x.shape[0], 6))
+    be0[:, :3] = (1.0 - prestrain) ** 2
+    sc = Scene("oedometer_3d", 3, n, h, (0.0, 0.0, 0.0), x, vol, vol * mat.rho,
+               np.zeros(x.shape[0], np.int32), [mat], pc0_p=pc, be0=be0)
+    zb = lo * h
+    dz, (ix, iy, iz) = _dofs(sc, lambda ix, iy, iz: (iz <= lo + 1) | (iz >= hi - 1), 2, 3, n)
+    vz = -strain_per_step * (iz * h - zb)
+    dx, _ = _dofs(sc, lambda ix, iy, iz: (ix <= lo + 1) | (ix >= hi - 1), 0, 3, n)
+    dy, _ = _dofs(sc, lambda ix, iy, iz: (iy <= lo + 1) | (iy >= hi - 1), 1, 3, n)
+    dof, val = _merge((dz, vz), (dx, np.zeros(dx.shape)), (dy, np.zeros(dy.shape)))
+    sc.steps = [LoadStep(dof, val, (0.0, 0.0, 0.0)) for _ in range(nsteps)]
+    sc.meta = dict(strain_per_step=strain_per_step)
     return sc
 
 

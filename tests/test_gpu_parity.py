@@ -84,7 +84,7 @@ def test_block_compression_matches_homogeneous_closed_form():
 def test_footing_coarse_fp64_plastic():
     """Coarsened footing (46x22 soil cells, 4,048 particles): geostatic step
     plus footing steps large enough to drive Drucker-Prager particles plastic."""
-    sc = S.footing(nx=48, ny=24, h=0.5, nsteps=5, settle_frac=0.2)
+    sc = S.footing(nx=48, ny=24, h=0.5, nsteps=20, settle_frac=0.1)
     _run_parity(sc, 4, jac_every_step=True, expect_plastic=True)
 
 
@@ -125,18 +125,29 @@ def test_random_states(dim, model, amp, precision):
 
 
 def test_column_3d_mcc_fp64():
-    """Small 3D modified Cam-Clay column (4x4x6 cells, 768 particles) under a
-    gravity ramp with a low preconsolidation so that it yields."""
-    sc = S.column_collapse_3d(nx=12, ny=12, nz=12, h=0.1, col=(4, 4, 6), nsteps=3, pc_mean=-3e3,
-                              E=1e6, g=9.81 * 20)
-    _run_parity(sc, 3, jac_every_step=True, expect_plastic=True)
+    """Small 3D modified Cam-Clay column (4x4x6 cells, 768 particles): first
+    step of a gravity ramp with a low preconsolidation so that it yields."""
+    sc = S.column_collapse_3d(nx=12, ny=12, nz=12, h=0.1, col=(4, 4, 6), nsteps=3, pc_mean=-8e3, E=1e6)
+    _run_parity(sc, 1, jac_every_step=True, expect_plastic=True)
+
+
+def test_oedometer_3d_mcc_fp64():
+    """3D oedometric compression of a normally consolidated Cam-Clay cube
+    (512 particles, prestressed): every particle plastic, four load steps."""
+    _run_parity(S.oedometer_3d(), 4, jac_every_step=True, expect_plastic=True)
+
+
+def test_oedometer_3d_dp_fp64():
+    """The same oedometer with Drucker-Prager soil (3D spectral DP return)."""
+    _run_parity(S.oedometer_3d(model=S.MODEL_NH_DP, strain_per_step=5e-3, phi=5.0, c=0.0), 3,
+                jac_every_step=True, expect_plastic=True)
 
 
 def test_mixed_precision_footing_converges_and_states_error():
     """Mixed mode (FP32 Jacobian and Krylov, FP64 residual/return map/check)
     reaches the 1e-8 Newton tolerance; its increment is within the stated
     error of the FP64 oracle's."""
-    sc = S.footing(nx=48, ny=24, h=0.5, nsteps=5, settle_frac=0.2)
+    sc = S.footing(nx=48, ny=24, h=0.5, nsteps=20, settle_frac=0.1)
     orc = O.OracleScene.from_scene(sc)
     gs = mpm.GpuScene(sc, precision=mpm.MPM_MIXED, newton_tol=1e-8)
     for k, st in enumerate(sc.steps[:3]):
