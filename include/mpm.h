@@ -79,7 +79,7 @@ typedef struct {
   int newton_maxit;
   int forcing;             /* MPM_FORCING_FIXED: linear rtol = krylov_rtol;
                               MPM_FORCING_EW: Eisenstat-Walker choice 2,
-                              clamped to [krylov_rtol, 0.1]                      */
+                              clamped to [krylov_rtol, 0.01]                     */
   double krylov_rtol;
   int krylov_maxit;
 } mpm_scene_desc;

@@ -352,11 +352,14 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
   DevMatrix<T> K = matview<T>(s);
   cudaEventRecord(s->ev[0], st);
   assemble_impl<D, T>(s);
-  // linear tolerance: fixed, or Eisenstat-Walker choice 2 (gamma 0.9, alpha 2)
+  // linear tolerance: fixed, or Eisenstat-Walker choice 2 (gamma 0.9,
+  // alpha 2) capped at ETA_MAX = 1e-2: with the classical cap of 0.1 loose
+  // steps through the plastic zone made Newton diverge on footing problems.
   double eta = s->desc.krylov_rtol;
   if (s->desc.forcing == MPM_FORCING_EW) {
+    constexpr double ETA_MAX = 1e-2;
     if (s->k == 0) {
-      eta = 0.1;
+      eta = ETA_MAX;
     } else {
       double ratio = s->rk / s->rprev;
       eta = 0.9 * ratio * ratio;
@@ -365,7 +368,7 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
     }
     // no need to solve below what the Newton tolerance asks of this step
     eta = std::max(eta, 0.5 * s->desc.newton_tol * s->r0 / std::max(s->rk, 1e-300));
-    eta = std::min(std::max(eta, s->desc.krylov_rtol), 0.1);
+    eta = std::min(std::max(eta, s->desc.krylov_rtol), ETA_MAX);
   }
   s->eta_prev = eta;
   const int nblk = (s->cap + KTPB - 1) / KTPB;

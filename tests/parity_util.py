@@ -1,6 +1,7 @@
 """Comparison helpers for the GPU-vs-oracle parity tests.
 
-Tolerances (SURVEY readings, written out here so the tests state them):
+Tolerances (the parity bar of the CUDA path, written out here so the tests
+state them):
 * residual: max |r_gpu - r_oracle| over free DOFs divided by the largest
   per-DOF sum of absolute particle contributions (the scale at which the
   summation rounds): 1e-10;

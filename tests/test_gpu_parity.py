@@ -153,7 +153,8 @@ def test_mixed_precision_footing_converges_and_states_error():
     for k, st in enumerate(sc.steps[:3]):
         gs.set_step(st)
         rep = mpm.mpm_solve_step(gs.h, check=False)
-        assert rep.converged, [rep.hist[i] for i in range(rep.newton_iters + 1)]
+        assert rep.converged, (rep.status, mpm.lib().mpm_last_error(gs.h).decode(),
+                               [rep.hist[i] for i in range(rep.newton_iters + 1)])
         assert rep.rel_residual <= 1e-8
         out = orc.solve_step(st.dof, st.value, st.gravity, tol=1e-12)
         part = gs.particles()
