@@ -212,6 +212,33 @@ mpm_status mpm_time_spmv(mpm_scene* s, int reps, double* ms_per_launch, double* 
  * MPM_ERR_INVALID_ARG for a non-positive-definite be or det(F) <= 0. */
 mpm_status mpm_set_particles(mpm_scene* s, const double* be, const double* pc, const double* F);
 
+/* Free-DOF residual norm that allocates nothing (the paper has no counterpart;
+ * this is a convenience of this library).  For callers that cannot call
+ * cudaMalloc where they need the Newton convergence check: code running while
+ * a host framework owns every device allocation, or a loop that forbids
+ * allocation after start-up.
+ *   r      device pointer, nnode*dim FP64 residual on the dense node grid
+ *   rows   device pointer, nrow int32 node indices (the rows to include)
+ *   fixed  device pointer, nnode*dim uint8 prescribed-DOF flags (1 = skip)
+ *   out_norm  host pointer, receives sqrt(sum of r^2 over the free DOFs)
+ *   stream cudaStream_t to run on (NULL = legacy default stream); the call
+ *          synchronises this stream before returning.
+ * Its only scratch is a file-scope device array of 8192 FP64 partial sums
+ * (64 KiB per GPU that loads the library, held until exit), so nrow is
+ * limited to 8192*256 = 2,097,152 rows; larger nrow returns
+ * MPM_ERR_INVALID_ARG.  No cudaMalloc, cudaFree or allocating library call is
+ * made.  The first call on a device looks up that array's device address with
+ * cudaGetSymbolAddress (once per device, with that device current): make that
+ * first call before any stream capture.  Every call shares the array, so
+ * calls that overlap on the GPU race; order them on one stream or with events.
+ * Errors: MPM_ERR_INVALID_ARG, MPM_ERR_CUDA; message from
+ * mpm_noalloc_last_error. */
+mpm_status mpm_residual_norm_noalloc(const double* r, const int* rows, int nrow,
+                                     const unsigned char* fixed, int dim, double* out_norm,
+                                     void* stream);
+/* Message of the last failed mpm_residual_norm_noalloc call on this thread. */
+const char* mpm_noalloc_last_error(void);
+
 /* Device memory a scene of this size would take (for admission control). */
 mpm_status mpm_footprint_bytes(const mpm_scene_desc* desc, int np, size_t* out);
 

@@ -77,7 +77,8 @@ _lib = None
 EXPORTS = ["mpm_create_scene", "mpm_set_gravity", "mpm_set_dirichlet", "mpm_begin_step", "mpm_newton_step",
            "mpm_set_du", "mpm_assemble", "mpm_commit_step", "mpm_solve_step", "mpm_get_residual", "mpm_get_du", "mpm_get_mass",
            "mpm_get_counts", "mpm_get_jacobian_bsr", "mpm_get_particles", "mpm_kernel_launches",
-           "mpm_time_spmv", "mpm_set_particles", "mpm_footprint_bytes",
+           "mpm_time_spmv", "mpm_set_particles", "mpm_residual_norm_noalloc", "mpm_noalloc_last_error",
+           "mpm_footprint_bytes",
            "mpm_destroy_scene", "mpm_status_string", "mpm_last_error"]
 
 
@@ -108,6 +109,9 @@ def lib(build: bool = True):
     L.mpm_get_particles.argtypes = [_P, _D, _D, _D, _D, _D]
     L.mpm_kernel_launches.argtypes = [_P, _LL]
     L.mpm_set_particles.argtypes = [_P, _D, _D, _D]
+    L.mpm_residual_norm_noalloc.argtypes = [_P, _P, ctypes.c_int, _P, ctypes.c_int, _D, _P]
+    L.mpm_noalloc_last_error.argtypes = []
+    L.mpm_noalloc_last_error.restype = ctypes.c_char_p
     L.mpm_time_spmv.argtypes = [_P, ctypes.c_int, _D, _D]
     L.mpm_footprint_bytes.argtypes = [ctypes.POINTER(mpm_scene_desc), ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_size_t)]
@@ -118,7 +122,7 @@ def lib(build: bool = True):
     L.mpm_last_error.argtypes = [_P]
     L.mpm_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("mpm_destroy_scene", "mpm_status_string", "mpm_last_error"):
+        if name not in ("mpm_destroy_scene", "mpm_status_string", "mpm_last_error", "mpm_noalloc_last_error"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -287,6 +291,17 @@ def mpm_get_particles(h, np_, x=True, be=True, pc=True, F=True, tau=True):
 
 def mpm_set_particles(h, be=None, pc=None, F=None):
     _check(lib().mpm_set_particles(h, _p(_f64(be)), _p(_f64(pc)), _p(_f64(F))), h)
+
+
+def mpm_residual_norm_noalloc(r_dev, rows_dev, nrow, fixed_dev, dim, stream=None):
+    """Free-DOF residual norm from caller-owned device buffers (integer device
+    addresses), using no device allocation; see include/mpm.h."""
+    out = ctypes.c_double(0)
+    rc = lib().mpm_residual_norm_noalloc(_P(r_dev), _P(rows_dev), int(nrow), _P(fixed_dev), int(dim),
+                                         ctypes.byref(out), _P(stream) if stream else None)
+    if rc != MPM_OK:
+        raise MPMError(rc, lib().mpm_noalloc_last_error().decode())
+    return out.value
 
 
 def mpm_kernel_launches(h):
