@@ -263,15 +263,27 @@ def main():
     newton_all, krylov_all = float(tt[1]), float(tt[2])
     value = newton_all / (t_all / 1e3)
 
-    # ---- dominant kernel (Jacobian-vector product), timed live ---------------
+    # ---- dominant kernel: the persistent BiCGStab solve, timed live ----------
+    # achieved = algorithmic bytes of all timed Krylov iterations / the
+    # CUDA-event time of the Krylov phases (one cooperative launch per Newton
+    # iteration).  Bytes per iteration: two stencil-BSR products (present
+    # blocks + input/output vectors + row list) + 19 vector passes of the
+    # BLAS-1 phases + two block-Jacobi applications.
     gs.begin(next_step())
+    na, _ = mpm.mpm_get_counts(gs.h)
     spmv_ms, spmv_bytes = mpm.mpm_time_spmv(gs.h, 200)
+    tsz = 4 if args.precision == "mixed" else 8
+    bytes_iter = 2 * spmv_bytes + 19 * na * sc.dim * tsz + 2 * na * sc.dim * sc.dim * tsz
     peaks, src = read_peaks()
-    achieved = spmv_bytes / (spmv_ms * 1e-3) / 1e9
-    roof = {"kernel": "k_bicg_2/k_bicg_4 (stencil-BSR SpMV)", "bound": "hbm", "achieved": achieved,
-            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-            "peak_source": src, "bytes_per_launch": spmv_bytes, "ms_per_launch": spmv_ms,
-            "note": "matrix is L2-resident at this size (about 13 MB FP32)"}
+    t_kry_s = phase[3] * 1e-3
+    achieved = (krylov / max(newton, 1)) * newton * bytes_iter / max(t_kry_s, 1e-12) / 1e9
+    roof = {"kernel": "k_bicg_persistent (whole BiCGStab solve, one cooperative launch per Newton iteration)",
+            "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+            "bytes_per_iteration": bytes_iter, "us_per_iteration": 1e6 * t_kry_s / max(krylov, 1),
+            "spmv_alone": {"kernel": "k_spmv", "ms_per_launch": spmv_ms, "bytes_per_launch": spmv_bytes,
+                           "gbs": spmv_bytes / (spmv_ms * 1e-3) / 1e9},
+            "note": "2D footing matrix (about 13.6 MB FP32) is L2-resident; HBM fraction is not the bound here"}
 
     # ---- end to end through the C ABI with host buffers ----------------------
     e2e = None

@@ -8,6 +8,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -82,6 +83,8 @@ struct mpm_scene {
   long long launches = 0;   // kernels launched by this scene
   long long halvings = 0;   // Newton steps halved after a return-map failure
   double* d_duprev = nullptr;
+  int pblocks = 0;          // co-resident blocks for the persistent Krylov kernel (0 = use graphs)
+  GridBarrier* d_bar = nullptr;
   std::string err;
 
   template <class T>
@@ -112,6 +115,7 @@ mpm_status map_err_bits(int bits, std::string& msg) {
   if (bits & ERRF_BOUNDS) { msg = "a particle's B-spline support left the grid"; return MPM_ERR_BOUNDS; }
   if (bits & ERRF_RETURN) { msg = "return-map local Newton did not converge"; return MPM_ERR_RETURN_MAP; }
   if (bits & (ERRF_NONFINITE | ERRF_DET)) { msg = "non-finite value or non-positive det(F)"; return MPM_ERR_NONFINITE; }
+  if (bits & ERRF_BARRIER) { msg = "grid barrier of the persistent Krylov kernel timed out"; return MPM_ERR_TIMEOUT; }
   return MPM_OK;
 }
 
@@ -377,9 +381,19 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
   double tol2 = eta * eta * s->rk * s->rk;
   ck(launch_bicgstab_init<D, T>(K, s->d_r, s->d_fixed, v, s->d_S, tol2, s->desc.krylov_maxit, nblk, st),
      "krylov init");
-  if (s->use_graph && s->graph_cap != s->cap) build_graph<D, T>(s, nblk);
+  const int pblk = std::min(s->pblocks, std::max(1, (s->nrow * 4 + KTPB - 1) / KTPB));
+  if (s->pblocks > 0) {
+    // whole solve in one cooperative launch
+    ck(launch_bicgstab_persistent<D, T>(s->G, K, v, s->d_S, s->d_bar, s->d_err, pblk, st), "persistent krylov");
+    s->launches += 1;
+    ck(cudaMemcpyAsync(s->h_S, s->d_S, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st), "copy S");
+    ck(cudaMemcpyAsync(s->h_int + 2, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "copy err");
+    ck(cudaStreamSynchronize(st), "sync");
+    check_err_bits(s);
+  }
+  if (s->pblocks == 0 && s->use_graph && s->graph_cap != s->cap) build_graph<D, T>(s, nblk);
   int launched = 0;
-  for (;;) {
+  for (; s->pblocks == 0;) {
     if (s->use_graph) {
       ck(cudaGraphLaunch(s->gexec, st), "graph launch");
     } else {
@@ -709,6 +723,19 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
     else s->d_vec = s->dalloc<double>(9 * s->vlen);
     ck(cudaMemsetAsync(s->d_vec, 0, 9 * s->vlen * T, s->st), "memset");
     s->d_S = s->dalloc<KrylovScalars>(1);
+    s->d_bar = s->dalloc<GridBarrier>(1);
+    {
+      // the persistent cooperative Krylov kernel unless the caller forces
+      // the multi-kernel CUDA-graph form (MPM_KRYLOV_GRAPH=1)
+      const char* env = getenv("MPM_KRYLOV_GRAPH");
+      int dev = 0;
+      ck(cudaGetDevice(&dev), "device");
+      bool force_graph = env && env[0] == '1';
+      if (!force_graph && desc->krylov == MPM_BICGSTAB) {
+        if (s->D == 2) s->pblocks = s->mixed ? persistent_blocks<2, float>(dev) : persistent_blocks<2, double>(dev);
+        else s->pblocks = s->mixed ? persistent_blocks<3, float>(dev) : persistent_blocks<3, double>(dev);
+      }
+    }
     ck(cudaStreamSynchronize(s->st), "sync");
   });
   if (rc != MPM_OK) {

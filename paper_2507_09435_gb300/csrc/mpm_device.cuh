@@ -12,7 +12,7 @@ namespace mpm {
 constexpr int MODEL_NH = 0, MODEL_NH_DP = 1, MODEL_NH_MCC = 2;
 
 // error flag bits raised by kernels
-constexpr int ERRF_BOUNDS = 1, ERRF_RETURN = 2, ERRF_NONFINITE = 4, ERRF_DET = 8;
+constexpr int ERRF_BOUNDS = 1, ERRF_RETURN = 2, ERRF_NONFINITE = 4, ERRF_DET = 8, ERRF_BARRIER = 16;
 
 // Material constants as used by the kernels.
 struct MatC {

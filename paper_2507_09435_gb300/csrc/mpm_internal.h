@@ -45,6 +45,11 @@ struct DevMatrix {
   const int* nrow;  // device scalar: active row count
 };
 
+struct GridBarrier {
+  unsigned int count;
+  unsigned int gen;
+};
+
 struct KrylovScalars {
   double rho, alpha, omega;
   double acc_rv, acc_ts, acc_tt, acc_rho, acc_rr;
@@ -127,6 +132,12 @@ cudaError_t launch_step_du(DevMatrix<T> K, const T* x, const uint8_t* fixed, con
                            double alpha, int nblk, cudaStream_t st);
 // kernels launched by one scan_exclusive call of n elements
 int scan_launches(long long n);
+// persistent cooperative BiCGStab (one launch per solve); 0 blocks = unsupported
+template <int D, class T>
+int persistent_blocks(int device);
+template <int D, class T>
+cudaError_t launch_bicgstab_persistent(const DevGrid& G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S,
+                                       GridBarrier* bar, int* err, int nblocks, cudaStream_t st);
 
 // GMRES(m) with classical Gram-Schmidt applied twice
 template <int D, class T>

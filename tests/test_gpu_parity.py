@@ -164,6 +164,25 @@ def test_mixed_precision_footing_converges_and_states_error():
     gs.close()
 
 
+@pytest.mark.parametrize("precision", [mpm.MPM_FP64, mpm.MPM_MIXED])
+def test_multikernel_graph_krylov_path_matches_persistent(precision, monkeypatch):
+    """The multi-kernel CUDA-graph BiCGStab (fallback when cooperative launch
+    is unavailable) converges to the same step as the persistent kernel."""
+    sc = S.footing(nx=48, ny=24, h=0.5, nsteps=20, settle_frac=0.1)
+    out = []
+    for graph in ("1", "0"):
+        monkeypatch.setenv("MPM_KRYLOV_GRAPH", graph)
+        gs = mpm.GpuScene(sc, precision=precision, newton_tol=1e-10, forcing=mpm.MPM_FORCING_FIXED,
+                          krylov_rtol=1e-12 if precision == mpm.MPM_FP64 else 1e-6)
+        for st in sc.steps[:2]:
+            rep = gs.solve_step(st)
+            assert rep.converged
+        out.append(gs.particles()["x"])
+        gs.close()
+    scale = np.abs(out[0] - sc.x).max()
+    assert np.abs(out[0] - out[1]).max() < (1e-8 if precision == mpm.MPM_FP64 else 1e-5) * scale
+
+
 def test_empty_scene_and_state_errors():
     sc = S.block_compression()
     d = mpm.make_desc(2, sc.n, sc.h)
