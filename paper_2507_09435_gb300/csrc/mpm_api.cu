@@ -84,7 +84,8 @@ struct mpm_scene {
   long long halvings = 0;   // Newton steps halved after a return-map failure
   double* d_duprev = nullptr;
   int pblocks = 0;          // co-resident blocks for the persistent Krylov kernel (0 = use graphs)
-  GridBarrier* d_bar = nullptr;
+  unsigned int* d_bar = nullptr;   // barrier tree words of the persistent kernel
+  double* d_part = nullptr;        // per-block partial sums of its reductions
   std::string err;
 
   template <class T>
@@ -381,10 +382,11 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
   double tol2 = eta * eta * s->rk * s->rk;
   ck(launch_bicgstab_init<D, T>(K, s->d_r, s->d_fixed, v, s->d_S, tol2, s->desc.krylov_maxit, nblk, st),
      "krylov init");
-  const int pblk = std::min(s->pblocks, std::max(1, (s->nrow * 4 + KTPB - 1) / KTPB));
+  const int pblk = std::min(s->pblocks, std::max(1, (s->nrow * 4 + 511) / 512));
   if (s->pblocks > 0) {
     // whole solve in one cooperative launch
-    ck(launch_bicgstab_persistent<D, T>(s->G, K, v, s->d_S, s->d_bar, s->d_err, pblk, st), "persistent krylov");
+    ck(launch_bicgstab_persistent<D, T>(s->G, K, v, s->d_S, s->d_part, s->d_bar, s->d_err, pblk, st),
+       "persistent krylov");
     s->launches += 1;
     ck(cudaMemcpyAsync(s->h_S, s->d_S, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st), "copy S");
     ck(cudaMemcpyAsync(s->h_int + 2, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "copy err");
@@ -723,7 +725,8 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
     else s->d_vec = s->dalloc<double>(9 * s->vlen);
     ck(cudaMemsetAsync(s->d_vec, 0, 9 * s->vlen * T, s->st), "memset");
     s->d_S = s->dalloc<KrylovScalars>(1);
-    s->d_bar = s->dalloc<GridBarrier>(1);
+    s->d_bar = s->dalloc<unsigned int>(PERSIST_BAR_WORDS);
+    s->d_part = s->dalloc<double>(5 * PERSIST_MAX_BLOCKS);
     {
       // the persistent cooperative Krylov kernel unless the caller forces
       // the multi-kernel CUDA-graph form (MPM_KRYLOV_GRAPH=1)

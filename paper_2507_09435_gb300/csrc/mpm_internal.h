@@ -133,11 +133,13 @@ cudaError_t launch_step_du(DevMatrix<T> K, const T* x, const uint8_t* fixed, con
 // kernels launched by one scan_exclusive call of n elements
 int scan_launches(long long n);
 // persistent cooperative BiCGStab (one launch per solve); 0 blocks = unsupported
+constexpr int PERSIST_MAX_BLOCKS = 1024;   // partial-sum slots per reduction
+constexpr int PERSIST_BAR_WORDS = 1024;    // barrier tree counters (128-byte lines)
 template <int D, class T>
 int persistent_blocks(int device);
 template <int D, class T>
 cudaError_t launch_bicgstab_persistent(const DevGrid& G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S,
-                                       GridBarrier* bar, int* err, int nblocks, cudaStream_t st);
+                                       double* part, unsigned int* bar, int* err, int nblocks, cudaStream_t st);
 
 // GMRES(m) with classical Gram-Schmidt applied twice
 template <int D, class T>

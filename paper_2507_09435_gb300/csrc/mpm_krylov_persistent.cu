@@ -4,10 +4,19 @@
 // kernel boundaries, removing the per-kernel launch and drain latency that
 // dominates the multi-kernel form on L2-resident 2D problems.
 //
-// Grid barrier: sense-counting on a global counter and generation word, with
-// a bounded spin (about a second): on timeout the block raises ERRF_BARRIER,
-// and every block returns at its next barrier.  The kernel is launched with
-// cudaLaunchCooperativeKernel so that all blocks are co-resident.
+// Same-address atomics are what makes a naive grid-wide form slow (every
+// barrier and every dot product serialises one atomic per block on one L2
+// line), so:
+//  * dot products are deterministic two-level sums: each block writes its
+//    partial to its own slot; after the barrier every block adds all slots in
+//    the same order, so every block holds bit-identical scalars (alpha, beta,
+//    omega, the convergence test) without any further communication;
+//  * the grid barrier is a two-level tree: blocks arrive on one of NGROUP
+//    counters (each on its own 128-byte line), the last arrival of a group
+//    arrives on the root, the last root arrival advances the generation word.
+// Every spin is bounded (about a second): on timeout the block raises
+// ERRF_BARRIER and returns; every other block then returns at its next
+// barrier.  Launched with cudaLaunchCooperativeKernel (all blocks co-resident).
 //
 // Coherence: vectors written inside the kernel are read with ld.global.cg
 // (L2, not the non-coherent L1); the matrix, the block-Jacobi inverse and
@@ -19,8 +28,10 @@
 namespace mpm {
 
 namespace {
-constexpr int PTPB = 256;
-constexpr int RSPLIT = 4;   // threads per row in the products
+constexpr int PTPB = 512;
+constexpr int RSPLIT = 4;     // threads per row in the products
+constexpr int NGROUP = 16;    // barrier tree fan-in groups
+constexpr int LINE = 32;      // unsigned ints per 128-byte line
 
 __device__ __forceinline__ double wsum(double v) {
 #pragma unroll
@@ -28,36 +39,9 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
-// Returns false when the barrier timed out (every block then exits).
-__device__ __forceinline__ bool grid_barrier(GridBarrier* b, unsigned int nblocks, int* err) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = &b->gen;
-    const unsigned int g = *vgen;
-    __threadfence();
-    const unsigned int arrived = atomicAdd(&b->count, 1u) + 1u;
-    if (arrived == nblocks) {
-      atomicExch(&b->count, 0u);
-      __threadfence();
-      atomicAdd(&b->gen, 1u);
-    } else {
-      unsigned int spins = 0;
-      while (*vgen == g) {
-        if (++spins > (1u << 25)) {
-          atomicOr(err, ERRF_BARRIER);
-          break;
-        }
-        __nanosleep(32);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return *(volatile int*)err == 0 || !(*(volatile int*)err & ERRF_BARRIER);
-}
-
+// Block-wide sum of NV values; the result is returned to every thread.
 template <int NV>
-__device__ __forceinline__ void block_add(double v[NV], double* const out[NV]) {
+__device__ __forceinline__ void block_sum(double v[NV]) {
   __shared__ double sh[NV][PTPB / 32];
 #pragma unroll
   for (int k = 0; k < NV; ++k) v[k] = wsum(v[k]);
@@ -67,19 +51,81 @@ __device__ __forceinline__ void block_add(double v[NV], double* const out[NV]) {
     for (int k = 0; k < NV; ++k) sh[k][w] = v[k];
   }
   __syncthreads();
-  if (w == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double t = (lane < PTPB / 32) ? sh[k][lane] : 0.0;
-      t = wsum(t);
-      if (lane == 0 && t != 0.0) atomicAdd(out[k], t);
-    }
+  for (int k = 0; k < NV; ++k) {
+    double t = (lane < PTPB / 32) ? sh[k][lane] : 0.0;
+    v[k] = wsum(t);
   }
   __syncthreads();
 }
 
-// Partial product of one row over the slots sub, sub+RSPLIT, ...: the caller
-// reduces the RSPLIT partials with shuffles.
+// Write this block's NV partials to part[k*stride + block].
+template <int NV>
+__device__ __forceinline__ void publish(double v[NV], double* part, int stride) {
+  block_sum<NV>(v);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) part[k * stride + blockIdx.x] = v[k];
+  }
+}
+
+// Every block: sum the NV partial arrays in a fixed order (bitwise identical
+// in all blocks).
+template <int NV>
+__device__ __forceinline__ void gather(const double* part, int stride, int nb, double out[NV]) {
+  double v[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = 0.0;
+  // thread t adds blocks t, t + PTPB, ... ; the block sum then fixes the order
+  for (int b = threadIdx.x; b < nb; b += PTPB) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] += __ldcg(&part[k * stride + b]);
+  }
+  block_sum<NV>(v);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = v[k];
+}
+
+// Returns false when a barrier timed out (the caller returns).
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, int* err) {
+  __syncthreads();
+  __shared__ int timed_out;
+  if (threadIdx.x == 0) {
+    timed_out = 0;
+    volatile unsigned int* vgen = &bar[(NGROUP + 1) * LINE];
+    const unsigned int g = *vgen;
+    __threadfence();
+    const unsigned int grp = blockIdx.x % NGROUP;
+    const unsigned int gsize = (nblocks - grp + NGROUP - 1) / NGROUP;
+    const unsigned int ngroups = nblocks < NGROUP ? nblocks : NGROUP;
+    bool last = false;
+    if (atomicAdd(&bar[grp * LINE], 1u) + 1u == gsize) {
+      atomicExch(&bar[grp * LINE], 0u);
+      if (atomicAdd(&bar[NGROUP * LINE], 1u) + 1u == ngroups) {
+        atomicExch(&bar[NGROUP * LINE], 0u);
+        __threadfence();
+        atomicAdd((unsigned int*)vgen, 1u);
+        last = true;
+      }
+    }
+    if (!last) {
+      unsigned int spins = 0;
+      while (*vgen == g) {
+        if (++spins > (1u << 25)) {
+          atomicOr(err, ERRF_BARRIER);
+          timed_out = 1;
+          break;
+        }
+        __nanosleep(20);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return !timed_out && !(*(volatile int*)err & ERRF_BARRIER);
+}
+
+// Partial product of one row over the slots sub, sub+RSPLIT, ...
 template <int D, class T>
 __device__ __forceinline__ void spmv_part(const DevMatrix<T>& K, int row, long long i, int sub, int nx1,
                                           int ny1, const T* x, T y[D]) {
@@ -99,47 +145,49 @@ __device__ __forceinline__ void spmv_part(const DevMatrix<T>& K, int row, long l
 #pragma unroll
       for (int b = 0; b < D; ++b) y[a] += __ldg(&K.val[((long long)(slot * D + a) * D + b) * cap + row]) * xj[b];
   }
-}
-
-template <int D, class T>
-__device__ __forceinline__ void reduce_split(T y[D]) {
 #pragma unroll
   for (int a = 0; a < D; ++a) {
 #pragma unroll
     for (int o = RSPLIT / 2; o > 0; o >>= 1) y[a] += __shfl_xor_sync(0xffffffffu, y[a], o);
   }
 }
+
+// partial-slot arrays: index k * PSTRIDE + block
+constexpr int P_RV = 0, P_TS = 1, P_TT = 2, P_RHO = 3, P_RR = 4;
 }  // namespace
 
-// S must hold the state k_bicg_init leaves (accumulators of (r,r), (rhat,r),
-// rho = alpha = omega = 1, iter = 0, tol2, maxit).
+// S must hold what k_bicg_init leaves: acc_rr = (r,r), acc_rho = (rhat, r),
+// tol2, maxit.  part holds 5 * PERSIST_MAX_BLOCKS doubles; bar the barrier
+// words (zeroed by the launcher).
 template <int D, class T>
 __global__ void __launch_bounds__(PTPB) k_bicg_persistent(DevGrid G, DevMatrix<T> K, KrylovVecs<D, T> v,
-                                                          KrylovScalars* S, GridBarrier* bar, int* err) {
+                                                          KrylovScalars* S, double* part, unsigned int* bar,
+                                                          int* err) {
+  constexpr int PS = PERSIST_MAX_BLOCKS;
   const unsigned int nb = gridDim.x;
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long gsz = (long long)gridDim.x * blockDim.x;
   const int nrow = *K.nrow;
-  volatile KrylovScalars* VS = S;
   const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
-  for (;;) {
+  const double tol2 = S->tol2;
+  const int maxit = S->maxit;
+  // scalars, identical in every block
+  double rr = S->acc_rr, rho_new = S->acc_rho;
+  double rho = 1.0, alpha = 1.0, omega = 1.0;
+  int status = 0;
+  int it = 0;
+  for (;; ++it) {
     // ---- P1: convergence test; p = r + beta (p - omega v); phat = M^-1 p
-    const double rr = VS->acc_rr;
-    const int it = VS->iter;
-    const bool conv = rr <= VS->tol2;
-    const bool maxed = it >= VS->maxit;
-    const bool bad = (it > 0 && (VS->rho == 0.0 || VS->omega == 0.0)) || !(rr == rr);
+    const bool conv = rr <= tol2;
+    const bool maxed = it >= maxit;
+    const bool bad = (it > 0 && (rho == 0.0 || omega == 0.0)) || !(rr == rr);
     if (conv || maxed || bad) {
-      if (lead) {
-        S->done = 1;
-        S->status = conv ? 0 : (maxed ? 1 : 2);
-        S->rr_last = rr;
-      }
-      return;
+      status = conv ? 0 : (maxed ? 1 : 2);
+      break;
     }
     {
-      const double beta = (it == 0) ? 0.0 : (VS->acc_rho / VS->rho) * (VS->alpha / VS->omega);
-      const T tb = (T)beta, tw = (T)VS->omega;
+      const double beta = (it == 0) ? 0.0 : (rho_new / rho) * (alpha / omega);
+      const T tb = (T)beta, tw = (T)omega;
       for (long long row = gtid; row < nrow; row += gsz) {
         const long long i = K.rows[row];
         T p[D];
@@ -157,26 +205,21 @@ __global__ void __launch_bounds__(PTPB) k_bicg_persistent(DevGrid G, DevMatrix<T
           v.phat[i * D + a] = z;
         }
       }
-      if (lead) S->acc_rv = 0.0;
     }
+    rho = rho_new;
     if (!grid_barrier(bar, nb, err)) return;
     // ---- P2: v = J phat; (rhat, v)
     {
       double acc[1] = {0.0};
       const long long items = (long long)nrow * RSPLIT;
-      const long long span = ((items + gsz - 1) / gsz) * gsz;   // every lane runs the same trip count
+      const long long span = ((items + gsz - 1) / gsz) * gsz;   // same trip count in every lane
       for (long long w = gtid; w < span; w += gsz) {
         const bool live = w < items;
         const int row = live ? (int)(w / RSPLIT) : 0;
         const int sub = (int)(w % RSPLIT);
         const long long i = live ? K.rows[row] : 0;
         T y[D];
-        if (live) spmv_part<D, T>(K, row, i, sub, G.nx1, G.ny1, v.phat, y);
-        else {
-#pragma unroll
-          for (int a = 0; a < D; ++a) y[a] = (T)0;
-        }
-        reduce_split<D, T>(y);
+        spmv_part<D, T>(K, row, i, live ? sub : 1000, G.nx1, G.ny1, v.phat, y);
         if (live && sub == 0) {
 #pragma unroll
           for (int a = 0; a < D; ++a) {
@@ -185,23 +228,18 @@ __global__ void __launch_bounds__(PTPB) k_bicg_persistent(DevGrid G, DevMatrix<T
           }
         }
       }
-      double* outs[1] = {&S->acc_rv};
-      block_add<1>(acc, outs);
-      if (lead) {
-        S->rho = VS->acc_rho;
-        S->acc_ts = 0.0;
-        S->acc_tt = 0.0;
-      }
+      publish<1>(acc, part + P_RV * PS, PS);
     }
     if (!grid_barrier(bar, nb, err)) return;
     // ---- P3: alpha = rho / (rhat, v); s = r - alpha v; shat = M^-1 s
     {
-      const double rv = VS->acc_rv;
-      if (rv == 0.0 || !(rv == rv)) {
-        if (lead) { S->done = 1; S->status = 2; S->rr_last = VS->acc_rr; }
-        return;
+      double rv[1];
+      gather<1>(part + P_RV * PS, PS, nb, rv);
+      if (rv[0] == 0.0 || !(rv[0] == rv[0])) {
+        status = 2;
+        break;
       }
-      const double alpha = VS->rho / rv;
+      alpha = rho / rv[0];
       const T ta = (T)alpha;
       for (long long row = gtid; row < nrow; row += gsz) {
         const long long i = K.rows[row];
@@ -220,11 +258,6 @@ __global__ void __launch_bounds__(PTPB) k_bicg_persistent(DevGrid G, DevMatrix<T
           v.shat[i * D + a] = z;
         }
       }
-      if (lead) {
-        S->alpha = alpha;
-        S->acc_rho = 0.0;
-        S->acc_rr = 0.0;
-      }
     }
     if (!grid_barrier(bar, nb, err)) return;
     // ---- P4: t = J shat; (t, s), (t, t)
@@ -238,12 +271,7 @@ __global__ void __launch_bounds__(PTPB) k_bicg_persistent(DevGrid G, DevMatrix<T
         const int sub = (int)(w % RSPLIT);
         const long long i = live ? K.rows[row] : 0;
         T y[D];
-        if (live) spmv_part<D, T>(K, row, i, sub, G.nx1, G.ny1, v.shat, y);
-        else {
-#pragma unroll
-          for (int a = 0; a < D; ++a) y[a] = (T)0;
-        }
-        reduce_split<D, T>(y);
+        spmv_part<D, T>(K, row, i, live ? sub : 1000, G.nx1, G.ny1, v.shat, y);
         if (live && sub == 0) {
 #pragma unroll
           for (int a = 0; a < D; ++a) {
@@ -254,15 +282,15 @@ __global__ void __launch_bounds__(PTPB) k_bicg_persistent(DevGrid G, DevMatrix<T
           }
         }
       }
-      double* outs[2] = {&S->acc_ts, &S->acc_tt};
-      block_add<2>(acc, outs);
+      publish<2>(acc, part + P_TS * PS, PS);
     }
     if (!grid_barrier(bar, nb, err)) return;
     // ---- P5: omega; x += alpha phat + omega shat; r = s - omega t; (rhat,r), (r,r)
     {
-      const double tt = VS->acc_tt;
-      const double omega = (tt > 0.0) ? VS->acc_ts / tt : 0.0;
-      const T ta = (T)VS->alpha, tw = (T)omega;
+      double tsn[2];
+      gather<2>(part + P_TS * PS, PS, nb, tsn);
+      omega = (tsn[1] > 0.0) ? tsn[0] / tsn[1] : 0.0;
+      const T ta = (T)alpha, tw = (T)omega;
       double acc[2] = {0.0, 0.0};
       for (long long row = gtid; row < nrow; row += gsz) {
         const long long i = K.rows[row];
@@ -276,42 +304,52 @@ __global__ void __launch_bounds__(PTPB) k_bicg_persistent(DevGrid G, DevMatrix<T
           acc[1] += (double)rn * (double)rn;
         }
       }
-      double* outs[2] = {&S->acc_rho, &S->acc_rr};
-      block_add<2>(acc, outs);
-      if (lead) {
-        S->omega = omega;
-        S->iter = it + 1;
-      }
+      publish<2>(acc, part + P_RHO * PS, PS);
     }
     if (!grid_barrier(bar, nb, err)) return;
+    {
+      double rr2[2];
+      gather<2>(part + P_RHO * PS, PS, nb, rr2);
+      rho_new = rr2[0];
+      rr = rr2[1];
+    }
+  }
+  if (lead) {
+    S->done = 1;
+    S->status = status;
+    S->rr_last = rr;
+    S->iter = it;
+    S->rho = rho;
+    S->alpha = alpha;
+    S->omega = omega;
   }
 }
 
 template <int D, class T>
 int persistent_blocks(int device) {
-  int nsm = 0, per = 0;
+  int nsm = 0, per = 0, coop = 0;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_bicg_persistent<D, T>, PTPB, 0) != cudaSuccess) return 0;
-  int coop = 0;
-  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
-  if (!coop) return 0;
-  return nsm * std::min(per, 2);
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop) return 0;
+  if (per < 1) return 0;
+  return std::min(nsm, PERSIST_MAX_BLOCKS);   // one block per SM
 }
 
 template <int D, class T>
 cudaError_t launch_bicgstab_persistent(const DevGrid& G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S,
-                                       GridBarrier* bar, int* err, int nblocks, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), st);
+                                       double* part, unsigned int* bar, int* err, int nblocks, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(bar, 0, PERSIST_BAR_WORDS * sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
   DevGrid g = G;
-  void* args[] = {&g, &K, &v, &S, &bar, &err};
+  void* args[] = {&g, &K, &v, &S, &part, &bar, &err};
   return cudaLaunchCooperativeKernel((void*)k_bicg_persistent<D, T>, dim3(nblocks), dim3(PTPB), args, 0, st);
 }
 
 #define MPM_PERSIST_INST(D, T)                                                                          \
   template int persistent_blocks<D, T>(int);                                                            \
   template cudaError_t launch_bicgstab_persistent<D, T>(const DevGrid&, DevMatrix<T>, KrylovVecs<D, T>, \
-                                                        KrylovScalars*, GridBarrier*, int*, int, cudaStream_t);
+                                                        KrylovScalars*, double*, unsigned int*, int*,   \
+                                                        int, cudaStream_t);
 MPM_PERSIST_INST(2, float)
 MPM_PERSIST_INST(2, double)
 MPM_PERSIST_INST(3, float)
