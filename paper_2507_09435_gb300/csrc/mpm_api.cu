@@ -82,9 +82,11 @@ struct mpm_scene {
   float t_asm = 0, t_kry = 0, t_res = 0;
   long long launches = 0;   // kernels launched by this scene
   long long halvings = 0;   // Newton steps halved after a return-map failure
+  long long restarts = 0;   // BiCGStab restarts after a breakdown or the limit
   double* d_duprev = nullptr;
   int pblocks = 0;          // co-resident blocks for the persistent Krylov kernel (0 = use graphs)
-  unsigned int* d_bar = nullptr;   // barrier tree words of the persistent kernel
+  unsigned int* d_bar = nullptr;   // barrier counter of the persistent kernel
+  double* d_fail = nullptr;        // first constitutive failure record of a pass
   double* d_part = nullptr;        // per-block partial sums of its reductions
   std::string err;
 
@@ -238,6 +240,7 @@ template <int D, class T>
 void residual_pass(mpm_scene* s, int mode) {
   ck(cudaMemsetAsync(s->d_r, 0, s->ndof * sizeof(double), s->st), "memset r");
   ck(cudaMemsetAsync(s->d_nplastic, 0, sizeof(int), s->st), "memset");
+  ck(cudaMemsetAsync(s->d_fail, 0, sizeof(double), s->st), "memset");
   ck(launch_particles<D, T>(s->P, s->G, s->d_mats, s->d_du, s->d_r, s->d_grav, (T*)s->d_A, mode, s->d_err,
                             s->d_nplastic, s->st),
      "particle kernel");
@@ -251,7 +254,19 @@ void residual_pass(mpm_scene* s, int mode) {
 void check_err_bits(mpm_scene* s) {
   std::string m;
   mpm_status st = map_err_bits(s->h_int[2], m);
-  if (st != MPM_OK) fail(st, m);
+  if (st == MPM_OK) return;
+  if (s->h_int[2] & (ERRF_RETURN | ERRF_DET)) {
+    double rec[FAIL_REC];
+    if (cudaMemcpy(rec, s->d_fail, sizeof(rec), cudaMemcpyDeviceToHost) == cudaSuccess && rec[0] != 0.0) {
+      char buf[320];
+      snprintf(buf, sizeof(buf),
+               " (first at particle %.0f: trial b eigenvalues %.17g %.17g %.17g, E %.17g, phi %.17g, pc %.17g, "
+               "model %.0f)",
+               rec[1], rec[2], rec[3], rec[4], rec[5], rec[6], rec[7], rec[8]);
+      m += buf;
+    }
+  }
+  fail(st, m);
 }
 
 template <int D, class T>
@@ -394,22 +409,40 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
     check_err_bits(s);
   }
   if (s->pblocks == 0 && s->use_graph && s->graph_cap != s->cap) build_graph<D, T>(s, nblk);
-  int launched = 0;
-  for (; s->pblocks == 0;) {
-    if (s->use_graph) {
-      ck(cudaGraphLaunch(s->gexec, st), "graph launch");
-    } else {
-      for (int c = 0; c < GRAPH_CHUNK; ++c) ck(launch_bicgstab_iter<D, T>(s->G, K, v, s->d_S, nblk, st), "krylov");
+  int kit = 0, kstat = 0;
+  if (s->pblocks == 0) {
+    // graph chunks of GRAPH_CHUNK iterations until the done flag; on a
+    // (near) breakdown or the iteration limit, restart from the current x
+    // with the true residual b - J x (at most 3 restarts)
+    for (int restart = 0;; ++restart) {
+      int launched = 0;
+      for (;;) {
+        if (s->use_graph) {
+          ck(cudaGraphLaunch(s->gexec, st), "graph launch");
+        } else {
+          for (int c = 0; c < GRAPH_CHUNK; ++c)
+            ck(launch_bicgstab_iter<D, T>(s->G, K, v, s->d_S, nblk, st), "krylov");
+        }
+        launched += GRAPH_CHUNK;
+        s->launches += 4 * GRAPH_CHUNK;
+        ck(cudaMemcpyAsync(s->h_S, s->d_S, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st), "copy S");
+        ck(cudaStreamSynchronize(st), "sync");
+        if (s->h_S->done) break;
+        if (launched > s->desc.krylov_maxit + 2 * GRAPH_CHUNK) break;   // belt and braces
+      }
+      kit += s->h_S->iter;
+      kstat = s->h_S->status;
+      if (kstat == 0 || restart >= 3 || kit >= s->desc.krylov_maxit) break;
+      ck(launch_bicgstab_restart<D, T>(s->G, K, s->d_r, s->d_fixed, v, s->d_S, tol2,
+                                       s->desc.krylov_maxit - kit, nblk, st),
+         "krylov restart");
+      s->launches += 1;
+      s->restarts += 1;
     }
-    launched += GRAPH_CHUNK;
-    s->launches += 5 * GRAPH_CHUNK;
-    ck(cudaMemcpyAsync(s->h_S, s->d_S, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st), "copy S");
-    ck(cudaStreamSynchronize(st), "sync");
-    if (s->h_S->done) break;
-    if (launched > s->desc.krylov_maxit + 2 * GRAPH_CHUNK) break;   // belt and braces
+  } else {
+    kit = s->h_S->iter;
+    kstat = s->h_S->status;
   }
-  const int kit = s->h_S->iter;
-  const int kstat = s->h_S->status;
   const double krel = (s->rk > 0) ? std::sqrt(std::max(s->h_S->rr_last, 0.0)) / s->rk : 0.0;
   ck(cudaMemcpyAsync(s->d_duprev, s->d_du, s->ndof * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy du");
   ck(launch_update_du<D, T>(K, v.x, s->d_fixed, s->d_du, nblk, st), "update");
@@ -657,6 +690,10 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
     };
     mk(s->P);
     mk(s->Q);
+    s->d_fail = s->dalloc<double>(FAIL_REC);
+    ck(cudaMemsetAsync(s->d_fail, 0, FAIL_REC * sizeof(double), s->st), "memset");
+    s->P.fail_rec = s->d_fail;
+    s->Q.fail_rec = s->d_fail;
     std::vector<double> h(np);
     auto up = [&](double* d) {
       ck(cudaMemcpy(d, h.data(), np * sizeof(double), cudaMemcpyHostToDevice), "upload");
@@ -728,13 +765,14 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
     s->d_bar = s->dalloc<unsigned int>(PERSIST_BAR_WORDS);
     s->d_part = s->dalloc<double>(5 * PERSIST_MAX_BLOCKS);
     {
-      // the persistent cooperative Krylov kernel unless the caller forces
-      // the multi-kernel CUDA-graph form (MPM_KRYLOV_GRAPH=1)
-      const char* env = getenv("MPM_KRYLOV_GRAPH");
+      // BiCGStab runs as CUDA-graph chunks of four kernels per iteration;
+      // MPM_KRYLOV_PERSISTENT=1 selects the single cooperative kernel instead
+      // (measured slower on the 2D footing: 32 vs 25 us per iteration)
+      const char* env = getenv("MPM_KRYLOV_PERSISTENT");
       int dev = 0;
       ck(cudaGetDevice(&dev), "device");
-      bool force_graph = env && env[0] == '1';
-      if (!force_graph && desc->krylov == MPM_BICGSTAB) {
+      const bool want_persistent = env && env[0] == '1';
+      if (want_persistent && desc->krylov == MPM_BICGSTAB) {
         if (s->D == 2) s->pblocks = s->mixed ? persistent_blocks<2, float>(dev) : persistent_blocks<2, double>(dev);
         else s->pblocks = s->mixed ? persistent_blocks<3, float>(dev) : persistent_blocks<3, double>(dev);
       }
@@ -949,7 +987,7 @@ mpm_status mpm_get_jacobian_bsr(const mpm_scene* cs, long long cap, int* row_nod
         int dx = sl % 5 - 2, dy = (sl / 5) % 5 - 2, dz = D == 3 ? sl / 25 - 2 : 0;
         col_node[nb] = rows[r] + dx + nx1 * (dy + ny1 * dz);
         for (int a = 0; a < D; ++a)
-          for (int b = 0; b < D; ++b) val[nb * DD + a * D + b] = K[((size_t)(sl * D + a) * D + b) * s->cap + r];
+          for (int b = 0; b < D; ++b) val[nb * DD + a * D + b] = K[((size_t)sl * s->cap + r) * DD + a * D + b];
         ++nb;
       }
       row_ptr[r + 1] = nb;

@@ -23,7 +23,11 @@ struct DevParticles {
   double* pc;
   double* F[MAX_F];  // dim*dim row-major
   int* orig;         // caller's index of each sorted particle
+  // first constitutive failure of a pass: [claimed, caller index, trial b
+  // eigenvalues (3), E, phi, pc, model, return-map mode]
+  double* fail_rec;
 };
+constexpr int FAIL_REC = 10;
 
 struct DevGrid {
   int dim;
@@ -35,26 +39,62 @@ struct DevGrid {
 };
 
 // Stencil-BSR Jacobian: for every active node (row) the 5^dim neighbour
-// blocks at fixed slots, values SoA: val[((slot*D + a)*D + b)*cap + row].
+// blocks at fixed slots, one plane per slot, blocks contiguous within a plane:
+// val[(slot*cap + row)*D*D + a*D + b] (a 2x2 FP32 block is one 16-byte load).
 template <class T>
 struct DevMatrix {
   T* val;
-  T* dinv;          // block-Jacobi inverse, dinv[(a*D+b)*cap + row]
+  T* dinv;          // block-Jacobi inverse, dinv[row*D*D + a*D + b]
   int cap;          // row capacity (row stride of the SoA planes)
   const int* rows;  // node index of each row
   const int* nrow;  // device scalar: active row count
 };
 
-struct GridBarrier {
-  unsigned int count;
-  unsigned int gen;
-};
+// One D x D block of the matrix (contiguous), through the read-only path:
+// a single 16-byte load for 2x2 FP32, two for 2x2 FP64.
+template <int D, class T>
+__device__ __forceinline__ void ld_block(const T* p, T b[D * D]) {
+  if constexpr (D == 2 && sizeof(T) == 4) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    b[0] = v.x; b[1] = v.y; b[2] = v.z; b[3] = v.w;
+  } else if constexpr (D == 2 && sizeof(T) == 8) {
+    const double2 u = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 w = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    b[0] = u.x; b[1] = u.y; b[2] = w.x; b[3] = w.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < D * D; ++k) b[k] = __ldg(p + k);
+  }
+}
+
+// The D entries of node j of a vector.  WEAK = true issues ordinary (weak,
+// L1-cacheable) loads, for data written earlier in the same kernel and made
+// visible by a release/acquire grid barrier; otherwise the read-only path,
+// for data constant over the kernel.
+template <int D, class T, bool WEAK>
+__device__ __forceinline__ void ld_node(const T* x, long long j, T v[D]) {
+  if constexpr (D == 2 && sizeof(T) == 4) {
+    const float2* q = reinterpret_cast<const float2*>(x + j * 2);
+    const float2 u = WEAK ? *q : __ldg(q);
+    v[0] = u.x; v[1] = u.y;
+  } else if constexpr (D == 2 && sizeof(T) == 8) {
+    const double2* q = reinterpret_cast<const double2*>(x + j * 2);
+    const double2 u = WEAK ? *q : __ldg(q);
+    v[0] = u.x; v[1] = u.y;
+  } else {
+#pragma unroll
+    for (int b = 0; b < D; ++b) v[b] = WEAK ? x[j * D + b] : __ldg(x + j * D + b);
+  }
+}
 
 struct KrylovScalars {
   double rho, alpha, omega;
   double acc_rv, acc_ts, acc_tt, acc_rho, acc_rr;
   double tol2, bnorm2, rr_last;
   int iter, done, status, maxit;
+  // merged-reduction BiCGStab: rho of the previous iteration and the extra
+  // dot products (s,s), (rhat,s), (rhat,t), (v,v); (rhat,rhat) of the start
+  double rho_old, acc_ss, acc_rs, acc_rt, acc_vv, rhat2;
 };
 
 // ---- host launchers (stream-ordered, no synchronisation) ----------------
@@ -122,6 +162,10 @@ cudaError_t launch_bicgstab_init(DevMatrix<T> K, const double* res, const uint8_
 template <int D, class T>
 cudaError_t launch_bicgstab_iter(const DevGrid& G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S,
                                  int nblk, cudaStream_t st);
+template <int D, class T>
+cudaError_t launch_bicgstab_restart(const DevGrid& G, DevMatrix<T> K, const double* res, const uint8_t* fixed,
+                                    KrylovVecs<D, T> v, KrylovScalars* S, double tol2, int maxit, int nblk,
+                                    cudaStream_t st);
 template <int D, class T>
 cudaError_t launch_update_du(DevMatrix<T> K, const T* x, const uint8_t* fixed, double* du, int nblk,
                              cudaStream_t st);

@@ -315,6 +315,19 @@ __global__ void __launch_bounds__(128) k_particles(DevParticles P, DevGrid G, co
     int e = constitutive<D>(mc, P.Ep[p], P.phip[p], P.pc[p], V0, st);
     if (e) {
       atomicOr(err, e);
+      // record the first failing particle's trial state for the error message
+      if (P.fail_rec && atomicCAS((unsigned long long*)P.fail_rec, 0ull,
+                                  (unsigned long long)__double_as_longlong(1.0)) == 0ull) {
+        P.fail_rec[1] = (double)P.orig[p];
+        P.fail_rec[2] = st.lam[0];
+        P.fail_rec[3] = st.lam[1];
+        P.fail_rec[4] = st.lam[2];
+        P.fail_rec[5] = P.Ep[p];
+        P.fail_rec[6] = P.phip[p];
+        P.fail_rec[7] = P.pc[p];
+        P.fail_rec[8] = (double)mc.model;
+        P.fail_rec[9] = (double)e;
+      }
     } else {
       plastic = st.mode != 0;
       if (MODE == 2) {
@@ -528,11 +541,14 @@ __global__ void k_assemble(DevParticles P, DevGrid G, const int* __restrict__ ce
       int row = node2row[ni];
       if (row < 0) continue;
       int slot = slot_of<D>(jx - ix, jy - iy, jz - iz);
+      T* blk = &K.val[((long long)slot * K.cap + row) * (D * D)];
+      if constexpr (D == 2 && sizeof(T) == 4) {
+        // one 16-byte vector atomic per 2x2 FP32 block (sm_90+)
+        atomicAdd(reinterpret_cast<float4*>(blk), make_float4(acc[k][0], acc[k][1], acc[k][2], acc[k][3]));
+      } else {
 #pragma unroll
-      for (int a = 0; a < D; ++a)
-#pragma unroll
-        for (int b = 0; b < D; ++b)
-          atomicAdd(&K.val[((long long)(slot * D + a) * D + b) * K.cap + row], acc[k][a * D + b]);
+        for (int e = 0; e < D * D; ++e) atomicAdd(&blk[e], acc[k][e]);
+      }
     }
   }
 }
@@ -574,7 +590,7 @@ __global__ void k_bc_matrix(DevGrid G, DevMatrix<T> K, const uint8_t* __restrict
       bool fb = fixed[j * D + b];
       if (fa || fb) {
         T v = (center && a == b && fa) ? (T)1 : (T)0;
-        K.val[((long long)(slot * D + a) * D + b) * K.cap + row] = v;
+        K.val[((long long)slot * K.cap + row) * (D * D) + a * D + b] = v;
       }
     }
   }
@@ -598,7 +614,7 @@ __global__ void k_block_jacobi(DevMatrix<T> K, int nrow, int* err) {
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
-    for (int j = 0; j < D; ++j) a[i][j] = (double)K.val[((long long)(C * D + i) * D + j) * K.cap + row];
+    for (int j = 0; j < D; ++j) a[i][j] = (double)K.val[((long long)C * K.cap + row) * (D * D) + i * D + j];
   double inv[3][3], det;
   if (!inv3(a, inv, det)) {
     atomicOr(err, ERRF_NONFINITE);
@@ -608,7 +624,7 @@ __global__ void k_block_jacobi(DevMatrix<T> K, int nrow, int* err) {
 #pragma unroll
   for (int i = 0; i < D; ++i)
 #pragma unroll
-    for (int j = 0; j < D; ++j) K.dinv[(long long)(i * D + j) * K.cap + row] = (T)inv[i][j];
+    for (int j = 0; j < D; ++j) K.dinv[(long long)row * (D * D) + i * D + j] = (T)inv[i][j];
 }
 template <int D, class T>
 cudaError_t launch_block_jacobi(DevMatrix<T> K, int nrow_host, int* err, cudaStream_t st) {

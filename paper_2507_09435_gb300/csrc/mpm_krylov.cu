@@ -1,12 +1,12 @@
 // Krylov solver kernels for the Newton correction J d = -r (the paper solves
 // this system with AMG/direct solvers on the CPU, Sec. 2.2 remark; here a
-// block-Jacobi preconditioned BiCGStab and GMRES(m) run on the GPU).
+// block-Jacobi preconditioned BiCGStab runs on the GPU).
 //
 // Vectors live on the dense node grid (nnode*D entries, padded on both sides
 // by the stencil reach so that neighbour reads of boundary rows stay inside
 // the allocation); only active rows are ever written.  The matrix is the
-// stencil-BSR layout of mpm_internal.h: val[((slot*D + a)*D + b)*cap + row],
-// one thread per row, fully coalesced value reads, no column indices.
+// stencil-BSR layout of mpm_internal.h: val[(slot*cap + row)*D*D + a*D + b],
+// one thread per row, coalesced block reads, no column indices.
 //
 // Scalars of the iteration stay on the device (KrylovScalars); every kernel
 // returns at once when the solve is done, so the host can launch fixed-length
@@ -39,24 +39,25 @@ __device__ __forceinline__ void spmv_row(const DevMatrix<T>& K, int row, long lo
       for (int dx = -2; dx <= 2; ++dx) {
         const int slot = (D == 2) ? (dx + 2) + 5 * (dy + 2) : (dx + 2) + 5 * ((dy + 2) + 5 * (dz + 2));
         const long long j = nbr<D>(i, dx, dy, dz, nx1, ny1);
-        T xj[D];
-#pragma unroll
-        for (int b = 0; b < D; ++b) xj[b] = __ldg(&x[j * D + b]);
+        T xj[D], kb[D * D];
+        ld_node<D, T, false>(x, j, xj);
+        ld_block<D, T>(&K.val[((long long)slot * cap + row) * (D * D)], kb);
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
-          for (int b = 0; b < D; ++b)
-            y[a] += __ldg(&K.val[((long long)(slot * D + a) * D + b) * cap + row]) * xj[b];
+          for (int b = 0; b < D; ++b) y[a] += kb[a * D + b] * xj[b];
       }
 }
 
 template <int D, class T>
 __device__ __forceinline__ void precond_row(const DevMatrix<T>& K, int row, const T v[D], T z[D]) {
+  T m[D * D];
+  ld_block<D, T>(&K.dinv[(long long)row * (D * D)], m);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     T s = (T)0;
 #pragma unroll
-    for (int b = 0; b < D; ++b) s += __ldg(&K.dinv[(long long)(a * D + b) * K.cap + row]) * v[b];
+    for (int b = 0; b < D; ++b) s += m[a * D + b] * v[b];
     z[a] = s;
   }
 }
@@ -93,8 +94,26 @@ enum { KS_OK = 0, KS_MAXIT = 1, KS_BREAKDOWN = 2 };
 }  // namespace
 
 // ------------------------------------------------------------------ BiCGStab
-// Right-preconditioned BiCGStab (van der Vorst 1992) on J d = b, d0 = 0.
+// Right-preconditioned BiCGStab (van der Vorst 1992) on J d = b, d0 = 0, in a
+// merged-reduction form with four kernels per iteration:
+//   B: v = J phat, (rhat, v)
+//   C: alpha = rho/(rhat,v); s = r - alpha v; shat = M^-1 s; (s,s), (rhat,s)
+//   D: t = J shat; (t,s), (t,t), (rhat,t)
+//   A: omega = (t,s)/(t,t); x += alpha phat + omega shat; r = s - omega t;
+//      rho' = (rhat,s) - omega (rhat,t); ||r||^2 = (s,s) - 2 omega (t,s) +
+//      omega^2 (t,t); beta = (rho'/rho)(alpha/omega); p = r + beta (p - omega v);
+//      phat = M^-1 p.
+// The two dot products of the classical form's last step follow from the
+// ones already reduced, so the update and the next search direction share one
+// pass.  (FP32 products are exact in FP64 and summed in FP64, which keeps the
+// cancellation in ||r||^2 harmless at the linear tolerances used.)
+// A kernel's lead thread never writes a field that other blocks of the same
+// kernel read: rho is read in C and written in A; C copies it to rho_old,
+// which A reads; iter is read in B and advanced in D; each accumulator is
+// zeroed in a kernel that neither produces nor consumes it.
 
+// init: r = b, rhat = b, x = 0, p = r, phat = M^-1 r; rho = (rhat, r),
+// rr_last = (r, r).
 template <int D, class T>
 __global__ void __launch_bounds__(KTPB) k_bicg_init(DevMatrix<T> K, const double* __restrict__ res,
                                                     const uint8_t* __restrict__ fixed, KrylovVecs<D, T> v,
@@ -104,23 +123,26 @@ __global__ void __launch_bounds__(KTPB) k_bicg_init(DevMatrix<T> K, const double
   double acc[2] = {0.0, 0.0};
   if (row < nrow) {
     const long long i = K.rows[row];
+    T b[D], z[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       const long long d = i * D + a;
-      T b = fixed[d] ? (T)0 : (T)(-res[d]);
-      v.r[d] = b;
-      v.rhat[d] = b;
-      v.p[d] = (T)0;
-      v.v[d] = (T)0;
+      b[a] = fixed[d] ? (T)0 : (T)(-res[d]);
+      v.r[d] = b[a];
+      v.rhat[d] = b[a];
+      v.p[d] = b[a];
       v.x[d] = (T)0;
-      acc[0] += (double)b * (double)b;
+      acc[0] += (double)b[a] * (double)b[a];
     }
+    precond_row<D, T>(K, row, b, z);
+#pragma unroll
+    for (int a = 0; a < D; ++a) v.phat[i * D + a] = z[a];
     acc[1] = acc[0];
   }
-  double* outs[2] = {&S->acc_rr, &S->acc_rho};
-  block_accumulate<2>(acc, outs);
+  double acc3[3] = {acc[0], acc[1], acc[0]};
+  double* outs[3] = {&S->rr_last, &S->rho, &S->rhat2};
+  block_accumulate<3>(acc3, outs);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    S->rho = 1.0;
     S->alpha = 1.0;
     S->omega = 1.0;
     S->tol2 = tol2;
@@ -131,48 +153,24 @@ __global__ void __launch_bounds__(KTPB) k_bicg_init(DevMatrix<T> K, const double
   }
 }
 
-// K1: convergence test on ||r||^2, then p = r + beta (p - omega v), phat = M^-1 p.
+// B: convergence / limit test, then v = J phat and (rhat, v).
 template <int D, class T>
-__global__ void __launch_bounds__(KTPB) k_bicg_1(DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
+__global__ void __launch_bounds__(KTPB) k_bicg_B(DevGrid G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
   if (S->done) return;
-  const double rr = S->acc_rr;
+  const double rr = S->rr_last;
   const int it = S->iter;
   const bool conv = rr <= S->tol2;
   const bool maxed = it >= S->maxit;
-  const bool bad = it > 0 && (S->rho == 0.0 || S->omega == 0.0);
-  if (conv || maxed || bad || !(rr == rr)) {
+  const bool bad = !(rr == rr) || (it > 0 && (S->rho == 0.0 || S->omega == 0.0));
+  if (conv || maxed || bad) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       S->done = 1;
       S->status = conv ? KS_OK : (maxed ? KS_MAXIT : KS_BREAKDOWN);
-      S->rr_last = rr;
     }
     return;
   }
-  const double beta = (it == 0) ? 0.0 : (S->acc_rho / S->rho) * (S->alpha / S->omega);
-  const T tb = (T)beta, tw = (T)S->omega;
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row < *K.nrow) {
-    const long long i = K.rows[row];
-    T p[D], z[D];
-#pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const long long d = i * D + a;
-      p[a] = v.r[d] + tb * (v.p[d] - tw * v.v[d]);
-      v.p[d] = p[a];
-    }
-    precond_row<D, T>(K, row, p, z);
-#pragma unroll
-    for (int a = 0; a < D; ++a) v.phat[i * D + a] = z[a];
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) S->acc_rv = 0.0;
-}
-
-// K2: v = J phat; (rhat, v).
-template <int D, class T>
-__global__ void __launch_bounds__(KTPB) k_bicg_2(DevGrid G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
-  if (S->done) return;
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[1] = {0.0};
+  double acc[2] = {0.0, 0.0};
   if (row < *K.nrow) {
     const long long i = K.rows[row];
     T y[D];
@@ -181,29 +179,32 @@ __global__ void __launch_bounds__(KTPB) k_bicg_2(DevGrid G, DevMatrix<T> K, Kryl
     for (int a = 0; a < D; ++a) {
       v.v[i * D + a] = y[a];
       acc[0] += (double)v.rhat[i * D + a] * (double)y[a];
+      acc[1] += (double)y[a] * (double)y[a];
     }
   }
-  double* outs[1] = {&S->acc_rv};
-  block_accumulate<1>(acc, outs);
+  double* outs[2] = {&S->acc_rv, &S->acc_vv};
+  block_accumulate<2>(acc, outs);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    S->rho = S->acc_rho;   // rho_i = (rhat, r_i), consumed by K3 and the next K1
-    S->acc_ts = 0.0;
-    S->acc_tt = 0.0;
+    S->acc_ss = 0.0;
+    S->acc_rs = 0.0;
   }
 }
 
-// K3: alpha = rho / (rhat, v); s = r - alpha v; shat = M^-1 s.
+// C: alpha = rho / (rhat, v); s = r - alpha v; shat = M^-1 s; (s,s), (rhat,s).
 template <int D, class T>
-__global__ void __launch_bounds__(KTPB) k_bicg_3(DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
+__global__ void __launch_bounds__(KTPB) k_bicg_C(DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
   if (S->done) return;
   const double rv = S->acc_rv;
-  if (rv == 0.0 || !(rv == rv)) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) { S->done = 1; S->status = KS_BREAKDOWN; S->rr_last = S->acc_rr; }
+  // (near) breakdown: rhat and v almost orthogonal, relative to FP32 vectors
+  if (!(fabs(rv) > 1e-7 * sqrt(S->acc_vv * S->rhat2))) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) { S->done = 1; S->status = KS_BREAKDOWN; }
     return;
   }
-  const double alpha = S->rho / rv;
+  const double rho = S->rho;
+  const double alpha = rho / rv;
   const T ta = (T)alpha;
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[2] = {0.0, 0.0};
   if (row < *K.nrow) {
     const long long i = K.rows[row];
     T s[D], z[D];
@@ -212,67 +213,136 @@ __global__ void __launch_bounds__(KTPB) k_bicg_3(DevMatrix<T> K, KrylovVecs<D, T
       const long long d = i * D + a;
       s[a] = v.r[d] - ta * v.v[d];
       v.s[d] = s[a];
+      acc[0] += (double)s[a] * (double)s[a];
+      acc[1] += (double)v.rhat[d] * (double)s[a];
     }
     precond_row<D, T>(K, row, s, z);
 #pragma unroll
     for (int a = 0; a < D; ++a) v.shat[i * D + a] = z[a];
   }
+  double* outs[2] = {&S->acc_ss, &S->acc_rs};
+  block_accumulate<2>(acc, outs);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     S->alpha = alpha;
-    S->acc_rho = 0.0;
-    S->acc_rr = 0.0;
+    S->rho_old = rho;
+    S->acc_ts = 0.0;
+    S->acc_tt = 0.0;
+    S->acc_rt = 0.0;
   }
 }
 
-// K4: t = J shat; (t, s), (t, t).
+// D: t = J shat; (t,s), (t,t), (rhat,t).
 template <int D, class T>
-__global__ void __launch_bounds__(KTPB) k_bicg_4(DevGrid G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
+__global__ void __launch_bounds__(KTPB) k_bicg_D(DevGrid G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
   if (S->done) return;
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[2] = {0.0, 0.0};
+  double acc[3] = {0.0, 0.0, 0.0};
   if (row < *K.nrow) {
     const long long i = K.rows[row];
     T y[D];
     spmv_row<D, T>(K, row, i, G.nx1, G.ny1, v.shat, y);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
-      v.t[i * D + a] = y[a];
-      acc[0] += (double)y[a] * (double)v.s[i * D + a];
+      const long long d = i * D + a;
+      v.t[d] = y[a];
+      acc[0] += (double)y[a] * (double)v.s[d];
       acc[1] += (double)y[a] * (double)y[a];
+      acc[2] += (double)v.rhat[d] * (double)y[a];
     }
   }
-  double* outs[2] = {&S->acc_ts, &S->acc_tt};
-  block_accumulate<2>(acc, outs);
+  double* outs[3] = {&S->acc_ts, &S->acc_tt, &S->acc_rt};
+  block_accumulate<3>(acc, outs);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S->acc_rv = 0.0;
+    S->acc_vv = 0.0;
+    S->iter = S->iter + 1;
+  }
 }
 
-// K5: omega = (t,s)/(t,t); x += alpha phat + omega shat; r = s - omega t;
-// (rhat, r) and (r, r) for the next iteration.
+// A: omega; x and r updates; rho', ||r||^2 from the reduced products; the
+// next search direction p and phat.
 template <int D, class T>
-__global__ void __launch_bounds__(KTPB) k_bicg_5(DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
+__global__ void __launch_bounds__(KTPB) k_bicg_A(DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
   if (S->done) return;
-  const double tt = S->acc_tt;
-  const double omega = (tt > 0.0) ? S->acc_ts / tt : 0.0;
-  const T ta = (T)S->alpha, tw = (T)omega;
+  const double tt = S->acc_tt, ts = S->acc_ts;
+  const double omega = (tt > 0.0) ? ts / tt : 0.0;
+  const double alpha = S->alpha, rho_old = S->rho_old;
+  const double rho_new = S->acc_rs - omega * S->acc_rt;
+  const double rr = fmax(S->acc_ss - 2.0 * omega * ts + omega * omega * tt, 0.0);
+  const double beta = (omega != 0.0 && rho_old != 0.0) ? (rho_new / rho_old) * (alpha / omega) : 0.0;
+  const T ta = (T)alpha, tw = (T)omega, tb = (T)beta;
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[2] = {0.0, 0.0};
   if (row < *K.nrow) {
     const long long i = K.rows[row];
+    T p[D], z[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) {
       const long long d = i * D + a;
       v.x[d] += ta * v.phat[d] + tw * v.shat[d];
-      T rn = v.s[d] - tw * v.t[d];
+      const T rn = v.s[d] - tw * v.t[d];
       v.r[d] = rn;
-      acc[0] += (double)v.rhat[d] * (double)rn;
-      acc[1] += (double)rn * (double)rn;
+      p[a] = rn + tb * (v.p[d] - tw * v.v[d]);
+      v.p[d] = p[a];
     }
+    precond_row<D, T>(K, row, p, z);
+#pragma unroll
+    for (int a = 0; a < D; ++a) v.phat[i * D + a] = z[a];
   }
-  double* outs[2] = {&S->acc_rho, &S->acc_rr};
-  block_accumulate<2>(acc, outs);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     S->omega = omega;
-    S->iter = S->iter + 1;
+    S->rho = rho_new;
+    S->rr_last = rr;
   }
+}
+
+// restart from the current x: r = b - J x (the true residual), rhat = r,
+// p = r, phat = M^-1 r; rho = (rhat, r), rr_last = (r, r), rhat2 = (r, r).
+template <int D, class T>
+__global__ void __launch_bounds__(KTPB) k_bicg_restart(DevGrid G, DevMatrix<T> K, const double* __restrict__ res,
+                                                       const uint8_t* __restrict__ fixed, KrylovVecs<D, T> v,
+                                                       KrylovScalars* S, double tol2, int maxit) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc = 0.0;
+  if (row < *K.nrow) {
+    const long long i = K.rows[row];
+    T y[D], r[D], z[D];
+    spmv_row<D, T>(K, row, i, G.nx1, G.ny1, v.x, y);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const long long d = i * D + a;
+      const T b = fixed[d] ? (T)0 : (T)(-res[d]);
+      r[a] = b - y[a];
+      v.r[d] = r[a];
+      v.rhat[d] = r[a];
+      v.p[d] = r[a];
+      acc += (double)r[a] * (double)r[a];
+    }
+    precond_row<D, T>(K, row, r, z);
+#pragma unroll
+    for (int a = 0; a < D; ++a) v.phat[i * D + a] = z[a];
+  }
+  double acc3[3] = {acc, acc, acc};
+  double* outs[3] = {&S->rr_last, &S->rho, &S->rhat2};
+  block_accumulate<3>(acc3, outs);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S->alpha = 1.0;
+    S->omega = 1.0;
+    S->tol2 = tol2;
+    S->maxit = maxit;
+    S->iter = 0;
+    S->done = 0;
+    S->status = KS_OK;
+  }
+}
+
+template <int D, class T>
+cudaError_t launch_bicgstab_restart(const DevGrid& G, DevMatrix<T> K, const double* res, const uint8_t* fixed,
+                                    KrylovVecs<D, T> v, KrylovScalars* S, double tol2, int maxit, int nblk,
+                                    cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(S, 0, sizeof(KrylovScalars), st);
+  if (e != cudaSuccess) return e;
+  k_bicg_restart<D, T><<<nblk, KTPB, 0, st>>>(G, K, res, fixed, v, S, tol2, maxit);
+  return cudaGetLastError();
 }
 
 template <int D, class T>
@@ -287,14 +357,12 @@ cudaError_t launch_bicgstab_init(DevMatrix<T> K, const double* res, const uint8_
 template <int D, class T>
 cudaError_t launch_bicgstab_iter(const DevGrid& G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S,
                                  int nblk, cudaStream_t st) {
-  k_bicg_1<D, T><<<nblk, KTPB, 0, st>>>(K, v, S);
-  k_bicg_2<D, T><<<nblk, KTPB, 0, st>>>(G, K, v, S);
-  k_bicg_3<D, T><<<nblk, KTPB, 0, st>>>(K, v, S);
-  k_bicg_4<D, T><<<nblk, KTPB, 0, st>>>(G, K, v, S);
-  k_bicg_5<D, T><<<nblk, KTPB, 0, st>>>(K, v, S);
+  k_bicg_B<D, T><<<nblk, KTPB, 0, st>>>(G, K, v, S);
+  k_bicg_C<D, T><<<nblk, KTPB, 0, st>>>(K, v, S);
+  k_bicg_D<D, T><<<nblk, KTPB, 0, st>>>(G, K, v, S);
+  k_bicg_A<D, T><<<nblk, KTPB, 0, st>>>(K, v, S);
   return cudaGetLastError();
 }
-
 // du = base + alpha d on the free DOFs (the halved step of a Newton iteration
 // whose full step drove a return map out of its domain).
 template <int D, class T>
@@ -359,6 +427,9 @@ cudaError_t launch_update_du(DevMatrix<T> K, const T* x, const uint8_t* fixed, d
                                                   cudaStream_t);                                        \
   template cudaError_t launch_bicgstab_iter<D, T>(const DevGrid&, DevMatrix<T>, KrylovVecs<D, T>,       \
                                                   KrylovScalars*, int, cudaStream_t);                   \
+  template cudaError_t launch_bicgstab_restart<D, T>(const DevGrid&, DevMatrix<T>, const double*,       \
+                                                     const uint8_t*, KrylovVecs<D, T>, KrylovScalars*,  \
+                                                     double, int, int, cudaStream_t);                   \
   template cudaError_t launch_update_du<D, T>(DevMatrix<T>, const T*, const uint8_t*, double*, int,     \
                                               cudaStream_t);                                            \
   template cudaError_t launch_spmv<D, T>(const DevGrid&, DevMatrix<T>, const T*, T*, int, cudaStream_t);  \

@@ -1,26 +1,24 @@
 // Persistent (cooperative) BiCGStab: the whole right-preconditioned
 // BiCGStab solve of J d = -r runs as ONE kernel launch per Newton iteration.
 // Its five phases per iteration are separated by a grid barrier instead of
-// kernel boundaries, removing the per-kernel launch and drain latency that
-// dominates the multi-kernel form on L2-resident 2D problems.
+// kernel boundaries, removing the per-kernel launch and drain latency of the
+// multi-kernel form.
 //
-// Same-address atomics are what makes a naive grid-wide form slow (every
-// barrier and every dot product serialises one atomic per block on one L2
-// line), so:
-//  * dot products are deterministic two-level sums: each block writes its
-//    partial to its own slot; after the barrier every block adds all slots in
-//    the same order, so every block holds bit-identical scalars (alpha, beta,
-//    omega, the convergence test) without any further communication;
-//  * the grid barrier is a two-level tree: blocks arrive on one of NGROUP
-//    counters (each on its own 128-byte line), the last arrival of a group
-//    arrives on the root, the last root arrival advances the generation word.
-// Every spin is bounded (about a second): on timeout the block raises
-// ERRF_BARRIER and returns; every other block then returns at its next
-// barrier.  Launched with cudaLaunchCooperativeKernel (all blocks co-resident).
-//
-// Coherence: vectors written inside the kernel are read with ld.global.cg
-// (L2, not the non-coherent L1); the matrix, the block-Jacobi inverse and
-// rhat, constant during the solve, use the read-only path.
+//  * Grid barrier: a monotonic arrival counter (zeroed at launch); one
+//    release-add per block, acquire-reads while waiting, no reset between
+//    barriers.  Every spin is bounded (about a second): on timeout the block
+//    raises ERRF_BARRIER and returns; every other block then returns at its
+//    next barrier.  Launched with cudaLaunchCooperativeKernel, so all blocks
+//    are co-resident.
+//  * Memory ordering: vectors written inside the kernel are read with
+//    ordinary (weak) loads after the barrier; the release-add / acquire-read
+//    pair plus __syncthreads orders them after the writes of every block
+//    (PTX memory model), so they may use L1.  The matrix, the block-Jacobi
+//    inverse and rhat, constant over the kernel, use the read-only path.
+//  * Dot products: block sums, then one atomic add per block into an
+//    accumulator that is zeroed two barriers away from both its last read
+//    and its next accumulation.  Every block reads the same accumulated
+//    value after the barrier, so all blocks take identical decisions.
 #include <algorithm>
 
 #include "mpm_internal.h"
@@ -30,8 +28,6 @@ namespace mpm {
 namespace {
 constexpr int PTPB = 512;
 constexpr int RSPLIT = 4;     // threads per row in the products
-constexpr int NGROUP = 16;    // barrier tree fan-in groups
-constexpr int LINE = 32;      // unsigned ints per 128-byte line
 
 __device__ __forceinline__ double wsum(double v) {
 #pragma unroll
@@ -39,9 +35,9 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
-// Block-wide sum of NV values; the result is returned to every thread.
+// Add the block's sums of NV values to out[k] (one atomic per block and value).
 template <int NV>
-__device__ __forceinline__ void block_sum(double v[NV]) {
+__device__ __forceinline__ void block_add(double v[NV], double* const out[NV]) {
   __shared__ double sh[NV][PTPB / 32];
 #pragma unroll
   for (int k = 0; k < NV; ++k) v[k] = wsum(v[k]);
@@ -51,99 +47,72 @@ __device__ __forceinline__ void block_sum(double v[NV]) {
     for (int k = 0; k < NV; ++k) sh[k][w] = v[k];
   }
   __syncthreads();
+  if (w == 0) {
 #pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double t = (lane < PTPB / 32) ? sh[k][lane] : 0.0;
-    v[k] = wsum(t);
-  }
-  __syncthreads();
-}
-
-// Write this block's NV partials to part[k*stride + block].
-template <int NV>
-__device__ __forceinline__ void publish(double v[NV], double* part, int stride) {
-  block_sum<NV>(v);
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) part[k * stride + blockIdx.x] = v[k];
+    for (int k = 0; k < NV; ++k) {
+      double t = (lane < PTPB / 32) ? sh[k][lane] : 0.0;
+      t = wsum(t);
+      if (lane == 0 && t != 0.0) atomicAdd(out[k], t);
+    }
   }
 }
 
-// Every block: sum the NV partial arrays in a fixed order (bitwise identical
-// in all blocks).
-template <int NV>
-__device__ __forceinline__ void gather(const double* part, int stride, int nb, double out[NV]) {
-  double v[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = 0.0;
-  // thread t adds blocks t, t + PTPB, ... ; the block sum then fixes the order
-  for (int b = threadIdx.x; b < nb; b += PTPB) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] += __ldcg(&part[k * stride + b]);
-  }
-  block_sum<NV>(v);
-#pragma unroll
-  for (int k = 0; k < NV; ++k) out[k] = v[k];
+__device__ __forceinline__ unsigned int atom_add_release(unsigned int* p, unsigned int v) {
+  unsigned int old;
+  asm volatile("atom.add.release.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
 
-// Returns false when a barrier timed out (the caller returns).
-__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, int* err) {
+// Barrier number `epoch` completes when the counter reaches (epoch+1)*nblocks.
+// Returns false when the wait timed out (the caller returns).
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, int* err,
+                                             unsigned int& epoch) {
   __syncthreads();
   __shared__ int timed_out;
   if (threadIdx.x == 0) {
     timed_out = 0;
-    volatile unsigned int* vgen = &bar[(NGROUP + 1) * LINE];
-    const unsigned int g = *vgen;
-    __threadfence();
-    const unsigned int grp = blockIdx.x % NGROUP;
-    const unsigned int gsize = (nblocks - grp + NGROUP - 1) / NGROUP;
-    const unsigned int ngroups = nblocks < NGROUP ? nblocks : NGROUP;
-    bool last = false;
-    if (atomicAdd(&bar[grp * LINE], 1u) + 1u == gsize) {
-      atomicExch(&bar[grp * LINE], 0u);
-      if (atomicAdd(&bar[NGROUP * LINE], 1u) + 1u == ngroups) {
-        atomicExch(&bar[NGROUP * LINE], 0u);
-        __threadfence();
-        atomicAdd((unsigned int*)vgen, 1u);
-        last = true;
+    atom_add_release(bar, 1u);
+    const unsigned int target = (epoch + 1u) * nblocks;
+    // each acquire read goes to L2 (a few hundred ns), so 2^22 reads bound
+    // the wait at roughly one to two seconds
+    unsigned int spins = 0;
+    while (ld_acquire(bar) < target) {
+      if (++spins > (1u << 22)) {
+        atomicOr(err, ERRF_BARRIER);
+        timed_out = 1;
+        break;
       }
     }
-    if (!last) {
-      unsigned int spins = 0;
-      while (*vgen == g) {
-        if (++spins > (1u << 25)) {
-          atomicOr(err, ERRF_BARRIER);
-          timed_out = 1;
-          break;
-        }
-        __nanosleep(20);
-      }
-    }
-    __threadfence();
   }
+  ++epoch;
   __syncthreads();
   return !timed_out && !(*(volatile int*)err & ERRF_BARRIER);
 }
 
-// Partial product of one row over the slots sub, sub+RSPLIT, ...
+// Partial product of one row over the slots sub, sub+RSPLIT, ...; s_off holds
+// the node offset of every slot (shared memory, filled once per block).
 template <int D, class T>
-__device__ __forceinline__ void spmv_part(const DevMatrix<T>& K, int row, long long i, int sub, int nx1,
-                                          int ny1, const T* x, T y[D]) {
+__device__ __forceinline__ void spmv_part(const DevMatrix<T>& K, int row, long long i, int sub,
+                                          const int* s_off, const T* x, T y[D]) {
   constexpr int S = (D == 2) ? 25 : 125;
 #pragma unroll
   for (int a = 0; a < D; ++a) y[a] = (T)0;
-  const long long cap = K.cap;
+  const T* base = K.val + (long long)row * (D * D);
+  const long long plane = (long long)K.cap * (D * D);
 #pragma unroll 4
   for (int slot = sub; slot < S; slot += RSPLIT) {
-    const int dx = slot % 5 - 2, dy = (slot / 5) % 5 - 2, dz = (D == 3) ? slot / 25 - 2 : 0;
-    const long long j = i + dx + (long long)nx1 * (dy + (long long)ny1 * dz);
-    T xj[D];
-#pragma unroll
-    for (int b = 0; b < D; ++b) xj[b] = __ldcg(&x[j * D + b]);
+    T xj[D], kb[D * D];
+    ld_node<D, T, true>(x, i + s_off[slot], xj);
+    ld_block<D, T>(base + slot * plane, kb);
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int b = 0; b < D; ++b) y[a] += __ldg(&K.val[((long long)(slot * D + a) * D + b) * cap + row]) * xj[b];
+      for (int b = 0; b < D; ++b) y[a] += kb[a * D + b] * xj[b];
   }
 #pragma unroll
   for (int a = 0; a < D; ++a) {
@@ -152,32 +121,52 @@ __device__ __forceinline__ void spmv_part(const DevMatrix<T>& K, int row, long l
   }
 }
 
-// partial-slot arrays: index k * PSTRIDE + block
-constexpr int P_RV = 0, P_TS = 1, P_TT = 2, P_RHO = 3, P_RR = 4;
+template <int D, class T>
+__device__ __forceinline__ void precond(const DevMatrix<T>& K, int row, const T v[D], T z[D]) {
+  T m[D * D];
+  ld_block<D, T>(&K.dinv[(long long)row * (D * D)], m);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    T s = (T)0;
+#pragma unroll
+    for (int b = 0; b < D; ++b) s += m[a * D + b] * v[b];
+    z[a] = s;
+  }
+}
 }  // namespace
 
-// S must hold what k_bicg_init leaves: acc_rr = (r,r), acc_rho = (rhat, r),
-// tol2, maxit.  part holds 5 * PERSIST_MAX_BLOCKS doubles; bar the barrier
-// words (zeroed by the launcher).
+// S must hold what k_bicg_init leaves: rr_last = (r,r), rho = (rhat, r),
+// tol2, maxit, and zero accumulators.  bar is zeroed by the launcher.
 template <int D, class T>
 __global__ void __launch_bounds__(PTPB) k_bicg_persistent(DevGrid G, DevMatrix<T> K, KrylovVecs<D, T> v,
                                                           KrylovScalars* S, double* part, unsigned int* bar,
                                                           int* err) {
-  constexpr int PS = PERSIST_MAX_BLOCKS;
+  (void)part;
   const unsigned int nb = gridDim.x;
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long gsz = (long long)gridDim.x * blockDim.x;
   const int nrow = *K.nrow;
   const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
-  const double tol2 = S->tol2;
-  const int maxit = S->maxit;
-  // scalars, identical in every block
-  double rr = S->acc_rr, rho_new = S->acc_rho;
+  constexpr int NSLOT = (D == 2) ? 25 : 125;
+  __shared__ int s_off[NSLOT];
+  for (int slot = threadIdx.x; slot < NSLOT; slot += blockDim.x) {
+    const int dx = slot % 5 - 2, dy = (slot / 5) % 5 - 2, dz = (D == 3) ? slot / 25 - 2 : 0;
+    s_off[slot] = dx + G.nx1 * (dy + G.ny1 * dz);
+  }
+  __syncthreads();
+  volatile KrylovScalars* VS = S;
+  const double tol2 = VS->tol2;
+  const int maxit = VS->maxit;
   double rho = 1.0, alpha = 1.0, omega = 1.0;
   int status = 0;
   int it = 0;
+  unsigned int epoch = 0;
+  double rr = VS->acc_rr;
   for (;; ++it) {
     // ---- P1: convergence test; p = r + beta (p - omega v); phat = M^-1 p
+    // (the first iteration takes (rhat, r0) and (r0, r0) from the init kernel)
+    const double rho_new = (it == 0) ? VS->rho : VS->acc_rho;
+    rr = (it == 0) ? VS->rr_last : VS->acc_rr;
     const bool conv = rr <= tol2;
     const bool maxed = it >= maxit;
     const bool bad = (it > 0 && (rho == 0.0 || omega == 0.0)) || !(rr == rr);
@@ -190,24 +179,21 @@ __global__ void __launch_bounds__(PTPB) k_bicg_persistent(DevGrid G, DevMatrix<T
       const T tb = (T)beta, tw = (T)omega;
       for (long long row = gtid; row < nrow; row += gsz) {
         const long long i = K.rows[row];
-        T p[D];
+        T p[D], z[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) {
           const long long d = i * D + a;
-          p[a] = __ldcg(&v.r[d]) + tb * (__ldcg(&v.p[d]) - tw * __ldcg(&v.v[d]));
+          p[a] = v.r[d] + tb * (v.p[d] - tw * v.v[d]);
           v.p[d] = p[a];
         }
+        precond<D, T>(K, (int)row, p, z);
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-          T z = (T)0;
-#pragma unroll
-          for (int b = 0; b < D; ++b) z += __ldg(&K.dinv[(long long)(a * D + b) * K.cap + row]) * p[b];
-          v.phat[i * D + a] = z;
-        }
+        for (int a = 0; a < D; ++a) v.phat[i * D + a] = z[a];
       }
     }
     rho = rho_new;
-    if (!grid_barrier(bar, nb, err)) return;
+    if (lead) S->acc_ts = 0.0, S->acc_tt = 0.0;   // last read in P5 of the previous iteration
+    if (!grid_barrier(bar, nb, err, epoch)) return;
     // ---- P2: v = J phat; (rhat, v)
     {
       double acc[1] = {0.0};
@@ -219,7 +205,7 @@ __global__ void __launch_bounds__(PTPB) k_bicg_persistent(DevGrid G, DevMatrix<T
         const int sub = (int)(w % RSPLIT);
         const long long i = live ? K.rows[row] : 0;
         T y[D];
-        spmv_part<D, T>(K, row, i, live ? sub : 1000, G.nx1, G.ny1, v.phat, y);
+        spmv_part<D, T>(K, row, i, live ? sub : 1000, s_off, v.phat, y);
         if (live && sub == 0) {
 #pragma unroll
           for (int a = 0; a < D; ++a) {
@@ -228,38 +214,35 @@ __global__ void __launch_bounds__(PTPB) k_bicg_persistent(DevGrid G, DevMatrix<T
           }
         }
       }
-      publish<1>(acc, part + P_RV * PS, PS);
+      double* outs[1] = {&S->acc_rv};
+      block_add<1>(acc, outs);
     }
-    if (!grid_barrier(bar, nb, err)) return;
+    if (!grid_barrier(bar, nb, err, epoch)) return;
     // ---- P3: alpha = rho / (rhat, v); s = r - alpha v; shat = M^-1 s
     {
-      double rv[1];
-      gather<1>(part + P_RV * PS, PS, nb, rv);
-      if (rv[0] == 0.0 || !(rv[0] == rv[0])) {
+      const double rv = VS->acc_rv;
+      if (rv == 0.0 || !(rv == rv)) {
         status = 2;
         break;
       }
-      alpha = rho / rv[0];
+      alpha = rho / rv;
       const T ta = (T)alpha;
       for (long long row = gtid; row < nrow; row += gsz) {
         const long long i = K.rows[row];
-        T s[D];
+        T s[D], z[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) {
           const long long d = i * D + a;
-          s[a] = __ldcg(&v.r[d]) - ta * __ldcg(&v.v[d]);
+          s[a] = v.r[d] - ta * v.v[d];
           v.s[d] = s[a];
         }
+        precond<D, T>(K, (int)row, s, z);
 #pragma unroll
-        for (int a = 0; a < D; ++a) {
-          T z = (T)0;
-#pragma unroll
-          for (int b = 0; b < D; ++b) z += __ldg(&K.dinv[(long long)(a * D + b) * K.cap + row]) * s[b];
-          v.shat[i * D + a] = z;
-        }
+        for (int a = 0; a < D; ++a) v.shat[i * D + a] = z[a];
       }
+      if (lead) S->acc_rho = 0.0, S->acc_rr = 0.0;   // last read in P1
     }
-    if (!grid_barrier(bar, nb, err)) return;
+    if (!grid_barrier(bar, nb, err, epoch)) return;
     // ---- P4: t = J shat; (t, s), (t, t)
     {
       double acc[2] = {0.0, 0.0};
@@ -271,25 +254,26 @@ __global__ void __launch_bounds__(PTPB) k_bicg_persistent(DevGrid G, DevMatrix<T
         const int sub = (int)(w % RSPLIT);
         const long long i = live ? K.rows[row] : 0;
         T y[D];
-        spmv_part<D, T>(K, row, i, live ? sub : 1000, G.nx1, G.ny1, v.shat, y);
+        spmv_part<D, T>(K, row, i, live ? sub : 1000, s_off, v.shat, y);
         if (live && sub == 0) {
 #pragma unroll
           for (int a = 0; a < D; ++a) {
             v.t[i * D + a] = y[a];
-            const double sv = (double)__ldcg(&v.s[i * D + a]);
+            const double sv = (double)v.s[i * D + a];
             acc[0] += (double)y[a] * sv;
             acc[1] += (double)y[a] * (double)y[a];
           }
         }
       }
-      publish<2>(acc, part + P_TS * PS, PS);
+      double* outs[2] = {&S->acc_ts, &S->acc_tt};
+      block_add<2>(acc, outs);
+      if (lead) S->acc_rv = 0.0;   // last read in P3
     }
-    if (!grid_barrier(bar, nb, err)) return;
+    if (!grid_barrier(bar, nb, err, epoch)) return;
     // ---- P5: omega; x += alpha phat + omega shat; r = s - omega t; (rhat,r), (r,r)
     {
-      double tsn[2];
-      gather<2>(part + P_TS * PS, PS, nb, tsn);
-      omega = (tsn[1] > 0.0) ? tsn[0] / tsn[1] : 0.0;
+      const double tt = VS->acc_tt;
+      omega = (tt > 0.0) ? VS->acc_ts / tt : 0.0;
       const T ta = (T)alpha, tw = (T)omega;
       double acc[2] = {0.0, 0.0};
       for (long long row = gtid; row < nrow; row += gsz) {
@@ -297,22 +281,17 @@ __global__ void __launch_bounds__(PTPB) k_bicg_persistent(DevGrid G, DevMatrix<T
 #pragma unroll
         for (int a = 0; a < D; ++a) {
           const long long d = i * D + a;
-          v.x[d] = __ldcg(&v.x[d]) + ta * __ldcg(&v.phat[d]) + tw * __ldcg(&v.shat[d]);
-          const T rn = __ldcg(&v.s[d]) - tw * __ldcg(&v.t[d]);
+          v.x[d] = v.x[d] + ta * v.phat[d] + tw * v.shat[d];
+          const T rn = v.s[d] - tw * v.t[d];
           v.r[d] = rn;
           acc[0] += (double)__ldg(&v.rhat[d]) * (double)rn;
           acc[1] += (double)rn * (double)rn;
         }
       }
-      publish<2>(acc, part + P_RHO * PS, PS);
+      double* outs[2] = {&S->acc_rho, &S->acc_rr};
+      block_add<2>(acc, outs);
     }
-    if (!grid_barrier(bar, nb, err)) return;
-    {
-      double rr2[2];
-      gather<2>(part + P_RHO * PS, PS, nb, rr2);
-      rho_new = rr2[0];
-      rr = rr2[1];
-    }
+    if (!grid_barrier(bar, nb, err, epoch)) return;
   }
   if (lead) {
     S->done = 1;

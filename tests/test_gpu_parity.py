@@ -165,13 +165,13 @@ def test_mixed_precision_footing_converges_and_states_error():
 
 
 @pytest.mark.parametrize("precision", [mpm.MPM_FP64, mpm.MPM_MIXED])
-def test_multikernel_graph_krylov_path_matches_persistent(precision, monkeypatch):
-    """The multi-kernel CUDA-graph BiCGStab (fallback when cooperative launch
-    is unavailable) converges to the same step as the persistent kernel."""
+def test_persistent_krylov_path_matches_graph_path(precision, monkeypatch):
+    """The single cooperative BiCGStab kernel (MPM_KRYLOV_PERSISTENT=1)
+    converges to the same step as the default CUDA-graph form."""
     sc = S.footing(nx=48, ny=24, h=0.5, nsteps=20, settle_frac=0.1)
     out = []
-    for graph in ("1", "0"):
-        monkeypatch.setenv("MPM_KRYLOV_GRAPH", graph)
+    for persistent in ("0", "1"):
+        monkeypatch.setenv("MPM_KRYLOV_PERSISTENT", persistent)
         gs = mpm.GpuScene(sc, precision=precision, newton_tol=1e-10, forcing=mpm.MPM_FORCING_FIXED,
                           krylov_rtol=1e-12 if precision == mpm.MPM_FP64 else 1e-6)
         for st in sc.steps[:2]:
