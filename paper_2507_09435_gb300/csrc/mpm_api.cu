@@ -83,6 +83,13 @@ struct mpm_scene {
   long long launches = 0;   // kernels launched by this scene
   long long halvings = 0;   // Newton steps halved after a return-map failure
   long long restarts = 0;   // BiCGStab restarts after a breakdown or the limit
+  // GMRES(m)
+  int gm = 0;
+  void* d_gvec = nullptr;
+  GmresState* d_gst = nullptr;
+  char* h_gst = nullptr;              // pinned copy of the scalar tail of GmresState
+  cudaGraphExec_t gexec_gm = nullptr;
+  int gm_graph_cap = -1;
   double* d_duprev = nullptr;
   int pblocks = 0;          // co-resident blocks for the persistent Krylov kernel (0 = use graphs)
   unsigned int* d_bar = nullptr;   // barrier counter of the persistent kernel
@@ -365,6 +372,51 @@ void assemble_impl(mpm_scene* s) {
   s->launches += 3;
 }
 
+// Restarted GMRES(m) on J d = -r to an absolute residual `tol`: cycles of m
+// Arnoldi steps (one CUDA graph per cycle), polled once per cycle.
+template <int D, class T>
+void gmres_solve(mpm_scene* s, DevMatrix<T> K, T* x, double tol, int nblk, int& kit, int& kstat, double& kres2) {
+  cudaStream_t st = s->st;
+  T* base = (T*)s->d_gvec;
+  GmresVecs<T> g;
+  g.base = base;
+  g.stride = s->vlen;
+  g.pad = s->vpad;
+  g.w = base + (long long)(s->gm + 1) * s->vlen + s->vpad;
+  g.z = base + (long long)(s->gm + 2) * s->vlen + s->vpad;
+  if (s->use_graph && s->gm_graph_cap != s->cap) {
+    if (s->gexec_gm) {
+      cudaGraphExecDestroy(s->gexec_gm);
+      s->gexec_gm = nullptr;
+    }
+    cudaGraph_t gr;
+    ck(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "capture");
+    launch_gmres_cycle<D, T>(s->G, K, g, x, s->d_gst, s->gm, nblk, st);
+    ck(cudaStreamEndCapture(st, &gr), "end capture");
+    ck(cudaGraphInstantiate(&s->gexec_gm, gr, 0), "instantiate");
+    cudaGraphDestroy(gr);
+    s->gm_graph_cap = s->cap;
+  }
+  const size_t tail = offsetof(GmresState, wn2);
+  const size_t tail_bytes = sizeof(GmresState) - tail;
+  GmresState* h = (GmresState*)(s->h_gst - tail);   // fields from wn2 on are valid
+  for (int cycle = 0;; ++cycle) {
+    ck(launch_gmres_begin<D, T>(s->G, K, s->d_r, s->d_fixed, g, x, s->d_gst, cycle == 0 ? 1 : 0, tol,
+                                s->desc.krylov_maxit, nblk, st),
+       "gmres begin");
+    s->launches += 3;
+    if (s->use_graph) ck(cudaGraphLaunch(s->gexec_gm, st), "graph launch");
+    else ck(launch_gmres_cycle<D, T>(s->G, K, g, x, s->d_gst, s->gm, nblk, st), "gmres cycle");
+    s->launches += 4LL * s->gm + 2;
+    ck(cudaMemcpyAsync(s->h_gst, (char*)s->d_gst + tail, tail_bytes, cudaMemcpyDeviceToHost, st), "copy");
+    ck(cudaStreamSynchronize(st), "sync");
+    if (h->finished || h->iter >= s->desc.krylov_maxit || cycle > s->desc.krylov_maxit) break;
+  }
+  kit = h->iter;
+  kstat = h->status;
+  kres2 = h->res * h->res;
+}
+
 template <int D, class T>
 void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
   if (!s->staged) fail(MPM_ERR_STATE, "no load step staged (call mpm_begin_step)");
@@ -395,6 +447,11 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
   cudaEventRecord(s->ev[1], st);
   KrylovVecs<D, T> v = vecview<D, T>(s);
   double tol2 = eta * eta * s->rk * s->rk;
+  int kit = 0, kstat = 0;
+  double kres2 = 0.0;
+  if (s->gm > 0) {
+    gmres_solve<D, T>(s, K, v.x, eta * s->rk, nblk, kit, kstat, kres2);
+  } else {
   ck(launch_bicgstab_init<D, T>(K, s->d_r, s->d_fixed, v, s->d_S, tol2, s->desc.krylov_maxit, nblk, st),
      "krylov init");
   const int pblk = std::min(s->pblocks, std::max(1, (s->nrow * 4 + 511) / 512));
@@ -409,7 +466,6 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
     check_err_bits(s);
   }
   if (s->pblocks == 0 && s->use_graph && s->graph_cap != s->cap) build_graph<D, T>(s, nblk);
-  int kit = 0, kstat = 0;
   if (s->pblocks == 0) {
     // graph chunks of GRAPH_CHUNK iterations until the done flag; on a
     // (near) breakdown or the iteration limit, restart from the current x
@@ -443,7 +499,9 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
     kit = s->h_S->iter;
     kstat = s->h_S->status;
   }
-  const double krel = (s->rk > 0) ? std::sqrt(std::max(s->h_S->rr_last, 0.0)) / s->rk : 0.0;
+  kres2 = s->h_S->rr_last;
+  }
+  const double krel = (s->rk > 0) ? std::sqrt(std::max(kres2, 0.0)) / s->rk : 0.0;
   ck(cudaMemcpyAsync(s->d_duprev, s->d_du, s->ndof * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy du");
   ck(launch_update_du<D, T>(K, v.x, s->d_fixed, s->d_du, nblk, st), "update");
   s->launches += 2;   // Krylov init + update
@@ -589,6 +647,8 @@ void destroy(mpm_scene* s) {
   if (s->st) cudaStreamSynchronize(s->st);
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
   for (void* p : s->allocs) cudaFree(p);
+  if (s->gexec_gm) cudaGraphExecDestroy(s->gexec_gm);
+  if (s->h_gst) cudaFreeHost(s->h_gst);
   if (s->h_S) cudaFreeHost(s->h_S);
   if (s->h_int) cudaFreeHost(s->h_int);
   if (s->h_dbl) cudaFreeHost(s->h_dbl);
@@ -762,6 +822,15 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
     else s->d_vec = s->dalloc<double>(9 * s->vlen);
     ck(cudaMemsetAsync(s->d_vec, 0, 9 * s->vlen * T, s->st), "memset");
     s->d_S = s->dalloc<KrylovScalars>(1);
+    if (desc->krylov == MPM_GMRES) {
+      s->gm = desc->gmres_restart > 0 ? std::min(std::max(desc->gmres_restart, 2), GMRES_MMAX) : 30;
+      const size_t nv = (size_t)(s->gm + 3) * s->vlen;
+      if (s->mixed) s->d_gvec = s->dalloc<float>(nv);
+      else s->d_gvec = s->dalloc<double>(nv);
+      ck(cudaMemsetAsync(s->d_gvec, 0, nv * T, s->st), "memset");
+      s->d_gst = s->dalloc<GmresState>(1);
+      ck(cudaMallocHost(&s->h_gst, 128), "host alloc");
+    }
     s->d_bar = s->dalloc<unsigned int>(PERSIST_BAR_WORDS);
     s->d_part = s->dalloc<double>(5 * PERSIST_MAX_BLOCKS);
     {

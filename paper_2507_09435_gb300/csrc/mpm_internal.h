@@ -186,15 +186,27 @@ cudaError_t launch_bicgstab_persistent(const DevGrid& G, DevMatrix<T> K, KrylovV
                                        double* part, unsigned int* bar, int* err, int nblocks, cudaStream_t st);
 
 // GMRES(m) with classical Gram-Schmidt applied twice
-template <int D, class T>
-struct GmresWork {
-  T* V;            // (m+1) basis vectors, each nvec long
-  T* Z;            // m preconditioned vectors (flexible form: x = Z y)
-  long long nvec;  // length of one vector (nnode*D)
-  int m;
-  double* H;       // (m+1) x m Hessenberg, column-major, on device
-  double* dots;    // m+1 partial dot accumulators
-  double* cs;      // Givens cosines (m), sines (m), g (m+1)
+constexpr int GMRES_MMAX = 64;
+struct GmresState {
+  double H[(GMRES_MMAX + 1) * GMRES_MMAX];   // Hessenberg, column-major, leading dim MMAX+1
+  double cs[GMRES_MMAX], sn[GMRES_MMAX], gv[GMRES_MMAX + 1], y[GMRES_MMAX];
+  double h1[GMRES_MMAX + 1], h2[GMRES_MMAX + 1];  // projection accumulators of one step
+  double wn2, wn2b, res, tol;
+  int jdone, done, finished, status, iter, maxit;
 };
+template <class T>
+struct GmresVecs {
+  T* base;           // m+1 basis vectors, each `stride` elements, padded by `pad`
+  long long stride, pad;
+  T* w;              // Arnoldi work vector
+  T* z;              // preconditioned basis vector
+};
+template <int D, class T>
+cudaError_t launch_gmres_begin(const DevGrid& G, DevMatrix<T> K, const double* res, const uint8_t* fixed,
+                               GmresVecs<T> g, T* x, GmresState* st, int first, double tol, int maxit,
+                               int nblk, cudaStream_t s);
+template <int D, class T>
+cudaError_t launch_gmres_cycle(const DevGrid& G, DevMatrix<T> K, GmresVecs<T> g, T* x, GmresState* st, int m,
+                               int nblk, cudaStream_t s);
 
 }  // namespace mpm
