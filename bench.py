@@ -48,21 +48,44 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--krylov", default="bicgstab", choices=["bicgstab", "gmres"])
+    ap.add_argument("--workload", default="footing", choices=["footing", "column3d", "column3d_stated"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
 
-def workload_scene():
+WORKLOADS = {
+    # the 2D footing: the headline workload
+    "footing": "footing_256x128_dp",
+    # the 3D modified Cam-Clay column under a gravity ramp: ~2M particles
+    # (72x72x48-cell column, 8 per cell) and the stated 32x32x48-cell column
+    "column3d": "column3d_128x128x64_mcc_2M",
+    "column3d_stated": "column3d_128x128x64_mcc_393k",
+}
+
+
+def workload_scene(name="footing"):
     from paper_2507_09435_gb300 import scenes
-    return scenes.footing(nx=256, ny=128, h=0.1, ppc=2, nsteps=50)
+    if name == "footing":
+        return scenes.footing(nx=256, ny=128, h=0.1, ppc=2, nsteps=50)
+    if name == "column3d":
+        return scenes.column_collapse_3d(col=(72, 72, 48))
+    if name == "column3d_stated":
+        return scenes.column_collapse_3d(col=(32, 32, 48))
+    raise ValueError(name)
 
 
 def config(args, sc):
-    return {"workload": WORKLOAD, "grid": [sc.n[0], sc.n[1]], "h": sc.h, "particles": sc.np,
-            "ppc": 4, "model": "neo-hookean + drucker-prager (phi 30, psi 0, c 5 kPa)",
-            "precision": args.precision, "krylov": args.krylov, "preconditioner": "block-jacobi",
-            "newton_tol": 1e-8, "step": "one load step (footing increment 4 mm)",
+    if args.workload == "footing":
+        extra = {"ppc": 4, "model": "neo-hookean + drucker-prager (phi 30, psi 0, c 5 kPa)",
+                 "step": "one load step (footing increment 4 mm)"}
+    else:
+        extra = {"ppc": 8, "model": "neo-hookean + modified cam-clay (M 1.2, lambda 0.1, kappa 0.02, "
+                                    "pc0 lognormal sigma 0.1 about -100 kPa)",
+                 "step": "one load step of a 20-step gravity ramp"}
+    return {"workload": WORKLOADS[args.workload], "grid": [int(v) for v in sc.n[:sc.dim]], "h": sc.h,
+            "particles": sc.np, **extra, "precision": args.precision, "krylov": args.krylov,
+            "preconditioner": "block-jacobi", "newton_tol": 1e-8,
             "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas{args.gpus}"}
 
 
@@ -121,6 +144,25 @@ class ClockSampler:
 # CPU legs: the FP64 oracle, as it stands, on a bounded sample of the workload
 # ----------------------------------------------------------------------------
 
+def cpu_sample_scene(sc, workload):
+    """The bounded CPU sample of a workload and the factor that scales its
+    per-iteration time to the full workload.  2D footing: the whole scene.
+    3D column: a 6x6-cell sub-column through the full height (particle work,
+    Jacobian assembly and Krylov products all scale with the particle count)."""
+    if workload == "footing":
+        return sc, 1.0, "the whole workload"
+    import dataclasses
+    cx = np.floor(sc.x[:, 0] / sc.h).astype(int)
+    cy = np.floor(sc.x[:, 1] / sc.h).astype(int)
+    x0, y0 = cx.min(), cy.min()
+    sel = (cx < x0 + 6) & (cy < y0 + 6)
+    sub = dataclasses.replace(
+        sc, x=sc.x[sel], vol0=sc.vol0[sel], mass=sc.mass[sel], mat_id=sc.mat_id[sel],
+        E_p=None if sc.E_p is None else sc.E_p[sel], phi_p=None if sc.phi_p is None else sc.phi_p[sel],
+        pc0_p=None if sc.pc0_p is None else sc.pc0_p[sel], be0=None if sc.be0 is None else sc.be0[sel])
+    return sub, sc.np / sub.np, f"a 6x6-cell sub-column of {sub.np} particles, time scaled by {sc.np / sub.np:.1f}"
+
+
 def oracle_newton_sample(sc, krylov_iters, max_newton=1):
     """Time `max_newton` oracle Newton iterations of the geostatic step of the
     workload: oracle residual + exact Jacobian (C++, single thread) + a
@@ -159,14 +201,15 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    sc = workload_scene()
+    sc = workload_scene(args.workload)
     kry = float(os.environ.get("MPM_BENCH_KRYLOV_PER_NEWTON", "400"))
     for _ in range(max(0, min(args.warmup, 1))):
         pass  # the oracle has no warm-up state; each step is an independent bounded sample
+    sub, scale, what = cpu_sample_scene(sc, args.workload)
     times, iters = [], 0
     for _ in range(args.steps):
-        t, n = oracle_newton_sample(sc, kry, 1)
-        times.append(t)
+        t, n = oracle_newton_sample(sub, kry, 1)
+        times.append(t * scale)
         iters += n
     tot = sum(times)
     value = iters / tot
@@ -175,7 +218,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config(args, sc),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"1 oracle Newton iteration per step of the geostatic load step "
+                             "sample": f"1 oracle Newton iteration per step of the first load step on {what} "
                                        f"(residual + exact Jacobian + {int(kry)} block-Jacobi BiCGStab iterations)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -205,7 +248,7 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
     mpm.lib()   # build / load libmpm before timing
 
-    sc = workload_scene()
+    sc = workload_scene(args.workload)
     prec = mpm.MPM_MIXED if args.precision == "mixed" else mpm.MPM_FP64
     kry = mpm.MPM_BICGSTAB if args.krylov == "bicgstab" else mpm.MPM_GMRES
     stream = torch.cuda.Stream(device=dev)
@@ -283,7 +326,8 @@ def main():
             "bytes_per_iteration": bytes_iter, "us_per_iteration": 1e6 * t_kry_s / max(krylov, 1),
             "spmv_alone": {"kernel": "k_spmv", "ms_per_launch": spmv_ms, "bytes_per_launch": spmv_bytes,
                            "gbs": spmv_bytes / (spmv_ms * 1e-3) / 1e9},
-            "note": "2D footing matrix (about 13.6 MB FP32) is L2-resident; HBM fraction is not the bound here"}
+            "note": ("2D footing matrix (about 13.6 MB FP32) is L2-resident; HBM fraction is not the bound here"
+                     if sc.dim == 2 else "3D matrix exceeds L2 (129 MB): HBM-bound")}
 
     # ---- end to end through the C ABI with host buffers ----------------------
     e2e = None
@@ -324,11 +368,12 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         kpn = krylov_all / max(newton_all, 1.0)
-        t, n = oracle_newton_sample(sc, kpn, 1)
-        cpu = {"value": n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"1 oracle Newton iteration of the geostatic step (residual + exact Jacobian + "
-                         f"{int(round(kpn))} block-Jacobi BiCGStab iterations, the GPU's mean per Newton "
-                         f"iteration), {t:.1f} s"}
+        sub, scale, what = cpu_sample_scene(sc, args.workload)
+        t, n = oracle_newton_sample(sub, kpn, 1)
+        cpu = {"value": n / (t * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"1 oracle Newton iteration of the first load step on {what} (residual + exact "
+                         f"Jacobian + {int(round(kpn))} block-Jacobi BiCGStab iterations, the GPU's mean per "
+                         f"Newton iteration), {t:.1f} s"}
 
     if rank == 0:
         n_gpus = world

@@ -83,6 +83,8 @@ struct mpm_scene {
   long long launches = 0;   // kernels launched by this scene
   long long halvings = 0;   // Newton steps halved after a return-map failure
   long long restarts = 0;   // BiCGStab restarts after a breakdown or the limit
+  long long limited = 0;    // Newton corrections scaled by the step-length limit
+  unsigned long long* d_absmax = nullptr;
   // GMRES(m)
   int gm = 0;
   void* d_gvec = nullptr;
@@ -502,9 +504,20 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
   kres2 = s->h_S->rr_last;
   }
   const double krel = (s->rk > 0) ? std::sqrt(std::max(kres2, 0.0)) / s->rk : 0.0;
+  // step-length limit (reading): a Newton correction that would move a node
+  // by more than one cell width h is scaled down to h (a near-singular J, as
+  // at the onset of a mechanism, otherwise yields astronomically large steps)
+  ck(launch_absmax<D, T>(K, v.x, s->d_fixed, s->d_absmax, nblk, st), "absmax");
+  ck(cudaMemcpyAsync(s->h_dbl + 2, s->d_absmax, sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
+  ck(cudaStreamSynchronize(st), "sync");
+  const double xmax = s->h_dbl[2];
+  double step = 1.0;
+  if (!std::isfinite(xmax)) step = 0.0;
+  else if (xmax > s->G.h) step = s->G.h / xmax;
+  if (step < 1.0) s->limited += 1;
   ck(cudaMemcpyAsync(s->d_duprev, s->d_du, s->ndof * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy du");
-  ck(launch_update_du<D, T>(K, v.x, s->d_fixed, s->d_du, nblk, st), "update");
-  s->launches += 2;   // Krylov init + update
+  ck(launch_step_du<D, T>(K, v.x, s->d_fixed, s->d_duprev, s->d_du, step, nblk, st), "update");
+  s->launches += 3;   // Krylov init + absmax + update
   cudaEventRecord(s->ev[2], st);
   residual_pass<D, T>(s, 1);
   cudaEventRecord(s->ev[3], st);
@@ -513,7 +526,8 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
   // non-finite state) is halved, at most four times, before giving up
   for (int half = 1; half <= 4 && (s->h_int[2] & (ERRF_RETURN | ERRF_NONFINITE | ERRF_DET)); ++half) {
     ck(cudaMemsetAsync(s->d_err, 0, sizeof(int), st), "memset");
-    ck(launch_step_du<D, T>(K, v.x, s->d_fixed, s->d_duprev, s->d_du, std::ldexp(1.0, -half), nblk, st), "step");
+    ck(launch_step_du<D, T>(K, v.x, s->d_fixed, s->d_duprev, s->d_du, step * std::ldexp(1.0, -half), nblk, st),
+       "step");
     s->launches += 1;
     residual_pass<D, T>(s, 1);
     cudaEventRecord(s->ev[3], st);
@@ -803,6 +817,7 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
     s->d_M = s->dalloc<double>(nn);
     s->d_du = s->dalloc<double>(s->ndof);
     s->d_duprev = s->dalloc<double>(s->ndof);
+    s->d_absmax = s->dalloc<unsigned long long>(1);
     s->d_r = s->dalloc<double>(s->ndof);
     s->d_bcval = s->dalloc<double>(s->ndof);
     s->d_grav = s->dalloc<double>(3);

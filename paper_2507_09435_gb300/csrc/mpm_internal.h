@@ -174,6 +174,9 @@ cudaError_t launch_spmv(const DevGrid& G, DevMatrix<T> K, const T* x, T* y, int 
 template <int D, class T>
 cudaError_t launch_step_du(DevMatrix<T> K, const T* x, const uint8_t* fixed, const double* base, double* du,
                            double alpha, int nblk, cudaStream_t st);
+template <int D, class T>
+cudaError_t launch_absmax(DevMatrix<T> K, const T* x, const uint8_t* fixed, unsigned long long* out, int nblk,
+                          cudaStream_t st);
 // kernels launched by one scan_exclusive call of n elements
 int scan_launches(long long n);
 // persistent cooperative BiCGStab (one launch per solve); 0 blocks = unsupported

@@ -363,6 +363,35 @@ cudaError_t launch_bicgstab_iter(const DevGrid& G, DevMatrix<T> K, KrylovVecs<D,
   k_bicg_A<D, T><<<nblk, KTPB, 0, st>>>(K, v, S);
   return cudaGetLastError();
 }
+// max |d| over the free DOFs of the active rows, as the ordered bits of a
+// non-negative double (atomicMax on the integer image preserves the order).
+template <int D, class T>
+__global__ void k_absmax(DevMatrix<T> K, const T* __restrict__ x, const uint8_t* __restrict__ fixed,
+                         unsigned long long* out) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  double m = 0.0;
+  if (row < *K.nrow) {
+    const long long i = K.rows[row];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const long long d = i * D + a;
+      const double v = fabs((double)x[d]);
+      if (!fixed[d]) m = (v == v) ? fmax(m, v) : INFINITY;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+template <int D, class T>
+cudaError_t launch_absmax(DevMatrix<T> K, const T* x, const uint8_t* fixed, unsigned long long* out, int nblk,
+                          cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess) return e;
+  k_absmax<D, T><<<nblk, KTPB, 0, st>>>(K, x, fixed, out);
+  return cudaGetLastError();
+}
+
 // du = base + alpha d on the free DOFs (the halved step of a Newton iteration
 // whose full step drove a return map out of its domain).
 template <int D, class T>
@@ -433,6 +462,8 @@ cudaError_t launch_update_du(DevMatrix<T> K, const T* x, const uint8_t* fixed, d
   template cudaError_t launch_update_du<D, T>(DevMatrix<T>, const T*, const uint8_t*, double*, int,     \
                                               cudaStream_t);                                            \
   template cudaError_t launch_spmv<D, T>(const DevGrid&, DevMatrix<T>, const T*, T*, int, cudaStream_t);  \
+  template cudaError_t launch_absmax<D, T>(DevMatrix<T>, const T*, const uint8_t*, unsigned long long*, int, \
+                                           cudaStream_t);                                                  \
   template cudaError_t launch_step_du<D, T>(DevMatrix<T>, const T*, const uint8_t*, const double*, double*, \
                                             double, int, cudaStream_t);
 MPM_KRYLOV_INST(2, float)
