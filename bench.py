@@ -306,10 +306,9 @@ def main():
     newton_all, krylov_all = float(tt[1]), float(tt[2])
     value = newton_all / (t_all / 1e3)
 
-    # ---- dominant kernel: the persistent BiCGStab solve, timed live ----------
+    # ---- dominant kernel: the Krylov iteration, timed live -------------------
     # achieved = algorithmic bytes of all timed Krylov iterations / the
-    # CUDA-event time of the Krylov phases (one cooperative launch per Newton
-    # iteration).  Bytes per iteration: two stencil-BSR products (present
+    # CUDA-event time of the Krylov phases.  Bytes per iteration: two stencil-BSR products (present
     # blocks + input/output vectors + row list) + 19 vector passes of the
     # BLAS-1 phases + two block-Jacobi applications.
     gs.begin(next_step())
@@ -320,7 +319,14 @@ def main():
     peaks, src = read_peaks()
     t_kry_s = phase[3] * 1e-3
     achieved = (krylov / max(newton, 1)) * newton * bytes_iter / max(t_kry_s, 1e-12) / 1e9
-    roof = {"kernel": "k_bicg_persistent (whole BiCGStab solve, one cooperative launch per Newton iteration)",
+    if args.krylov == "gmres":
+        kname = "GMRES(m) cycle kernels (k_gmres_spmv/orth1/orth2/norm/update, one CUDA graph per cycle)"
+    elif os.environ.get("MPM_KRYLOV_PERSISTENT", "0") == "1":
+        kname = "k_bicg_persistent (whole BiCGStab solve, one cooperative launch per Newton iteration)"
+    else:
+        kname = ("merged BiCGStab iteration k_bicg_B/C/D/A (4 launches per iteration, "
+                 "CUDA graph of 8 iterations)")
+    roof = {"kernel": kname,
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
             "bytes_per_iteration": bytes_iter, "us_per_iteration": 1e6 * t_kry_s / max(krylov, 1),

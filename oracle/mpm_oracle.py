@@ -19,7 +19,10 @@ Readings (the paper is silent on these):
 * active DOFs are those of nodes with nodal mass M_i > ACTIVE_REL * max_p m_p;
 * a prescribed DOF takes its increment at k = 0; its row and column of J are
   replaced by the identity and its residual entry is excluded from the norm;
-* a prescribed DOF on an inactive node is ignored.
+* a prescribed DOF on an inactive node is ignored;
+* u-p: the pressure DOF holds the pore pressure at the end of the step (a
+  prescribed pressure is its value, not an increment) and starts each step
+  at zero; the Newton norm weighs the mass-balance rows by ``p_scale``.
 
 It also provides the coloured central finite-difference Jacobian used to pin
 the exact tangent: the seeding pattern of the paper's sparse differentiation
@@ -75,6 +78,11 @@ def lib():
         L.orc_jacobian.argtypes = [_I, _D, ctypes.c_int, _D, _D, _I, _D, _D, _D, _D,
                                    ctypes.c_long, _L, _L, _D]
         L.orc_commit.argtypes = [_I, _D, ctypes.c_int, _D, _D, _I, _D, _D, _D, _D, _D]
+        L.orc_residual_up.argtypes = [_I, _D, _D, ctypes.c_int, _D, _D, _D, _D, _I, _D, _D, _D, _D,
+                                      _D, _D, _D, _D, _I, _D]
+        L.orc_jacobian_up.argtypes = [_I, _D, ctypes.c_int, _D, _D, _D, _I, _D, _D, _D, _D, _D,
+                                      ctypes.c_long, _L, _L, _D]
+        L.orc_commit_up.argtypes = [_I, _D, ctypes.c_int, _D, _D, _I, _D, _D, _D, _D, _D, _D]
         _lib = L
     return _lib
 
@@ -151,9 +159,17 @@ def particle(model, params, be6, pcn, dF, V0=1.0, tangent=True):
 # --------------------------------------------------------------------------
 
 class OracleScene:
-    """Particle state plus grid, evolved load step by load step."""
+    """Particle state plus grid, evolved load step by load step.
 
-    def __init__(self, dim, n, h, origin, x, vol0, mass, model, params, pc0):
+    ``formulation`` is ``"solid"`` (dim displacement DOFs per node) or
+    ``"up"`` (dim displacements and the pore pressure per node, the coupled
+    formulation of the paper's Sec. 2.2 remark).  For u-p, ``kdt`` is the
+    mobility times the time step per particle, ``p_scale`` the factor that
+    puts the mass-balance rows and pressure unknowns on the scale of the
+    momentum rows in the Newton norm (default max mu / h)."""
+
+    def __init__(self, dim, n, h, origin, x, vol0, mass, model, params, pc0, formulation="solid",
+                 kdt=None, p_scale=None):
         self.dim = int(dim)
         self.n = (int(n[0]), int(n[1]), int(n[2]) if dim == 3 else 0)
         self.h = float(h)
@@ -171,6 +187,15 @@ class OracleScene:
         self.pc = _f64(pc0).copy()
         self.F = np.tile(np.eye(3).reshape(9), (self.np, 1))
         self.gravity = np.zeros(3)
+        self.formulation = formulation
+        self.B = self.dim + (1 if formulation == "up" else 0)
+        self.kdt = np.zeros(self.np) if kdt is None else _f64(kdt).copy()
+        self.fext = np.zeros((self.np, 3))
+        self.pp = np.zeros(self.np)
+        if p_scale is None:
+            mu = self.params[:, 0] / (2.0 * (1.0 + self.params[:, 1])) if self.np else np.zeros(1)
+            p_scale = float(mu.max()) / self.h if self.np else 1.0
+        self.p_scale = float(p_scale)
         nn = 1
         for a in range(self.dim):
             nn *= self.n[a] + 1
@@ -179,24 +204,40 @@ class OracleScene:
     @classmethod
     def from_scene(cls, sc):
         model, params, pc0 = sc.particle_params()
-        o = cls(sc.dim, sc.n, sc.h, sc.origin, sc.x, sc.vol0, sc.mass, model, params, pc0)
+        form = getattr(sc, "formulation", "solid")
+        kdt = sc.particle_kdt() if form == "up" else None
+        o = cls(sc.dim, sc.n, sc.h, sc.origin, sc.x, sc.vol0, sc.mass, model, params, pc0,
+                formulation=form, kdt=kdt)
         if getattr(sc, "be0", None) is not None:
             o.be[:] = sc.be0
+        if getattr(sc, "fext", None) is not None:
+            o.fext[:] = sc.fext
         return o
+
+    @property
+    def ndof(self):
+        return self.nnode * self.B
 
     # ---- residual / Jacobian -------------------------------------------
     def residual(self, du, with_mode=False, with_scale=False):
         """r(du) on the dense DOF grid and the nodal mass; optionally the
         per-particle modes and the per-DOF sum of absolute contributions."""
         du = _f64(du)
-        r = np.zeros(self.nnode * self.dim)
+        r = np.zeros(self.ndof)
         M = np.zeros(self.nnode)
         mode = np.zeros(self.np, dtype=np.int32)
-        rabs = np.zeros(self.nnode * self.dim) if with_scale else None
-        rc = lib().orc_residual(_p(self.gi, _I), _p(self.gd), _p(_f64(self.gravity)), self.np,
-                                _p(self.x), _p(self.V0), _p(self.m), _p(self.model, _I),
-                                _p(self.params), _p(self.be), _p(self.pc), _p(du), _p(r), _p(M),
-                                _p(mode, _I), _p(rabs) if with_scale else None)
+        rabs = np.zeros(self.ndof) if with_scale else None
+        if self.formulation == "up":
+            rc = lib().orc_residual_up(_p(self.gi, _I), _p(self.gd), _p(_f64(self.gravity)), self.np,
+                                       _p(self.x), _p(self.V0), _p(self.F), _p(self.m),
+                                       _p(self.model, _I), _p(self.params), _p(self.be), _p(self.pc),
+                                       _p(self.kdt), _p(self.fext), _p(du), _p(r), _p(M),
+                                       _p(mode, _I), _p(rabs) if with_scale else None)
+        else:
+            rc = lib().orc_residual(_p(self.gi, _I), _p(self.gd), _p(_f64(self.gravity)), self.np,
+                                    _p(self.x), _p(self.V0), _p(self.m), _p(self.model, _I),
+                                    _p(self.params), _p(self.be), _p(self.pc), _p(du), _p(r), _p(M),
+                                    _p(mode, _I), _p(rabs) if with_scale else None)
         if rc:
             raise OracleError(f"residual failed ({rc})")
         out = (r, M)
@@ -208,21 +249,27 @@ class OracleScene:
 
     def jacobian_blocks(self, du):
         """Node-pair blocks (bi, bj, val[nb, d, d]) of J = dr/du, summed."""
-        d = self.dim
-        cap = self.nnode * (5 ** d)
+        d = self.B
+        cap = self.nnode * (5 ** self.dim)
         bi = np.zeros(cap, dtype=np.int64)
         bj = np.zeros(cap, dtype=np.int64)
         val = np.zeros(cap * d * d)
-        nb = lib().orc_jacobian(_p(self.gi, _I), _p(self.gd), self.np, _p(self.x), _p(self.V0),
-                                _p(self.model, _I), _p(self.params), _p(self.be), _p(self.pc),
-                                _p(_f64(du)), cap, _p(bi, _L), _p(bj, _L), _p(val))
+        if self.formulation == "up":
+            nb = lib().orc_jacobian_up(_p(self.gi, _I), _p(self.gd), self.np, _p(self.x), _p(self.V0),
+                                       _p(self.F), _p(self.model, _I), _p(self.params), _p(self.be),
+                                       _p(self.pc), _p(self.kdt), _p(_f64(du)), cap, _p(bi, _L),
+                                       _p(bj, _L), _p(val))
+        else:
+            nb = lib().orc_jacobian(_p(self.gi, _I), _p(self.gd), self.np, _p(self.x), _p(self.V0),
+                                    _p(self.model, _I), _p(self.params), _p(self.be), _p(self.pc),
+                                    _p(_f64(du)), cap, _p(bi, _L), _p(bj, _L), _p(val))
         if nb < 0:
             raise OracleError(f"jacobian failed ({nb})")
         return bi[:nb], bj[:nb], val[:nb * d * d].reshape(nb, d, d)
 
     def jacobian(self, du):
         """J over the dense DOF space as a scipy CSR matrix."""
-        d = self.dim
+        d = self.B
         bi, bj, val = self.jacobian_blocks(du)
         rows = (bi[:, None, None] * d + np.arange(d)[None, :, None]) + 0 * np.arange(d)[None, None, :]
         cols = (bj[:, None, None] * d + np.arange(d)[None, None, :]) + 0 * np.arange(d)[None, :, None]
@@ -231,13 +278,22 @@ class OracleScene:
 
     def active_dofs(self, M):
         act = M > ACTIVE_REL * self.m.max()
-        return np.repeat(act, self.dim)
+        return np.repeat(act, self.B)
+
+    def norm_weights(self):
+        """Per-DOF weights of the Newton norm: 1 for displacement rows,
+        p_scale for the u-p mass-balance rows."""
+        w = np.ones(self.ndof)
+        if self.formulation == "up":
+            w[self.dim::self.B] = self.p_scale
+        return w
 
     # ---- Newton (paper Sec. 2.2) ------------------------------------------
     def solve_step(self, dof, value, gravity, tol=1e-12, maxit=25, commit=True):
         """One load step.  Returns dict(du, hist, iters, converged, r0)."""
         self.gravity = _f64(gravity).copy()
-        N = self.nnode * self.dim
+        N = self.ndof
+        wn = self.norm_weights()
         du = np.zeros(N)
         r, M = self.residual(du)
         act = self.active_dofs(M)
@@ -249,7 +305,7 @@ class OracleScene:
         free = act & ~fixed
         fidx = np.nonzero(free)[0]
         r, M = self.residual(du)
-        r0 = np.linalg.norm(r[free])
+        r0 = np.linalg.norm((wn * r)[free])
         hist = [1.0]
         it = 0
         conv = r0 == 0.0
@@ -259,7 +315,7 @@ class OracleScene:
             du[fidx] += delta
             r, M = self.residual(du)
             it += 1
-            rel = np.linalg.norm(r[free]) / r0
+            rel = np.linalg.norm((wn * r)[free]) / r0
             hist.append(rel)
             conv = rel <= tol
         out = dict(du=du, hist=np.array(hist), iters=it, converged=bool(conv), r0=r0,
@@ -269,6 +325,13 @@ class OracleScene:
         return out
 
     def commit(self, du):
+        if self.formulation == "up":
+            rc = lib().orc_commit_up(_p(self.gi, _I), _p(self.gd), self.np, _p(self.x), _p(self.V0),
+                                     _p(self.model, _I), _p(self.params), _p(self.be), _p(self.pc),
+                                     _p(self.F), _p(_f64(du)), _p(self.pp))
+            if rc:
+                raise OracleError(f"commit failed ({rc})")
+            return
         rc = lib().orc_commit(_p(self.gi, _I), _p(self.gd), self.np, _p(self.x), _p(self.V0),
                               _p(self.model, _I), _p(self.params), _p(self.be), _p(self.pc),
                               _p(self.F), _p(_f64(du)))
@@ -280,7 +343,7 @@ class OracleScene:
         """Kirchhoff stress (np,3,3) and mode of each particle at increment du
         (zero increment by default: the committed state)."""
         if du is None:
-            du = np.zeros(self.nnode * self.dim)
+            du = np.zeros(self.ndof)
         out = np.zeros((self.np, 3, 3))
         modes = np.zeros(self.np, dtype=np.int32)
         for p in range(self.np):
@@ -289,7 +352,7 @@ class OracleScene:
             for l in range(len(node)):
                 for a in range(self.dim):
                     for c in range(self.dim):
-                        dF[a, c] += du[node[l] * self.dim + a] * g[l, c]
+                        dF[a, c] += du[node[l] * self.B + a] * g[l, c]
             o = particle(self.model[p], self.params[p], self.be[p], self.pc[p], dF,
                          self.V0[p], tangent=False)
             out[p] = o["tau"]
@@ -297,13 +360,15 @@ class OracleScene:
         return out, modes
 
     def snapshot(self):
-        return dict(x=self.x.copy(), be=self.be.copy(), pc=self.pc.copy(), F=self.F.copy())
+        return dict(x=self.x.copy(), be=self.be.copy(), pc=self.pc.copy(), F=self.F.copy(),
+                    pp=self.pp.copy())
 
     def restore(self, s):
         self.x[:] = s["x"]
         self.be[:] = s["be"]
         self.pc[:] = s["pc"]
         self.F[:] = s["F"]
+        self.pp[:] = s["pp"]
 
 
 def node_ijk(sc: OracleScene, node):
@@ -319,9 +384,11 @@ def fd_jacobian_colored(sc: OracleScene, du, eps, b=5):
     """Central-difference Jacobian with the sparse-differentiation colouring:
     one colour per (local_x, local_y[, local_z], component) with block size b,
     seeding every DOF of that colour at once; each seeded column is read off
-    the rows within +-2 nodes of its node.  Returns a dense (N, N) array."""
+    the rows within +-2 nodes of its node.  ``eps`` is one step for every
+    DOF or one step per node component.  Returns a dense (N, N) array."""
     d = sc.dim
-    N = sc.nnode * d
+    B = sc.B
+    N = sc.nnode * B
     nodes = np.arange(sc.nnode)
     ix, iy, iz = node_ijk(sc, nodes)
     J = np.zeros((N, N))
@@ -329,20 +396,21 @@ def fd_jacobian_colored(sc: OracleScene, du, eps, b=5):
     for (lx, ly, lz) in locs:
         sel = (ix % b == lx) & (iy % b == ly) & ((iz % b == lz) if d == 3 else True)
         seeded = nodes[sel]
-        for comp in range(d):
+        for comp in range(B):
+            ec = float(np.broadcast_to(np.asarray(eps, dtype=np.float64), (B,))[comp])
             e = np.zeros(N)
-            e[seeded * d + comp] = 1.0
-            rp, _ = sc.residual(du + eps * e)
-            rm, _ = sc.residual(du - eps * e)
-            col = (rp - rm) / (2 * eps)
+            e[seeded * B + comp] = 1.0
+            rp, _ = sc.residual(du + ec * e)
+            rm, _ = sc.residual(du - ec * e)
+            col = (rp - rm) / (2 * ec)
             for j in seeded:
                 jx, jy, jz = ix[j], iy[j], iz[j]
                 near = (np.abs(ix - jx) <= 2) & (np.abs(iy - jy) <= 2)
                 if d == 3:
                     near &= np.abs(iz - jz) <= 2
                 rows = nodes[near]
-                for a in range(d):
-                    J[rows * d + a, j * d + comp] = col[rows * d + a]
+                for a in range(B):
+                    J[rows * B + a, j * B + comp] = col[rows * B + a]
     return J
 
 
@@ -350,7 +418,7 @@ def fd_jacobian_plain(sc: OracleScene, du, eps, cols):
     """Central-difference columns of J, one DOF at a time (the dense
     differentiation of the paper's Algorithm 1 with a difference in place of a
     reverse pass).  Returns (N, len(cols))."""
-    N = sc.nnode * sc.dim
+    N = sc.ndof
     out = np.zeros((N, len(cols)))
     for k, j in enumerate(cols):
         e = np.zeros(N)

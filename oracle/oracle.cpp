@@ -23,7 +23,9 @@
 //     forward-mode dual numbers through the principal-space return map plus
 //     the implicit-function theorem, and the Daleckii-Krein rule for the
 //     spectral (eigenvector) part;
-//   * the commit of the particle state after convergence (Sec. 2.2 stage 4).
+//   * the commit of the particle state after convergence (Sec. 2.2 stage 4);
+//   * the coupled u-p residual, its exact Jacobian and commit (Sec. 2.2,
+//     remark on poromechanics; the equations are a stated reading).
 // The Newton loop and the sparse linear solve live in mpm_oracle.py.
 //
 // Readings of points the paper leaves open are stated where they are used.
@@ -610,6 +612,65 @@ void g2p_dF(const Grid& G, const Stencil& S, const double* du, M3 dF) {
       for (int c = 0; c < G.dim; ++c) dF[a][c] += du[S.node[l] * G.dim + a] * S.g[l][c];
 }
 
+
+// ------------------------------------------------------------------------
+// u-p poromechanics (paper Sec. 2.2, remark on the coupled formulation; the
+// paper defers the equations to the stabilised MPM u-p literature, so the
+// form here is the reading: mixture momentum with total stress
+// sigma = sigma' - p 1, fluid mass balance with incompressible constituents
+// (J^{n+1} - J^n)/(dt J^{n+1}) + div q = 0, Darcy q = -kappa grad p, backward
+// Euler in time, no stabilisation, the same quadratic B-splines for u and p).
+// Per particle, with dF the step's deformation gradient, V^n = V0 det F^n,
+// p_p = sum_j w_jp p_j and G_p = sum_j p_j grad w_jp (start-of-step
+// gradients), multiplied through by dt:
+//   pressure part of P:  Pp = -p_p V^n det(dF) dF^-T
+//   volume term:         vol = V^n (det dF - 1)         (tested with w_ip)
+//   flux term:           fl = kdt V^n det(dF) dF^-1 dF^-T G_p  (with grad w_ip)
+// kdt = kappa dt.  Written once for plain doubles and once for dual numbers,
+// whose derivative parts give the exact Jacobian of these terms.
+// ------------------------------------------------------------------------
+template <class S>
+void up_terms(const S dF[3][3], S pp, const S G[3], double Vn, double kdt, S Pp[3][3], S& vol, S fl[3]) {
+  S det = dF[0][0] * (dF[1][1] * dF[2][2] - dF[1][2] * dF[2][1]) -
+          dF[0][1] * (dF[1][0] * dF[2][2] - dF[1][2] * dF[2][0]) +
+          dF[0][2] * (dF[1][0] * dF[2][1] - dF[1][1] * dF[2][0]);
+  // inverse by the adjugate
+  S inv[3][3];
+  inv[0][0] = (dF[1][1] * dF[2][2] - dF[1][2] * dF[2][1]) / det;
+  inv[0][1] = (dF[0][2] * dF[2][1] - dF[0][1] * dF[2][2]) / det;
+  inv[0][2] = (dF[0][1] * dF[1][2] - dF[0][2] * dF[1][1]) / det;
+  inv[1][0] = (dF[1][2] * dF[2][0] - dF[1][0] * dF[2][2]) / det;
+  inv[1][1] = (dF[0][0] * dF[2][2] - dF[0][2] * dF[2][0]) / det;
+  inv[1][2] = (dF[0][2] * dF[1][0] - dF[0][0] * dF[1][2]) / det;
+  inv[2][0] = (dF[1][0] * dF[2][1] - dF[1][1] * dF[2][0]) / det;
+  inv[2][1] = (dF[0][1] * dF[2][0] - dF[0][0] * dF[2][1]) / det;
+  inv[2][2] = (dF[0][0] * dF[1][1] - dF[0][1] * dF[1][0]) / det;
+  const S Vnew = S(Vn) * det;
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) Pp[a][c] = S(0.0) - pp * Vnew * inv[c][a];
+  vol = S(Vn) * (det - S(1.0));
+  // t = dF^-T G, fl = kdt V^{n+1} dF^-1 t
+  S t[3];
+  for (int k = 0; k < 3; ++k) t[k] = inv[0][k] * G[0] + inv[1][k] * G[1] + inv[2][k] * G[2];
+  for (int c = 0; c < 3; ++c) fl[c] = S(kdt) * Vnew * (inv[c][0] * t[0] + inv[c][1] * t[1] + inv[c][2] * t[2]);
+}
+
+// G2P of the u-p nodal vector U (stride B = dim + 1): dF, p_p and G_p.
+void g2p_up(const Grid& G, const Stencil& S, const double* U, M3 dF, double& pp, double Gp[3]) {
+  const int B = G.dim + 1;
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) dF[a][c] = (a == c) ? 1.0 : 0.0;
+  pp = 0.0;
+  Gp[0] = Gp[1] = Gp[2] = 0.0;
+  for (int l = 0; l < S.cnt; ++l) {
+    const double* u = U + S.node[l] * B;
+    for (int a = 0; a < G.dim; ++a)
+      for (int c = 0; c < G.dim; ++c) dF[a][c] += u[a] * S.g[l][c];
+    pp += S.w[l] * u[G.dim];
+    for (int c = 0; c < G.dim; ++c) Gp[c] += u[G.dim] * S.g[l][c];
+  }
+}
+
 }  // namespace
 
 extern "C" {
@@ -777,6 +838,195 @@ int orc_commit(const int* gi, const double* gd, int np, double* x, const double*
     std::memcpy(Fo, F + 9 * p, sizeof(M3));
     matmul(dF, Fo, Fn);
     std::memcpy(F + 9 * p, Fn, sizeof(M3));
+  }
+  return 0;
+}
+
+// ---- u-p formulation --------------------------------------------------
+// U and r hold B = dim + 1 values per node: (du_0 .. du_{dim-1}, p), with p
+// the pore pressure at the end of the step (positive in compression) and
+// r_p the fluid mass balance multiplied by dt.  F (9 per particle) is the
+// start-of-step deformation gradient (V^n = V0 det F); kdt = kappa dt per
+// particle; fext (3 per particle, nullable) is an external force carried by
+// the particle (a surface traction times the particle's face area), spread
+// to the nodes with w_ip like gravity.
+int orc_residual_up(const int* gi, const double* gd, const double* grav, int np, const double* x,
+                    const double* V0, const double* F, const double* m, const int* model,
+                    const double* params, const double* be, const double* pc, const double* kdt,
+                    const double* fext, const double* U, double* r, double* mass, int* mode_out,
+                    double* rabs) {
+  Grid G = make_grid(gi, gd);
+  const int d = G.dim, B = d + 1;
+  long nn = G.nnode();
+  std::fill(r, r + nn * B, 0.0);
+  std::fill(mass, mass + nn, 0.0);
+  if (rabs) std::fill(rabs, rabs + nn * B, 0.0);
+  for (int p = 0; p < np; ++p) {
+    Stencil S;
+    if (make_stencil(G, x + 3 * p, S)) return -1;
+    M3 dF, ben, Fn;
+    double pp, Gp[3];
+    g2p_up(G, S, U, dF, pp, Gp);
+    sym6_to_m3(be + 6 * p, ben);
+    std::memcpy(Fn, F + 9 * p, sizeof(M3));
+    const double Vn = V0[p] * det3(Fn);
+    Mat mt = make_mat(model[p], params + 8 * p);
+    PartOut o;
+    int rc = particle_update(mt, ben, pc[p], dF, V0[p], o, nullptr);
+    if (rc) return rc;
+    if (mode_out) mode_out[p] = o.mode;
+    double Pp[3][3], vol, fl[3];
+    up_terms<double>(dF, pp, Gp, Vn, kdt[p], Pp, vol, fl);
+    for (int l = 0; l < S.cnt; ++l) {
+      long i = S.node[l];
+      mass[i] += S.w[l] * m[p];
+      for (int a = 0; a < d; ++a) {
+        double f = 0, fa = 0;
+        for (int c = 0; c < d; ++c) {
+          f += (o.P[a][c] + Pp[a][c]) * S.g[l][c];
+          fa += std::fabs(o.P[a][c] * S.g[l][c]) + std::fabs(Pp[a][c] * S.g[l][c]);
+        }
+        const double fe = S.w[l] * (m[p] * grav[a] + (fext ? fext[3 * p + a] : 0.0));
+        r[i * B + a] += f - fe;
+        if (rabs) rabs[i * B + a] += fa + std::fabs(fe);
+      }
+      double q = S.w[l] * vol, qa = std::fabs(S.w[l] * vol);
+      for (int c = 0; c < d; ++c) {
+        q += fl[c] * S.g[l][c];
+        qa += std::fabs(fl[c] * S.g[l][c]);
+      }
+      r[i * B + d] += q;
+      if (rabs) rabs[i * B + d] += qa;
+    }
+  }
+  return 0;
+}
+
+// Exact Jacobian of the u-p residual as (B x B) node-pair blocks: the
+// effective-stress part through the tangent A_p of the solid oracle, the
+// pressure, volume and flux terms through forward-mode dual numbers seeded
+// on dF_be, p_p and G_p,e.
+int orc_jacobian_up(const int* gi, const double* gd, int np, const double* x, const double* V0,
+                    const double* F, const int* model, const double* params, const double* be,
+                    const double* pc, const double* kdt, const double* U, long cap, long* bi, long* bj,
+                    double* bval) {
+  Grid G = make_grid(gi, gd);
+  const int d = G.dim, B = d + 1;
+  std::map<std::pair<long, long>, std::array<double, 16>> K;
+  for (int p = 0; p < np; ++p) {
+    Stencil S;
+    if (make_stencil(G, x + 3 * p, S)) return -1;
+    M3 dF, ben, Fn;
+    double pp, Gp[3];
+    g2p_up(G, S, U, dF, pp, Gp);
+    sym6_to_m3(be + 6 * p, ben);
+    std::memcpy(Fn, F + 9 * p, sizeof(M3));
+    const double Vn = V0[p] * det3(Fn);
+    Mat mt = make_mat(model[p], params + 8 * p);
+    PartOut o;
+    double A[81];
+    int rc = particle_update(mt, ben, pc[p], dF, V0[p], o, A);
+    if (rc) return rc;
+    // derivatives of (Pp, vol, fl): seeds 0..8 = dF_be (b*3+e), 9 = p_p, 10..12 = G_e
+    double dPp[13][3][3], dvol[13], dfl[13][3];
+    for (int sd = 0; sd < 13; ++sd) {
+      Dual dFd[3][3], ppd(pp, sd == 9 ? 1.0 : 0.0), Gd[3];
+      for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) dFd[a][c] = Dual(dF[a][c], (sd < 9 && sd == 3 * a + c) ? 1.0 : 0.0);
+      for (int c = 0; c < 3; ++c) Gd[c] = Dual(Gp[c], (sd == 10 + c) ? 1.0 : 0.0);
+      Dual Ppd[3][3], vold, fld[3];
+      up_terms<Dual>(dFd, ppd, Gd, Vn, kdt[p], Ppd, vold, fld);
+      for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) dPp[sd][a][c] = Ppd[a][c].d;
+      dvol[sd] = vold.d;
+      for (int c = 0; c < 3; ++c) dfl[sd][c] = fld[c].d;
+    }
+    for (int li = 0; li < S.cnt; ++li)
+      for (int lj = 0; lj < S.cnt; ++lj) {
+        auto& blk = K[std::make_pair(S.node[li], S.node[lj])];
+        const double* gi_ = S.g[li];
+        const double* gj_ = S.g[lj];
+        const double wi = S.w[li], wj = S.w[lj];
+        // momentum rows a, displacement columns b
+        for (int a = 0; a < d; ++a)
+          for (int b = 0; b < d; ++b) {
+            double s = 0;
+            for (int c = 0; c < d; ++c)
+              for (int e = 0; e < d; ++e)
+                s += gi_[c] * (A[(3 * a + c) * 9 + 3 * b + e] + dPp[3 * b + e][a][c]) * gj_[e];
+            blk[a * B + b] += s;
+          }
+        // momentum rows a, pressure column: through p_p (w_j) and G_p (g_j)
+        for (int a = 0; a < d; ++a) {
+          double s = 0;
+          for (int c = 0; c < d; ++c) {
+            s += gi_[c] * dPp[9][a][c] * wj;
+            for (int e = 0; e < d; ++e) s += gi_[c] * dPp[10 + e][a][c] * gj_[e];
+          }
+          blk[a * B + d] += s;
+        }
+        // mass-balance row, displacement columns b
+        for (int b = 0; b < d; ++b) {
+          double s = 0;
+          for (int e = 0; e < d; ++e) {
+            double t = wi * dvol[3 * b + e];
+            for (int c = 0; c < d; ++c) t += gi_[c] * dfl[3 * b + e][c];
+            s += t * gj_[e];
+          }
+          blk[d * B + b] += s;
+        }
+        // mass-balance row, pressure column
+        {
+          double s = wi * dvol[9] * wj;
+          for (int e = 0; e < d; ++e) s += wi * dvol[10 + e] * gj_[e];
+          for (int c = 0; c < d; ++c) {
+            s += gi_[c] * dfl[9][c] * wj;
+            for (int e = 0; e < d; ++e) s += gi_[c] * dfl[10 + e][c] * gj_[e];
+          }
+          blk[d * B + d] += s;
+        }
+      }
+  }
+  long k = 0;
+  for (auto& kv : K) {
+    if (k >= cap) return -4;
+    bi[k] = kv.first.first;
+    bj[k] = kv.first.second;
+    for (int t = 0; t < B * B; ++t) bval[k * B * B + t] = kv.second[t];
+    ++k;
+  }
+  return (int)k;
+}
+
+// Commit of a u-p step: as orc_commit with the displacement part of U, and
+// the particle pore pressure p_p = sum_i w_ip p_i written to pp.
+int orc_commit_up(const int* gi, const double* gd, int np, double* x, const double* V0,
+                  const int* model, const double* params, double* be, double* pc, double* F,
+                  const double* U, double* pp) {
+  Grid G = make_grid(gi, gd);
+  const int d = G.dim, B = d + 1;
+  for (int p = 0; p < np; ++p) {
+    Stencil S;
+    if (make_stencil(G, x + 3 * p, S)) return -1;
+    M3 dF, ben;
+    double ppv, Gp[3];
+    g2p_up(G, S, U, dF, ppv, Gp);
+    sym6_to_m3(be + 6 * p, ben);
+    Mat mt = make_mat(model[p], params + 8 * p);
+    PartOut o;
+    int rc = particle_update(mt, ben, pc[p], dF, V0[p], o, nullptr);
+    if (rc) return rc;
+    double dx[3] = {0, 0, 0};
+    for (int l = 0; l < S.cnt; ++l)
+      for (int a = 0; a < d; ++a) dx[a] += S.w[l] * U[S.node[l] * B + a];
+    for (int a = 0; a < d; ++a) x[3 * p + a] += dx[a];
+    m3_to_sym6(o.be, be + 6 * p);
+    pc[p] = o.pc;
+    M3 Fo, Fnew;
+    std::memcpy(Fo, F + 9 * p, sizeof(M3));
+    matmul(dF, Fo, Fnew);
+    std::memcpy(F + 9 * p, Fnew, sizeof(M3));
+    pp[p] = ppv;
   }
   return 0;
 }

@@ -364,11 +364,9 @@ template <int D, class T>
 void assemble_impl(mpm_scene* s) {
   if (!s->staged) fail(MPM_ERR_STATE, "no load step staged (call mpm_begin_step)");
   cudaStream_t st = s->st;
-  const int S = stencil_slots(D);
   DevMatrix<T> K = matview<T>(s);
-  ck(cudaMemsetAsync(s->d_K, 0, (size_t)s->cap * S * D * D * sizeof(T), st), "memset K");
-  ck(launch_assemble<D, T>(s->P, s->G, s->d_cells, s->ncell, s->d_cstart, s->d_node2row, (const T*)s->d_A, K, st),
-     "assemble");
+  // every block of every active row is stored by the assembly (no zero fill)
+  ck(launch_assemble<D, T>(s->P, s->G, s->d_cstart, s->d_node2row, (const T*)s->d_A, K, st), "assemble");
   ck(launch_bc_matrix<D, T>(s->G, K, s->d_fixed, s->d_node2row, s->nrow, st), "bc matrix");
   ck(launch_block_jacobi<D, T>(K, s->nrow, s->d_err, st), "block jacobi");
   s->launches += 3;

@@ -134,9 +134,8 @@ cudaError_t launch_stress_out(const DevParticles& P, const DevGrid& G, const Mat
                               cudaStream_t st);
 
 template <int D, class T>
-cudaError_t launch_assemble(const DevParticles& P, const DevGrid& G, const int* cells, int ncell,
-                            const int* cstart, const int* node2row, const T* A, DevMatrix<T> K,
-                            cudaStream_t st);
+cudaError_t launch_assemble(const DevParticles& P, const DevGrid& G, const int* cstart, const int* node2row,
+                            const T* A, DevMatrix<T> K, cudaStream_t st);
 template <int D, class T>
 cudaError_t launch_bc_matrix(const DevGrid& G, DevMatrix<T> K, const uint8_t* fixed, const int* node2row,
                              int nrow_host, cudaStream_t st);

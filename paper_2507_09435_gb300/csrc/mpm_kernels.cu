@@ -444,126 +444,281 @@ cudaError_t launch_stress_out(const DevParticles& P, const DevGrid& G, const Mat
 }
 
 // ---------------------------------------------------------------- assembly
-// One CTA per occupied base cell.  Every particle of the cell touches the
-// same 3^D nodes, so the cell's contribution is a dense (3^D x 3^D) block
-// matrix K_ij[a][b] = sum_p sum_c g_pi[c] T_pj[a c b], with
-// T_pj[a c b] = sum_e A_p[a c b e] g_pj[e].  Particles are staged CH at a
-// time in shared memory; each thread owns up to PPT node pairs (all D x D
-// entries) and adds them to the global matrix once per cell.
+// Owner-computes assembly, K_ij[a][b] = sum_p sum_c,e g_pi[c] A_p[a c b e] g_pj[e]
+// (the Jacobian of Sec. 3 written with the consistent tangent A_p).  One CTA
+// owns a tile of TX x TY x TZ grid nodes and computes every block of the rows
+// of those nodes, reading the particles of the surrounding cells (the cells
+// with base node in [tile - 2, tile end) per axis) in chunks through shared
+// memory.  Blocks accumulate in shared memory and are stored once, so the
+// matrix needs no zero fill and no global atomics.  For a row node i and a
+// cell c whose 3^D nodes contain i, the row-side contraction
+// U_pi[a b e] = sum_c g_pi[c] A_p[a c b e] is shared by the 3^D nodes j of c.
 template <int D>
 __device__ __forceinline__ int slot_of(int dx, int dy, int dz) {
   return (D == 2) ? (dx + 2) + 5 * (dy + 2) : (dx + 2) + 5 * ((dy + 2) + 5 * (dz + 2));
 }
 
-template <int D, class T, int CH, int PPT>
-__global__ void k_assemble(DevParticles P, DevGrid G, const int* __restrict__ cells,
-                           const int* __restrict__ cstart, const int* __restrict__ node2row,
-                           const T* __restrict__ A, DevMatrix<T> K) {
-  constexpr int NN = (D == 2) ? 9 : 27;
-  constexpr int D2 = D * D, D3 = D * D * D, D4 = D * D * D * D;
-  __shared__ T sg[CH][NN][D];
-  __shared__ T sA[CH][D4];
-  __shared__ T sT[CH][NN][D3];
-  const int cell = cells[blockIdx.x];
-  const int p0 = cstart[cell], p1 = cstart[cell + 1];
-  const int bx = cell % G.nx1, by = (cell / G.nx1) % G.ny1, bz = cell / (G.nx1 * G.ny1);
-  T acc[PPT][D2];
-#pragma unroll
-  for (int k = 0; k < PPT; ++k)
-#pragma unroll
-    for (int e = 0; e < D2; ++e) acc[k][e] = (T)0;
-  for (int c0 = p0; c0 < p1; c0 += CH) {
-    const int nc = min(CH, p1 - c0);
-    // stage gradients and tangents
-    for (int t = threadIdx.x; t < nc * NN; t += blockDim.x) {
-      int q = t / NN, l = t % NN;
-      int p = c0 + q;
-      int kx = l % 3, ky = (l / 3) % 3, kz = l / 9;
-      // B-spline about the cell's base node (the particle's own base node)
-      Spline1 a0 = spline1_at((P.x[0][p] - G.o[0]) / G.h, bx);
-      Spline1 a1 = spline1_at((P.x[1][p] - G.o[1]) / G.h, by);
-      double Nx = a0.N[kx], Ny = a1.N[ky], dNx = a0.dN[kx], dNy = a1.dN[ky];
-      double Nz = 1.0, dNz = 0.0;
-      if (D == 3) {
-        Spline1 a2 = spline1_at((P.x[2][p] - G.o[2]) / G.h, bz);
-        Nz = a2.N[kz];
-        dNz = a2.dN[kz];
-      }
-      sg[q][l][0] = (T)(dNx * Ny * Nz * G.ih);
-      sg[q][l][1] = (T)(Nx * dNy * Nz * G.ih);
-      if (D == 3) sg[q][l][D - 1] = (T)(Nx * Ny * dNz * G.ih);
-    }
-    for (int t = threadIdx.x; t < nc * D4; t += blockDim.x) {
-      int q = t / D4, k = t % D4;
-      sA[q][k] = A[(long long)k * P.np + (c0 + q)];
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < nc * NN * D3; t += blockDim.x) {
-      int q = t / (NN * D3), rem = t % (NN * D3);
-      int j = rem / D3, acb = rem % D3;
-      T s = (T)0;
-#pragma unroll
-      for (int e = 0; e < D; ++e) s += sA[q][acb * D + e] * sg[q][j][e];
-      sT[q][j][acb] = s;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      int pair = threadIdx.x + k * blockDim.x;
-      if (pair < NN * NN) {
-        int i = pair / NN, j = pair % NN;
-        for (int q = 0; q < nc; ++q) {
-          T gi[D];
-#pragma unroll
-          for (int c = 0; c < D; ++c) gi[c] = sg[q][i][c];
-#pragma unroll
-          for (int a = 0; a < D; ++a)
-#pragma unroll
-            for (int b = 0; b < D; ++b) {
-              T s = acc[k][a * D + b];
-#pragma unroll
-              for (int c = 0; c < D; ++c) s += gi[c] * sT[q][j][(a * D + c) * D + b];
-              acc[k][a * D + b] = s;
-            }
-        }
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int k = 0; k < PPT; ++k) {
-    int pair = threadIdx.x + k * blockDim.x;
-    if (pair < NN * NN) {
-      int i = pair / NN, j = pair % NN;
-      int ix = i % 3, iy = (i / 3) % 3, iz = i / 9;
-      int jx = j % 3, jy = (j / 3) % 3, jz = j / 9;
-      long long ni = (bx + ix) + (long long)G.nx1 * ((by + iy) + (long long)G.ny1 * (bz + iz));
-      int row = node2row[ni];
-      if (row < 0) continue;
-      int slot = slot_of<D>(jx - ix, jy - iy, jz - iz);
-      T* blk = &K.val[((long long)slot * K.cap + row) * (D * D)];
-      if constexpr (D == 2 && sizeof(T) == 4) {
-        // one 16-byte vector atomic per 2x2 FP32 block (sm_90+)
-        atomicAdd(reinterpret_cast<float4*>(blk), make_float4(acc[k][0], acc[k][1], acc[k][2], acc[k][3]));
-      } else {
-#pragma unroll
-        for (int e = 0; e < D * D; ++e) atomicAdd(&blk[e], acc[k][e]);
-      }
-    }
+template <int D, class T>
+struct AsmCfg;
+template <> struct AsmCfg<2, float>  { static constexpr int TX = 16, TY = 8, TZ = 1, CHP = 64; };
+template <> struct AsmCfg<2, double> { static constexpr int TX = 8,  TY = 8, TZ = 1, CHP = 64; };
+template <> struct AsmCfg<3, float>  { static constexpr int TX = 4,  TY = 2, TZ = 2, CHP = 32; };
+template <> struct AsmCfg<3, double> { static constexpr int TX = 2,  TY = 2, TZ = 2, CHP = 16; };
+constexpr int ASM_TPB = 256;
+constexpr int ASM_UB = 8;   // particles per U batch of a 3D task
+
+template <int D, class T>
+struct AsmSmem {
+  static constexpr int TX = AsmCfg<D, T>::TX, TY = AsmCfg<D, T>::TY, TZ = AsmCfg<D, T>::TZ;
+  static constexpr int CHP = AsmCfg<D, T>::CHP;
+  static constexpr int NN = (D == 2) ? 9 : 27, S = (D == 2) ? 25 : 125;
+  static constexpr int D2 = D * D, D4 = D2 * D2, NT = TX * TY * TZ;
+  static constexpr int AST = D4 + (D == 2 ? 0 : 0);   // row stride of the staged tangents
+  // byte offsets (all multiples of 16)
+  static constexpr size_t acc = 0;
+  static constexpr size_t sA = acc + sizeof(T) * NT * S * D2;
+  static constexpr size_t sG = sA + ((sizeof(T) * CHP * AST + 15) / 16) * 16;
+  static constexpr size_t sU = sG + sizeof(T) * CHP * NN * 4;
+  static constexpr size_t sW = sU + sizeof(T) * (ASM_TPB / 32) * ASM_UB * 28;
+  static constexpr size_t srow = sW + ((sizeof(T) * CHP * 3 * 6 + 15) / 16) * 16;
+  static constexpr size_t bytes = srow + sizeof(int) * ((NT + 3) / 4) * 4;
+};
+
+template <class T>
+__device__ __forceinline__ void lds4(const T* p, T v[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 u = *reinterpret_cast<const float4*>(p);
+    v[0] = u.x; v[1] = u.y; v[2] = u.z; v[3] = u.w;
+  } else {
+    const double2 u = reinterpret_cast<const double2*>(p)[0];
+    const double2 w = reinterpret_cast<const double2*>(p)[1];
+    v[0] = u.x; v[1] = u.y; v[2] = w.x; v[3] = w.y;
   }
 }
 
 template <int D, class T>
-cudaError_t launch_assemble(const DevParticles& P, const DevGrid& G, const int* cells, int ncell,
-                            const int* cstart, const int* node2row, const T* A, DevMatrix<T> K,
-                            cudaStream_t st) {
-  if (ncell == 0) return cudaSuccess;
-  if (D == 2) {
-    k_assemble<D, T, 8, 1><<<ncell, 96, 0, st>>>(P, G, cells, cstart, node2row, A, K);
-  } else {
-    constexpr int CH = sizeof(T) == 4 ? 4 : 2;
-    k_assemble<D, T, CH, 3><<<ncell, 256, 0, st>>>(P, G, cells, cstart, node2row, A, K);
+__global__ void __launch_bounds__(ASM_TPB) k_assemble(DevParticles P, DevGrid G, const int* __restrict__ cstart,
+                                                      const int* __restrict__ node2row, const T* __restrict__ A,
+                                                      DevMatrix<T> K, int ntx, int nty) {
+  using L = AsmSmem<D, T>;
+  constexpr int TX = L::TX, TY = L::TY, TZ = L::TZ, CHP = L::CHP, NN = L::NN, S = L::S;
+  constexpr int D2 = L::D2, D4 = L::D4, NT = L::NT, AST = L::AST;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* acc = reinterpret_cast<T*>(smem + L::acc);    // [NT][S][D2]
+  T* sA = reinterpret_cast<T*>(smem + L::sA);      // [CHP][AST]
+  T* sG = reinterpret_cast<T*>(smem + L::sG);      // [CHP][NN][4]
+  T* sU = reinterpret_cast<T*>(smem + L::sU);      // [warps][ASM_UB][28]
+  T* sW = reinterpret_cast<T*>(smem + L::sW);      // [CHP][3 axes][N0..2, dN0..2]
+  int* srow = reinterpret_cast<int*>(smem + L::srow);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tx0 = (blockIdx.x % ntx) * TX;
+  const int ty0 = ((blockIdx.x / ntx) % nty) * TY;
+  const int tz0 = (blockIdx.x / (ntx * nty)) * TZ;
+  // rows of the tile
+  int mine = 0;
+  for (int l = tid; l < NT; l += ASM_TPB) {
+    const int ix = tx0 + l % TX, iy = ty0 + (l / TX) % TY, iz = tz0 + l / (TX * TY);
+    int row = -1;
+    if (ix < G.nx1 && iy < G.ny1 && iz < G.nz1)
+      row = node2row[ix + (long long)G.nx1 * (iy + (long long)G.ny1 * iz)];
+    srow[l] = row;
+    mine |= (row >= 0);
   }
+  if (!__syncthreads_or(mine)) return;
+  for (int t = tid; t < NT * S * D2; t += ASM_TPB) acc[t] = (T)0;
+
+  const int cx_lo = max(tx0 - 2, 0), cx_hi = min(tx0 + TX - 1, G.nx1 - 1);
+  const int cy_lo = max(ty0 - 2, 0), cy_hi = min(ty0 + TY - 1, G.ny1 - 1);
+  const int cz_lo = (D == 3) ? max(tz0 - 2, 0) : 0, cz_hi = (D == 3) ? min(tz0 + TZ - 1, G.nz1 - 1) : 0;
+  for (int cz = cz_lo; cz <= cz_hi; ++cz)
+    for (int cy = cy_lo; cy <= cy_hi; ++cy) {
+      // one run of cells along x: their particles are contiguous
+      const long long crow = (long long)G.nx1 * (cy + (long long)G.ny1 * cz);
+      const int pb = cstart[crow + cx_lo], pe = cstart[crow + cx_hi + 1];
+      // tile nodes inside the 3^D nodes of the run's cells along y and z
+      const int iy_lo = max(cy, ty0), iy_hi = min(min(cy + 2, ty0 + TY - 1), G.ny1 - 1);
+      const int iz_lo = (D == 3) ? max(cz, tz0) : 0;
+      const int iz_hi = (D == 3) ? min(min(cz + 2, tz0 + TZ - 1), G.nz1 - 1) : 0;
+      const int ny_ov = iy_hi - iy_lo + 1, nz_ov = iz_hi - iz_lo + 1;
+      if (ny_ov <= 0 || nz_ov <= 0) continue;
+      for (int q0 = pb; q0 < pe; q0 += CHP) {
+        const int nq = min(CHP, pe - q0);
+        __syncthreads();   // previous chunk's readers are done
+        // tangents, k-major global reads -> [q][k] in shared memory
+        for (int k = warp; k < D4; k += ASM_TPB / 32)
+          for (int q = lane; q < nq; q += 32) sA[q * AST + k] = A[(long long)k * P.np + q0 + q];
+        // per particle and axis: the three B-spline weights and derivatives
+        // about the particle's base node (its cell's x from the run's cell
+        // starts, y and z those of the run); FP64 offset, then type T
+        for (int t = tid; t < nq; t += ASM_TPB) {
+          const int p = q0 + t;
+          int cx = cx_lo;
+          while (cx < cx_hi && cstart[crow + cx + 1] <= p) ++cx;
+          const int base[3] = {cx, cy, cz};
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            T* w = sW + (t * 3 + a) * 6;
+            if (a < D) {
+              const T tt = (T)((P.x[a][p] - G.o[a]) * G.ih - (double)base[a] - 0.5);
+              // quadratic B-spline of Sec. 2 at nodes base, base + 1, base + 2
+              const T u = (T)1 - tt, c = tt - (T)0.5;
+              w[0] = (T)0.5 * u * u;  w[3] = -u;
+              w[1] = (T)0.75 - c * c; w[4] = (T)-2 * c;
+              w[2] = (T)0.5 * tt * tt; w[5] = tt;
+            } else {
+              w[0] = (T)1; w[1] = w[2] = (T)0;
+              w[3] = w[4] = w[5] = (T)0;
+            }
+          }
+        }
+        __syncthreads();
+        // gradients of the 3^D nodes of each particle's base cell
+        for (int t = tid; t < nq * NN; t += ASM_TPB) {
+          const int q = t / NN, l = t - q * NN;
+          const int kx = l % 3, ky = (l / 3) % 3, kz = l / 9;
+          const T* wx = sW + (q * 3 + 0) * 6;
+          const T* wy = sW + (q * 3 + 1) * 6;
+          const T* wz = sW + (q * 3 + 2) * 6;
+          const T ih = (T)G.ih;
+          T* g = sG + (q * NN + l) * 4;
+          g[0] = wx[3 + kx] * wy[ky] * wz[kz] * ih;
+          g[1] = wx[kx] * wy[3 + ky] * wz[kz] * ih;
+          g[2] = (D == 3) ? wx[kx] * wy[ky] * wz[3 + kz] * ih : (T)0;
+          g[3] = (T)0;
+        }
+        __syncthreads();
+        // tasks: (tile node i with y/z overlap, x offset kx of i in the cell)
+        const int ntask = TX * ny_ov * nz_ov * 3;
+        for (int task = warp; task < ntask; task += ASM_TPB / 32) {
+          const int kx = task % 3;
+          const int ixl = (task / 3) % TX;
+          const int iyl = (task / (3 * TX)) % ny_ov;
+          const int izl = task / (3 * TX * ny_ov);
+          const int ix = tx0 + ixl, iy = iy_lo + iyl, iz = iz_lo + izl;
+          const int cx = ix - kx;
+          if (cx < cx_lo || cx > cx_hi) continue;
+          const int l_i = ixl + TX * ((iy - ty0) + TY * (iz - tz0));
+          if (srow[l_i] < 0) continue;
+          const int qa = max(cstart[crow + cx], q0) - q0;
+          const int qb = min(cstart[crow + cx + 1], q0 + nq) - q0;
+          if (qa >= qb) continue;
+          const int ky = iy - cy, kz = (D == 3) ? iz - cz : 0;
+          const int il = kx + 3 * ky + 9 * kz;   // i among the cell's nodes
+          T* arow = acc + (size_t)l_i * S * D2;
+          if constexpr (D == 3) {
+            // lane j = node of the cell.  Particles go in batches of UB:
+            // lanes 0..26 first form U = g_i . A of every particle of the
+            // batch (independent products), then each lane contracts them
+            // with its own g_j.
+            const int j = lane;
+            const int ua = lane / 9, ub = (lane / 3) % 3, ue = lane % 3;
+            T k9[9];
+#pragma unroll
+            for (int e = 0; e < 9; ++e) k9[e] = (T)0;
+            T* su = sU + warp * (ASM_UB * 28);
+            for (int qb0 = qa; qb0 < qb; qb0 += ASM_UB) {
+              const int nb = min(ASM_UB, qb - qb0);
+              if (lane < 27) {
+#pragma unroll
+                for (int k = 0; k < ASM_UB; ++k) {
+                  if (k < nb) {
+                    const int q = qb0 + k;
+                    T gi[4];
+                    lds4(sG + (q * NN + il) * 4, gi);
+                    const T* aq = sA + q * AST + ua * 27 + ub * 3 + ue;
+                    su[k * 28 + lane] = gi[0] * aq[0] + gi[1] * aq[9] + gi[2] * aq[18];
+                  }
+                }
+              }
+              __syncwarp();
+              if (j < 27) {
+#pragma unroll
+                for (int k = 0; k < ASM_UB; ++k) {
+                  if (k < nb) {
+                    T gj[4];
+                    lds4(sG + ((qb0 + k) * NN + j) * 4, gj);
+                    T u[28];
+#pragma unroll
+                    for (int v = 0; v < 7; ++v) lds4(su + k * 28 + 4 * v, u + 4 * v);
+#pragma unroll
+                    for (int ab = 0; ab < 9; ++ab)
+                      k9[ab] += u[ab * 3 + 0] * gj[0] + u[ab * 3 + 1] * gj[1] + u[ab * 3 + 2] * gj[2];
+                  }
+                }
+              }
+              __syncwarp();
+            }
+            if (j < 27) {
+              const int jx = j % 3, jy = (j / 3) % 3, jz = j / 9;
+              T* blk = arow + slot_of<3>(jx - kx, jy - ky, jz - kz) * D2;
+#pragma unroll
+              for (int ab = 0; ab < 9; ++ab) atomicAdd(blk + ab, k9[ab]);
+            }
+          } else {
+            // lane = j + 9 * sub: node j of the cell, particles sub, sub+3, ...
+            const int j = lane % 9, sub = lane / 9;
+            T k4[4] = {(T)0, (T)0, (T)0, (T)0};
+            if (lane < 27) {
+              for (int q = qa + sub; q < qb; q += 3) {
+                T gi[4], gj[4], a16[16];
+                lds4(sG + (q * NN + il) * 4, gi);
+                lds4(sG + (q * NN + j) * 4, gj);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) lds4(sA + q * AST + 4 * v, a16 + 4 * v);
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                  for (int b = 0; b < 2; ++b) {
+                    T s = (T)0;
+#pragma unroll
+                    for (int c = 0; c < 2; ++c)
+#pragma unroll
+                      for (int e = 0; e < 2; ++e) s += gi[c] * a16[((a * 2 + c) * 2 + b) * 2 + e] * gj[e];
+                    k4[a * 2 + b] += s;
+                  }
+              }
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              // lanes j, j + 9, j + 18 hold the three particle subsets of node j
+              const T v9 = __shfl_sync(0xffffffffu, k4[e], (lane + 9) & 31);
+              const T v18 = __shfl_sync(0xffffffffu, k4[e], (lane + 18) & 31);
+              k4[e] += v9 + v18;
+            }
+            if (lane < 9) {
+              const int jx = j % 3, jy = j / 3;
+              T* blk = arow + slot_of<2>(jx - kx, jy - ky, 0) * D2;
+#pragma unroll
+              for (int e = 0; e < 4; ++e) atomicAdd(blk + e, k4[e]);
+            }
+          }
+        }
+      }
+    }
+  __syncthreads();
+  // store the tile's rows: all S slots, slot-major so that the rows of one
+  // x-line of nodes land contiguously in each slot plane
+  for (int t = tid; t < NT * S * D2; t += ASM_TPB) {
+    const int ab = t % D2, l = (t / D2) % NT, slot = t / (D2 * NT);
+    const int row = srow[l];
+    if (row >= 0) K.val[((long long)slot * K.cap + row) * D2 + ab] = acc[((size_t)l * S + slot) * D2 + ab];
+  }
+}
+
+template <int D, class T>
+cudaError_t launch_assemble(const DevParticles& P, const DevGrid& G, const int* cstart, const int* node2row,
+                            const T* A, DevMatrix<T> K, cudaStream_t st) {
+  using L = AsmSmem<D, T>;
+  if (P.np == 0) return cudaSuccess;
+  static_assert(L::bytes <= 227 * 1024, "assembly tile exceeds shared memory");
+  cudaError_t e = cudaFuncSetAttribute(k_assemble<D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)L::bytes);
+  if (e != cudaSuccess) return e;
+  const int ntx = (G.nx1 + L::TX - 1) / L::TX, nty = (G.ny1 + L::TY - 1) / L::TY;
+  const int ntz = (G.nz1 + L::TZ - 1) / L::TZ;
+  const long long nt = (long long)ntx * nty * ntz;
+  if (nt > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_assemble<D, T><<<(unsigned)nt, ASM_TPB, L::bytes, st>>>(P, G, cstart, node2row, A, K, ntx, nty);
   return cudaGetLastError();
 }
 
@@ -726,9 +881,8 @@ MPM_INST_D(3)
   template cudaError_t launch_particles<D, T>(const DevParticles&, const DevGrid&, const MatC*,          \
                                               const double*, double*, const double*, T*, int, int*,      \
                                               int*, cudaStream_t);                                       \
-  template cudaError_t launch_assemble<D, T>(const DevParticles&, const DevGrid&, const int*, int,       \
-                                             const int*, const int*, const T*, DevMatrix<T>,             \
-                                             cudaStream_t);                                              \
+  template cudaError_t launch_assemble<D, T>(const DevParticles&, const DevGrid&, const int*, const int*,  \
+                                             const T*, DevMatrix<T>, cudaStream_t);                                              \
   template cudaError_t launch_bc_matrix<D, T>(const DevGrid&, DevMatrix<T>, const uint8_t*, const int*,  \
                                               int, cudaStream_t);                                        \
   template cudaError_t launch_block_jacobi<D, T>(DevMatrix<T>, int, int*, cudaStream_t);

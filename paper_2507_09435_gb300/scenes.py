@@ -52,6 +52,8 @@ class Material:
     lambda_cc: float = 0.1  # virgin compression index
     kappa_cc: float = 0.02  # swelling index
     pc0: float = -1e5       # initial preconsolidation pressure, Pa
+    k_hyd: float = 0.0      # hydraulic conductivity, m/s (u-p only)
+    gamma_w: float = 9810.0  # unit weight of the pore fluid, N/m^3 (u-p only)
 
     def params8(self) -> np.ndarray:
         """The eight per-particle parameters in the order both sides read them:
@@ -87,6 +89,19 @@ class Scene:
     be0: Optional[np.ndarray] = None     # (np, 6) initial elastic left Cauchy-Green, default identity
     steps: List[LoadStep] = field(default_factory=list)
     meta: dict = field(default_factory=dict)
+    formulation: str = "solid"           # "solid" or "up" (displacement + pore pressure per node)
+    dt: float = 0.0                      # time step of a u-p load step, s
+    fext: Optional[np.ndarray] = None    # (np, 3) external force carried by each particle, N
+
+    @property
+    def B(self) -> int:
+        """DOFs per node: dim, plus the pore pressure for u-p."""
+        return self.dim + (1 if self.formulation == "up" else 0)
+
+    def particle_kdt(self) -> np.ndarray:
+        """Per-particle mobility times time step, k_hyd / gamma_w * dt (u-p)."""
+        k = np.array([self.materials[m].k_hyd / self.materials[m].gamma_w for m in self.mat_id])
+        return k * self.dt
 
     @property
     def np(self) -> int:
@@ -157,8 +172,9 @@ def box_cells(lo, hi) -> np.ndarray:
     return np.stack([m.ravel() for m in mesh[::-1]], axis=1)
 
 
-def _dofs(scene_like, nodes_mask_fn, comp, dim, n):
-    """DOF indices of nodes selected by a predicate on integer node coords."""
+def _dofs(scene_like, nodes_mask_fn, comp, dim, n, stride=None):
+    """DOF indices of nodes selected by a predicate on integer node coords
+    (``stride`` DOFs per node, default ``dim``)."""
     axes = [np.arange(n[a] + 1) for a in range(dim)]
     mesh = np.meshgrid(*axes[::-1], indexing="ij")
     coords = [m.ravel() for m in mesh[::-1]]          # x-fastest enumeration
@@ -169,7 +185,8 @@ def _dofs(scene_like, nodes_mask_fn, comp, dim, n):
     else:
         lin = coords[0] + nx1 * (coords[1] + ny1 * coords[2])
     lin = lin[sel]
-    return lin.astype(np.int64) * dim + comp, [c[sel] for c in coords]
+    stride = dim if stride is None else stride
+    return lin.astype(np.int64) * stride + comp, [c[sel] for c in coords]
 
 
 def _merge(*pairs):
@@ -414,6 +431,48 @@ def self_weight_column(ncell: int, l0: float = 50.0, rho0: float = 80.0, E: floa
     dof, val = _merge((ax, np.zeros(ax.shape)), (by, np.zeros(by.shape)))
     sc.steps = [LoadStep(dof, val, (0.0, -g * (k + 1) / nsteps, 0.0)) for k in range(nsteps)]
     sc.meta = dict(l0=l0, rho0=rho0, g=g, y_base=2 * h)
+    return sc
+
+
+def terzaghi(ncell: int = 100, H: float = 10.0, ppc: int = 2, lam: float = 600e3, mu: float = 600e3,
+             k_hyd: float = 9.81e-9, t_load: float = 1e3, dt: float = 1e5, nsteps: int = 40) -> Scene:
+    """One-dimensional consolidation (paper Sec. 4.4): a column H = 10 m tall,
+    one cell wide and ``ncell`` cells high (100 in the paper) with 2x2
+    particles per cell, Neo-Hookean skeleton with lambda = mu = 600 kPa,
+    a surface load t = 1 kPa on the top, which is also the only drained
+    boundary, time step 1e5 s.  The paper's intrinsic permeability 1e-15 m^2
+    with a fluid of density 1 t/m^3 (and water's viscosity 1e-3 Pa s) is the
+    hydraulic conductivity 9.81e-9 m/s, giving c_v = k/gamma_w (lambda + 2 mu)
+    = 1.8e-6 m^2/s as the paper states.
+
+    u-p scene: DOFs (u_x, u_y, p) per node.  u_x = 0 on every node (rollers
+    on both sides of a one-cell column), u_y = 0 on the base nodes (y <= base),
+    p = 0 on the top nodes (y >= top); no gravity (p is the excess pressure).
+    The load is a force of t * h / ppc on each particle of the top lattice row
+    (its share of the loaded face)."""
+    h = H / ncell
+    n = (3, ncell + 2, 0)
+    cells = box_cells((1, 1), (2, 1 + ncell))
+    x = lattice(cells, h, ppc, 2)
+    E = mu * (3 * lam + 2 * mu) / (lam + mu)
+    nu = lam / (2 * (lam + mu))
+    mat = Material(model=MODEL_NH, E=E, nu=nu, rho=2000.0, k_hyd=k_hyd)
+    vol = np.full(x.shape[0], h * h / ppc ** 2)
+    sc = Scene("terzaghi", 2, n, h, (0.0, 0.0, 0.0), x, vol, vol * mat.rho,
+               np.zeros(x.shape[0], np.int32), [mat], formulation="up", dt=dt)
+    y_top = (1 + ncell) * h
+    fext = np.zeros((x.shape[0], 3))
+    top_row = x[:, 1] > y_top - h / ppc
+    fext[top_row, 1] = -t_load * h / ppc
+    sc.fext = fext
+    B = 3
+    ax, _ = _dofs(sc, lambda ix, iy: ix >= 0, 0, 2, n, B)
+    by, _ = _dofs(sc, lambda ix, iy: iy <= 1, 1, 2, n, B)
+    pt, _ = _dofs(sc, lambda ix, iy: iy >= 1 + ncell, 2, 2, n, B)
+    dof, val = _merge((ax, np.zeros(ax.shape)), (by, np.zeros(by.shape)), (pt, np.zeros(pt.shape)))
+    sc.steps = [LoadStep(dof, val, (0.0, 0.0, 0.0)) for _ in range(nsteps)]
+    cv = k_hyd / mat.gamma_w * (lam + 2 * mu)
+    sc.meta = dict(H=H, y_top=y_top, y_base=h, t_load=t_load, cv=cv, dt=dt)
     return sc
 
 

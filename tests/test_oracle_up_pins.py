@@ -1,0 +1,142 @@
+"""Pins of the CPU oracle's coupled u-p formulation (paper Sec. 2.2 remark;
+Sec. 4.4 one-dimensional consolidation), no GPU.
+
+* With zero pore pressure and zero mobility the momentum rows are those of
+  the single-phase residual (a wrong sign or factor on the pressure term of
+  the total stress cannot hide behind the solid part).
+* The exact u-p Jacobian equals central differences of the oracle's own
+  residual (coupling blocks, the flux term's dependence on dF and the
+  pressure-pressure block).
+* Discrete flux energy: with du = 0, sum_i p_i r_p,i = sum_p kdt V_p |grad p_p|^2
+  >= 0 (the sign and the quadratic form of the Darcy term).
+* Terzaghi (Sec. 4.4): pore pressure and settlement converge to the series
+  solution p/p0 = sum 2/M sin(M z/H) exp(-M^2 T) and s = s_inf U(T) as the
+  column is refined (time step proportional to h^2).
+"""
+import numpy as np
+import pytest
+
+from paper_2507_09435_gb300 import scenes as S
+
+
+def _up_tiny(model, seed, kdt_scale=1.0):
+    sc = S.tiny_scene(2, model, seed=seed, ncell=3)
+    sc.formulation = "up"
+    sc.dt = 1e4 * kdt_scale
+    sc.materials[0].k_hyd = 9.81e-9
+    return sc
+
+
+def _random_U(sc, amp, p_amp, seed):
+    rng = np.random.default_rng(seed)
+    B = sc.B
+    U = np.zeros(sc.nnode * B)
+    U[0::B] = rng.standard_normal(sc.nnode) * amp * sc.h
+    U[1::B] = rng.standard_normal(sc.nnode) * amp * sc.h
+    U[2::B] = rng.standard_normal(sc.nnode) * p_amp
+    return U
+
+
+def test_up_momentum_rows_reduce_to_single_phase(oracle):
+    sc = _up_tiny(S.MODEL_NH_DP, seed=3, kdt_scale=0.0)
+    up = oracle.OracleScene.from_scene(sc)
+    sc.formulation = "solid"
+    so = oracle.OracleScene.from_scene(sc)
+    g = np.array([0.0, -9.81, 0.0])
+    up.gravity = g
+    so.gravity = g
+    du = S.random_increment(sc, 0.02, seed=4)
+    U = np.zeros(sc.nnode * 3)
+    U[0::3] = du[0::2]
+    U[1::3] = du[1::2]
+    ru, Mu = up.residual(U)
+    rs, Ms = so.residual(du)
+    assert np.array_equal(Mu, Ms)
+    scale = np.abs(rs).max()
+    assert np.abs(ru[0::3] - rs[0::2]).max() <= 1e-14 * scale
+    assert np.abs(ru[1::3] - rs[1::2]).max() <= 1e-14 * scale
+
+
+@pytest.mark.parametrize("model", [S.MODEL_NH, S.MODEL_NH_DP])
+def test_up_jacobian_matches_colored_central_differences(oracle, model):
+    sc = _up_tiny(model, seed=11)
+    orc = oracle.OracleScene.from_scene(sc)
+    orc.gravity = np.array([0.0, -9.81, 0.0])
+    U = _random_U(sc, 0.02, 1e4, seed=12)
+    r, M, modes = orc.residual(U, with_mode=True)
+    if model != S.MODEL_NH:
+        assert (modes > 0).sum() >= 4
+    J = orc.jacobian(U).toarray()
+    Jfd = oracle.fd_jacobian_colored(orc, U, eps=[1e-6 * sc.h, 1e-6 * sc.h, 1e-2])
+    act = orc.active_dofs(M)
+    Ja, Jf = J[np.ix_(act, act)], Jfd[np.ix_(act, act)]
+    # compare each (row kind, column kind) block on its own scale
+    B = 3
+    kind = np.arange(J.shape[0])[act] % B
+    for a in range(B):
+        for b in range(B):
+            blk = np.ix_(kind == a, kind == b)
+            ref = np.abs(Ja[blk]).max()
+            assert ref > 0
+            assert np.abs(Ja[blk] - Jf[blk]).max() < 1e-6 * ref, (a, b)
+
+
+def test_up_flux_energy_identity(oracle):
+    sc = _up_tiny(S.MODEL_NH, seed=21)
+    orc = oracle.OracleScene.from_scene(sc)
+    U = _random_U(sc, 0.0, 1e4, seed=22)
+    r, _ = orc.residual(U)
+    kdt = sc.particle_kdt()
+    lhs = np.dot(U[2::3], r[2::3])
+    rhs = 0.0
+    for p in range(sc.np):
+        node, w, g = oracle.stencil(2, sc.n, sc.h, sc.origin, orc.x[p])
+        G = (U[node * 3 + 2][:, None] * g).sum(axis=0)
+        rhs += kdt[p] * orc.V0[p] * float(G @ G)
+    assert rhs > 0
+    assert abs(lhs - rhs) <= 1e-12 * rhs
+
+
+def _terzaghi_series(z, T, H, nterms=400):
+    s = np.zeros_like(z)
+    U = 1.0
+    for m in range(nterms):
+        M = np.pi * (2 * m + 1) / 2
+        s += 2.0 / M * np.sin(M * z / H) * np.exp(-M * M * T)
+        U -= 2.0 / (M * M) * np.exp(-M * M * T)
+    return s, U
+
+
+@pytest.mark.slow
+def test_terzaghi_consolidation_converges_to_series(oracle):
+    """Sec. 4.4: H = 10 m, lambda = mu = 600 kPa, c_v = 1.8e-6 m^2/s, load
+    1 kPa, drained top.  At T = 0.2 the pore pressure at the particles and the
+    settlement of the loaded face approach the Terzaghi series at first order
+    in h (the drained boundary sits on a node and its ghost, a boundary layer
+    of one cell), with c_v dt / h^2 = 1/2 held fixed."""
+    H, cv, t_load, T_end = 10.0, 1.8e-6, 1e3, 0.2
+    M_c = 600e3 + 2 * 600e3
+    perr, serr = [], []
+    for N in (10, 20, 40):
+        h = H / N
+        dt = 0.5 * h * h / cv
+        nsteps = int(round(T_end * H * H / cv / dt))
+        sc = S.terzaghi(ncell=N, dt=dt, nsteps=nsteps)
+        assert abs(sc.meta["cv"] - cv) < 1e-9 * cv
+        orc = oracle.OracleScene.from_scene(sc)
+        y0 = orc.x[:, 1].copy()
+        for st in sc.steps:
+            out = orc.solve_step(st.dof, st.value, st.gravity, tol=1e-10)
+            assert out["converged"] and out["iters"] <= 4
+        T = cv * nsteps * dt / H ** 2
+        shape, Udeg = _terzaghi_series(sc.meta["y_top"] - y0, T, H)
+        perr.append(np.abs(orc.pp - t_load * shape).max() / t_load)
+        top = y0 > y0.max() - 1e-9
+        s_num = -(orc.x[top, 1] - y0[top]).mean()
+        s_ref = t_load * H / M_c * Udeg
+        serr.append(abs(s_num - s_ref) / s_ref)
+    perr, serr = np.array(perr), np.array(serr)
+    for e in (perr, serr):
+        assert (np.diff(e) < 0).all()
+        assert (np.log2(e[:-1] / e[1:]) > 0.8).all()
+    assert perr[-1] < 0.015 and serr[-1] < 0.025
