@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--krylov", default="bicgstab", choices=["bicgstab", "gmres"])
+    ap.add_argument("--precond", default="auto", choices=["auto", "node", "seg4"],
+                    help="block-Jacobi blocks: one node, or four consecutive active nodes")
     ap.add_argument("--workload", default="footing", choices=["footing", "column3d", "column3d_stated"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -85,6 +87,7 @@ def config(args, sc):
                  "step": "one load step of a 20-step gravity ramp"}
     return {"workload": WORKLOADS[args.workload], "grid": [int(v) for v in sc.n[:sc.dim]], "h": sc.h,
             "particles": sc.np, **extra, "precision": args.precision, "krylov": args.krylov,
+            "precond": args.precond,
             "preconditioner": "block-jacobi", "newton_tol": 1e-8,
             "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas{args.gpus}"}
 
@@ -252,7 +255,8 @@ def main():
     prec = mpm.MPM_MIXED if args.precision == "mixed" else mpm.MPM_FP64
     kry = mpm.MPM_BICGSTAB if args.krylov == "bicgstab" else mpm.MPM_GMRES
     stream = torch.cuda.Stream(device=dev)
-    gs = mpm.GpuScene(sc, precision=prec, krylov=kry, stream=stream.cuda_stream, newton_tol=1e-8,
+    pc = {"auto": mpm.MPM_PC_AUTO, "node": mpm.MPM_PC_NODE, "seg4": mpm.MPM_PC_SEG4}[args.precond]
+    gs = mpm.GpuScene(sc, precision=prec, krylov=kry, stream=stream.cuda_stream, newton_tol=1e-8, precond=pc,
                       krylov_maxit=50000)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     steps = sc.steps
@@ -340,7 +344,7 @@ def main():
     if not args.no_e2e:
         pin_dof = [torch.from_numpy(np.asarray(s.dof, dtype=np.int64)).pin_memory() for s in steps]
         pin_val = [torch.from_numpy(np.asarray(s.value, dtype=np.float64)).pin_memory() for s in steps]
-        gs2 = mpm.GpuScene(sc, precision=prec, krylov=kry, stream=stream.cuda_stream, newton_tol=1e-8,
+        gs2 = mpm.GpuScene(sc, precision=prec, krylov=kry, stream=stream.cuda_stream, newton_tol=1e-8, precond=pc,
                            krylov_maxit=50000)
         gs2.solve_step(steps[0])
         h2d = d2h = 0

@@ -22,7 +22,9 @@
  *   - Units SI; stress positive in tension; pressure p = tr(tau)/3.
  *   - Grid: n[a] cells per axis (n[2] ignored in 2D), spacing h, nodes at
  *     origin + i*h, 0 <= i <= n[a].  Node index ix + (nx+1)*(iy + (ny+1)*iz);
- *     a DOF index is node*dim + component.  2D is plane strain.
+ *     a DOF index is node*B + component with B values per node: B = dim for
+ *     MPM_SOLID, B = dim + 1 for MPM_UP (component dim is the pore pressure,
+ *     positive in compression).  2D is plane strain.
  *   - Particle arrays passed in are HOST arrays in the caller's order; they
  *     are copied at the call.  The library keeps particles sorted by cell on
  *     the device; every getter returns them in the caller's original order.
@@ -63,6 +65,8 @@ enum { MPM_NH = 0, MPM_NH_DP = 1, MPM_NH_MCC = 2 };        /* material models   
 enum { MPM_FP64 = 0, MPM_MIXED = 1 };                       /* precision modes   */
 enum { MPM_BICGSTAB = 0, MPM_GMRES = 1 };                   /* Krylov methods    */
 enum { MPM_FORCING_FIXED = 0, MPM_FORCING_EW = 1 };         /* linear tolerances */
+enum { MPM_SOLID = 0, MPM_UP = 1 };                         /* formulations      */
+enum { MPM_PC_AUTO = 0, MPM_PC_NODE = 1, MPM_PC_SEG4 = 2 };  /* preconditioners   */
 
 typedef struct {
   int dim;                 /* 2 (plane strain) or 3                              */
@@ -82,6 +86,21 @@ typedef struct {
                               clamped to [krylov_rtol, 0.01]                     */
   double krylov_rtol;
   int krylov_maxit;
+  int formulation;         /* MPM_SOLID: dim displacement values per node;
+                              MPM_UP (2D only): displacements and the pore
+                              pressure, B = dim + 1 values per node (the
+                              coupled formulation of the paper's Sec. 2.2
+                              remark, verified in Sec. 4.4)                   */
+  double dt;               /* MPM_UP: time step of a load step, s (> 0)          */
+  double p_scale;          /* MPM_UP: weight of the mass-balance rows in the
+                              Newton and Krylov norms and inverse scale of the
+                              pressure unknown inside the solver; 0 = max over
+                              materials of mu / h                              */
+  int precond;             /* block-Jacobi blocks: MPM_PC_NODE one node's
+                              B x B diagonal block; MPM_PC_SEG4 the 4B x 4B
+                              diagonal block of four consecutive active nodes
+                              (row order, mostly x-neighbours); MPM_PC_AUTO
+                              (0): SEG4 for MPM_UP, NODE otherwise            */
 } mpm_scene_desc;
 
 typedef struct {
@@ -90,6 +109,9 @@ typedef struct {
   double phi, psi, c;      /* DP friction / dilation angle (degrees), cohesion    */
   double M, lambda_cc, kappa_cc; /* MCC critical-state slope, compression indices */
   double pc0;              /* MCC initial preconsolidation pressure (negative)    */
+  double k_hyd;            /* MPM_UP: hydraulic conductivity, m/s (Darcy flux
+                              q = -(k_hyd / gamma_w) grad p)                   */
+  double gamma_w;          /* MPM_UP: unit weight of the pore fluid, N/m^3      */
 } mpm_material;
 
 typedef struct {
@@ -133,11 +155,20 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
 /* Gravity vector used by the following load steps (f_ext = sum_p w_ip m_p g). */
 mpm_status mpm_set_gravity(mpm_scene* s, const double g[3]);
 
-/* Prescribed displacement increments for the following load steps:
- * dof[k] = node*dim + comp on the dense node grid, value[k] the increment per
- * load step.  Replaces the previous set.  DOFs on nodes without mass are
- * ignored.  Errors: MPM_ERR_INVALID_ARG for an index outside the grid. */
+/* Prescribed values for the following load steps: dof[k] = node*B + comp on
+ * the dense node grid; value[k] is the displacement increment per load step,
+ * or, for a pore-pressure DOF (MPM_UP), the pressure at the end of the step.
+ * Replaces the previous set.  DOFs on nodes without mass are ignored.
+ * Errors: MPM_ERR_INVALID_ARG for an index outside the grid. */
 mpm_status mpm_set_dirichlet(mpm_scene* s, int n, const long long* dof, const double* value);
+
+/* External forces carried by particles for the following load steps (the
+ * Neumann term of the paper's weak form, Sec. 2.1: a surface traction times
+ * the area of the particle's share of the loaded face), spread to the nodes
+ * with w_ip like gravity.  particle[k] is a caller-order index, f[3k..3k+2]
+ * the force in N (2D: N per unit thickness).  Replaces the previous set (all
+ * other particles carry none).  Errors: MPM_ERR_INVALID_ARG. */
+mpm_status mpm_set_traction(mpm_scene* s, int n, const int* particle, const double* f);
 
 /* Stage a load step: sort particles by cell, find the active nodes
  * (nodal mass > 1e-12 * max particle mass) and the Jacobian pattern, apply the
@@ -149,7 +180,7 @@ mpm_status mpm_begin_step(mpm_scene* s, mpm_newton_report* rep);
  * Returns MPM_ERR_STATE if no step is staged.  Does not commit. */
 mpm_status mpm_newton_step(mpm_scene* s, mpm_newton_report* rep);
 
-/* Replace the iterate of the staged step by du (host, nnode*dim) and
+/* Replace the iterate of the staged step by du (host, nnode*B) and
  * re-evaluate the residual and the per-particle tangents there; prescribed
  * DOFs keep their prescribed increments.  For checks at chosen states and
  * for warm starts.  MPM_ERR_STATE if no step is staged. */
@@ -168,10 +199,12 @@ mpm_status mpm_commit_step(mpm_scene* s);
  * Returns MPM_ERR_NOT_CONVERGED (state not committed) when tol is missed. */
 mpm_status mpm_solve_step(mpm_scene* s, mpm_step_report* rep);
 
-/* FP64 residual of the current iterate on the dense node grid, nnode*dim
- * entries; prescribed and inactive DOFs read 0. */
+/* FP64 residual of the current iterate on the dense node grid, nnode*B
+ * entries; prescribed and inactive DOFs read 0.  For MPM_UP the pressure rows
+ * hold the fluid mass balance multiplied by dt (m^3; m^2 in 2D). */
 mpm_status mpm_get_residual(const mpm_scene* s, double* r);
-/* Current nodal increment du (nnode*dim) and nodal mass (nnode). */
+/* Current nodal iterate du (nnode*B: displacement increments, and for MPM_UP
+ * the pore pressure) and nodal mass (nnode). */
 mpm_status mpm_get_du(const mpm_scene* s, double* du);
 mpm_status mpm_get_mass(const mpm_scene* s, double* mass);
 
@@ -181,7 +214,7 @@ mpm_status mpm_get_counts(const mpm_scene* s, int* n_active, long long* nnzb);
 
 /* The Jacobian assembled for the latest Newton iteration, in block CSR:
  * row_node[n_active] node index of each block row, row_ptr[n_active+1],
- * col_node[nnzb] node index of each block, val[nnzb*dim*dim] row-major
+ * col_node[nnzb] node index of each block, val[nnzb*B*B] row-major
  * blocks converted to double.  Rows and columns of prescribed DOFs hold the
  * identity.  Capacity `cap` in blocks; MPM_ERR_INVALID_ARG if too small. */
 mpm_status mpm_get_jacobian_bsr(const mpm_scene* s, long long cap, int* row_node,
@@ -193,6 +226,11 @@ mpm_status mpm_get_jacobian_bsr(const mpm_scene* s, long long cap, int* row_node
  * tau[np*9] Kirchhoff stress of the committed state. */
 mpm_status mpm_get_particles(const mpm_scene* s, double* x, double* be, double* pc, double* F,
                              double* tau);
+
+/* MPM_UP: pore pressure of each particle after the last commit,
+ * p_p = sum_i w_ip p_i (caller's order, np values).  MPM_ERR_INVALID_ARG for a
+ * single-phase scene. */
+mpm_status mpm_get_pressure(const mpm_scene* s, double* pp);
 
 /* Number of CUDA kernels this scene has launched so far (including those
  * inside CUDA-graph launches). */

@@ -39,8 +39,11 @@ thread_local std::string g_create_err;  // message of the last failed mpm_create
 
 struct mpm_scene {
   mpm_scene_desc desc{};
-  int D = 2, np = 0, nmat = 0, nbe = 4, nF = 4;
+  int D = 2, B = 2, np = 0, nmat = 0, nbe = 4, nF = 4;
   bool mixed = false;
+  bool up = false;          // coupled u-p: B = D + 1 values per node
+  double psc = 1.0;         // u-p: pressure unknown / mass-balance row scale
+  int seg = 1;              // rows per block-Jacobi block (1 node, 4 row segment)
   DevGrid G{};
   long long nnode = 0, ndof = 0;
   cudaStream_t st = nullptr;
@@ -142,7 +145,17 @@ void validate_desc(const mpm_scene_desc* d) {
   if (!(d->newton_tol > 0) || d->newton_maxit < 1 || d->newton_maxit > 32)
     fail(MPM_ERR_INVALID_ARG, "newton_tol > 0 and 1 <= newton_maxit <= 32 required");
   if (!(d->krylov_rtol > 0) || d->krylov_maxit < 1) fail(MPM_ERR_INVALID_ARG, "bad Krylov settings");
+  if (d->formulation != MPM_SOLID && d->formulation != MPM_UP) fail(MPM_ERR_INVALID_ARG, "bad formulation");
+  if (d->precond != MPM_PC_AUTO && d->precond != MPM_PC_NODE && d->precond != MPM_PC_SEG4)
+    fail(MPM_ERR_INVALID_ARG, "bad precond");
+  if (d->formulation == MPM_UP) {
+    if (d->dim != 2) fail(MPM_ERR_INVALID_ARG, "the u-p formulation is built for dim 2");
+    if (!(d->dt > 0)) fail(MPM_ERR_INVALID_ARG, "u-p needs dt > 0");
+    if (!(d->p_scale >= 0)) fail(MPM_ERR_INVALID_ARG, "p_scale must be >= 0");
+  }
 }
+
+int dofs_per_node(const mpm_scene_desc* d) { return d->dim + (d->formulation == MPM_UP ? 1 : 0); }
 
 long long nnode_of(const mpm_scene_desc* d) {
   long long c = 1;
@@ -152,18 +165,19 @@ long long nnode_of(const mpm_scene_desc* d) {
 
 // Device bytes of a scene, excluding the matrix capacity growth margin.
 size_t footprint(const mpm_scene_desc* d, int np) {
-  const int D = d->dim;
+  const int D = d->dim, B = dofs_per_node(d), NPHI = D + (B > D ? 1 : 0);
   const size_t T = d->precision == MPM_MIXED ? 4 : 8;
-  const long long nn = nnode_of(d), ndof = nn * D;
+  const long long nn = nnode_of(d), ndof = nn * B;
   const int nbe = D == 2 ? 4 : 6, nF = D * D;
-  size_t part = (size_t)np * (2 * (D + 2 + 2 + nbe + 1 + nF) * 8 + 2 * 2 * 4 + 3 * 4);
+  const int up_extra = (B > D) ? 2 : 0;   // kdt, pp
+  size_t part = (size_t)np * (2 * (D + 2 + 2 + nbe + 1 + nF + up_extra) * 8 + 2 * 2 * 4 + 3 * 4);
   size_t grid = (size_t)nn * (7 * 4 + 8) + (size_t)ndof * (4 * 8 + 1);
-  size_t tang = (size_t)np * D * D * D * D * T;
+  size_t tang = (size_t)np * B * NPHI * B * NPHI * T;
   long long pad = 2 + 2LL * (d->n[0] + 1) + (D == 3 ? 2LL * (d->n[0] + 1) * (d->n[1] + 1) : 0);
-  size_t vec = 9 * (size_t)(nn + 2 * pad) * D * T;
+  size_t vec = 9 * (size_t)(nn + 2 * pad) * B * T;
   // active rows are bounded by the nodes the particles can reach
   long long rows = std::min<long long>(nn, (long long)np * (D == 2 ? 9 : 27));
-  size_t mat = (size_t)rows * (stencil_slots(D) + 1) * D * D * T;
+  size_t mat = (size_t)rows * (stencil_slots(D) + 1) * B * B * T;
   return part + grid + tang + vec + mat + (1 << 20);
 }
 
@@ -175,6 +189,7 @@ DevMatrix<T> matview(mpm_scene* s) {
   K.cap = s->cap;
   K.rows = s->d_rows;
   K.nrow = s->d_nrow;
+  K.seg = s->seg;
   return K;
 }
 
@@ -194,13 +209,13 @@ void ensure_capacity(mpm_scene* s, int nrow) {
   s->dfree(s->d_dinv);
   s->d_K = nullptr;
   s->d_dinv = nullptr;
-  const size_t S = stencil_slots(s->D), DD = s->D * s->D;
+  const size_t S = stencil_slots(s->D), DD = (size_t)s->B * s->B;
   if (s->mixed) {
     s->d_K = s->dalloc<float>((size_t)cap * S * DD);
-    s->d_dinv = s->dalloc<float>((size_t)cap * DD);
+    s->d_dinv = s->dalloc<float>((size_t)(cap + 4) * DD * s->seg);
   } else {
     s->d_K = s->dalloc<double>((size_t)cap * S * DD);
-    s->d_dinv = s->dalloc<double>((size_t)cap * DD);
+    s->d_dinv = s->dalloc<double>((size_t)(cap + 4) * DD * s->seg);
   }
   s->cap = cap;
   if (s->gexec) {
@@ -224,6 +239,9 @@ DevParticles make_particles(mpm_scene* s) {
   P.pc = s->dalloc<double>(s->np);
   for (int k = 0; k < MAX_F; ++k) P.F[k] = (k < s->nF) ? s->dalloc<double>(s->np) : nullptr;
   P.orig = s->dalloc<int>(s->np);
+  P.kdt = s->up ? s->dalloc<double>(s->np) : nullptr;
+  P.pp = s->up ? s->dalloc<double>(s->np) : nullptr;
+  for (int a = 0; a < 3; ++a) P.fext[a] = nullptr;
   return P;
 }
 
@@ -238,6 +256,10 @@ GatherArrays gather_list(mpm_scene* s, const DevParticles& src, DevParticles& ds
   for (int k = 0; k < s->nbe; ++k) { g.dsrc[nd] = src.be[k]; g.ddst[nd++] = dst.be[k]; }
   g.dsrc[nd] = src.pc; g.ddst[nd++] = dst.pc;
   for (int k = 0; k < s->nF; ++k) { g.dsrc[nd] = src.F[k]; g.ddst[nd++] = dst.F[k]; }
+  if (src.kdt) { g.dsrc[nd] = src.kdt; g.ddst[nd++] = dst.kdt; }
+  if (src.pp) { g.dsrc[nd] = src.pp; g.ddst[nd++] = dst.pp; }
+  for (int a = 0; a < s->D; ++a)
+    if (src.fext[a]) { g.dsrc[nd] = src.fext[a]; g.ddst[nd++] = dst.fext[a]; }
   g.nd = nd;
   g.isrc[0] = src.mat; g.idst[0] = dst.mat;
   g.isrc[1] = src.orig; g.idst[1] = dst.orig;
@@ -245,16 +267,26 @@ GatherArrays gather_list(mpm_scene* s, const DevParticles& src, DevParticles& ds
   return g;
 }
 
-template <int D, class T>
+template <int D, class T, int B>
+void launch_particle_pass(mpm_scene* s, int mode, int* nplastic) {
+  if constexpr (B > D)
+    ck(launch_particles_up<D, T>(s->P, s->G, s->d_mats, s->d_du, s->d_r, s->d_grav, (T*)s->d_A, mode, s->psc,
+                                 s->d_err, nplastic, s->st),
+       "u-p particle kernel");
+  else
+    ck(launch_particles<D, T>(s->P, s->G, s->d_mats, s->d_du, s->d_r, s->d_grav, (T*)s->d_A, mode, s->d_err,
+                              nplastic, s->st),
+       "particle kernel");
+}
+
+template <int D, class T, int B>
 void residual_pass(mpm_scene* s, int mode) {
   ck(cudaMemsetAsync(s->d_r, 0, s->ndof * sizeof(double), s->st), "memset r");
   ck(cudaMemsetAsync(s->d_nplastic, 0, sizeof(int), s->st), "memset");
   ck(cudaMemsetAsync(s->d_fail, 0, sizeof(double), s->st), "memset");
-  ck(launch_particles<D, T>(s->P, s->G, s->d_mats, s->d_du, s->d_r, s->d_grav, (T*)s->d_A, mode, s->d_err,
-                            s->d_nplastic, s->st),
-     "particle kernel");
+  launch_particle_pass<D, T, B>(s, mode, s->d_nplastic);
   ck(cudaMemsetAsync(s->d_norm, 0, sizeof(double), s->st), "memset");
-  ck(launch_norm_free<D>(s->d_r, s->d_rows, s->nrow, s->d_fixed, s->d_norm, s->st), "norm kernel");
+  ck(launch_norm_free<B>(s->d_r, s->d_rows, s->nrow, s->d_fixed, s->d_norm, s->st), "norm kernel");
   ck(cudaMemcpyAsync(s->h_dbl, s->d_norm, sizeof(double), cudaMemcpyDeviceToHost, s->st), "copy norm");
   ck(cudaMemcpyAsync(s->h_int + 2, s->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s->st), "copy err");
   s->launches += 2;
@@ -278,7 +310,7 @@ void check_err_bits(mpm_scene* s) {
   fail(st, m);
 }
 
-template <int D, class T>
+template <int D, class T, int B>
 void begin_step_impl(mpm_scene* s, mpm_newton_report* rep) {
   cudaStream_t st = s->st;
   const long long nn = s->nnode;
@@ -315,9 +347,9 @@ void begin_step_impl(mpm_scene* s, mpm_newton_report* rep) {
   ensure_capacity(s, s->nrow);
   // prescribed increments and r^0 (with the tangent for the first iteration)
   ck(cudaMemcpyAsync(s->d_grav, s->grav, 3 * sizeof(double), cudaMemcpyHostToDevice, st), "grav");
-  ck(launch_apply_bc(s->d_fixed, s->d_bcval, s->d_node2row, s->d_du, s->ndof, D, st), "bc");
+  ck(launch_apply_bc(s->d_fixed, s->d_bcval, s->d_node2row, s->d_du, s->ndof, B, st), "bc");
   cudaEventRecord(s->ev[2], st);
-  residual_pass<D, T>(s, 1);
+  residual_pass<D, T, B>(s, 1);
   cudaEventRecord(s->ev[3], st);
   ck(cudaStreamSynchronize(st), "sync");
   check_err_bits(s);
@@ -340,7 +372,7 @@ void begin_step_impl(mpm_scene* s, mpm_newton_report* rep) {
   }
 }
 
-template <int D, class T>
+template <int D, class T, int B>
 void build_graph(mpm_scene* s, int nblk) {
   if (s->gexec) {
     cudaGraphExecDestroy(s->gexec);
@@ -350,7 +382,7 @@ void build_graph(mpm_scene* s, int nblk) {
   ck(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal), "capture");
   DevMatrix<T> K = matview<T>(s);
   KrylovVecs<D, T> v = vecview<D, T>(s);
-  for (int c = 0; c < GRAPH_CHUNK; ++c) launch_bicgstab_iter<D, T>(s->G, K, v, s->d_S, nblk, s->st);
+  for (int c = 0; c < GRAPH_CHUNK; ++c) launch_bicgstab_iter<D, T, B>(s->G, K, v, s->d_S, nblk, s->st);
   ck(cudaStreamEndCapture(s->st, &g), "end capture");
   ck(cudaGraphInstantiate(&s->gexec, g, 0), "instantiate");
   cudaGraphDestroy(g);
@@ -360,21 +392,21 @@ void build_graph(mpm_scene* s, int nblk) {
 // Assembly of the per-particle consistent tangents (written by the last
 // residual pass) into the stencil-BSR Jacobian, prescribed rows/columns set
 // to the identity, block-Jacobi inverse.
-template <int D, class T>
+template <int D, class T, int B>
 void assemble_impl(mpm_scene* s) {
   if (!s->staged) fail(MPM_ERR_STATE, "no load step staged (call mpm_begin_step)");
   cudaStream_t st = s->st;
   DevMatrix<T> K = matview<T>(s);
   // every block of every active row is stored by the assembly (no zero fill)
-  ck(launch_assemble<D, T>(s->P, s->G, s->d_cstart, s->d_node2row, (const T*)s->d_A, K, st), "assemble");
-  ck(launch_bc_matrix<D, T>(s->G, K, s->d_fixed, s->d_node2row, s->nrow, st), "bc matrix");
-  ck(launch_block_jacobi<D, T>(K, s->nrow, s->d_err, st), "block jacobi");
+  ck(launch_assemble<D, T, B>(s->P, s->G, s->d_cstart, s->d_node2row, (const T*)s->d_A, K, st), "assemble");
+  ck(launch_bc_matrix<D, T, B>(s->G, K, s->d_fixed, s->d_node2row, s->nrow, st), "bc matrix");
+  ck(launch_block_jacobi<D, T, B>(s->G, K, s->nrow, s->d_err, st), "block jacobi");
   s->launches += 3;
 }
 
 // Restarted GMRES(m) on J d = -r to an absolute residual `tol`: cycles of m
 // Arnoldi steps (one CUDA graph per cycle), polled once per cycle.
-template <int D, class T>
+template <int D, class T, int B>
 void gmres_solve(mpm_scene* s, DevMatrix<T> K, T* x, double tol, int nblk, int& kit, int& kstat, double& kres2) {
   cudaStream_t st = s->st;
   T* base = (T*)s->d_gvec;
@@ -391,7 +423,7 @@ void gmres_solve(mpm_scene* s, DevMatrix<T> K, T* x, double tol, int nblk, int& 
     }
     cudaGraph_t gr;
     ck(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "capture");
-    launch_gmres_cycle<D, T>(s->G, K, g, x, s->d_gst, s->gm, nblk, st);
+    launch_gmres_cycle<D, T, B>(s->G, K, g, x, s->d_gst, s->gm, nblk, st);
     ck(cudaStreamEndCapture(st, &gr), "end capture");
     ck(cudaGraphInstantiate(&s->gexec_gm, gr, 0), "instantiate");
     cudaGraphDestroy(gr);
@@ -401,12 +433,12 @@ void gmres_solve(mpm_scene* s, DevMatrix<T> K, T* x, double tol, int nblk, int& 
   const size_t tail_bytes = sizeof(GmresState) - tail;
   GmresState* h = (GmresState*)(s->h_gst - tail);   // fields from wn2 on are valid
   for (int cycle = 0;; ++cycle) {
-    ck(launch_gmres_begin<D, T>(s->G, K, s->d_r, s->d_fixed, g, x, s->d_gst, cycle == 0 ? 1 : 0, tol,
+    ck(launch_gmres_begin<D, T, B>(s->G, K, s->d_r, s->d_fixed, g, x, s->d_gst, cycle == 0 ? 1 : 0, tol,
                                 s->desc.krylov_maxit, nblk, st),
        "gmres begin");
     s->launches += 3;
     if (s->use_graph) ck(cudaGraphLaunch(s->gexec_gm, st), "graph launch");
-    else ck(launch_gmres_cycle<D, T>(s->G, K, g, x, s->d_gst, s->gm, nblk, st), "gmres cycle");
+    else ck(launch_gmres_cycle<D, T, B>(s->G, K, g, x, s->d_gst, s->gm, nblk, st), "gmres cycle");
     s->launches += 4LL * s->gm + 2;
     ck(cudaMemcpyAsync(s->h_gst, (char*)s->d_gst + tail, tail_bytes, cudaMemcpyDeviceToHost, st), "copy");
     ck(cudaStreamSynchronize(st), "sync");
@@ -417,13 +449,13 @@ void gmres_solve(mpm_scene* s, DevMatrix<T> K, T* x, double tol, int nblk, int& 
   kres2 = h->res * h->res;
 }
 
-template <int D, class T>
+template <int D, class T, int B>
 void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
   if (!s->staged) fail(MPM_ERR_STATE, "no load step staged (call mpm_begin_step)");
   cudaStream_t st = s->st;
   DevMatrix<T> K = matview<T>(s);
   cudaEventRecord(s->ev[0], st);
-  assemble_impl<D, T>(s);
+  assemble_impl<D, T, B>(s);
   // linear tolerance: fixed, or Eisenstat-Walker choice 2 (gamma 0.9,
   // alpha 2) capped at ETA_MAX = 1e-2: with the classical cap of 0.1 loose
   // steps through the plastic zone made Newton diverge on footing problems.
@@ -450,22 +482,23 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
   int kit = 0, kstat = 0;
   double kres2 = 0.0;
   if (s->gm > 0) {
-    gmres_solve<D, T>(s, K, v.x, eta * s->rk, nblk, kit, kstat, kres2);
+    gmres_solve<D, T, B>(s, K, v.x, eta * s->rk, nblk, kit, kstat, kres2);
   } else {
-  ck(launch_bicgstab_init<D, T>(K, s->d_r, s->d_fixed, v, s->d_S, tol2, s->desc.krylov_maxit, nblk, st),
+  ck(launch_bicgstab_init<D, T, B>(K, s->d_r, s->d_fixed, v, s->d_S, tol2, s->desc.krylov_maxit, nblk, st),
      "krylov init");
   const int pblk = std::min(s->pblocks, std::max(1, (s->nrow * 4 + 511) / 512));
   if (s->pblocks > 0) {
     // whole solve in one cooperative launch
-    ck(launch_bicgstab_persistent<D, T>(s->G, K, v, s->d_S, s->d_part, s->d_bar, s->d_err, pblk, st),
-       "persistent krylov");
+    if constexpr (B == D)
+      ck(launch_bicgstab_persistent<D, T>(s->G, K, v, s->d_S, s->d_part, s->d_bar, s->d_err, pblk, st),
+         "persistent krylov");
     s->launches += 1;
     ck(cudaMemcpyAsync(s->h_S, s->d_S, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st), "copy S");
     ck(cudaMemcpyAsync(s->h_int + 2, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "copy err");
     ck(cudaStreamSynchronize(st), "sync");
     check_err_bits(s);
   }
-  if (s->pblocks == 0 && s->use_graph && s->graph_cap != s->cap) build_graph<D, T>(s, nblk);
+  if (s->pblocks == 0 && s->use_graph && s->graph_cap != s->cap) build_graph<D, T, B>(s, nblk);
   if (s->pblocks == 0) {
     // graph chunks of GRAPH_CHUNK iterations until the done flag; on a
     // (near) breakdown or the iteration limit, restart from the current x
@@ -477,7 +510,7 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
           ck(cudaGraphLaunch(s->gexec, st), "graph launch");
         } else {
           for (int c = 0; c < GRAPH_CHUNK; ++c)
-            ck(launch_bicgstab_iter<D, T>(s->G, K, v, s->d_S, nblk, st), "krylov");
+            ck(launch_bicgstab_iter<D, T, B>(s->G, K, v, s->d_S, nblk, st), "krylov");
         }
         launched += GRAPH_CHUNK;
         s->launches += 4 * GRAPH_CHUNK;
@@ -488,11 +521,18 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
       }
       kit += s->h_S->iter;
       kstat = s->h_S->status;
-      if (kstat == 0 || restart >= 3 || kit >= s->desc.krylov_maxit) break;
-      ck(launch_bicgstab_restart<D, T>(s->G, K, s->d_r, s->d_fixed, v, s->d_S, tol2,
+      if (restart >= 3 || kit >= s->desc.krylov_maxit) break;
+      // restart from the true residual b - J x; when the recurrence reported
+      // convergence this also checks it (the recurrence residual can drift
+      // from the true one on ill-conditioned systems such as u-p)
+      ck(launch_bicgstab_restart<D, T, B>(s->G, K, s->d_r, s->d_fixed, v, s->d_S, tol2,
                                        s->desc.krylov_maxit - kit, nblk, st),
          "krylov restart");
       s->launches += 1;
+      ck(cudaMemcpyAsync(s->h_S, s->d_S, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st), "copy S");
+      ck(cudaStreamSynchronize(st), "sync");
+      if (kstat == 0 && s->h_S->rr_last <= 4.0 * tol2) break;   // true residual within 2x of the tolerance
+      kstat = 0;
       s->restarts += 1;
     }
   } else {
@@ -505,7 +545,7 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
   // step-length limit (reading): a Newton correction that would move a node
   // by more than one cell width h is scaled down to h (a near-singular J, as
   // at the onset of a mechanism, otherwise yields astronomically large steps)
-  ck(launch_absmax<D, T>(K, v.x, s->d_fixed, s->d_absmax, nblk, st), "absmax");
+  ck(launch_absmax<D, T, B>(K, v.x, s->d_fixed, s->d_absmax, nblk, st), "absmax");
   ck(cudaMemcpyAsync(s->h_dbl + 2, s->d_absmax, sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
   ck(cudaStreamSynchronize(st), "sync");
   const double xmax = s->h_dbl[2];
@@ -514,20 +554,20 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
   else if (xmax > s->G.h) step = s->G.h / xmax;
   if (step < 1.0) s->limited += 1;
   ck(cudaMemcpyAsync(s->d_duprev, s->d_du, s->ndof * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy du");
-  ck(launch_step_du<D, T>(K, v.x, s->d_fixed, s->d_duprev, s->d_du, step, nblk, st), "update");
+  ck(launch_step_du<D, T, B>(K, v.x, s->d_fixed, s->d_duprev, s->d_du, step, nblk, st), "update");
   s->launches += 3;   // Krylov init + absmax + update
   cudaEventRecord(s->ev[2], st);
-  residual_pass<D, T>(s, 1);
+  residual_pass<D, T, B>(s, 1);
   cudaEventRecord(s->ev[3], st);
   ck(cudaStreamSynchronize(st), "sync");
   // a full step that drives a return map out of its domain (or to a
   // non-finite state) is halved, at most four times, before giving up
   for (int half = 1; half <= 4 && (s->h_int[2] & (ERRF_RETURN | ERRF_NONFINITE | ERRF_DET)); ++half) {
     ck(cudaMemsetAsync(s->d_err, 0, sizeof(int), st), "memset");
-    ck(launch_step_du<D, T>(K, v.x, s->d_fixed, s->d_duprev, s->d_du, step * std::ldexp(1.0, -half), nblk, st),
+    ck(launch_step_du<D, T, B>(K, v.x, s->d_fixed, s->d_duprev, s->d_du, step * std::ldexp(1.0, -half), nblk, st),
        "step");
     s->launches += 1;
-    residual_pass<D, T>(s, 1);
+    residual_pass<D, T, B>(s, 1);
     cudaEventRecord(s->ev[3], st);
     ck(cudaStreamSynchronize(st), "sync");
     s->halvings += 1;
@@ -551,10 +591,12 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
   }
 }
 
-template <int D, class T>
+template <int D, class T, int B>
 void set_du_impl(mpm_scene* s, const double* du) {
   if (!s->staged) fail(MPM_ERR_STATE, "no load step staged (call mpm_begin_step)");
   std::vector<double> h(du, du + s->ndof);
+  if (B > D)
+    for (long long d = D; d < s->ndof; d += B) h[d] /= s->psc;
   std::vector<uint8_t> f(s->ndof);
   std::vector<double> bc(s->ndof);
   std::vector<int> n2r(s->nnode);
@@ -563,20 +605,18 @@ void set_du_impl(mpm_scene* s, const double* du) {
   ck(cudaMemcpy(bc.data(), s->d_bcval, s->ndof * sizeof(double), cudaMemcpyDeviceToHost), "download");
   ck(cudaMemcpy(n2r.data(), s->d_node2row, s->nnode * sizeof(int), cudaMemcpyDeviceToHost), "download");
   for (long long d = 0; d < s->ndof; ++d)
-    if (f[d] && n2r[d / D] >= 0) h[d] = bc[d];
+    if (f[d] && n2r[d / B] >= 0) h[d] = bc[d];
   ck(cudaMemcpy(s->d_du, h.data(), s->ndof * sizeof(double), cudaMemcpyHostToDevice), "upload");
-  residual_pass<D, T>(s, 1);
+  residual_pass<D, T, B>(s, 1);
   ck(cudaStreamSynchronize(s->st), "sync");
   check_err_bits(s);
   s->rk = std::sqrt(s->h_dbl[0]);
 }
 
-template <int D, class T>
+template <int D, class T, int B>
 void commit_impl(mpm_scene* s) {
   if (!s->staged) fail(MPM_ERR_STATE, "no load step staged");
-  ck(launch_particles<D, T>(s->P, s->G, s->d_mats, s->d_du, s->d_r, s->d_grav, (T*)s->d_A, 2, s->d_err, nullptr,
-                            s->st),
-     "commit kernel");
+  launch_particle_pass<D, T, B>(s, 2, nullptr);
   ck(cudaMemcpyAsync(s->h_int + 2, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->st), "copy");
   ck(cudaStreamSynchronize(s->st), "sync");
   s->launches += 1;
@@ -584,16 +624,16 @@ void commit_impl(mpm_scene* s) {
   s->staged = false;
 }
 
-template <int D, class T>
+template <int D, class T, int B>
 void time_spmv_impl(mpm_scene* s, int reps, double* ms, double* bytes) {
   if (!s->staged) fail(MPM_ERR_STATE, "no load step staged");
   if (reps < 1) fail(MPM_ERR_INVALID_ARG, "reps must be positive");
   DevMatrix<T> K = matview<T>(s);
   KrylovVecs<D, T> v = vecview<D, T>(s);
   const int nblk = (s->cap + KTPB - 1) / KTPB;
-  ck(launch_spmv<D, T>(s->G, K, v.phat, v.v, nblk, s->st), "spmv");   // warm-up
+  ck(launch_spmv<D, T, B>(s->G, K, v.phat, v.v, nblk, s->st), "spmv");   // warm-up
   ck(cudaEventRecord(s->ev[4], s->st), "event");
-  for (int k = 0; k < reps; ++k) ck(launch_spmv<D, T>(s->G, K, v.phat, v.v, nblk, s->st), "spmv");
+  for (int k = 0; k < reps; ++k) ck(launch_spmv<D, T, B>(s->G, K, v.phat, v.v, nblk, s->st), "spmv");
   ck(cudaEventRecord(s->ev[5], s->st), "event");
   ck(cudaEventSynchronize(s->ev[5]), "sync");
   float t = 0;
@@ -607,30 +647,33 @@ void time_spmv_impl(mpm_scene* s, int reps, double* ms, double* bytes) {
     for (int m : mask) nnzb += m;
   }
   const double ts = sizeof(T);
-  *bytes = (double)nnzb * D * D * ts + (double)s->nrow * D * ts * 2.0 + (double)s->nrow * 4.0;
+  *bytes = (double)nnzb * B * B * ts + (double)s->nrow * B * ts * 2.0 + (double)s->nrow * 4.0;
 }
 
-// dispatch on (dim, precision)
-template <template <int, class> class F, class... Args>
+// dispatch on (dim, precision, values per node)
+template <template <int, class, int> class F, class... Args>
 void dispatch(mpm_scene* s, Args... args) {
-  if (s->D == 2) {
-    if (s->mixed) F<2, float>::run(s, args...);
-    else F<2, double>::run(s, args...);
+  if (s->up) {
+    if (s->mixed) F<2, float, 3>::run(s, args...);
+    else F<2, double, 3>::run(s, args...);
+  } else if (s->D == 2) {
+    if (s->mixed) F<2, float, 2>::run(s, args...);
+    else F<2, double, 2>::run(s, args...);
   } else {
-    if (s->mixed) F<3, float>::run(s, args...);
-    else F<3, double>::run(s, args...);
+    if (s->mixed) F<3, float, 3>::run(s, args...);
+    else F<3, double, 3>::run(s, args...);
   }
 }
-template <int D, class T> struct BeginF { static void run(mpm_scene* s, mpm_newton_report* r) { begin_step_impl<D, T>(s, r); } };
-template <int D, class T> struct NewtonF { static void run(mpm_scene* s, mpm_newton_report* r) { newton_impl<D, T>(s, r); } };
-template <int D, class T> struct CommitF { static void run(mpm_scene* s) { commit_impl<D, T>(s); } };
-template <int D, class T> struct SetDuF { static void run(mpm_scene* s, const double* du) { set_du_impl<D, T>(s, du); } };
-template <int D, class T> struct TimeSpmvF {
-  static void run(mpm_scene* s, int reps, double* ms, double* bytes) { time_spmv_impl<D, T>(s, reps, ms, bytes); }
+template <int D, class T, int B> struct BeginF { static void run(mpm_scene* s, mpm_newton_report* r) { begin_step_impl<D, T, B>(s, r); } };
+template <int D, class T, int B> struct NewtonF { static void run(mpm_scene* s, mpm_newton_report* r) { newton_impl<D, T, B>(s, r); } };
+template <int D, class T, int B> struct CommitF { static void run(mpm_scene* s) { commit_impl<D, T, B>(s); } };
+template <int D, class T, int B> struct SetDuF { static void run(mpm_scene* s, const double* du) { set_du_impl<D, T, B>(s, du); } };
+template <int D, class T, int B> struct TimeSpmvF {
+  static void run(mpm_scene* s, int reps, double* ms, double* bytes) { time_spmv_impl<D, T, B>(s, reps, ms, bytes); }
 };
-template <int D, class T> struct AssembleF {
+template <int D, class T, int B> struct AssembleF {
   static void run(mpm_scene* s) {
-    assemble_impl<D, T>(s);
+    assemble_impl<D, T, B>(s);
     ck(cudaMemcpyAsync(s->h_int + 2, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->st), "copy");
     ck(cudaStreamSynchronize(s->st), "sync");
     check_err_bits(s);
@@ -688,6 +731,12 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
     if (!mats || nmat < 1) fail(MPM_ERR_INVALID_ARG, "need at least one material");
     s->desc = *desc;
     s->D = desc->dim;
+    s->up = desc->formulation == MPM_UP;
+    s->B = dofs_per_node(desc);
+    // preconditioner blocks: the u-p default is the row segment, whose exact
+    // 4-node solves take in the lateral pressure modes that only the small
+    // Darcy term controls (node blocks leave them to the Krylov method)
+    s->seg = (desc->precond == MPM_PC_SEG4 || (desc->precond == MPM_PC_AUTO && s->up)) ? 4 : 1;
     s->np = np;
     s->nmat = nmat;
     s->nbe = s->D == 2 ? 4 : 6;
@@ -706,7 +755,7 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
     G.ih = 1.0 / desc->h;
     s->nnode = (long long)G.nx1 * G.ny1 * G.nz1;
     G.nnode = s->nnode;
-    s->ndof = s->nnode * s->D;
+    s->ndof = s->nnode * s->B;
     if (s->nnode + 1 > 2000000000LL) fail(MPM_ERR_INVALID_ARG, "grid too large");
     // materials
     for (int m = 0; m < nmat; ++m) {
@@ -727,6 +776,15 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
       c.lmk = q.lambda_cc - q.kappa_cc;
       c.pc0 = q.pc0;
       s->hmats.push_back(c);
+      if (s->up && (!(q.k_hyd >= 0) || !(q.gamma_w > 0)))
+        fail(MPM_ERR_INVALID_ARG, "u-p materials need k_hyd >= 0 and gamma_w > 0");
+    }
+    if (s->up) {
+      // pressure scale: the largest shear modulus over the grid spacing
+      // (p / psc is then a length, psc * (mass balance) a force)
+      double mu_max = 0.0;
+      for (int m = 0; m < nmat; ++m) mu_max = std::max(mu_max, mats[m].E / (2.0 * (1.0 + mats[m].nu)));
+      s->psc = desc->p_scale > 0 ? desc->p_scale : mu_max / desc->h;
     }
     // host-side validation of particles
     for (int p = 0; p < np; ++p) {
@@ -792,6 +850,12 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
         up(s->P.F[k]);
       }
       ck(cudaMemcpy(s->P.mat, mat_id, np * sizeof(int), cudaMemcpyHostToDevice), "upload");
+      if (s->up) {
+        for (int p = 0; p < np; ++p) h[p] = mats[mat_id[p]].k_hyd / mats[mat_id[p]].gamma_w * desc->dt;
+        up(s->P.kdt);
+        std::fill(h.begin(), h.end(), 0.0);
+        up(s->P.pp);
+      }
       std::vector<int> o(np);
       for (int p = 0; p < np; ++p) o[p] = p;
       ck(cudaMemcpy(s->P.orig, o.data(), np * sizeof(int), cudaMemcpyHostToDevice), "upload");
@@ -827,9 +891,10 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
     ck(cudaMemsetAsync(s->d_fixed, 0, s->ndof, s->st), "memset");
     ck(cudaMemsetAsync(s->d_nrow, 0, sizeof(int), s->st), "memset");
     const size_t T = tsize(s);
-    const size_t D4 = (size_t)s->D * s->D * s->D * s->D;
+    const size_t NPHI = s->D + (s->up ? 1 : 0);
+    const size_t D4 = (size_t)s->B * NPHI * s->B * NPHI;   // tangent entries per particle
     s->d_A = s->mixed ? (void*)s->dalloc<float>((size_t)np * D4) : (void*)s->dalloc<double>((size_t)np * D4);
-    s->vpad = (2 + 2LL * G.nx1 + (s->D == 3 ? 2LL * G.nx1 * G.ny1 : 0)) * s->D;
+    s->vpad = (2 + 2LL * G.nx1 + (s->D == 3 ? 2LL * G.nx1 * G.ny1 : 0)) * s->B;
     s->vlen = s->ndof + 2 * s->vpad;
     if (s->mixed) s->d_vec = s->dalloc<float>(9 * s->vlen);
     else s->d_vec = s->dalloc<double>(9 * s->vlen);
@@ -854,7 +919,7 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
       int dev = 0;
       ck(cudaGetDevice(&dev), "device");
       const bool want_persistent = env && env[0] == '1';
-      if (want_persistent && desc->krylov == MPM_BICGSTAB) {
+      if (want_persistent && desc->krylov == MPM_BICGSTAB && !s->up && s->seg == 1) {
         if (s->D == 2) s->pblocks = s->mixed ? persistent_blocks<2, float>(dev) : persistent_blocks<2, double>(dev);
         else s->pblocks = s->mixed ? persistent_blocks<3, float>(dev) : persistent_blocks<3, double>(dev);
       }
@@ -885,7 +950,8 @@ mpm_status mpm_set_dirichlet(mpm_scene* s, int n, const long long* dof, const do
     for (int k = 0; k < n; ++k) {
       if (dof[k] < 0 || dof[k] >= s->ndof) fail(MPM_ERR_INVALID_ARG, "dirichlet dof out of range");
       f[dof[k]] = 1;
-      v[dof[k]] = value[k];
+      // a prescribed pore pressure is held as p / psc inside the solver
+      v[dof[k]] = (s->up && dof[k] % s->B == s->D) ? value[k] / s->psc : value[k];
     }
     ck(cudaStreamSynchronize(s->st), "sync");
     ck(cudaMemcpy(s->d_fixed, f.data(), s->ndof, cudaMemcpyHostToDevice), "upload");
@@ -979,7 +1045,10 @@ mpm_status mpm_get_residual(const mpm_scene* cs, double* r) {
     ck(cudaMemcpy(f.data(), s->d_fixed, s->ndof, cudaMemcpyDeviceToHost), "download");
     std::vector<int> n2r(s->nnode);
     ck(cudaMemcpy(n2r.data(), s->d_node2row, s->nnode * sizeof(int), cudaMemcpyDeviceToHost), "download");
-    for (long long d = 0; d < s->ndof; ++d) r[d] = (f[d] || n2r[d / s->D] < 0) ? 0.0 : full[d];
+    for (long long d = 0; d < s->ndof; ++d) {
+      r[d] = (f[d] || n2r[d / s->B] < 0) ? 0.0 : full[d];
+      if (s->up && d % s->B == s->D) r[d] /= s->psc;   // mass-balance rows in physical units
+    }
   });
 }
 
@@ -989,6 +1058,8 @@ mpm_status mpm_get_du(const mpm_scene* cs, double* du) {
   return guarded(s, [&] {
     ck(cudaStreamSynchronize(s->st), "sync");
     ck(cudaMemcpy(du, s->d_du, s->ndof * sizeof(double), cudaMemcpyDeviceToHost), "download");
+    if (s->up)
+      for (long long d = s->D; d < s->ndof; d += s->B) du[d] *= s->psc;
   });
 }
 
@@ -1043,12 +1114,14 @@ mpm_status mpm_get_jacobian_bsr(const mpm_scene* cs, long long cap, int* row_nod
   if (!s || !row_node || !row_ptr || !col_node || !val) return MPM_ERR_INVALID_ARG;
   return guarded(s, [&] {
     if (!s->staged && s->nrow == 0) fail(MPM_ERR_STATE, "no Jacobian assembled");
-    const int D = s->D, S = stencil_slots(D), DD = D * D;
+    const int D = s->D, S = stencil_slots(D), B = s->B, DD = B * B;
     std::vector<int> mask;
     if (D == 2) pattern_mask<2>(s, mask);
     else pattern_mask<3>(s, mask);
     std::vector<int> rows(s->nrow);
     ck(cudaMemcpy(rows.data(), s->d_rows, s->nrow * sizeof(int), cudaMemcpyDeviceToHost), "download");
+    std::vector<uint8_t> fx(s->ndof);
+    ck(cudaMemcpy(fx.data(), s->d_fixed, s->ndof, cudaMemcpyDeviceToHost), "download");
     const size_t nval = (size_t)s->cap * S * DD;
     std::vector<double> K(nval);
     if (s->mixed) {
@@ -1068,8 +1141,17 @@ mpm_status mpm_get_jacobian_bsr(const mpm_scene* cs, long long cap, int* row_nod
         if (nb >= cap) fail(MPM_ERR_INVALID_ARG, "capacity too small for the Jacobian");
         int dx = sl % 5 - 2, dy = (sl / 5) % 5 - 2, dz = D == 3 ? sl / 25 - 2 : 0;
         col_node[nb] = rows[r] + dx + nx1 * (dy + ny1 * dz);
-        for (int a = 0; a < D; ++a)
-          for (int b = 0; b < D; ++b) val[nb * DD + a * D + b] = K[((size_t)sl * s->cap + r) * DD + a * D + b];
+        // back to physical units: the pressure rows and columns carry psc
+        // (the identity entry of a prescribed pressure stays 1)
+        const bool centre = (dx == 0 && dy == 0 && dz == 0);
+        for (int a = 0; a < B; ++a)
+          for (int b = 0; b < B; ++b) {
+            double sc = 1.0;
+            const bool ident = centre && a == b && fx[(size_t)rows[r] * B + a];
+            if (s->up && a == D && !ident) sc /= s->psc;
+            if (s->up && b == D && !ident) sc /= s->psc;
+            val[nb * DD + a * B + b] = K[((size_t)sl * s->cap + r) * DD + a * B + b] * sc;
+          }
         ++nb;
       }
       row_ptr[r + 1] = nb;
@@ -1129,6 +1211,54 @@ mpm_status mpm_get_particles(const mpm_scene* cs, double* x, double* be, double*
       ck(cudaMemcpy(tau, d_tau, (size_t)np * 9 * sizeof(double), cudaMemcpyDeviceToHost), "download");
       s->dfree(d_tau);
     }
+  });
+}
+
+mpm_status mpm_get_pressure(const mpm_scene* cs, double* pp) {
+  mpm_scene* s = const_cast<mpm_scene*>(cs);
+  if (!s || !pp) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] {
+    if (!s->up) fail(MPM_ERR_INVALID_ARG, "not a u-p scene");
+    ck(cudaStreamSynchronize(s->st), "sync");
+    const int np = s->np;
+    if (np == 0) return;
+    std::vector<int> orig(np);
+    std::vector<double> h(np);
+    ck(cudaMemcpy(orig.data(), s->P.orig, np * sizeof(int), cudaMemcpyDeviceToHost), "download");
+    ck(cudaMemcpy(h.data(), s->P.pp, np * sizeof(double), cudaMemcpyDeviceToHost), "download");
+    for (int p = 0; p < np; ++p) pp[orig[p]] = h[p];
+  });
+}
+
+mpm_status mpm_set_traction(mpm_scene* s, int n, const int* particle, const double* f) {
+  if (!s) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] {
+    if (n < 0 || (n > 0 && (!particle || !f))) fail(MPM_ERR_INVALID_ARG, "traction arrays");
+    const int np = s->np, D = s->D;
+    for (int k = 0; k < n; ++k) {
+      if (particle[k] < 0 || particle[k] >= np) fail(MPM_ERR_INVALID_ARG, "traction particle out of range");
+      for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(f[3 * k + a])) fail(MPM_ERR_INVALID_ARG, "non-finite traction force");
+    }
+    ck(cudaStreamSynchronize(s->st), "sync");
+    if (!s->P.fext[0]) {
+      // allocated on first use, for both the live arrays and the sort target
+      for (int a = 0; a < D; ++a) {
+        s->P.fext[a] = s->dalloc<double>(np);
+        s->Q.fext[a] = s->dalloc<double>(np);
+      }
+    }
+    if (np == 0) return;
+    std::vector<int> orig(np), inv(np);
+    ck(cudaMemcpy(orig.data(), s->P.orig, np * sizeof(int), cudaMemcpyDeviceToHost), "download");
+    for (int p = 0; p < np; ++p) inv[orig[p]] = p;
+    std::vector<double> h((size_t)D * np, 0.0);
+    for (int k = 0; k < n; ++k)
+      for (int a = 0; a < D; ++a) h[(size_t)a * np + inv[particle[k]]] = f[3 * k + a];
+    for (int a = 0; a < D; ++a)
+      ck(cudaMemcpy(s->P.fext[a], h.data() + (size_t)a * np, np * sizeof(double), cudaMemcpyHostToDevice),
+         "upload");
+    s->staged = false;
   });
 }
 

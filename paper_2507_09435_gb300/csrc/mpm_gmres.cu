@@ -42,24 +42,12 @@ __device__ __forceinline__ void block_add_n(double* acc, int n, double* out) {
   }
 }
 
-template <int D, class T>
-__device__ __forceinline__ void precond(const DevMatrix<T>& K, int row, const T v[D], T z[D]) {
-  T m[D * D];
-  ld_block<D, T>(&K.dinv[(long long)row * (D * D)], m);
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    T s = (T)0;
-#pragma unroll
-    for (int b = 0; b < D; ++b) s += m[a * D + b] * v[b];
-    z[a] = s;
-  }
-}
 
-template <int D, class T>
+template <int D, class T, int B>
 __device__ __forceinline__ void spmv(const DevMatrix<T>& K, int row, long long i, int nx1, int ny1, const T* x,
-                                     T y[D]) {
+                                     T y[B]) {
 #pragma unroll
-  for (int a = 0; a < D; ++a) y[a] = (T)0;
+  for (int a = 0; a < B; ++a) y[a] = (T)0;
   constexpr int ZR = (D == 3) ? 2 : 0;
 #pragma unroll
   for (int dz = -ZR; dz <= ZR; ++dz)
@@ -69,13 +57,13 @@ __device__ __forceinline__ void spmv(const DevMatrix<T>& K, int row, long long i
       for (int dx = -2; dx <= 2; ++dx) {
         const int slot = (D == 2) ? (dx + 2) + 5 * (dy + 2) : (dx + 2) + 5 * ((dy + 2) + 5 * (dz + 2));
         const long long j = i + dx + (long long)nx1 * (dy + (long long)ny1 * dz);
-        T xj[D], kb[D * D];
-        ld_node<D, T, false>(x, j, xj);
-        ld_block<D, T>(&K.val[((long long)slot * K.cap + row) * (D * D)], kb);
+        T xj[B], kb[B * B];
+        ld_node<B, T, false>(x, j, xj);
+        ld_block<B, T>(&K.val[((long long)slot * K.cap + row) * (B * B)], kb);
 #pragma unroll
-        for (int a = 0; a < D; ++a)
+        for (int a = 0; a < B; ++a)
 #pragma unroll
-          for (int b = 0; b < D; ++b) y[a] += kb[a * D + b] * xj[b];
+          for (int b = 0; b < B; ++b) y[a] += kb[a * B + b] * xj[b];
       }
 }
 
@@ -90,7 +78,7 @@ __device__ __forceinline__ T* gvec(const GmresVecs<T>& g, int i) {
 
 // start of a cycle: v0 = r (r = b on the first cycle, b - J x on a restart;
 // x = 0 on the first cycle); accumulates ||r||^2 into st->wn2.
-template <int D, class T>
+template <int D, class T, int B>
 __global__ void __launch_bounds__(GTPB) k_gmres_residual(DevGrid G, DevMatrix<T> K, const double* __restrict__ res,
                                                          const uint8_t* __restrict__ fixed, GmresVecs<T> g, T* x,
                                                          GmresState* st, int first) {
@@ -98,17 +86,17 @@ __global__ void __launch_bounds__(GTPB) k_gmres_residual(DevGrid G, DevMatrix<T>
   double acc = 0.0;
   if (row < *K.nrow) {
     const long long i = K.rows[row];
-    T y[D];
+    T y[B];
     if (first) {
 #pragma unroll
-      for (int a = 0; a < D; ++a) y[a] = (T)0;
+      for (int a = 0; a < B; ++a) y[a] = (T)0;
     } else {
-      spmv<D, T>(K, row, i, G.nx1, G.ny1, x, y);
+      spmv<D, T, B>(K, row, i, G.nx1, G.ny1, x, y);
     }
     T* v0 = gvec(g, 0);
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const long long d = i * D + a;
+    for (int a = 0; a < B; ++a) {
+      const long long d = i * B + a;
       const T b = fixed[d] ? (T)0 : (T)(-res[d]);
       const T r = b - y[a];
       if (first) x[d] = (T)0;
@@ -120,24 +108,25 @@ __global__ void __launch_bounds__(GTPB) k_gmres_residual(DevGrid G, DevMatrix<T>
 }
 
 // v0 /= beta; z = M^-1 v0; g = beta e1; reset the cycle.
-template <int D, class T>
+template <int D, class T, int B>
 __global__ void __launch_bounds__(GTPB) k_gmres_start(DevMatrix<T> K, GmresVecs<T> g, GmresState* st) {
   const double beta = sqrt(st->wn2);
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   const bool zero = !(beta > st->tol);
+  const unsigned live = __ballot_sync(0xffffffffu, !zero && row < *K.nrow);
   if (!zero && row < *K.nrow) {
     const long long i = K.rows[row];
     T* v0 = gvec(g, 0);
-    T u[D], z[D];
+    T u[B], z[B];
     const T ib = (T)(1.0 / beta);
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      u[a] = v0[i * D + a] * ib;
-      v0[i * D + a] = u[a];
+    for (int a = 0; a < B; ++a) {
+      u[a] = v0[i * B + a] * ib;
+      v0[i * B + a] = u[a];
     }
-    precond<D, T>(K, row, u, z);
+    precond_apply<B, T>(K, row, u, z, live);
 #pragma unroll
-    for (int a = 0; a < D; ++a) g.z[i * D + a] = z[a];
+    for (int a = 0; a < B; ++a) g.z[i * B + a] = z[a];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int k = 0; k <= GMRES_MMAX; ++k) {
@@ -158,7 +147,7 @@ __global__ void __launch_bounds__(GTPB) k_gmres_start(DevMatrix<T> K, GmresVecs<
 }
 
 // S_j: w = J z ; h1_i = (v_i, w), i <= j
-template <int D, class T>
+template <int D, class T, int B>
 __global__ void __launch_bounds__(GTPB) k_gmres_spmv(DevGrid G, DevMatrix<T> K, GmresVecs<T> g, GmresState* st,
                                                      int j) {
   if (st->done) return;
@@ -168,15 +157,15 @@ __global__ void __launch_bounds__(GTPB) k_gmres_spmv(DevGrid G, DevMatrix<T> K, 
   if (blockIdx.x == 0 && threadIdx.x == 0) st->wn2b = 0.0;   // read last in the previous N kernel
   if (row < *K.nrow) {
     const long long i = K.rows[row];
-    T y[D];
-    spmv<D, T>(K, row, i, G.nx1, G.ny1, g.z, y);
+    T y[B];
+    spmv<D, T, B>(K, row, i, G.nx1, G.ny1, g.z, y);
 #pragma unroll
-    for (int a = 0; a < D; ++a) g.w[i * D + a] = y[a];
+    for (int a = 0; a < B; ++a) g.w[i * B + a] = y[a];
     for (int k = 0; k <= j; ++k) {
       const T* vk = gvec(g, k);
       double s = 0.0;
 #pragma unroll
-      for (int a = 0; a < D; ++a) s += (double)vk[i * D + a] * (double)y[a];
+      for (int a = 0; a < B; ++a) s += (double)vk[i * B + a] * (double)y[a];
       acc[k] = s;
     }
   }
@@ -184,7 +173,7 @@ __global__ void __launch_bounds__(GTPB) k_gmres_spmv(DevGrid G, DevMatrix<T> K, 
 }
 
 // O1_j: w -= sum h1_i v_i ; h2_i = (v_i, w)
-template <int D, class T>
+template <int D, class T, int B>
 __global__ void __launch_bounds__(GTPB) k_gmres_orth1(DevMatrix<T> K, GmresVecs<T> g, GmresState* st, int j) {
   if (st->done) return;
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
@@ -192,48 +181,48 @@ __global__ void __launch_bounds__(GTPB) k_gmres_orth1(DevMatrix<T> K, GmresVecs<
   for (int k = 0; k <= j; ++k) acc[k] = 0.0;
   if (row < *K.nrow) {
     const long long i = K.rows[row];
-    T w[D];
+    T w[B];
 #pragma unroll
-    for (int a = 0; a < D; ++a) w[a] = g.w[i * D + a];
+    for (int a = 0; a < B; ++a) w[a] = g.w[i * B + a];
     for (int k = 0; k <= j; ++k) {
       const T* vk = gvec(g, k);
       const T h = (T)st->h1[k];
 #pragma unroll
-      for (int a = 0; a < D; ++a) w[a] -= h * vk[i * D + a];
+      for (int a = 0; a < B; ++a) w[a] -= h * vk[i * B + a];
     }
     for (int k = 0; k <= j; ++k) {
       const T* vk = gvec(g, k);
       double s = 0.0;
 #pragma unroll
-      for (int a = 0; a < D; ++a) s += (double)vk[i * D + a] * (double)w[a];
+      for (int a = 0; a < B; ++a) s += (double)vk[i * B + a] * (double)w[a];
       acc[k] = s;
     }
 #pragma unroll
-    for (int a = 0; a < D; ++a) g.w[i * D + a] = w[a];
+    for (int a = 0; a < B; ++a) g.w[i * B + a] = w[a];
   }
   block_add_n(acc, j + 1, st->h2);
 }
 
 // O2_j: w -= sum h2_i v_i ; (w, w) ; H(:, j) = h1 + h2
-template <int D, class T>
+template <int D, class T, int B>
 __global__ void __launch_bounds__(GTPB) k_gmres_orth2(DevMatrix<T> K, GmresVecs<T> g, GmresState* st, int j) {
   if (st->done) return;
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   double acc = 0.0;
   if (row < *K.nrow) {
     const long long i = K.rows[row];
-    T w[D];
+    T w[B];
 #pragma unroll
-    for (int a = 0; a < D; ++a) w[a] = g.w[i * D + a];
+    for (int a = 0; a < B; ++a) w[a] = g.w[i * B + a];
     for (int k = 0; k <= j; ++k) {
       const T* vk = gvec(g, k);
       const T h = (T)st->h2[k];
 #pragma unroll
-      for (int a = 0; a < D; ++a) w[a] -= h * vk[i * D + a];
+      for (int a = 0; a < B; ++a) w[a] -= h * vk[i * B + a];
     }
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      g.w[i * D + a] = w[a];
+    for (int a = 0; a < B; ++a) {
+      g.w[i * B + a] = w[a];
       acc += (double)w[a] * (double)w[a];
     }
   }
@@ -243,25 +232,26 @@ __global__ void __launch_bounds__(GTPB) k_gmres_orth2(DevMatrix<T> K, GmresVecs<
 }
 
 // N_j: H(j+1,j) = ||w|| ; v_{j+1} = w/||w|| ; z = M^-1 v_{j+1} ; Givens.
-template <int D, class T>
+template <int D, class T, int B>
 __global__ void __launch_bounds__(GTPB) k_gmres_norm(DevMatrix<T> K, GmresVecs<T> g, GmresState* st, int j, int m) {
   if (st->done) return;
   const double hn = sqrt(st->wn2b);
   const bool lucky = !(hn > 1e-300);
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned live = __ballot_sync(0xffffffffu, !lucky && j + 1 <= m && row < *K.nrow);
   if (!lucky && j + 1 <= m && row < *K.nrow) {
     const long long i = K.rows[row];
     T* vn = gvec(g, j + 1);
-    T u[D], z[D];
+    T u[B], z[B];
     const T ih = (T)(1.0 / hn);
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      u[a] = g.w[i * D + a] * ih;
-      vn[i * D + a] = u[a];
+    for (int a = 0; a < B; ++a) {
+      u[a] = g.w[i * B + a] * ih;
+      vn[i * B + a] = u[a];
     }
-    precond<D, T>(K, row, u, z);
+    precond_apply<B, T>(K, row, u, z, live);
 #pragma unroll
-    for (int a = 0; a < D; ++a) g.z[i * D + a] = z[a];
+    for (int a = 0; a < B; ++a) g.z[i * B + a] = z[a];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     double* Hj = st->H + (GMRES_MMAX + 1) * j;
@@ -319,27 +309,28 @@ __global__ void k_gmres_solve(GmresState* st) {
   }
 }
 
-template <int D, class T>
+template <int D, class T, int B>
 __global__ void __launch_bounds__(GTPB) k_gmres_update(DevMatrix<T> K, GmresVecs<T> g, GmresState* st, T* x) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned live = __ballot_sync(0xffffffffu, row < *K.nrow);
   if (row >= *K.nrow) return;
   const int k = st->jdone;
   const long long i = K.rows[row];
-  T u[D], z[D];
+  T u[B], z[B];
 #pragma unroll
-  for (int a = 0; a < D; ++a) u[a] = (T)0;
+  for (int a = 0; a < B; ++a) u[a] = (T)0;
   for (int c = 0; c < k; ++c) {
     const T* vc = gvec(g, c);
     const T yc = (T)st->y[c];
 #pragma unroll
-    for (int a = 0; a < D; ++a) u[a] += yc * vc[i * D + a];
+    for (int a = 0; a < B; ++a) u[a] += yc * vc[i * B + a];
   }
-  precond<D, T>(K, row, u, z);
+  precond_apply<B, T>(K, row, u, z, live);
 #pragma unroll
-  for (int a = 0; a < D; ++a) x[i * D + a] += z[a];
+  for (int a = 0; a < B; ++a) x[i * B + a] += z[a];
 }
 
-template <int D, class T>
+template <int D, class T, int B>
 cudaError_t launch_gmres_begin(const DevGrid& G, DevMatrix<T> K, const double* res, const uint8_t* fixed,
                                GmresVecs<T> g, T* x, GmresState* st, int first, double tol, int maxit_left,
                                int nblk, cudaStream_t s) {
@@ -355,34 +346,36 @@ cudaError_t launch_gmres_begin(const DevGrid& G, DevMatrix<T> K, const double* r
   e = cudaMemsetAsync(&st->finished, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   k_gmres_set<<<1, 1, 0, s>>>(st, tol, maxit_left);
-  k_gmres_residual<D, T><<<nblk, GTPB, 0, s>>>(G, K, res, fixed, g, x, st, first);
-  k_gmres_start<D, T><<<nblk, GTPB, 0, s>>>(K, g, st);
+  k_gmres_residual<D, T, B><<<nblk, GTPB, 0, s>>>(G, K, res, fixed, g, x, st, first);
+  k_gmres_start<D, T, B><<<nblk, GTPB, 0, s>>>(K, g, st);
   return cudaGetLastError();
 }
 
-template <int D, class T>
+template <int D, class T, int B>
 cudaError_t launch_gmres_cycle(const DevGrid& G, DevMatrix<T> K, GmresVecs<T> g, T* x, GmresState* st, int m,
                                int nblk, cudaStream_t s) {
   for (int j = 0; j < m; ++j) {
-    k_gmres_spmv<D, T><<<nblk, GTPB, 0, s>>>(G, K, g, st, j);
-    k_gmres_orth1<D, T><<<nblk, GTPB, 0, s>>>(K, g, st, j);
-    k_gmres_orth2<D, T><<<nblk, GTPB, 0, s>>>(K, g, st, j);
-    k_gmres_norm<D, T><<<nblk, GTPB, 0, s>>>(K, g, st, j, m);
+    k_gmres_spmv<D, T, B><<<nblk, GTPB, 0, s>>>(G, K, g, st, j);
+    k_gmres_orth1<D, T, B><<<nblk, GTPB, 0, s>>>(K, g, st, j);
+    k_gmres_orth2<D, T, B><<<nblk, GTPB, 0, s>>>(K, g, st, j);
+    k_gmres_norm<D, T, B><<<nblk, GTPB, 0, s>>>(K, g, st, j, m);
   }
   k_gmres_solve<<<1, 32, 0, s>>>(st);
-  k_gmres_update<D, T><<<nblk, GTPB, 0, s>>>(K, g, st, x);
+  k_gmres_update<D, T, B><<<nblk, GTPB, 0, s>>>(K, g, st, x);
   return cudaGetLastError();
 }
 
-#define MPM_GMRES_INST(D, T)                                                                            \
-  template cudaError_t launch_gmres_begin<D, T>(const DevGrid&, DevMatrix<T>, const double*, const uint8_t*, \
+#define MPM_GMRES_INST(D, T, B)                                                                            \
+  template cudaError_t launch_gmres_begin<D, T, B>(const DevGrid&, DevMatrix<T>, const double*, const uint8_t*, \
                                                 GmresVecs<T>, T*, GmresState*, int, double, int, int,   \
                                                 cudaStream_t);                                          \
-  template cudaError_t launch_gmres_cycle<D, T>(const DevGrid&, DevMatrix<T>, GmresVecs<T>, T*, GmresState*, \
+  template cudaError_t launch_gmres_cycle<D, T, B>(const DevGrid&, DevMatrix<T>, GmresVecs<T>, T*, GmresState*, \
                                                 int, int, cudaStream_t);
-MPM_GMRES_INST(2, float)
-MPM_GMRES_INST(2, double)
-MPM_GMRES_INST(3, float)
-MPM_GMRES_INST(3, double)
+MPM_GMRES_INST(2, float, 2)
+MPM_GMRES_INST(2, double, 2)
+MPM_GMRES_INST(3, float, 3)
+MPM_GMRES_INST(3, double, 3)
+MPM_GMRES_INST(2, float, 3)
+MPM_GMRES_INST(2, double, 3)
 
 }  // namespace mpm

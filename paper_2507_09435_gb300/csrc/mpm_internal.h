@@ -23,6 +23,9 @@ struct DevParticles {
   double* pc;
   double* F[MAX_F];  // dim*dim row-major
   int* orig;         // caller's index of each sorted particle
+  double* kdt;       // u-p: mobility times time step (null for the solid formulation)
+  double* pp;        // u-p: pore pressure at the particle after the last commit
+  double* fext[3];   // external force carried by the particle (null: none)
   // first constitutive failure of a pass: [claimed, caller index, trial b
   // eigenvalues (3), E, phi, pc, model, return-map mode]
   double* fail_rec;
@@ -40,14 +43,18 @@ struct DevGrid {
 
 // Stencil-BSR Jacobian: for every active node (row) the 5^dim neighbour
 // blocks at fixed slots, one plane per slot, blocks contiguous within a plane:
-// val[(slot*cap + row)*D*D + a*D + b] (a 2x2 FP32 block is one 16-byte load).
+// val[(slot*cap + row)*B*B + a*B + b] with B values per node (a 2x2 FP32
+// block is one 16-byte load).
 template <class T>
 struct DevMatrix {
   T* val;
-  T* dinv;          // block-Jacobi inverse, dinv[row*D*D + a*D + b]
+  T* dinv;          // block-Jacobi inverse: seg == 1: dinv[row*B*B + a*B + b], the
+                    // node's diagonal block; seg == 4: dinv[(s*4B + i)*4B + j], the
+                    // inverse of the 4B x 4B diagonal block of rows 4s..4s+3
   int cap;          // row capacity (row stride of the SoA planes)
   const int* rows;  // node index of each row
   const int* nrow;  // device scalar: active row count
+  int seg;          // rows per preconditioner block: 1 (node) or 4 (row segment)
 };
 
 // One D x D block of the matrix (contiguous), through the read-only path:
@@ -84,6 +91,44 @@ __device__ __forceinline__ void ld_node(const T* x, long long j, T v[D]) {
   } else {
 #pragma unroll
     for (int b = 0; b < D; ++b) v[b] = WEAK ? x[j * D + b] : __ldg(x + j * D + b);
+  }
+}
+
+// z = M^-1 v for one row, M the block-Jacobi preconditioner.  With row
+// segments (K.seg == 4) the four rows of a segment sit on four consecutive
+// lanes of one warp (one thread per row, blockDim a multiple of 32, rows
+// aligned to 4), which exchange their values by shuffles.  `live` is the
+// ballot of the lanes that call this (exactly the lanes executing it).
+template <int B, class T>
+__device__ __forceinline__ void precond_apply(const DevMatrix<T>& K, int row, const T v[B], T z[B],
+                                              unsigned live) {
+  if (K.seg <= 1) {
+    T m[B * B];
+    ld_block<B, T>(&K.dinv[(long long)row * (B * B)], m);
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+      T s = (T)0;
+#pragma unroll
+      for (int b = 0; b < B; ++b) s += m[a * B + b] * v[b];
+      z[a] = s;
+    }
+    return;
+  }
+  constexpr int W = 4 * B;
+  const int lane = threadIdx.x & 31, base = lane & ~3, r = lane & 3;
+  const T* M = K.dinv + ((long long)(row >> 2) * W + r * B) * W;
+#pragma unroll
+  for (int a = 0; a < B; ++a) z[a] = (T)0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const bool src = (live >> (base + q)) & 1u;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const T t = __shfl_sync(live, v[b], base + q);
+      const T vb = src ? t : (T)0;
+#pragma unroll
+      for (int a = 0; a < B; ++a) z[a] += __ldg(M + a * W + q * B + b) * vb;
+    }
   }
 }
 
@@ -129,18 +174,25 @@ template <int D, class T>
 cudaError_t launch_particles(const DevParticles& P, const DevGrid& G, const MatC* mats, const double* du,
                              double* r, const double* grav, T* A, int mode, int* err, int* nplastic,
                              cudaStream_t st);
+// u-p particle pass (B = D + 1 values per node, the last the scaled pore
+// pressure p / psc; the mass-balance rows of r are scaled by psc, and so are
+// the pressure rows and columns of the tangent)
+template <int D, class T>
+cudaError_t launch_particles_up(const DevParticles& P, const DevGrid& G, const MatC* mats, const double* U,
+                                double* r, const double* grav, T* A, int mode, double psc, int* err,
+                                int* nplastic, cudaStream_t st);
 template <int D>
 cudaError_t launch_stress_out(const DevParticles& P, const DevGrid& G, const MatC* mats, double* tau9,
                               cudaStream_t st);
 
-template <int D, class T>
+template <int D, class T, int B = D>
 cudaError_t launch_assemble(const DevParticles& P, const DevGrid& G, const int* cstart, const int* node2row,
                             const T* A, DevMatrix<T> K, cudaStream_t st);
-template <int D, class T>
+template <int D, class T, int B = D>
 cudaError_t launch_bc_matrix(const DevGrid& G, DevMatrix<T> K, const uint8_t* fixed, const int* node2row,
                              int nrow_host, cudaStream_t st);
-template <int D, class T>
-cudaError_t launch_block_jacobi(DevMatrix<T> K, int nrow_host, int* err, cudaStream_t st);
+template <int D, class T, int B = D>
+cudaError_t launch_block_jacobi(const DevGrid& G, DevMatrix<T> K, int nrow_host, int* err, cudaStream_t st);
 template <int D>
 cudaError_t launch_pattern_count(const DevGrid& G, const int* rows, int nrow_host, const int* node2row,
                                  const int* count, int* mask, cudaStream_t st);
@@ -155,25 +207,25 @@ template <int D, class T>
 struct KrylovVecs {
   T *x, *r, *rhat, *p, *phat, *v, *s, *shat, *t;
 };
-template <int D, class T>
+template <int D, class T, int B = D>
 cudaError_t launch_bicgstab_init(DevMatrix<T> K, const double* res, const uint8_t* fixed, KrylovVecs<D, T> v,
                                  KrylovScalars* S, double tol2, int maxit, int nblk, cudaStream_t st);
-template <int D, class T>
+template <int D, class T, int B = D>
 cudaError_t launch_bicgstab_iter(const DevGrid& G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S,
                                  int nblk, cudaStream_t st);
-template <int D, class T>
+template <int D, class T, int B = D>
 cudaError_t launch_bicgstab_restart(const DevGrid& G, DevMatrix<T> K, const double* res, const uint8_t* fixed,
                                     KrylovVecs<D, T> v, KrylovScalars* S, double tol2, int maxit, int nblk,
                                     cudaStream_t st);
-template <int D, class T>
+template <int D, class T, int B = D>
 cudaError_t launch_update_du(DevMatrix<T> K, const T* x, const uint8_t* fixed, double* du, int nblk,
                              cudaStream_t st);
-template <int D, class T>
+template <int D, class T, int B = D>
 cudaError_t launch_spmv(const DevGrid& G, DevMatrix<T> K, const T* x, T* y, int nblk, cudaStream_t st);
-template <int D, class T>
+template <int D, class T, int B = D>
 cudaError_t launch_step_du(DevMatrix<T> K, const T* x, const uint8_t* fixed, const double* base, double* du,
                            double alpha, int nblk, cudaStream_t st);
-template <int D, class T>
+template <int D, class T, int B = D>
 cudaError_t launch_absmax(DevMatrix<T> K, const T* x, const uint8_t* fixed, unsigned long long* out, int nblk,
                           cudaStream_t st);
 // kernels launched by one scan_exclusive call of n elements
@@ -203,11 +255,11 @@ struct GmresVecs {
   T* w;              // Arnoldi work vector
   T* z;              // preconditioned basis vector
 };
-template <int D, class T>
+template <int D, class T, int B = D>
 cudaError_t launch_gmres_begin(const DevGrid& G, DevMatrix<T> K, const double* res, const uint8_t* fixed,
                                GmresVecs<T> g, T* x, GmresState* st, int first, double tol, int maxit,
                                int nblk, cudaStream_t s);
-template <int D, class T>
+template <int D, class T, int B = D>
 cudaError_t launch_gmres_cycle(const DevGrid& G, DevMatrix<T> K, GmresVecs<T> g, T* x, GmresState* st, int m,
                                int nblk, cudaStream_t s);
 

@@ -367,7 +367,10 @@ __global__ void __launch_bounds__(128) k_particles(DevParticles P, DevGrid G, co
           }
       } else {
         const double m = P.mass[p];
-        double gv[3] = {grav[0], grav[1], grav[2]};
+        // body force per particle: gravity plus any carried external force
+        double gv[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) gv[a] = m * grav[a] + (P.fext[a] ? P.fext[a][p] : 0.0);
         bool finite = true;
         for (int kz = 0; kz < KZ; ++kz)
 #pragma unroll
@@ -382,7 +385,7 @@ __global__ void __launch_bounds__(128) k_particles(DevParticles P, DevGrid G, co
               g[2] = sp[0].N[kx] * sp[1].N[ky] * sp[2].dN[kz] * G.ih;
 #pragma unroll
               for (int a = 0; a < D; ++a) {
-                double f = -w * m * gv[a];
+                double f = -w * gv[a];
 #pragma unroll
                 for (int c = 0; c < D; ++c) f += st.P[a][c] * g[c];
                 finite = finite && isfinite(f);
@@ -458,22 +461,29 @@ __device__ __forceinline__ int slot_of(int dx, int dy, int dz) {
   return (D == 2) ? (dx + 2) + 5 * (dy + 2) : (dx + 2) + 5 * ((dy + 2) + 5 * (dz + 2));
 }
 
-template <int D, class T>
+// Tile and chunk sizes per (dim, precision, values per node).
+template <int D, class T, int B>
 struct AsmCfg;
-template <> struct AsmCfg<2, float>  { static constexpr int TX = 16, TY = 8, TZ = 1, CHP = 64; };
-template <> struct AsmCfg<2, double> { static constexpr int TX = 8,  TY = 8, TZ = 1, CHP = 64; };
-template <> struct AsmCfg<3, float>  { static constexpr int TX = 4,  TY = 2, TZ = 2, CHP = 32; };
-template <> struct AsmCfg<3, double> { static constexpr int TX = 2,  TY = 2, TZ = 2, CHP = 16; };
+template <> struct AsmCfg<2, float, 2>  { static constexpr int TX = 16, TY = 8, TZ = 1, CHP = 64; };
+template <> struct AsmCfg<2, double, 2> { static constexpr int TX = 8,  TY = 8, TZ = 1, CHP = 64; };
+template <> struct AsmCfg<3, float, 3>  { static constexpr int TX = 4,  TY = 2, TZ = 2, CHP = 32; };
+template <> struct AsmCfg<3, double, 3> { static constexpr int TX = 2,  TY = 2, TZ = 2, CHP = 16; };
+template <> struct AsmCfg<2, float, 3>  { static constexpr int TX = 8,  TY = 8, TZ = 1, CHP = 64; };
+template <> struct AsmCfg<2, double, 3> { static constexpr int TX = 8,  TY = 4, TZ = 1, CHP = 32; };
 constexpr int ASM_TPB = 256;
 constexpr int ASM_UB = 8;   // particles per U batch of a 3D task
 
-template <int D, class T>
+// Shared-memory layout of one assembly CTA.  A particle's tangent has
+// (B * NPHI)^2 entries A[a][c][b][e] (a, b < B values per node; c, e < NPHI
+// shape-function components: the D gradient entries, and for u-p the weight).
+template <int D, class T, int B>
 struct AsmSmem {
-  static constexpr int TX = AsmCfg<D, T>::TX, TY = AsmCfg<D, T>::TY, TZ = AsmCfg<D, T>::TZ;
-  static constexpr int CHP = AsmCfg<D, T>::CHP;
+  static constexpr int TX = AsmCfg<D, T, B>::TX, TY = AsmCfg<D, T, B>::TY, TZ = AsmCfg<D, T, B>::TZ;
+  static constexpr int CHP = AsmCfg<D, T, B>::CHP;
   static constexpr int NN = (D == 2) ? 9 : 27, S = (D == 2) ? 25 : 125;
-  static constexpr int D2 = D * D, D4 = D2 * D2, NT = TX * TY * TZ;
-  static constexpr int AST = D4 + (D == 2 ? 0 : 0);   // row stride of the staged tangents
+  static constexpr int NPHI = (B > D) ? D + 1 : D;
+  static constexpr int D2 = B * B, D4 = B * NPHI * B * NPHI, NT = TX * TY * TZ;
+  static constexpr int AST = (D == 2) ? (D4 + 3) / 4 * 4 : D4;   // row stride of the staged tangents
   // byte offsets (all multiples of 16)
   static constexpr size_t acc = 0;
   static constexpr size_t sA = acc + sizeof(T) * NT * S * D2;
@@ -496,13 +506,14 @@ __device__ __forceinline__ void lds4(const T* p, T v[4]) {
   }
 }
 
-template <int D, class T>
+template <int D, class T, int B>
 __global__ void __launch_bounds__(ASM_TPB) k_assemble(DevParticles P, DevGrid G, const int* __restrict__ cstart,
                                                       const int* __restrict__ node2row, const T* __restrict__ A,
                                                       DevMatrix<T> K, int ntx, int nty) {
-  using L = AsmSmem<D, T>;
+  using L = AsmSmem<D, T, B>;
   constexpr int TX = L::TX, TY = L::TY, TZ = L::TZ, CHP = L::CHP, NN = L::NN, S = L::S;
-  constexpr int D2 = L::D2, D4 = L::D4, NT = L::NT, AST = L::AST;
+  constexpr int D2 = L::D2, D4 = L::D4, NT = L::NT, AST = L::AST, NPHI = L::NPHI;
+  static_assert(D == 2 || B == D, "3D assembly is written for the single-phase blocks");
   extern __shared__ __align__(16) unsigned char smem[];
   T* acc = reinterpret_cast<T*>(smem + L::acc);    // [NT][S][D2]
   T* sA = reinterpret_cast<T*>(smem + L::sA);      // [CHP][AST]
@@ -583,8 +594,9 @@ __global__ void __launch_bounds__(ASM_TPB) k_assemble(DevParticles P, DevGrid G,
           T* g = sG + (q * NN + l) * 4;
           g[0] = wx[3 + kx] * wy[ky] * wz[kz] * ih;
           g[1] = wx[kx] * wy[3 + ky] * wz[kz] * ih;
-          g[2] = (D == 3) ? wx[kx] * wy[ky] * wz[3 + kz] * ih : (T)0;
-          g[3] = (T)0;
+          // gradient entries, then (u-p) the weight in entry D
+          g[2] = (D == 3) ? wx[kx] * wy[ky] * wz[3 + kz] * ih : ((NPHI > D) ? wx[kx] * wy[ky] : (T)0);
+          g[3] = (D == 3 && NPHI > D) ? wx[kx] * wy[ky] * wz[kz] : (T)0;
         }
         __syncthreads();
         // tasks: (tile node i with y/z overlap, x offset kx of i in the cell)
@@ -657,39 +669,41 @@ __global__ void __launch_bounds__(ASM_TPB) k_assemble(DevParticles P, DevGrid G,
           } else {
             // lane = j + 9 * sub: node j of the cell, particles sub, sub+3, ...
             const int j = lane % 9, sub = lane / 9;
-            T k4[4] = {(T)0, (T)0, (T)0, (T)0};
+            T kb[D2];
+#pragma unroll
+            for (int e = 0; e < D2; ++e) kb[e] = (T)0;
             if (lane < 27) {
               for (int q = qa + sub; q < qb; q += 3) {
-                T gi[4], gj[4], a16[16];
+                T gi[4], gj[4], aq[AST];
                 lds4(sG + (q * NN + il) * 4, gi);
                 lds4(sG + (q * NN + j) * 4, gj);
 #pragma unroll
-                for (int v = 0; v < 4; ++v) lds4(sA + q * AST + 4 * v, a16 + 4 * v);
+                for (int v = 0; v < AST / 4; ++v) lds4(sA + q * AST + 4 * v, aq + 4 * v);
 #pragma unroll
-                for (int a = 0; a < 2; ++a)
+                for (int a = 0; a < B; ++a)
 #pragma unroll
-                  for (int b = 0; b < 2; ++b) {
+                  for (int b = 0; b < B; ++b) {
                     T s = (T)0;
 #pragma unroll
-                    for (int c = 0; c < 2; ++c)
+                    for (int c = 0; c < NPHI; ++c)
 #pragma unroll
-                      for (int e = 0; e < 2; ++e) s += gi[c] * a16[((a * 2 + c) * 2 + b) * 2 + e] * gj[e];
-                    k4[a * 2 + b] += s;
+                      for (int e = 0; e < NPHI; ++e) s += gi[c] * aq[((a * NPHI + c) * B + b) * NPHI + e] * gj[e];
+                    kb[a * B + b] += s;
                   }
               }
             }
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
+            for (int e = 0; e < D2; ++e) {
               // lanes j, j + 9, j + 18 hold the three particle subsets of node j
-              const T v9 = __shfl_sync(0xffffffffu, k4[e], (lane + 9) & 31);
-              const T v18 = __shfl_sync(0xffffffffu, k4[e], (lane + 18) & 31);
-              k4[e] += v9 + v18;
+              const T v9 = __shfl_sync(0xffffffffu, kb[e], (lane + 9) & 31);
+              const T v18 = __shfl_sync(0xffffffffu, kb[e], (lane + 18) & 31);
+              kb[e] += v9 + v18;
             }
             if (lane < 9) {
               const int jx = j % 3, jy = j / 3;
               T* blk = arow + slot_of<2>(jx - kx, jy - ky, 0) * D2;
 #pragma unroll
-              for (int e = 0; e < 4; ++e) atomicAdd(blk + e, k4[e]);
+              for (int e = 0; e < D2; ++e) atomicAdd(blk + e, kb[e]);
             }
           }
         }
@@ -705,25 +719,25 @@ __global__ void __launch_bounds__(ASM_TPB) k_assemble(DevParticles P, DevGrid G,
   }
 }
 
-template <int D, class T>
+template <int D, class T, int B>
 cudaError_t launch_assemble(const DevParticles& P, const DevGrid& G, const int* cstart, const int* node2row,
                             const T* A, DevMatrix<T> K, cudaStream_t st) {
-  using L = AsmSmem<D, T>;
+  using L = AsmSmem<D, T, B>;
   if (P.np == 0) return cudaSuccess;
   static_assert(L::bytes <= 227 * 1024, "assembly tile exceeds shared memory");
-  cudaError_t e = cudaFuncSetAttribute(k_assemble<D, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_assemble<D, T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)L::bytes);
   if (e != cudaSuccess) return e;
   const int ntx = (G.nx1 + L::TX - 1) / L::TX, nty = (G.ny1 + L::TY - 1) / L::TY;
   const int ntz = (G.nz1 + L::TZ - 1) / L::TZ;
   const long long nt = (long long)ntx * nty * ntz;
   if (nt > 0x7fffffffLL) return cudaErrorInvalidValue;
-  k_assemble<D, T><<<(unsigned)nt, ASM_TPB, L::bytes, st>>>(P, G, cstart, node2row, A, K, ntx, nty);
+  k_assemble<D, T, B><<<(unsigned)nt, ASM_TPB, L::bytes, st>>>(P, G, cstart, node2row, A, K, ntx, nty);
   return cudaGetLastError();
 }
 
 // Prescribed DOFs: their rows and columns become the identity.
-template <int D, class T>
+template <int D, class T, int B>
 __global__ void k_bc_matrix(DevGrid G, DevMatrix<T> K, const uint8_t* __restrict__ fixed,
                             const int* __restrict__ node2row, int nrow) {
   constexpr int S = (D == 2) ? 25 : 125;
@@ -738,38 +752,39 @@ __global__ void k_bc_matrix(DevGrid G, DevMatrix<T> K, const uint8_t* __restrict
   long long j = jx + (long long)G.nx1 * (jy + (long long)G.ny1 * jz);
   const bool center = (dx == 0 && dy == 0 && dz == 0);
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    bool fa = fixed[(long long)i * D + a];
+  for (int a = 0; a < B; ++a) {
+    bool fa = fixed[(long long)i * B + a];
 #pragma unroll
-    for (int b = 0; b < D; ++b) {
-      bool fb = fixed[j * D + b];
+    for (int b = 0; b < B; ++b) {
+      bool fb = fixed[j * B + b];
       if (fa || fb) {
         T v = (center && a == b && fa) ? (T)1 : (T)0;
-        K.val[((long long)slot * K.cap + row) * (D * D) + a * D + b] = v;
+        K.val[((long long)slot * K.cap + row) * (B * B) + a * B + b] = v;
       }
     }
   }
 }
-template <int D, class T>
+template <int D, class T, int B>
 cudaError_t launch_bc_matrix(const DevGrid& G, DevMatrix<T> K, const uint8_t* fixed, const int* node2row,
                              int nrow_host, cudaStream_t st) {
   constexpr int S = (D == 2) ? 25 : 125;
   if (nrow_host == 0) return cudaSuccess;
-  k_bc_matrix<D, T><<<nblocks((long long)nrow_host * S), TPB, 0, st>>>(G, K, fixed, node2row, nrow_host);
+  k_bc_matrix<D, T, B><<<nblocks((long long)nrow_host * S), TPB, 0, st>>>(G, K, fixed, node2row, nrow_host);
   return cudaGetLastError();
 }
 
-// Block-Jacobi: inverse of each row's diagonal D x D block (computed in FP64).
-template <int D, class T>
+// Block-Jacobi: inverse of each row's diagonal B x B block (computed in FP64).
+template <int D, class T, int B>
 __global__ void k_block_jacobi(DevMatrix<T> K, int nrow, int* err) {
+  static_assert(B <= 3, "block inverse written for B <= 3");
   constexpr int C = (D == 2) ? 12 : 62;   // centre slot
   int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= nrow) return;
   double a[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
 #pragma unroll
-  for (int i = 0; i < D; ++i)
+  for (int i = 0; i < B; ++i)
 #pragma unroll
-    for (int j = 0; j < D; ++j) a[i][j] = (double)K.val[((long long)C * K.cap + row) * (D * D) + i * D + j];
+    for (int j = 0; j < B; ++j) a[i][j] = (double)K.val[((long long)C * K.cap + row) * (B * B) + i * B + j];
   double inv[3][3], det;
   if (!inv3(a, inv, det)) {
     atomicOr(err, ERRF_NONFINITE);
@@ -777,14 +792,77 @@ __global__ void k_block_jacobi(DevMatrix<T> K, int nrow, int* err) {
       for (int j = 0; j < 3; ++j) inv[i][j] = (i == j) ? 1.0 : 0.0;
   }
 #pragma unroll
-  for (int i = 0; i < D; ++i)
+  for (int i = 0; i < B; ++i)
 #pragma unroll
-    for (int j = 0; j < D; ++j) K.dinv[(long long)row * (D * D) + i * D + j] = (T)inv[i][j];
+    for (int j = 0; j < B; ++j) K.dinv[(long long)row * (B * B) + i * B + j] = (T)inv[i][j];
 }
-template <int D, class T>
-cudaError_t launch_block_jacobi(DevMatrix<T> K, int nrow_host, int* err, cudaStream_t st) {
+// Row-segment block-Jacobi: the inverse of the 4B x 4B diagonal block of the
+// rows 4s..4s+3 (consecutive active nodes, mostly neighbours along x), by
+// Gauss-Jordan elimination with partial pivoting in FP64.  Rows past the last
+// active row are identity.  One thread per segment.
+template <int D, class T, int B>
+__global__ void k_segment_inverse(DevGrid G, DevMatrix<T> K, int nrow, int* err) {
+  constexpr int W = 4 * B;
+  const int sg = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sg * 4 >= nrow) return;
+  double a[W][2 * W];
+#pragma unroll
+  for (int i = 0; i < W; ++i)
+#pragma unroll
+    for (int j = 0; j < 2 * W; ++j) a[i][j] = (j == W + i) ? 1.0 : 0.0;
+  for (int ra = 0; ra < 4; ++ra) {
+    const int row_a = sg * 4 + ra;
+    if (row_a >= nrow) {
+      for (int e = 0; e < B; ++e) a[ra * B + e][ra * B + e] = 1.0;
+      continue;
+    }
+    const int na = K.rows[row_a];
+    const int ax = na % G.nx1, ay = (na / G.nx1) % G.ny1, az = na / (G.nx1 * G.ny1);
+    for (int rb = 0; rb < 4; ++rb) {
+      const int row_b = sg * 4 + rb;
+      if (row_b >= nrow) continue;
+      const int nb = K.rows[row_b];
+      const int dx = nb % G.nx1 - ax, dy = (nb / G.nx1) % G.ny1 - ay, dz = nb / (G.nx1 * G.ny1) - az;
+      if (dx < -2 || dx > 2 || dy < -2 || dy > 2 || dz < -2 || dz > 2 || (D == 2 && dz != 0)) continue;
+      const int slot = (D == 2) ? (dx + 2) + 5 * (dy + 2) : (dx + 2) + 5 * ((dy + 2) + 5 * (dz + 2));
+      const T* blk = &K.val[((long long)slot * K.cap + row_a) * (B * B)];
+      for (int e = 0; e < B; ++e)
+        for (int f = 0; f < B; ++f) a[ra * B + e][rb * B + f] = (double)blk[e * B + f];
+    }
+  }
+  bool ok = true;
+  for (int c = 0; c < W; ++c) {
+    int piv = c;
+    double best = fabs(a[c][c]);
+    for (int r = c + 1; r < W; ++r)
+      if (fabs(a[r][c]) > best) { best = fabs(a[r][c]); piv = r; }
+    if (!(best > 0.0) || !isfinite(best)) { ok = false; break; }
+    if (piv != c)
+      for (int j = 0; j < 2 * W; ++j) { const double t = a[c][j]; a[c][j] = a[piv][j]; a[piv][j] = t; }
+    const double inv = 1.0 / a[c][c];
+    for (int j = 0; j < 2 * W; ++j) a[c][j] *= inv;
+    for (int r = 0; r < W; ++r) {
+      if (r == c) continue;
+      const double f = a[r][c];
+      if (f != 0.0)
+        for (int j = 0; j < 2 * W; ++j) a[r][j] -= f * a[c][j];
+    }
+  }
+  T* M = K.dinv + (long long)sg * W * W;
+  if (!ok) atomicOr(err, ERRF_NONFINITE);
+  for (int i = 0; i < W; ++i)
+    for (int j = 0; j < W; ++j) M[i * W + j] = ok ? (T)a[i][W + j] : (T)(i == j ? 1.0 : 0.0);
+}
+
+template <int D, class T, int B>
+cudaError_t launch_block_jacobi(const DevGrid& G, DevMatrix<T> K, int nrow_host, int* err, cudaStream_t st) {
   if (nrow_host == 0) return cudaSuccess;
-  k_block_jacobi<D, T><<<nblocks(nrow_host), TPB, 0, st>>>(K, nrow_host, err);
+  if (K.seg == 4) {
+    const int nseg = (nrow_host + 3) / 4;
+    k_segment_inverse<D, T, B><<<nblocks(nseg, 128), 128, 0, st>>>(G, K, nrow_host, err);
+    return cudaGetLastError();
+  }
+  k_block_jacobi<D, T, B><<<nblocks(nrow_host), TPB, 0, st>>>(K, nrow_host, err);
   return cudaGetLastError();
 }
 
@@ -880,15 +958,23 @@ MPM_INST_D(3)
 #define MPM_INST_DT(D, T)                                                                               \
   template cudaError_t launch_particles<D, T>(const DevParticles&, const DevGrid&, const MatC*,          \
                                               const double*, double*, const double*, T*, int, int*,      \
-                                              int*, cudaStream_t);                                       \
-  template cudaError_t launch_assemble<D, T>(const DevParticles&, const DevGrid&, const int*, const int*,  \
-                                             const T*, DevMatrix<T>, cudaStream_t);                                              \
-  template cudaError_t launch_bc_matrix<D, T>(const DevGrid&, DevMatrix<T>, const uint8_t*, const int*,  \
-                                              int, cudaStream_t);                                        \
-  template cudaError_t launch_block_jacobi<D, T>(DevMatrix<T>, int, int*, cudaStream_t);
+                                              int*, cudaStream_t);
 MPM_INST_DT(2, float)
 MPM_INST_DT(2, double)
 MPM_INST_DT(3, float)
 MPM_INST_DT(3, double)
+
+#define MPM_INST_DTB(D, T, B)                                                                           \
+  template cudaError_t launch_assemble<D, T, B>(const DevParticles&, const DevGrid&, const int*, const int*, \
+                                                const T*, DevMatrix<T>, cudaStream_t);                   \
+  template cudaError_t launch_bc_matrix<D, T, B>(const DevGrid&, DevMatrix<T>, const uint8_t*, const int*, \
+                                                 int, cudaStream_t);                                     \
+  template cudaError_t launch_block_jacobi<D, T, B>(const DevGrid&, DevMatrix<T>, int, int*, cudaStream_t);
+MPM_INST_DTB(2, float, 2)
+MPM_INST_DTB(2, double, 2)
+MPM_INST_DTB(3, float, 3)
+MPM_INST_DTB(3, double, 3)
+MPM_INST_DTB(2, float, 3)
+MPM_INST_DTB(2, double, 3)
 
 }  // namespace mpm

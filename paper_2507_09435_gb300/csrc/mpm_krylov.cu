@@ -2,10 +2,11 @@
 // this system with AMG/direct solvers on the CPU, Sec. 2.2 remark; here a
 // block-Jacobi preconditioned BiCGStab runs on the GPU).
 //
-// Vectors live on the dense node grid (nnode*D entries, padded on both sides
+// Vectors live on the dense node grid (nnode*B entries, B values per node:
+// the D displacements, plus the pore pressure for u-p; padded on both sides
 // by the stencil reach so that neighbour reads of boundary rows stay inside
 // the allocation); only active rows are ever written.  The matrix is the
-// stencil-BSR layout of mpm_internal.h: val[(slot*cap + row)*D*D + a*D + b],
+// stencil-BSR layout of mpm_internal.h: val[(slot*cap + row)*B*B + a*B + b],
 // one thread per row, coalesced block reads, no column indices.
 //
 // Scalars of the iteration stay on the device (KrylovScalars); every kernel
@@ -24,11 +25,11 @@ __device__ __forceinline__ long long nbr(long long i, int dx, int dy, int dz, in
 }
 
 // y = K x for one row (node i).
-template <int D, class T>
+template <int D, class T, int B>
 __device__ __forceinline__ void spmv_row(const DevMatrix<T>& K, int row, long long i, int nx1, int ny1,
-                                         const T* __restrict__ x, T y[D]) {
+                                         const T* __restrict__ x, T y[B]) {
 #pragma unroll
-  for (int a = 0; a < D; ++a) y[a] = (T)0;
+  for (int a = 0; a < B; ++a) y[a] = (T)0;
   constexpr int ZR = (D == 3) ? 2 : 0;
   const long long cap = K.cap;
 #pragma unroll
@@ -39,27 +40,14 @@ __device__ __forceinline__ void spmv_row(const DevMatrix<T>& K, int row, long lo
       for (int dx = -2; dx <= 2; ++dx) {
         const int slot = (D == 2) ? (dx + 2) + 5 * (dy + 2) : (dx + 2) + 5 * ((dy + 2) + 5 * (dz + 2));
         const long long j = nbr<D>(i, dx, dy, dz, nx1, ny1);
-        T xj[D], kb[D * D];
-        ld_node<D, T, false>(x, j, xj);
-        ld_block<D, T>(&K.val[((long long)slot * cap + row) * (D * D)], kb);
+        T xj[B], kb[B * B];
+        ld_node<B, T, false>(x, j, xj);
+        ld_block<B, T>(&K.val[((long long)slot * cap + row) * (B * B)], kb);
 #pragma unroll
-        for (int a = 0; a < D; ++a)
+        for (int a = 0; a < B; ++a)
 #pragma unroll
-          for (int b = 0; b < D; ++b) y[a] += kb[a * D + b] * xj[b];
+          for (int b = 0; b < B; ++b) y[a] += kb[a * B + b] * xj[b];
       }
-}
-
-template <int D, class T>
-__device__ __forceinline__ void precond_row(const DevMatrix<T>& K, int row, const T v[D], T z[D]) {
-  T m[D * D];
-  ld_block<D, T>(&K.dinv[(long long)row * (D * D)], m);
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    T s = (T)0;
-#pragma unroll
-    for (int b = 0; b < D; ++b) s += m[a * D + b] * v[b];
-    z[a] = s;
-  }
 }
 
 __device__ __forceinline__ double wsum(double v) {
@@ -114,19 +102,20 @@ enum { KS_OK = 0, KS_MAXIT = 1, KS_BREAKDOWN = 2 };
 
 // init: r = b, rhat = b, x = 0, p = r, phat = M^-1 r; rho = (rhat, r),
 // rr_last = (r, r).
-template <int D, class T>
+template <int D, class T, int B>
 __global__ void __launch_bounds__(KTPB) k_bicg_init(DevMatrix<T> K, const double* __restrict__ res,
                                                     const uint8_t* __restrict__ fixed, KrylovVecs<D, T> v,
                                                     KrylovScalars* S, double tol2, int maxit) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   const int nrow = *K.nrow;
+  const unsigned live = __ballot_sync(0xffffffffu, row < nrow);
   double acc[2] = {0.0, 0.0};
   if (row < nrow) {
     const long long i = K.rows[row];
-    T b[D], z[D];
+    T b[B], z[B];
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const long long d = i * D + a;
+    for (int a = 0; a < B; ++a) {
+      const long long d = i * B + a;
       b[a] = fixed[d] ? (T)0 : (T)(-res[d]);
       v.r[d] = b[a];
       v.rhat[d] = b[a];
@@ -134,9 +123,9 @@ __global__ void __launch_bounds__(KTPB) k_bicg_init(DevMatrix<T> K, const double
       v.x[d] = (T)0;
       acc[0] += (double)b[a] * (double)b[a];
     }
-    precond_row<D, T>(K, row, b, z);
+    precond_apply<B, T>(K, row, b, z, live);
 #pragma unroll
-    for (int a = 0; a < D; ++a) v.phat[i * D + a] = z[a];
+    for (int a = 0; a < B; ++a) v.phat[i * B + a] = z[a];
     acc[1] = acc[0];
   }
   double acc3[3] = {acc[0], acc[1], acc[0]};
@@ -154,7 +143,7 @@ __global__ void __launch_bounds__(KTPB) k_bicg_init(DevMatrix<T> K, const double
 }
 
 // B: convergence / limit test, then v = J phat and (rhat, v).
-template <int D, class T>
+template <int D, class T, int B>
 __global__ void __launch_bounds__(KTPB) k_bicg_B(DevGrid G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
   if (S->done) return;
   const double rr = S->rr_last;
@@ -173,12 +162,12 @@ __global__ void __launch_bounds__(KTPB) k_bicg_B(DevGrid G, DevMatrix<T> K, Kryl
   double acc[2] = {0.0, 0.0};
   if (row < *K.nrow) {
     const long long i = K.rows[row];
-    T y[D];
-    spmv_row<D, T>(K, row, i, G.nx1, G.ny1, v.phat, y);
+    T y[B];
+    spmv_row<D, T, B>(K, row, i, G.nx1, G.ny1, v.phat, y);
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      v.v[i * D + a] = y[a];
-      acc[0] += (double)v.rhat[i * D + a] * (double)y[a];
+    for (int a = 0; a < B; ++a) {
+      v.v[i * B + a] = y[a];
+      acc[0] += (double)v.rhat[i * B + a] * (double)y[a];
       acc[1] += (double)y[a] * (double)y[a];
     }
   }
@@ -191,7 +180,7 @@ __global__ void __launch_bounds__(KTPB) k_bicg_B(DevGrid G, DevMatrix<T> K, Kryl
 }
 
 // C: alpha = rho / (rhat, v); s = r - alpha v; shat = M^-1 s; (s,s), (rhat,s).
-template <int D, class T>
+template <int D, class T, int B>
 __global__ void __launch_bounds__(KTPB) k_bicg_C(DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
   if (S->done) return;
   const double rv = S->acc_rv;
@@ -204,21 +193,22 @@ __global__ void __launch_bounds__(KTPB) k_bicg_C(DevMatrix<T> K, KrylovVecs<D, T
   const double alpha = rho / rv;
   const T ta = (T)alpha;
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned live = __ballot_sync(0xffffffffu, row < *K.nrow);
   double acc[2] = {0.0, 0.0};
   if (row < *K.nrow) {
     const long long i = K.rows[row];
-    T s[D], z[D];
+    T s[B], z[B];
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const long long d = i * D + a;
+    for (int a = 0; a < B; ++a) {
+      const long long d = i * B + a;
       s[a] = v.r[d] - ta * v.v[d];
       v.s[d] = s[a];
       acc[0] += (double)s[a] * (double)s[a];
       acc[1] += (double)v.rhat[d] * (double)s[a];
     }
-    precond_row<D, T>(K, row, s, z);
+    precond_apply<B, T>(K, row, s, z, live);
 #pragma unroll
-    for (int a = 0; a < D; ++a) v.shat[i * D + a] = z[a];
+    for (int a = 0; a < B; ++a) v.shat[i * B + a] = z[a];
   }
   double* outs[2] = {&S->acc_ss, &S->acc_rs};
   block_accumulate<2>(acc, outs);
@@ -232,18 +222,18 @@ __global__ void __launch_bounds__(KTPB) k_bicg_C(DevMatrix<T> K, KrylovVecs<D, T
 }
 
 // D: t = J shat; (t,s), (t,t), (rhat,t).
-template <int D, class T>
+template <int D, class T, int B>
 __global__ void __launch_bounds__(KTPB) k_bicg_D(DevGrid G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
   if (S->done) return;
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[3] = {0.0, 0.0, 0.0};
   if (row < *K.nrow) {
     const long long i = K.rows[row];
-    T y[D];
-    spmv_row<D, T>(K, row, i, G.nx1, G.ny1, v.shat, y);
+    T y[B];
+    spmv_row<D, T, B>(K, row, i, G.nx1, G.ny1, v.shat, y);
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const long long d = i * D + a;
+    for (int a = 0; a < B; ++a) {
+      const long long d = i * B + a;
       v.t[d] = y[a];
       acc[0] += (double)y[a] * (double)v.s[d];
       acc[1] += (double)y[a] * (double)y[a];
@@ -261,7 +251,7 @@ __global__ void __launch_bounds__(KTPB) k_bicg_D(DevGrid G, DevMatrix<T> K, Kryl
 
 // A: omega; x and r updates; rho', ||r||^2 from the reduced products; the
 // next search direction p and phat.
-template <int D, class T>
+template <int D, class T, int B>
 __global__ void __launch_bounds__(KTPB) k_bicg_A(DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
   if (S->done) return;
   const double tt = S->acc_tt, ts = S->acc_ts;
@@ -272,21 +262,22 @@ __global__ void __launch_bounds__(KTPB) k_bicg_A(DevMatrix<T> K, KrylovVecs<D, T
   const double beta = (omega != 0.0 && rho_old != 0.0) ? (rho_new / rho_old) * (alpha / omega) : 0.0;
   const T ta = (T)alpha, tw = (T)omega, tb = (T)beta;
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned live = __ballot_sync(0xffffffffu, row < *K.nrow);
   if (row < *K.nrow) {
     const long long i = K.rows[row];
-    T p[D], z[D];
+    T p[B], z[B];
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const long long d = i * D + a;
+    for (int a = 0; a < B; ++a) {
+      const long long d = i * B + a;
       v.x[d] += ta * v.phat[d] + tw * v.shat[d];
       const T rn = v.s[d] - tw * v.t[d];
       v.r[d] = rn;
       p[a] = rn + tb * (v.p[d] - tw * v.v[d]);
       v.p[d] = p[a];
     }
-    precond_row<D, T>(K, row, p, z);
+    precond_apply<B, T>(K, row, p, z, live);
 #pragma unroll
-    for (int a = 0; a < D; ++a) v.phat[i * D + a] = z[a];
+    for (int a = 0; a < B; ++a) v.phat[i * B + a] = z[a];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     S->omega = omega;
@@ -297,19 +288,20 @@ __global__ void __launch_bounds__(KTPB) k_bicg_A(DevMatrix<T> K, KrylovVecs<D, T
 
 // restart from the current x: r = b - J x (the true residual), rhat = r,
 // p = r, phat = M^-1 r; rho = (rhat, r), rr_last = (r, r), rhat2 = (r, r).
-template <int D, class T>
+template <int D, class T, int B>
 __global__ void __launch_bounds__(KTPB) k_bicg_restart(DevGrid G, DevMatrix<T> K, const double* __restrict__ res,
                                                        const uint8_t* __restrict__ fixed, KrylovVecs<D, T> v,
                                                        KrylovScalars* S, double tol2, int maxit) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned live = __ballot_sync(0xffffffffu, row < *K.nrow);
   double acc = 0.0;
   if (row < *K.nrow) {
     const long long i = K.rows[row];
-    T y[D], r[D], z[D];
-    spmv_row<D, T>(K, row, i, G.nx1, G.ny1, v.x, y);
+    T y[B], r[B], z[B];
+    spmv_row<D, T, B>(K, row, i, G.nx1, G.ny1, v.x, y);
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const long long d = i * D + a;
+    for (int a = 0; a < B; ++a) {
+      const long long d = i * B + a;
       const T b = fixed[d] ? (T)0 : (T)(-res[d]);
       r[a] = b - y[a];
       v.r[d] = r[a];
@@ -317,9 +309,9 @@ __global__ void __launch_bounds__(KTPB) k_bicg_restart(DevGrid G, DevMatrix<T> K
       v.p[d] = r[a];
       acc += (double)r[a] * (double)r[a];
     }
-    precond_row<D, T>(K, row, r, z);
+    precond_apply<B, T>(K, row, r, z, live);
 #pragma unroll
-    for (int a = 0; a < D; ++a) v.phat[i * D + a] = z[a];
+    for (int a = 0; a < B; ++a) v.phat[i * B + a] = z[a];
   }
   double acc3[3] = {acc, acc, acc};
   double* outs[3] = {&S->rr_last, &S->rho, &S->rhat2};
@@ -335,37 +327,38 @@ __global__ void __launch_bounds__(KTPB) k_bicg_restart(DevGrid G, DevMatrix<T> K
   }
 }
 
-template <int D, class T>
+template <int D, class T, int B>
 cudaError_t launch_bicgstab_restart(const DevGrid& G, DevMatrix<T> K, const double* res, const uint8_t* fixed,
                                     KrylovVecs<D, T> v, KrylovScalars* S, double tol2, int maxit, int nblk,
                                     cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(S, 0, sizeof(KrylovScalars), st);
   if (e != cudaSuccess) return e;
-  k_bicg_restart<D, T><<<nblk, KTPB, 0, st>>>(G, K, res, fixed, v, S, tol2, maxit);
+  k_bicg_restart<D, T, B><<<nblk, KTPB, 0, st>>>(G, K, res, fixed, v, S, tol2, maxit);
   return cudaGetLastError();
 }
 
-template <int D, class T>
+template <int D, class T, int B>
 cudaError_t launch_bicgstab_init(DevMatrix<T> K, const double* res, const uint8_t* fixed, KrylovVecs<D, T> v,
                                  KrylovScalars* S, double tol2, int maxit, int nblk, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(S, 0, sizeof(KrylovScalars), st);
   if (e != cudaSuccess) return e;
-  k_bicg_init<D, T><<<nblk, KTPB, 0, st>>>(K, res, fixed, v, S, tol2, maxit);
+  k_bicg_init<D, T, B><<<nblk, KTPB, 0, st>>>(K, res, fixed, v, S, tol2, maxit);
   return cudaGetLastError();
 }
 
-template <int D, class T>
+template <int D, class T, int B>
 cudaError_t launch_bicgstab_iter(const DevGrid& G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S,
                                  int nblk, cudaStream_t st) {
-  k_bicg_B<D, T><<<nblk, KTPB, 0, st>>>(G, K, v, S);
-  k_bicg_C<D, T><<<nblk, KTPB, 0, st>>>(K, v, S);
-  k_bicg_D<D, T><<<nblk, KTPB, 0, st>>>(G, K, v, S);
-  k_bicg_A<D, T><<<nblk, KTPB, 0, st>>>(K, v, S);
+  k_bicg_B<D, T, B><<<nblk, KTPB, 0, st>>>(G, K, v, S);
+  k_bicg_C<D, T, B><<<nblk, KTPB, 0, st>>>(K, v, S);
+  k_bicg_D<D, T, B><<<nblk, KTPB, 0, st>>>(G, K, v, S);
+  k_bicg_A<D, T, B><<<nblk, KTPB, 0, st>>>(K, v, S);
   return cudaGetLastError();
 }
-// max |d| over the free DOFs of the active rows, as the ordered bits of a
-// non-negative double (atomicMax on the integer image preserves the order).
-template <int D, class T>
+// max |d| over the free displacement DOFs of the active rows (the first D of
+// the B values of a node), as the ordered bits of a non-negative double
+// (atomicMax on the integer image preserves the order).
+template <int D, class T, int B>
 __global__ void k_absmax(DevMatrix<T> K, const T* __restrict__ x, const uint8_t* __restrict__ fixed,
                          unsigned long long* out) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
@@ -373,102 +366,104 @@ __global__ void k_absmax(DevMatrix<T> K, const T* __restrict__ x, const uint8_t*
   if (row < *K.nrow) {
     const long long i = K.rows[row];
 #pragma unroll
-    for (int a = 0; a < D; ++a) {
-      const long long d = i * D + a;
+    for (int a = 0; a < B; ++a) {
+      const long long d = i * B + a;
       const double v = fabs((double)x[d]);
-      if (!fixed[d]) m = (v == v) ? fmax(m, v) : INFINITY;
+      if (!fixed[d]) m = (v <= 1.7976931348623157e308) ? ((a < D) ? fmax(m, v) : m) : INFINITY;
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
-template <int D, class T>
+template <int D, class T, int B>
 cudaError_t launch_absmax(DevMatrix<T> K, const T* x, const uint8_t* fixed, unsigned long long* out, int nblk,
                           cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
   if (e != cudaSuccess) return e;
-  k_absmax<D, T><<<nblk, KTPB, 0, st>>>(K, x, fixed, out);
+  k_absmax<D, T, B><<<nblk, KTPB, 0, st>>>(K, x, fixed, out);
   return cudaGetLastError();
 }
 
 // du = base + alpha d on the free DOFs (the halved step of a Newton iteration
 // whose full step drove a return map out of its domain).
-template <int D, class T>
+template <int D, class T, int B>
 __global__ void k_step_du(DevMatrix<T> K, const T* __restrict__ x, const uint8_t* __restrict__ fixed,
                           const double* __restrict__ base, double* du, double alpha) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= *K.nrow) return;
   const long long i = K.rows[row];
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    const long long d = i * D + a;
+  for (int a = 0; a < B; ++a) {
+    const long long d = i * B + a;
     if (!fixed[d]) du[d] = base[d] + alpha * (double)x[d];
   }
 }
-template <int D, class T>
+template <int D, class T, int B>
 cudaError_t launch_step_du(DevMatrix<T> K, const T* x, const uint8_t* fixed, const double* base, double* du,
                            double alpha, int nblk, cudaStream_t st) {
-  k_step_du<D, T><<<nblk, KTPB, 0, st>>>(K, x, fixed, base, du, alpha);
+  k_step_du<D, T, B><<<nblk, KTPB, 0, st>>>(K, x, fixed, base, du, alpha);
   return cudaGetLastError();
 }
 
 // Plain y = J x over the active rows (used to time the product in isolation).
-template <int D, class T>
+template <int D, class T, int B>
 __global__ void __launch_bounds__(KTPB) k_spmv(DevGrid G, DevMatrix<T> K, const T* __restrict__ x, T* y) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= *K.nrow) return;
   const long long i = K.rows[row];
-  T v[D];
-  spmv_row<D, T>(K, row, i, G.nx1, G.ny1, x, v);
+  T v[B];
+  spmv_row<D, T, B>(K, row, i, G.nx1, G.ny1, x, v);
 #pragma unroll
-  for (int a = 0; a < D; ++a) y[i * D + a] = v[a];
+  for (int a = 0; a < B; ++a) y[i * B + a] = v[a];
 }
-template <int D, class T>
+template <int D, class T, int B>
 cudaError_t launch_spmv(const DevGrid& G, DevMatrix<T> K, const T* x, T* y, int nblk, cudaStream_t st) {
-  k_spmv<D, T><<<nblk, KTPB, 0, st>>>(G, K, x, y);
+  k_spmv<D, T, B><<<nblk, KTPB, 0, st>>>(G, K, x, y);
   return cudaGetLastError();
 }
 
 // du += d on the free DOFs of active rows (FP64 accumulation of the update).
-template <int D, class T>
+template <int D, class T, int B>
 __global__ void k_update_du(DevMatrix<T> K, const T* __restrict__ x, const uint8_t* __restrict__ fixed,
                             double* du) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= *K.nrow) return;
   const long long i = K.rows[row];
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    const long long d = i * D + a;
+  for (int a = 0; a < B; ++a) {
+    const long long d = i * B + a;
     if (!fixed[d]) du[d] += (double)x[d];
   }
 }
-template <int D, class T>
+template <int D, class T, int B>
 cudaError_t launch_update_du(DevMatrix<T> K, const T* x, const uint8_t* fixed, double* du, int nblk,
                              cudaStream_t st) {
-  k_update_du<D, T><<<nblk, KTPB, 0, st>>>(K, x, fixed, du);
+  k_update_du<D, T, B><<<nblk, KTPB, 0, st>>>(K, x, fixed, du);
   return cudaGetLastError();
 }
 
-#define MPM_KRYLOV_INST(D, T)                                                                          \
-  template cudaError_t launch_bicgstab_init<D, T>(DevMatrix<T>, const double*, const uint8_t*,          \
+#define MPM_KRYLOV_INST(D, T, B)                                                                          \
+  template cudaError_t launch_bicgstab_init<D, T, B>(DevMatrix<T>, const double*, const uint8_t*,          \
                                                   KrylovVecs<D, T>, KrylovScalars*, double, int, int,   \
                                                   cudaStream_t);                                        \
-  template cudaError_t launch_bicgstab_iter<D, T>(const DevGrid&, DevMatrix<T>, KrylovVecs<D, T>,       \
+  template cudaError_t launch_bicgstab_iter<D, T, B>(const DevGrid&, DevMatrix<T>, KrylovVecs<D, T>,       \
                                                   KrylovScalars*, int, cudaStream_t);                   \
-  template cudaError_t launch_bicgstab_restart<D, T>(const DevGrid&, DevMatrix<T>, const double*,       \
+  template cudaError_t launch_bicgstab_restart<D, T, B>(const DevGrid&, DevMatrix<T>, const double*,       \
                                                      const uint8_t*, KrylovVecs<D, T>, KrylovScalars*,  \
                                                      double, int, int, cudaStream_t);                   \
-  template cudaError_t launch_update_du<D, T>(DevMatrix<T>, const T*, const uint8_t*, double*, int,     \
+  template cudaError_t launch_update_du<D, T, B>(DevMatrix<T>, const T*, const uint8_t*, double*, int,     \
                                               cudaStream_t);                                            \
-  template cudaError_t launch_spmv<D, T>(const DevGrid&, DevMatrix<T>, const T*, T*, int, cudaStream_t);  \
-  template cudaError_t launch_absmax<D, T>(DevMatrix<T>, const T*, const uint8_t*, unsigned long long*, int, \
+  template cudaError_t launch_spmv<D, T, B>(const DevGrid&, DevMatrix<T>, const T*, T*, int, cudaStream_t);  \
+  template cudaError_t launch_absmax<D, T, B>(DevMatrix<T>, const T*, const uint8_t*, unsigned long long*, int, \
                                            cudaStream_t);                                                  \
-  template cudaError_t launch_step_du<D, T>(DevMatrix<T>, const T*, const uint8_t*, const double*, double*, \
+  template cudaError_t launch_step_du<D, T, B>(DevMatrix<T>, const T*, const uint8_t*, const double*, double*, \
                                             double, int, cudaStream_t);
-MPM_KRYLOV_INST(2, float)
-MPM_KRYLOV_INST(2, double)
-MPM_KRYLOV_INST(3, float)
-MPM_KRYLOV_INST(3, double)
+MPM_KRYLOV_INST(2, float, 2)
+MPM_KRYLOV_INST(2, double, 2)
+MPM_KRYLOV_INST(3, float, 3)
+MPM_KRYLOV_INST(3, double, 3)
+MPM_KRYLOV_INST(2, float, 3)
+MPM_KRYLOV_INST(2, double, 3)
 
 }  // namespace mpm

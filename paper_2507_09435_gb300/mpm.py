@@ -21,6 +21,8 @@ MPM_NH, MPM_NH_DP, MPM_NH_MCC = 0, 1, 2
 MPM_FP64, MPM_MIXED = 0, 1
 MPM_BICGSTAB, MPM_GMRES = 0, 1
 MPM_FORCING_FIXED, MPM_FORCING_EW = 0, 1
+MPM_SOLID, MPM_UP = 0, 1
+MPM_PC_AUTO, MPM_PC_NODE, MPM_PC_SEG4 = 0, 1, 2
 
 STATUS = {
     0: "MPM_OK", 1: "MPM_ERR_INVALID_ARG", 2: "MPM_ERR_OOM", 3: "MPM_ERR_CUDA",
@@ -35,14 +37,16 @@ class mpm_scene_desc(ctypes.Structure):
                 ("origin", ctypes.c_double * 3), ("precision", ctypes.c_int), ("krylov", ctypes.c_int),
                 ("gmres_restart", ctypes.c_int), ("newton_tol", ctypes.c_double),
                 ("newton_maxit", ctypes.c_int), ("forcing", ctypes.c_int), ("krylov_rtol", ctypes.c_double),
-                ("krylov_maxit", ctypes.c_int)]
+                ("krylov_maxit", ctypes.c_int), ("formulation", ctypes.c_int), ("dt", ctypes.c_double),
+                ("p_scale", ctypes.c_double), ("precond", ctypes.c_int)]
 
 
 class mpm_material(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int), ("E", ctypes.c_double), ("nu", ctypes.c_double),
                 ("rho", ctypes.c_double), ("phi", ctypes.c_double), ("psi", ctypes.c_double),
                 ("c", ctypes.c_double), ("M", ctypes.c_double), ("lambda_cc", ctypes.c_double),
-                ("kappa_cc", ctypes.c_double), ("pc0", ctypes.c_double)]
+                ("kappa_cc", ctypes.c_double), ("pc0", ctypes.c_double), ("k_hyd", ctypes.c_double),
+                ("gamma_w", ctypes.c_double)]
 
 
 class mpm_newton_report(ctypes.Structure):
@@ -76,7 +80,8 @@ _lib = None
 # every symbol declared in include/mpm.h
 EXPORTS = ["mpm_create_scene", "mpm_set_gravity", "mpm_set_dirichlet", "mpm_begin_step", "mpm_newton_step",
            "mpm_set_du", "mpm_assemble", "mpm_commit_step", "mpm_solve_step", "mpm_get_residual", "mpm_get_du", "mpm_get_mass",
-           "mpm_get_counts", "mpm_get_jacobian_bsr", "mpm_get_particles", "mpm_kernel_launches",
+           "mpm_get_counts", "mpm_get_jacobian_bsr", "mpm_get_particles", "mpm_get_pressure",
+           "mpm_set_traction", "mpm_kernel_launches",
            "mpm_time_spmv", "mpm_set_particles", "mpm_residual_norm_noalloc", "mpm_noalloc_last_error",
            "mpm_footprint_bytes",
            "mpm_destroy_scene", "mpm_status_string", "mpm_last_error"]
@@ -107,6 +112,8 @@ def lib(build: bool = True):
     L.mpm_get_counts.argtypes = [_P, _I, _LL]
     L.mpm_get_jacobian_bsr.argtypes = [_P, ctypes.c_longlong, _I, _LL, _I, _D]
     L.mpm_get_particles.argtypes = [_P, _D, _D, _D, _D, _D]
+    L.mpm_get_pressure.argtypes = [_P, _D]
+    L.mpm_set_traction.argtypes = [_P, ctypes.c_int, _I, _D]
     L.mpm_kernel_launches.argtypes = [_P, _LL]
     L.mpm_set_particles.argtypes = [_P, _D, _D, _D]
     L.mpm_residual_norm_noalloc.argtypes = [_P, _P, ctypes.c_int, _P, ctypes.c_int, _D, _P]
@@ -143,7 +150,8 @@ def _check(rc, handle=None):
 
 
 def make_desc(dim, n, h, origin=(0.0, 0.0, 0.0), precision=MPM_FP64, krylov=MPM_BICGSTAB, gmres_restart=30,
-              newton_tol=1e-8, newton_maxit=25, forcing=None, krylov_rtol=None, krylov_maxit=20000):
+              newton_tol=1e-8, newton_maxit=25, forcing=None, krylov_rtol=None, krylov_maxit=20000,
+              formulation=MPM_SOLID, dt=0.0, p_scale=0.0, precond=MPM_PC_AUTO):
     d = mpm_scene_desc()
     d.dim = dim
     for a in range(3):
@@ -162,6 +170,10 @@ def make_desc(dim, n, h, origin=(0.0, 0.0, 0.0), precision=MPM_FP64, krylov=MPM_
     d.forcing = forcing
     d.krylov_rtol = krylov_rtol
     d.krylov_maxit = krylov_maxit
+    d.formulation = formulation
+    d.dt = float(dt)
+    d.p_scale = float(p_scale)
+    d.precond = int(precond)
     return d
 
 
@@ -289,6 +301,18 @@ def mpm_get_particles(h, np_, x=True, be=True, pc=True, F=True, tau=True):
     return out
 
 
+def mpm_get_pressure(h, np_):
+    out = np.zeros(np_)
+    _check(lib().mpm_get_pressure(h, _p(out)), h)
+    return out
+
+
+def mpm_set_traction(h, particle, f):
+    particle = np.ascontiguousarray(particle, dtype=np.int32)
+    f = _f64(np.asarray(f, dtype=np.float64).reshape(-1, 3))
+    _check(lib().mpm_set_traction(h, int(particle.size), _p(particle, _I), _p(f)), h)
+
+
 def mpm_set_particles(h, be=None, pc=None, F=None):
     _check(lib().mpm_set_particles(h, _p(_f64(be)), _p(_f64(pc)), _p(_f64(F))), h)
 
@@ -328,6 +352,7 @@ def materials_of(scene):
         q.model, q.E, q.nu, q.rho = m.model, m.E, m.nu, m.rho
         q.phi, q.psi, q.c = m.phi, m.psi, m.c
         q.M, q.lambda_cc, q.kappa_cc, q.pc0 = m.M, m.lambda_cc, m.kappa_cc, m.pc0
+        q.k_hyd, q.gamma_w = getattr(m, "k_hyd", 0.0), getattr(m, "gamma_w", 9810.0)
         out.append(q)
     return out
 
@@ -338,16 +363,25 @@ class GpuScene:
     def __init__(self, scene, precision=MPM_FP64, krylov=MPM_BICGSTAB, stream=None, **kw):
         self.scene = scene
         self.dim = scene.dim
+        up = getattr(scene, "formulation", "solid") == "up"
+        self.B = scene.dim + (1 if up else 0)
+        if up:
+            kw.setdefault("formulation", MPM_UP)
+            kw.setdefault("dt", scene.dt)
         self.desc = make_desc(scene.dim, scene.n, scene.h, scene.origin, precision=precision, krylov=krylov,
                               **kw)
         self.h = mpm_create_scene(self.desc, scene.x[:, :scene.dim], scene.vol0, scene.mass, scene.mat_id,
                                   materials_of(scene), E_p=scene.E_p, phi_p=scene.phi_p, pc0_p=scene.pc0_p,
                                   stream=stream)
         self.nnode = scene.nnode
-        self.ndof = scene.nnode * scene.dim
+        self.ndof = scene.nnode * self.B
         self.np = scene.np
         if getattr(scene, "be0", None) is not None:
             mpm_set_particles(self.h, be=scene.be0)
+        fext = getattr(scene, "fext", None)
+        if fext is not None:
+            idx = np.nonzero(np.abs(fext).sum(axis=1) > 0)[0]
+            mpm_set_traction(self.h, idx, fext[idx])
 
     def close(self):
         if self.h is not None:
@@ -394,7 +428,10 @@ class GpuScene:
         return mpm_get_mass(self.h, self.nnode)
 
     def jacobian_bsr(self):
-        return mpm_get_jacobian_bsr(self.h, self.dim)
+        return mpm_get_jacobian_bsr(self.h, self.B)
+
+    def pressure(self):
+        return mpm_get_pressure(self.h, self.np)
 
     def particles(self, **kw):
         return mpm_get_particles(self.h, self.np, **kw)

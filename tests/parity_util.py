@@ -11,6 +11,10 @@ state them):
   off-diagonal ones): 1e-10 in FP64 mode, 1e-5 in mixed mode (FP32 blocks);
 * converged increment: max |du_gpu - du_oracle| / max |du_oracle| <= 1e-7
   with both sides converged to a relative residual of 1e-12.
+For the coupled u-p formulation the momentum and mass-balance rows, and the
+displacement and pressure unknowns, carry different units, so every scale
+above is taken per kind: residual scales per row kind, Jacobian scales per
+(block row, row component, column kind), increment scales per unknown kind.
 """
 import numpy as np
 
@@ -20,8 +24,17 @@ JAC_TOL_MIXED = 1e-5
 DU_TOL = 1e-7
 
 
+def _B(x):
+    return getattr(x, "B", x.dim)
+
+
+def kinds(B, dim):
+    """Kind of each node component: 0 displacement, 1 pore pressure."""
+    return np.array([0] * dim + [1] * (B - dim))
+
+
 def fixed_mask(scene, step):
-    f = np.zeros(scene.nnode * scene.dim, dtype=bool)
+    f = np.zeros(scene.nnode * _B(scene), dtype=bool)
     f[np.asarray(step.dof, dtype=np.int64)] = True
     return f
 
@@ -33,10 +46,18 @@ def residual_error(gs, orc, du, fixed):
     free = act & ~fixed
     if not free.any():
         return 0.0
-    scale = max(rabs[free].max(), 1e-300)
     # the GPU reports zeros on prescribed and inactive DOFs
     assert np.all(r_g[~free] == 0.0)
-    return float(np.abs(r_g[free] - r_o[free]).max() / scale)
+    B = _B(orc)
+    kind = np.tile(kinds(B, orc.dim), orc.nnode)
+    worst = 0.0
+    for k in np.unique(kind):
+        sel = free & (kind == k)
+        if not sel.any():
+            continue
+        scale = max(rabs[sel].max(), 1e-300)
+        worst = max(worst, float(np.abs(r_g[sel] - r_o[sel]).max() / scale))
+    return worst
 
 
 def _bc_blocks(blocks, fixed, dim):
@@ -57,7 +78,7 @@ def _bc_blocks(blocks, fixed, dim):
 
 
 def jacobian_error(gs, orc, du, fixed):
-    dim = orc.dim
+    dim = _B(orc)
     row_node, row_ptr, col_node, val = gs.jacobian_bsr()
     G = {}
     for r in range(len(row_node)):
@@ -68,20 +89,49 @@ def jacobian_error(gs, orc, du, fixed):
     act_node = M > 1e-12 * orc.m.max()
     O = {(int(i), int(j)): v for i, j, v in zip(bi, bj, bv) if act_node[i] and act_node[j]}
     O = _bc_blocks(O, fixed, dim)
-    row_scale = {}
-    for (i, j), B in O.items():
-        row_scale[i] = max(row_scale.get(i, 0.0), float(np.abs(B).max()))
-    worst = 0.0
     keys = set(G) | set(O)
     zero = np.zeros((dim, dim))
+    worst = 0.0
+    if dim == orc.dim:
+        row_scale = {}
+        for (i, j), B in O.items():
+            row_scale[i] = max(row_scale.get(i, 0.0), float(np.abs(B).max()))
+        for key in keys:
+            i = key[0]
+            g = G.get(key, zero)
+            o = O.get(key, zero)
+            sc = row_scale.get(i, 1.0)
+            worst = max(worst, float(np.abs(g - o).max() / sc))
+        return worst, len(G), len(O)
+    # u-p: scale per (block row, row component, column kind)
+    kd = kinds(dim, orc.dim)
+    row_scale = {}
+    for (i, j), B in O.items():
+        for a in range(dim):
+            for kb in (0, 1):
+                v = float(np.abs(B[a, kd == kb]).max())
+                row_scale[(i, a, kb)] = max(row_scale.get((i, a, kb), 0.0), v)
     for key in keys:
         i = key[0]
         g = G.get(key, zero)
         o = O.get(key, zero)
-        sc = row_scale.get(i, 1.0)
-        worst = max(worst, float(np.abs(g - o).max() / sc))
+        for a in range(dim):
+            for b in range(dim):
+                sc = row_scale.get((i, a, kd[b]), 0.0)
+                d = abs(g[a, b] - o[a, b])
+                if sc > 0:
+                    worst = max(worst, d / sc)
+                elif d > 0:
+                    worst = np.inf
     return worst, len(G), len(O)
 
 
-def du_error(du_g, du_o):
-    return float(np.abs(du_g - du_o).max() / max(np.abs(du_o).max(), 1e-300))
+def du_error(du_g, du_o, B=None, dim=None):
+    if B is None or B == dim:
+        return float(np.abs(du_g - du_o).max() / max(np.abs(du_o).max(), 1e-300))
+    kind = np.tile(kinds(B, dim), du_o.size // B)
+    worst = 0.0
+    for k in (0, 1):
+        sel = kind == k
+        worst = max(worst, float(np.abs(du_g[sel] - du_o[sel]).max() / max(np.abs(du_o[sel]).max(), 1e-300)))
+    return worst

@@ -15,11 +15,11 @@ from parity_util import (DU_TOL, JAC_TOL_FP64, JAC_TOL_MIXED, RES_TOL, du_error,
 pytestmark = pytest.mark.gpu
 
 
-def _run_parity(sc, nsteps, precision=mpm.MPM_FP64, jac_every_step=True, expect_plastic=False):
+def _run_parity(sc, nsteps, precision=mpm.MPM_FP64, jac_every_step=True, expect_plastic=False, **kw):
     orc = O.OracleScene.from_scene(sc)
     gs = mpm.GpuScene(sc, precision=precision, newton_tol=1e-12, newton_maxit=30,
                       forcing=mpm.MPM_FORCING_FIXED, krylov_rtol=1e-13 if precision == mpm.MPM_FP64 else 1e-6,
-                      krylov_maxit=20000)
+                      krylov_maxit=20000, **kw)
     saw_plastic = False
     jtol = JAC_TOL_FP64 if precision == mpm.MPM_FP64 else JAC_TOL_MIXED
     for k, st in enumerate(sc.steps[:nsteps]):
@@ -92,6 +92,19 @@ def test_footing_coarse_fp64_plastic():
     plus footing steps large enough to drive Drucker-Prager particles plastic."""
     sc = S.footing(nx=48, ny=24, h=0.5, nsteps=20, settle_frac=0.1)
     _run_parity(sc, 4, jac_every_step=True, expect_plastic=True)
+
+
+@pytest.mark.parametrize("krylov", [mpm.MPM_BICGSTAB, mpm.MPM_GMRES])
+def test_segment_preconditioner_footing_fp64(krylov):
+    """Row-segment block-Jacobi (4 consecutive active nodes per block) on the
+    coarse footing: the converged steps match the oracle as with node blocks."""
+    sc = S.footing(nx=48, ny=24, h=0.5, nsteps=20, settle_frac=0.1)
+    _run_parity(sc, 3, jac_every_step=False, expect_plastic=True, precond=mpm.MPM_PC_SEG4, krylov=krylov)
+
+
+def test_segment_preconditioner_column_3d_fp64():
+    sc = S.column_collapse_3d(nx=12, ny=12, nz=12, h=0.1, col=(4, 4, 6), nsteps=3, pc_mean=-8e3, E=1e6)
+    _run_parity(sc, 1, jac_every_step=False, expect_plastic=True, precond=mpm.MPM_PC_SEG4)
 
 
 @pytest.mark.parametrize("dim,model,amp", [(2, S.MODEL_NH, 0.03), (2, S.MODEL_NH_DP, 0.03),
