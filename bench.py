@@ -50,7 +50,11 @@ def parse():
     ap.add_argument("--krylov", default="bicgstab", choices=["bicgstab", "gmres"])
     ap.add_argument("--precond", default="auto", choices=["auto", "node", "seg4"],
                     help="block-Jacobi blocks: one node, or four consecutive active nodes")
-    ap.add_argument("--workload", default="footing", choices=["footing", "column3d", "column3d_stated"])
+    ap.add_argument("--workload", default="footing", choices=["footing", "column3d", "column3d_stated", "serving"])
+    ap.add_argument("--serving", type=int, default=32,
+                    help="requests of the serving stream measured beside the main line (0: none); "
+                         "--workload serving runs the 512-request stream alone")
+    ap.add_argument("--slots", type=int, default=4, help="serving worker slots")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -63,6 +67,8 @@ WORKLOADS = {
     # (72x72x48-cell column, 8 per cell) and the stated 32x32x48-cell column
     "column3d": "column3d_128x128x64_mcc_2M",
     "column3d_stated": "column3d_128x128x64_mcc_393k",
+    # the serving stream (the reference arm samples its first footing request)
+    "serving": "serving_stream_512",
 }
 
 
@@ -74,11 +80,14 @@ def workload_scene(name="footing"):
         return scenes.column_collapse_3d(col=(72, 72, 48))
     if name == "column3d_stated":
         return scenes.column_collapse_3d(col=(32, 32, 48))
+    if name == "serving":
+        d = next(d for d in scenes.serving_draws(512) if d["kind"] == "dp_footing")
+        return scenes.serving_scene(d)[0]
     raise ValueError(name)
 
 
 def config(args, sc):
-    if args.workload == "footing":
+    if args.workload in ("footing", "serving"):
         extra = {"ppc": 4, "model": "neo-hookean + drucker-prager (phi 30, psi 0, c 5 kPa)",
                  "step": "one load step (footing increment 4 mm)"}
     else:
@@ -229,6 +238,105 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------
+# serving stream: continuous batching through the native server
+# ----------------------------------------------------------------------------
+
+def serving_measure(nreq, slots, precision, seed=2507_09435 + 4):
+    """Requests of the serving stream (kinds uniform over elastic block /
+    Drucker-Prager footing / u-p Terzaghi column, grid cells log-uniform in
+    [1e3, 6e4], 10-40 load steps) arriving as a Poisson process at 0.8 x the
+    single-stream capacity measured on the stream's first requests, served by
+    `slots` workers with admission by device footprint.  Latency = submit to
+    done (queueing included); throughput over the whole run."""
+    from paper_2507_09435_gb300 import mpm, scenes as S
+    draws = S.serving_draws(nreq, seed=seed)
+    # single-stream capacity on a sample of the stream
+    ncap = min(8, nreq)
+    sv1 = mpm.Server(slots=1)
+    svc = []
+    for d in draws[:ncap]:
+        sc, st = S.serving_scene(d)
+        t = sv1.submit(sc, steps=st, precision=precision, newton_maxit=40)
+        r = sv1.wait(t)
+        svc.append(r.t_service_ms)
+        sv1.release(t)
+    sv1.close()
+    cap = 1e3 / (sum(svc) / len(svc))
+    lam = 0.8 * cap
+    rng = np.random.default_rng(seed + 1)
+    gaps = rng.exponential(1.0 / lam, size=nreq)
+    sv = mpm.Server(slots=slots)
+    tickets = []
+    t0 = time.perf_counter()
+    due = 0.0
+    late = 0.0
+    for d, g in zip(draws, gaps):
+        due += g
+        sc, st = S.serving_scene(d)
+        now = time.perf_counter() - t0
+        if now < due:
+            time.sleep(due - now)
+        else:
+            late = max(late, now - due)
+        tickets.append(sv.submit(sc, steps=st, precision=precision, newton_maxit=40))
+        del sc, st
+    res = [sv.wait(t) for t in tickets]
+    wall = time.perf_counter() - t0
+    stats = sv.stats()
+    sv.close()
+    ok = [r for r in res if r.status == 0]
+    lat = np.array([r.t_latency_ms for r in ok]) if ok else np.zeros(1)
+    svt = np.array([r.t_service_ms for r in ok]) if ok else np.zeros(1)
+    newton = sum(r.newton_iters for r in ok)
+    kinds, fails = {}, {}
+    for d, r in zip(draws, res):
+        if r.status == 0:
+            kinds.setdefault(d["kind"], []).append(r.t_latency_ms)
+        else:
+            fails.setdefault(d["kind"], []).append(mpm.STATUS.get(r.status, r.status))
+    return {
+        "requests": nreq, "completed_ok": len(ok), "failed": nreq - len(ok), "slots": slots,
+        "arrival_rate_per_s": lam, "single_stream_capacity_per_s": cap,
+        "capacity_sample": f"first {ncap} requests, one slot",
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "mean": float(lat.mean())},
+        "service_ms": {"p50": float(np.percentile(svt, 50)), "p99": float(np.percentile(svt, 99))},
+        "latency_p50_ms_by_kind": {k: float(np.percentile(v, 50)) for k, v in kinds.items()},
+        "failures_by_kind": fails,
+        "throughput_requests_per_s": len(ok) / wall, "newton_iters_per_s": newton / wall,
+        "wall_s": wall, "max_arrival_lag_s": late,
+        "peak_running": stats.peak_running, "peak_footprint_bytes": int(stats.peak_in_use),
+        "budget_bytes": int(stats.budget),
+        "precision": "mixed" if precision == mpm.MPM_MIXED else "fp64",
+        "krylov": "BiCGStab; block-Jacobi per node (solid) or per 4-node row segment (u-p)",
+    }
+
+
+def run_serving_line(args):
+    import torch
+    from paper_2507_09435_gb300 import mpm
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if rank != 0:
+        return 0
+    prec = mpm.MPM_MIXED if args.precision == "mixed" else mpm.MPM_FP64
+    clk = ClockSampler(0)
+    s = serving_measure(512, args.slots, prec)
+    clocks = clk.stop()
+    line = {"metric": "served Newton iters/s with p50/p99 request latency", "value": s["newton_iters_per_s"],
+            "unit": UNIT, "n_gpus": 1, "steps": s["requests"], "warmup": 0,
+            "ms_per_step": 1e3 * s["wall_s"] / s["requests"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": "serving_stream_512", "kinds": "elastic block / DP footing / u-p Terzaghi 16xN",
+                       "cells": "log-uniform 1e3-6e4", "load_steps": "10-40", "arrivals": "Poisson, 0.8 x capacity",
+                       "slots": args.slots},
+            "serving": s, "clocks": clocks, "cpu_baseline": None, "e2e": None, "roofline": None,
+            "gpu_launches": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
 
@@ -236,6 +344,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "serving":
+        return run_serving_line(args)
     import torch
     import torch.distributed as dist
     from paper_2507_09435_gb300 import mpm
@@ -385,6 +495,10 @@ def main():
                          f"Jacobian + {int(round(kpn))} block-Jacobi BiCGStab iterations, the GPU's mean per "
                          f"Newton iteration), {t:.1f} s"}
 
+    serving = None
+    if rank == 0 and args.serving > 0:
+        serving = serving_measure(args.serving, args.slots, prec)
+
     if rank == 0:
         n_gpus = world
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": n_gpus, "steps": args.steps,
@@ -398,7 +512,7 @@ def main():
                 "phase_ms_per_step": {"setup": phase[0] / args.steps, "residual": phase[1] / args.steps,
                                       "assembly": phase[2] / args.steps, "krylov": phase[3] / args.steps},
                 "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "clocks": clocks}
+                "clocks": clocks, "serving": serving}
         print(json.dumps(line), flush=True)
     gs.close()
     if world > 1:

@@ -102,10 +102,16 @@ struct mpm_scene {
   double* d_part = nullptr;        // per-block partial sums of its reductions
   std::string err;
 
+  // Device memory comes from the stream-ordered pool on the scene's stream:
+  // unlike cudaMalloc/cudaFree it does not synchronise the device, so scenes
+  // created and destroyed while others run (a serving loop) do not stall
+  // them.  The stream is synchronised after each allocation so that the
+  // memory is ready for copies issued on other streams.
   template <class T>
   T* dalloc(size_t n) {
     void* p = nullptr;
-    ck(cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)), "cudaMalloc");
+    ck(cudaMallocAsync(&p, std::max<size_t>(n, 1) * sizeof(T), st), "cudaMallocAsync");
+    ck(cudaStreamSynchronize(st), "sync");
     allocs.push_back(p);
     return (T*)p;
   }
@@ -113,7 +119,7 @@ struct mpm_scene {
     if (!p) return;
     auto it = std::find(allocs.begin(), allocs.end(), p);
     if (it != allocs.end()) allocs.erase(it);
-    cudaFree(p);
+    cudaFreeAsync(p, st);
   }
 };
 
@@ -561,8 +567,16 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
   cudaEventRecord(s->ev[3], st);
   ck(cudaStreamSynchronize(st), "sync");
   // a full step that drives a return map out of its domain (or to a
-  // non-finite state) is halved, at most four times, before giving up
-  for (int half = 1; half <= 4 && (s->h_int[2] & (ERRF_RETURN | ERRF_NONFINITE | ERRF_DET)); ++half) {
+  // non-finite state), or that does not decrease ||r|| while ||r|| is still
+  // well above the tolerance (a backtracking line search on the residual
+  // norm, for the non-smooth plastic branches), is halved, at most four times;
+  // the last halving is taken whatever its residual
+  auto need_halving = [&]() {
+    if (s->h_int[2] & (ERRF_RETURN | ERRF_NONFINITE | ERRF_DET)) return true;
+    const double rnew = std::sqrt(s->h_dbl[0]);
+    return !(rnew < (1.0 - 1e-4) * s->rk) && s->rk > 10.0 * s->desc.newton_tol * s->r0;
+  };
+  for (int half = 1; half <= 4 && need_halving(); ++half) {
     ck(cudaMemsetAsync(s->d_err, 0, sizeof(int), st), "memset");
     ck(launch_step_du<D, T, B>(K, v.x, s->d_fixed, s->d_duprev, s->d_du, step * std::ldexp(1.0, -half), nblk, st),
        "step");
@@ -701,7 +715,8 @@ void destroy(mpm_scene* s) {
   if (!s) return;
   if (s->st) cudaStreamSynchronize(s->st);
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
-  for (void* p : s->allocs) cudaFree(p);
+  for (void* p : s->allocs) cudaFreeAsync(p, s->st);
+  if (s->st) cudaStreamSynchronize(s->st);
   if (s->gexec_gm) cudaGraphExecDestroy(s->gexec_gm);
   if (s->h_gst) cudaFreeHost(s->h_gst);
   if (s->h_S) cudaFreeHost(s->h_S);

@@ -65,6 +65,31 @@ class mpm_step_report(ctypes.Structure):
                 ("t_krylov_ms", ctypes.c_double), ("t_commit_ms", ctypes.c_double)]
 
 
+class mpm_request(ctypes.Structure):
+    _fields_ = [("desc", ctypes.POINTER(mpm_scene_desc)), ("np", ctypes.c_int),
+                ("x", ctypes.POINTER(ctypes.c_double)), ("vol0", ctypes.POINTER(ctypes.c_double)),
+                ("mass", ctypes.POINTER(ctypes.c_double)), ("mat_id", ctypes.POINTER(ctypes.c_int)),
+                ("E_p", ctypes.POINTER(ctypes.c_double)), ("phi_p", ctypes.POINTER(ctypes.c_double)),
+                ("pc0_p", ctypes.POINTER(ctypes.c_double)), ("be0", ctypes.POINTER(ctypes.c_double)),
+                ("mats", ctypes.POINTER(mpm_material)), ("nmat", ctypes.c_int),
+                ("ntraction", ctypes.c_int), ("traction_particle", ctypes.POINTER(ctypes.c_int)),
+                ("traction_force", ctypes.POINTER(ctypes.c_double)), ("nsteps", ctypes.c_int),
+                ("step_ndof", ctypes.POINTER(ctypes.c_int)), ("step_dof", ctypes.POINTER(ctypes.c_longlong)),
+                ("step_value", ctypes.POINTER(ctypes.c_double)), ("step_gravity", ctypes.POINTER(ctypes.c_double))]
+
+
+class mpm_request_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("steps_done", ctypes.c_int), ("newton_iters", ctypes.c_int),
+                ("krylov_iters", ctypes.c_int), ("t_queue_ms", ctypes.c_double), ("t_service_ms", ctypes.c_double),
+                ("t_latency_ms", ctypes.c_double), ("footprint", ctypes.c_size_t), ("slot", ctypes.c_int)]
+
+
+class mpm_server_stats(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("budget", ctypes.c_size_t), ("in_use", ctypes.c_size_t),
+                ("peak_in_use", ctypes.c_size_t), ("running", ctypes.c_int), ("peak_running", ctypes.c_int),
+                ("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong)]
+
+
 class MPMError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -84,7 +109,10 @@ EXPORTS = ["mpm_create_scene", "mpm_set_gravity", "mpm_set_dirichlet", "mpm_begi
            "mpm_set_traction", "mpm_kernel_launches",
            "mpm_time_spmv", "mpm_set_particles", "mpm_residual_norm_noalloc", "mpm_noalloc_last_error",
            "mpm_footprint_bytes",
-           "mpm_destroy_scene", "mpm_status_string", "mpm_last_error"]
+           "mpm_destroy_scene", "mpm_status_string", "mpm_last_error",
+           # include/mpm_serve.h
+           "mpm_server_create", "mpm_server_submit", "mpm_server_wait", "mpm_server_result_particles",
+           "mpm_server_release", "mpm_server_get_stats", "mpm_server_destroy"]
 
 
 def lib(build: bool = True):
@@ -128,8 +156,17 @@ def lib(build: bool = True):
     L.mpm_status_string.restype = ctypes.c_char_p
     L.mpm_last_error.argtypes = [_P]
     L.mpm_last_error.restype = ctypes.c_char_p
+    L.mpm_server_create.argtypes = [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_P)]
+    L.mpm_server_submit.argtypes = [_P, ctypes.POINTER(mpm_request), _LL]
+    L.mpm_server_wait.argtypes = [_P, ctypes.c_longlong, ctypes.POINTER(mpm_request_result)]
+    L.mpm_server_result_particles.argtypes = [_P, ctypes.c_longlong, _D, _D]
+    L.mpm_server_release.argtypes = [_P, ctypes.c_longlong]
+    L.mpm_server_get_stats.argtypes = [_P, ctypes.POINTER(mpm_server_stats)]
+    L.mpm_server_destroy.argtypes = [_P]
+    L.mpm_server_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("mpm_destroy_scene", "mpm_status_string", "mpm_last_error", "mpm_noalloc_last_error"):
+        if name not in ("mpm_destroy_scene", "mpm_status_string", "mpm_last_error", "mpm_noalloc_last_error",
+                        "mpm_server_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -435,3 +472,118 @@ class GpuScene:
 
     def particles(self, **kw):
         return mpm_get_particles(self.h, self.np, **kw)
+
+
+# --------------------------------------------------------------------------
+# serving loop (include/mpm_serve.h)
+# --------------------------------------------------------------------------
+
+def scene_desc(scene, precision=MPM_MIXED, krylov=None, **kw):
+    """The scene descriptor a generated scene is solved with (u-p scenes get
+    their time step)."""
+    up = getattr(scene, "formulation", "solid") == "up"
+    if up:
+        kw.setdefault("formulation", MPM_UP)
+        kw.setdefault("dt", scene.dt)
+    if krylov is None:
+        krylov = MPM_BICGSTAB
+    return make_desc(scene.dim, scene.n, scene.h, scene.origin, precision=precision, krylov=krylov, **kw)
+
+
+class Server:
+    """Continuous-batching server: ``slots`` worker threads with their own
+    CUDA streams, admission by device footprint within ``budget`` bytes."""
+
+    def __init__(self, slots=4, budget=0):
+        h = _P()
+        rc = lib().mpm_server_create(int(slots), int(budget), ctypes.byref(h))
+        if rc != MPM_OK:
+            raise MPMError(rc, "mpm_server_create failed")
+        self.h = h
+        self._np = {}
+
+    def submit(self, scene, steps=None, desc=None, **kw):
+        """Queue the scene with its load steps (all by default); returns the
+        ticket.  The arrays are copied by the call."""
+        steps = scene.steps if steps is None else steps
+        desc = desc if desc is not None else scene_desc(scene, **kw)
+        np_ = scene.np
+        x = np.zeros((np_, 3))
+        x[:, :scene.dim] = scene.x[:, :scene.dim]
+        keep = dict(x=x, vol0=_f64(scene.vol0), mass=_f64(scene.mass),
+                    mat_id=np.ascontiguousarray(scene.mat_id, dtype=np.int32),
+                    E_p=_f64(scene.E_p), phi_p=_f64(scene.phi_p), pc0_p=_f64(scene.pc0_p),
+                    be0=_f64(getattr(scene, "be0", None)))
+        mats = materials_of(scene)
+        marr = (mpm_material * len(mats))(*mats)
+        ndof = np.array([len(s.dof) for s in steps], dtype=np.int32)
+        dof = np.ascontiguousarray(np.concatenate([np.asarray(s.dof, dtype=np.int64) for s in steps])
+                                   if steps else np.zeros(0, np.int64))
+        val = _f64(np.concatenate([np.asarray(s.value, dtype=np.float64) for s in steps])
+                   if steps else np.zeros(0))
+        grav = _f64(np.array([s.gravity for s in steps], dtype=np.float64).reshape(-1))
+        fext = getattr(scene, "fext", None)
+        if fext is not None:
+            tp = np.ascontiguousarray(np.nonzero(np.abs(fext).sum(axis=1) > 0)[0], dtype=np.int32)
+            tf = _f64(fext[tp])
+        else:
+            tp, tf = np.zeros(0, np.int32), np.zeros((0, 3))
+        q = mpm_request()
+        q.desc = ctypes.pointer(desc)
+        q.np = np_
+        q.x, q.vol0, q.mass = _p(keep["x"]), _p(keep["vol0"]), _p(keep["mass"])
+        q.mat_id = _p(keep["mat_id"], _I)
+        q.E_p, q.phi_p, q.pc0_p, q.be0 = _p(keep["E_p"]), _p(keep["phi_p"]), _p(keep["pc0_p"]), _p(keep["be0"])
+        q.mats = ctypes.cast(marr, ctypes.POINTER(mpm_material))
+        q.nmat = len(mats)
+        q.ntraction = int(tp.size)
+        q.traction_particle = _p(tp, _I) if tp.size else None
+        q.traction_force = _p(tf) if tp.size else None
+        q.nsteps = len(steps)
+        q.step_ndof = _p(ndof, _I)
+        q.step_dof = _p(dof, _LL) if dof.size else None
+        q.step_value = _p(val) if val.size else None
+        q.step_gravity = _p(grav)
+        t = ctypes.c_longlong(0)
+        rc = lib().mpm_server_submit(self.h, ctypes.byref(q), ctypes.byref(t))
+        if rc != MPM_OK:
+            raise MPMError(rc, "mpm_server_submit rejected the request")
+        self._np[t.value] = (np_, desc.formulation == MPM_UP)
+        return t.value
+
+    def wait(self, ticket):
+        r = mpm_request_result()
+        rc = lib().mpm_server_wait(self.h, int(ticket), ctypes.byref(r))
+        if rc != MPM_OK:
+            raise MPMError(rc, "unknown ticket")
+        return r
+
+    def particles(self, ticket):
+        """(x[np,3], pore pressure[np] or None) of a finished request."""
+        np_, up = self._np[ticket]
+        x = np.zeros(np_ * 3)
+        pp = np.zeros(np_) if up else None
+        rc = lib().mpm_server_result_particles(self.h, int(ticket), _p(x), _p(pp))
+        if rc != MPM_OK:
+            raise MPMError(rc, "no particles for this ticket")
+        return x.reshape(np_, 3), pp
+
+    def release(self, ticket):
+        lib().mpm_server_release(self.h, int(ticket))
+        self._np.pop(ticket, None)
+
+    def stats(self):
+        st = mpm_server_stats()
+        _check(lib().mpm_server_get_stats(self.h, ctypes.byref(st)))
+        return st
+
+    def close(self):
+        if self.h is not None:
+            lib().mpm_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -205,10 +205,11 @@ def _merge(*pairs):
 # --------------------------------------------------------------------------
 
 def block_compression(nsteps: int = 5, strain_per_step: float = 1e-3, ppc: int = 2,
-                      E: float = 1e6, nu: float = 0.3) -> Scene:
+                      E: float = 1e6, nu: float = 0.3, ngrid: int = 32) -> Scene:
     """2D plane-strain Neo-Hookean block, 32x32 grid (h = 1/32), block on cells
     [2,18)^2 with 2x2 particles per cell (1024 particles), top face displaced
-    0.1 % of the height per step.
+    0.1 % of the height per step.  ``ngrid`` scales the grid (block on cells
+    [o, o + ngrid/2)^2, o = ngrid/16, h = 1/ngrid).
 
     Boundary reading: the affine increment du_y = -eps*(y - y_bottom) is
     prescribed on every node within one cell of the bottom (y <= 3h) or top
@@ -216,21 +217,22 @@ def block_compression(nsteps: int = 5, strain_per_step: float = 1e-3, ppc: int =
     With this node set and particles at the 1/4, 3/4 offsets the first load
     step has the homogeneous solution F = diag(l1, 1-eps, 1) as its exact
     discrete solution (the quadrature of grad w over a full column vanishes)."""
-    n = (32, 32, 0)
-    h = 1.0 / 32
-    cells = box_cells((2, 2), (18, 18))
+    n = (ngrid, ngrid, 0)
+    h = 1.0 / ngrid
+    o, L = max(ngrid // 16, 2), ngrid // 2
+    cells = box_cells((o, o), (o + L, o + L))
     x = lattice(cells, h, ppc, 2)
     mat = Material(model=MODEL_NH, E=E, nu=nu, rho=1000.0)
     vol = np.full(x.shape[0], h * h / ppc ** 2)
     sc = Scene("block_compression", 2, n, h, (0.0, 0.0, 0.0), x, vol, vol * mat.rho,
                np.zeros(x.shape[0], np.int32), [mat])
-    yb = 2 * h
-    dy, (ix, iy) = _dofs(sc, lambda ix, iy: (iy <= 3) | (iy >= 17), 1, 2, n)
+    yb = o * h
+    dy, (ix, iy) = _dofs(sc, lambda ix, iy: (iy <= o + 1) | (iy >= o + L - 1), 1, 2, n)
     vy = -strain_per_step * (iy * h - yb)
-    dx, _ = _dofs(sc, lambda ix, iy: ix == 2, 0, 2, n)
+    dx, _ = _dofs(sc, lambda ix, iy: ix == o, 0, 2, n)
     dof, val = _merge((dy, vy), (dx, np.zeros(dx.shape)))
     sc.steps = [LoadStep(dof, val, (0.0, 0.0, 0.0)) for _ in range(nsteps)]
-    sc.meta = dict(strain_per_step=strain_per_step, y_bottom=yb, x_left=2 * h)
+    sc.meta = dict(strain_per_step=strain_per_step, y_bottom=yb, x_left=o * h)
     return sc
 
 
@@ -435,7 +437,8 @@ def self_weight_column(ncell: int, l0: float = 50.0, rho0: float = 80.0, E: floa
 
 
 def terzaghi(ncell: int = 100, H: float = 10.0, ppc: int = 2, lam: float = 600e3, mu: float = 600e3,
-             k_hyd: float = 9.81e-9, t_load: float = 1e3, dt: float = 1e5, nsteps: int = 40) -> Scene:
+             k_hyd: float = 9.81e-9, t_load: float = 1e3, dt: float = 1e5, nsteps: int = 40,
+             ncell_x: int = 1) -> Scene:
     """One-dimensional consolidation (paper Sec. 4.4): a column H = 10 m tall,
     one cell wide and ``ncell`` cells high (100 in the paper) with 2x2
     particles per cell, Neo-Hookean skeleton with lambda = mu = 600 kPa,
@@ -449,10 +452,11 @@ def terzaghi(ncell: int = 100, H: float = 10.0, ppc: int = 2, lam: float = 600e3
     on both sides of a one-cell column), u_y = 0 on the base nodes (y <= base),
     p = 0 on the top nodes (y >= top); no gravity (p is the excess pressure).
     The load is a force of t * h / ppc on each particle of the top lattice row
-    (its share of the loaded face)."""
+    (its share of the loaded face).  ``ncell_x`` > 1 gives a wider column
+    (rollers on its two side walls only, u_x free inside)."""
     h = H / ncell
-    n = (3, ncell + 2, 0)
-    cells = box_cells((1, 1), (2, 1 + ncell))
+    n = (ncell_x + 2, ncell + 2, 0)
+    cells = box_cells((1, 1), (1 + ncell_x, 1 + ncell))
     x = lattice(cells, h, ppc, 2)
     E = mu * (3 * lam + 2 * mu) / (lam + mu)
     nu = lam / (2 * (lam + mu))
@@ -466,7 +470,10 @@ def terzaghi(ncell: int = 100, H: float = 10.0, ppc: int = 2, lam: float = 600e3
     fext[top_row, 1] = -t_load * h / ppc
     sc.fext = fext
     B = 3
-    ax, _ = _dofs(sc, lambda ix, iy: ix >= 0, 0, 2, n, B)
+    if ncell_x == 1:
+        ax, _ = _dofs(sc, lambda ix, iy: ix >= 0, 0, 2, n, B)
+    else:
+        ax, _ = _dofs(sc, lambda ix, iy: (ix <= 1) | (ix >= 1 + ncell_x), 0, 2, n, B)
     by, _ = _dofs(sc, lambda ix, iy: iy <= 1, 1, 2, n, B)
     pt, _ = _dofs(sc, lambda ix, iy: iy >= 1 + ncell, 2, 2, n, B)
     dof, val = _merge((ax, np.zeros(ax.shape)), (by, np.zeros(by.shape)), (pt, np.zeros(pt.shape)))
@@ -474,6 +481,59 @@ def terzaghi(ncell: int = 100, H: float = 10.0, ppc: int = 2, lam: float = 600e3
     cv = k_hyd / mat.gamma_w * (lam + 2 * mu)
     sc.meta = dict(H=H, y_top=y_top, y_base=h, t_load=t_load, cv=cv, dt=dt)
     return sc
+
+
+# --------------------------------------------------------------------------
+# serving stream
+# --------------------------------------------------------------------------
+
+SERVING_KINDS = ("elastic_block", "dp_footing", "up_terzaghi")
+
+
+def serving_draws(n: int, seed: int = SEED_BASE + 4, cells_lo: float = 1e3, cells_hi: float = 6e4,
+                  steps_lo: int = 10, steps_hi: int = 40):
+    """Seeded request descriptors of the serving stream: kind uniform over the
+    three kinds, grid cells log-uniform in [cells_lo, cells_hi], load steps
+    uniform in [steps_lo, steps_hi]."""
+    rng = np.random.default_rng(seed)
+    kinds = rng.integers(0, len(SERVING_KINDS), size=n)
+    cells = np.exp(rng.uniform(np.log(cells_lo), np.log(cells_hi), size=n))
+    steps = rng.integers(steps_lo, steps_hi + 1, size=n)
+    return [dict(kind=SERVING_KINDS[k], cells=float(c), nsteps=int(s)) for k, c, s in zip(kinds, cells, steps)]
+
+
+def serving_scene(d) -> Tuple[Scene, list]:
+    """The scene and load steps of one serving request descriptor.
+    elastic block: square grid of ~cells cells, block on a quarter of it,
+    1 % strain over the steps; footing: nx = 2 ny with nx*ny ~ cells, h = 0.1,
+    B = nx h / 12.8, settlement 0.001 B per step after the geostatic step; Terzaghi: a
+    column 16 cells wide and N = cells/16 (clipped to [64, 256]: taller columns
+    need the multilevel preconditioner too) high,
+    k = 1e-9 m/s, time step c_v dt / h^2 = 10 (the early, boundary-layer part of
+    the consolidation: with block-Jacobi Krylov the u-p system is solved
+    reliably near that ratio, while steps spanning T in [0, 1] give ratios in
+    the thousands, a pressure problem that wants a multilevel preconditioner)."""
+    kind, cells, ns = d["kind"], d["cells"], d["nsteps"]
+    if kind == "elastic_block":
+        ng = max(32, int(round(np.sqrt(cells) / 16)) * 16)
+        sc = block_compression(nsteps=ns, strain_per_step=0.01 / ns, ngrid=ng)
+        return sc, sc.steps
+    if kind == "dp_footing":
+        # footing width in the proportions of the 256 x 128 footing
+        # (B = domain width / 12.8); 0.001 B per step keeps the 40-step
+        # requests short of the bearing-capacity plateau
+        ny = max(16, int(round(np.sqrt(cells / 2.0))))
+        B = 2 * ny * 0.1 / 12.8
+        sc = footing(nx=2 * ny, ny=ny, h=0.1, nsteps=ns - 1, B=B, settle_frac=0.001 * (ns - 1))
+        return sc, sc.steps
+    N = int(np.clip(round(cells / 16.0), 64, 256))
+    lam = mu = 600e3
+    k_hyd = 1e-9
+    cv = k_hyd / 9810.0 * (lam + 2 * mu)
+    hh = 10.0 / N
+    dt = 10.0 * hh * hh / cv
+    sc = terzaghi(ncell=N, ncell_x=16, k_hyd=k_hyd, dt=dt, nsteps=ns)
+    return sc, sc.steps
 
 
 def tiny_scene(dim: int, model: int, seed: int, ncell: int = 4, ppc: int = 2,

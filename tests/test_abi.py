@@ -1,5 +1,5 @@
 """C-ABI checks that need no GPU: the library builds for sm_103a, loads, and
-exports exactly the symbols include/mpm.h declares; host-only calls work;
+exports exactly the symbols include/*.h declare; host-only calls work;
 compute calls fail loudly without a GPU (there is no CPU fallback)."""
 import os
 import re
@@ -13,9 +13,14 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def header_functions():
-    txt = open(os.path.join(ROOT, "include", "mpm.h")).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return set(re.findall(r"^\s*(?:mpm_status|void|const char\s*\*)\s*(mpm_\w+)\s*\(", txt, flags=re.M))
+    out = set()
+    for name in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not name.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", name)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        out |= set(re.findall(r"^\s*(?:mpm_status|void|const char\s*\*)\s*(mpm_\w+)\s*\(", txt, flags=re.M))
+    return out
 
 
 def test_header_and_binding_agree():

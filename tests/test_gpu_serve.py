@@ -1,0 +1,91 @@
+"""Serving loop (include/mpm_serve.h) on the GPU: each request's result is the
+same alone and in a concurrent mix (within the Newton tolerance), requests
+overlap on the device, admission keeps the running footprint within the
+budget, and a failing request is reported without stopping the others."""
+import numpy as np
+import pytest
+
+from paper_2507_09435_gb300 import mpm, scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _mix():
+    """Small requests of the serving kinds: elastic block, Drucker-Prager
+    footing, u-p Terzaghi column; different sizes and materials."""
+    out = []
+    out.append((S.block_compression(nsteps=4), None))
+    blk = S.block_compression(nsteps=3, strain_per_step=2e-3)
+    blk.materials[0].E = 3e6
+    out.append((blk, None))
+    fo = S.footing(nx=48, ny=24, h=0.5, nsteps=20, settle_frac=0.1)
+    out.append((fo, fo.steps[:3]))
+    fo2 = S.footing(nx=64, ny=32, h=0.4, nsteps=20, settle_frac=0.1)
+    out.append((fo2, fo2.steps[:2]))
+    out.append((S.terzaghi(ncell=24, dt=2e5, nsteps=4), None))
+    out.append((S.terzaghi(ncell=40, dt=5e4, nsteps=3), None))
+    return out
+
+
+KW = dict(precision=mpm.MPM_FP64, newton_tol=1e-11, newton_maxit=30)
+
+
+def _run_alone(sc, steps):
+    sv = mpm.Server(slots=1)
+    t = sv.submit(sc, steps=steps, **KW)
+    r = sv.wait(t)
+    assert r.status == mpm.MPM_OK, mpm.STATUS.get(r.status)
+    x, pp = sv.particles(t)
+    sv.close()
+    return x, pp
+
+
+def test_same_alone_and_in_the_mix():
+    mix = _mix()
+    alone = [_run_alone(sc, st) for sc, st in mix]
+    sv = mpm.Server(slots=4)
+    tickets = [sv.submit(sc, steps=st, **KW) for sc, st in mix]
+    res = [sv.wait(t) for t in tickets]
+    stats = sv.stats()
+    assert stats.peak_running >= 2, "requests should overlap on the device"
+    for (sc, st), t, r, (xa, pa) in zip(mix, tickets, res, alone):
+        assert r.status == mpm.MPM_OK, (sc.name, mpm.STATUS.get(r.status))
+        x, pp = sv.particles(t)
+        x0 = np.zeros_like(x)
+        x0[:, :sc.dim] = sc.x[:, :sc.dim]
+        disp = max(np.abs(xa - x0).max(), 1e-300)
+        assert np.abs(x - xa).max() <= 1e-7 * disp + 1e-13 * np.abs(xa).max(), sc.name
+        if pa is not None:
+            assert np.abs(pp - pa).max() <= 1e-7 * np.abs(pa).max(), sc.name
+    sv.close()
+
+
+def test_admission_keeps_footprint_within_budget():
+    mix = _mix()
+    fps = [mpm.mpm_footprint_bytes(mpm.scene_desc(sc, **KW), sc.np) for sc, _ in mix]
+    budget = int(1.5 * max(fps))
+    sv = mpm.Server(slots=4, budget=budget)
+    tickets = [sv.submit(sc, steps=st, **KW) for sc, st in mix]
+    for t in tickets:
+        assert sv.wait(t).status == mpm.MPM_OK
+    st = sv.stats()
+    assert st.completed == len(mix) and st.failed == 0
+    assert st.peak_in_use <= budget
+    assert st.in_use == 0 and st.running == 0
+    sv.close()
+
+
+def test_failed_request_does_not_stop_the_server():
+    sv = mpm.Server(slots=2)
+    bad = S.block_compression(nsteps=2)
+    # a prescribed increment of several cells pushes particles off the grid
+    bad.steps = [S.LoadStep(st.dof, st.value * 4000.0, st.gravity) for st in bad.steps]
+    good = S.block_compression(nsteps=2)
+    tb = sv.submit(bad, **KW)
+    tg = sv.submit(good, **KW)
+    rb, rg = sv.wait(tb), sv.wait(tg)
+    assert rb.status != mpm.MPM_OK
+    assert rg.status == mpm.MPM_OK and rg.steps_done == 2
+    st = sv.stats()
+    assert st.failed == 1 and st.completed == 2
+    sv.close()
