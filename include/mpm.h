@@ -227,6 +227,39 @@ mpm_status mpm_get_jacobian_bsr(const mpm_scene* s, long long cap, int* row_node
 mpm_status mpm_get_particles(const mpm_scene* s, double* x, double* be, double* pc, double* F,
                              double* tau);
 
+/* Per-particle material parameters for the following load steps (caller
+ * order, np values each; NULL keeps a field): Young's modulus E_p (> 0),
+ * friction angle phi_p (degrees, Drucker-Prager), hydraulic conductivity
+ * k_p (m/s, MPM_UP only).  Unstages a staged step. */
+mpm_status mpm_set_params(mpm_scene* s, const double* E_p, const double* phi_p, const double* k_p);
+
+/* Particle displacement increments of the staged step's current iterate,
+ * du_p = sum_i w_ip du_i (caller order, np*3; z = 0 in 2D). */
+mpm_status mpm_get_particle_increment(const mpm_scene* s, double* du_p);
+
+/* Adjoint of the staged step at its current iterate (call it after the
+ * Newton iterations have converged, before mpm_commit_step).  For a loss L
+ * of the step's converged increment it solves J^T lambda = dL/du with the
+ * Jacobian at that iterate and returns dL/dtheta = -lambda^T dr/dtheta
+ * (the implicit-function adjoint of r(du; theta) = 0; the paper's inverse
+ * analysis, Sec. 4.5, differentiates through its implicit steps the same
+ * way).  The start-of-step particle state is held fixed: this is the
+ * gradient of one load step.
+ *   dL_dU   host, nnode*B: dL/du on the nodal DOFs in physical units (NULL = 0)
+ *   dL_dx   host, np*3 (caller order): dL/d(du_p) on the particle
+ *           increments of mpm_get_particle_increment (NULL = 0)
+ *   grad_E, grad_phi  host, np (caller order) or NULL: dL/dE_p, dL/dphi_p
+ *           (phi in degrees; zero for models without friction)
+ *   grad_k  host, nmat or NULL: dL/dk_hyd per material (MPM_UP)
+ * The linear solve uses the scene's Krylov method to a relative tolerance of
+ * 1e-12 (FP64) or 1e-6 (mixed); a solve that stops early is accepted at a
+ * relative residual of 1e-8 (FP64) or 1e-5 (mixed).  Afterwards the scene's matrix holds J^T
+ * (mpm_get_jacobian_bsr would return it); a following mpm_newton_step
+ * reassembles J.  Errors: MPM_ERR_STATE without a staged step,
+ * MPM_ERR_KRYLOV_MAXIT / MPM_ERR_KRYLOV_BREAKDOWN if the solve fails. */
+mpm_status mpm_adjoint(mpm_scene* s, const double* dL_dU, const double* dL_dx, double* grad_E,
+                       double* grad_phi, double* grad_k);
+
 /* MPM_UP: pore pressure of each particle after the last commit,
  * p_p = sum_i w_ip p_i (caller's order, np values).  MPM_ERR_INVALID_ARG for a
  * single-phase scene. */

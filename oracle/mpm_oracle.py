@@ -427,3 +427,45 @@ def fd_jacobian_plain(sc: OracleScene, du, eps, cols):
         rm, _ = sc.residual(du - eps * e)
         out[:, k] = (rp - rm) / (2 * eps)
     return out
+
+
+# --------------------------------------------------------------------------
+# gradient of a load step's loss by its definition (the adjoint's oracle)
+# --------------------------------------------------------------------------
+
+def particle_increments(sc: OracleScene, du):
+    """du_p = sum_i w_ip du_i for every particle (np, 3), from the start-of-step
+    positions (the G2P of the increment, Sec. 2.2)."""
+    out = np.zeros((sc.np, 3))
+    for p in range(sc.np):
+        node, w, g = stencil(sc.dim, sc.n, sc.h, sc.origin, sc.x[p])
+        for a in range(sc.dim):
+            out[p, a] = float(np.dot(w, du[node * sc.B + a]))
+    return out
+
+
+def step_gradient_fd(make_scene, step, loss, which, index, rel=1e-5, tol=1e-13):
+    """Central difference of loss(converged du, particle increments) with
+    respect to one parameter: which = "E" or "phi" (per particle `index`) or
+    "k" (the conductivity of every particle scaled by 1 +- rel, i.e. the
+    derivative with respect to log k).  `make_scene()` returns a fresh
+    OracleScene at the start of the step."""
+    vals = []
+    for sgn in (1.0, -1.0):
+        sc = make_scene()
+        if which == "E":
+            h_ = rel * sc.params[index, 0]
+            sc.params[index, 0] += sgn * h_
+        elif which == "phi":
+            h_ = rel * max(abs(sc.params[index, 2]), 1.0)
+            sc.params[index, 2] += sgn * h_
+        elif which == "k":
+            h_ = rel
+            sc.kdt = sc.kdt * (1.0 + sgn * rel)
+        else:
+            raise ValueError(which)
+        out = sc.solve_step(step.dof, step.value, step.gravity, tol=tol, maxit=40, commit=False)
+        if not out["converged"]:
+            raise OracleError("finite-difference solve did not converge")
+        vals.append(loss(out["du"], particle_increments(sc, out["du"])))
+    return (vals[0] - vals[1]) / (2.0 * h_)

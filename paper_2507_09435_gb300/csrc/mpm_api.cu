@@ -58,6 +58,7 @@ struct mpm_scene {
   int *d_nrow = nullptr, *d_err = nullptr, *d_nplastic = nullptr;
   double *d_M = nullptr, *d_du = nullptr, *d_r = nullptr, *d_bcval = nullptr, *d_grav = nullptr,
          *d_norm = nullptr;
+  const double* krhs = nullptr;   // right-hand side source of the Krylov solve (d_r or the adjoint's)
   uint8_t* d_fixed = nullptr;
   void* d_A = nullptr;
   // matrix (stencil-BSR), grown on demand
@@ -100,6 +101,9 @@ struct mpm_scene {
   unsigned int* d_bar = nullptr;   // barrier counter of the persistent kernel
   double* d_fail = nullptr;        // first constitutive failure record of a pass
   double* d_part = nullptr;        // per-block partial sums of its reductions
+  void* d_KT = nullptr;            // adjoint: transposed Jacobian scratch
+  int kt_cap = -1;
+  int adj_kit = 0;                 // Krylov iterations of the last adjoint solve
   std::string err;
 
   // Device memory comes from the stream-ordered pool on the scene's stream:
@@ -439,7 +443,7 @@ void gmres_solve(mpm_scene* s, DevMatrix<T> K, T* x, double tol, int nblk, int& 
   const size_t tail_bytes = sizeof(GmresState) - tail;
   GmresState* h = (GmresState*)(s->h_gst - tail);   // fields from wn2 on are valid
   for (int cycle = 0;; ++cycle) {
-    ck(launch_gmres_begin<D, T, B>(s->G, K, s->d_r, s->d_fixed, g, x, s->d_gst, cycle == 0 ? 1 : 0, tol,
+    ck(launch_gmres_begin<D, T, B>(s->G, K, s->krhs, s->d_fixed, g, x, s->d_gst, cycle == 0 ? 1 : 0, tol,
                                 s->desc.krylov_maxit, nblk, st),
        "gmres begin");
     s->launches += 3;
@@ -455,42 +459,23 @@ void gmres_solve(mpm_scene* s, DevMatrix<T> K, T* x, double tol, int nblk, int& 
   kres2 = h->res * h->res;
 }
 
+// Krylov solve of J x = -b on the free DOFs (b = s->krhs, by default the
+// residual) to the absolute tolerance eta * rnorm; x is left in the Krylov
+// vector x.  BiCGStab (graph chunks or the persistent kernel) or GMRES(m).
 template <int D, class T, int B>
-void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
-  if (!s->staged) fail(MPM_ERR_STATE, "no load step staged (call mpm_begin_step)");
+void krylov_solve(mpm_scene* s, double eta, double rnorm, int& kit, int& kstat, double& kres2) {
   cudaStream_t st = s->st;
   DevMatrix<T> K = matview<T>(s);
-  cudaEventRecord(s->ev[0], st);
-  assemble_impl<D, T, B>(s);
-  // linear tolerance: fixed, or Eisenstat-Walker choice 2 (gamma 0.9,
-  // alpha 2) capped at ETA_MAX = 1e-2: with the classical cap of 0.1 loose
-  // steps through the plastic zone made Newton diverge on footing problems.
-  double eta = s->desc.krylov_rtol;
-  if (s->desc.forcing == MPM_FORCING_EW) {
-    constexpr double ETA_MAX = 1e-2;
-    if (s->k == 0) {
-      eta = ETA_MAX;
-    } else {
-      double ratio = s->rk / s->rprev;
-      eta = 0.9 * ratio * ratio;
-      double safe = 0.9 * s->eta_prev * s->eta_prev;
-      if (safe > 0.1) eta = std::max(eta, safe);
-    }
-    // no need to solve below what the Newton tolerance asks of this step
-    eta = std::max(eta, 0.5 * s->desc.newton_tol * s->r0 / std::max(s->rk, 1e-300));
-    eta = std::min(std::max(eta, s->desc.krylov_rtol), ETA_MAX);
-  }
-  s->eta_prev = eta;
   const int nblk = (s->cap + KTPB - 1) / KTPB;
-  cudaEventRecord(s->ev[1], st);
   KrylovVecs<D, T> v = vecview<D, T>(s);
-  double tol2 = eta * eta * s->rk * s->rk;
-  int kit = 0, kstat = 0;
-  double kres2 = 0.0;
+  double tol2 = eta * eta * rnorm * rnorm;
+  kit = 0;
+  kstat = 0;
+  kres2 = 0.0;
   if (s->gm > 0) {
-    gmres_solve<D, T, B>(s, K, v.x, eta * s->rk, nblk, kit, kstat, kres2);
+    gmres_solve<D, T, B>(s, K, v.x, eta * rnorm, nblk, kit, kstat, kres2);
   } else {
-  ck(launch_bicgstab_init<D, T, B>(K, s->d_r, s->d_fixed, v, s->d_S, tol2, s->desc.krylov_maxit, nblk, st),
+  ck(launch_bicgstab_init<D, T, B>(K, s->krhs, s->d_fixed, v, s->d_S, tol2, s->desc.krylov_maxit, nblk, st),
      "krylov init");
   const int pblk = std::min(s->pblocks, std::max(1, (s->nrow * 4 + 511) / 512));
   if (s->pblocks > 0) {
@@ -531,7 +516,7 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
       // restart from the true residual b - J x; when the recurrence reported
       // convergence this also checks it (the recurrence residual can drift
       // from the true one on ill-conditioned systems such as u-p)
-      ck(launch_bicgstab_restart<D, T, B>(s->G, K, s->d_r, s->d_fixed, v, s->d_S, tol2,
+      ck(launch_bicgstab_restart<D, T, B>(s->G, K, s->krhs, s->d_fixed, v, s->d_S, tol2,
                                        s->desc.krylov_maxit - kit, nblk, st),
          "krylov restart");
       s->launches += 1;
@@ -547,6 +532,40 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
   }
   kres2 = s->h_S->rr_last;
   }
+}
+
+template <int D, class T, int B>
+void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
+  if (!s->staged) fail(MPM_ERR_STATE, "no load step staged (call mpm_begin_step)");
+  cudaStream_t st = s->st;
+  DevMatrix<T> K = matview<T>(s);
+  cudaEventRecord(s->ev[0], st);
+  assemble_impl<D, T, B>(s);
+  // linear tolerance: fixed, or Eisenstat-Walker choice 2 (gamma 0.9,
+  // alpha 2) capped at ETA_MAX = 1e-2: with the classical cap of 0.1 loose
+  // steps through the plastic zone made Newton diverge on footing problems.
+  double eta = s->desc.krylov_rtol;
+  if (s->desc.forcing == MPM_FORCING_EW) {
+    constexpr double ETA_MAX = 1e-2;
+    if (s->k == 0) {
+      eta = ETA_MAX;
+    } else {
+      double ratio = s->rk / s->rprev;
+      eta = 0.9 * ratio * ratio;
+      double safe = 0.9 * s->eta_prev * s->eta_prev;
+      if (safe > 0.1) eta = std::max(eta, safe);
+    }
+    // no need to solve below what the Newton tolerance asks of this step
+    eta = std::max(eta, 0.5 * s->desc.newton_tol * s->r0 / std::max(s->rk, 1e-300));
+    eta = std::min(std::max(eta, s->desc.krylov_rtol), ETA_MAX);
+  }
+  s->eta_prev = eta;
+  const int nblk = (s->cap + KTPB - 1) / KTPB;
+  cudaEventRecord(s->ev[1], st);
+  KrylovVecs<D, T> v = vecview<D, T>(s);
+  int kit = 0, kstat = 0;
+  double kres2 = 0.0;
+  krylov_solve<D, T, B>(s, eta, s->rk, kit, kstat, kres2);
   const double krel = (s->rk > 0) ? std::sqrt(std::max(kres2, 0.0)) / s->rk : 0.0;
   // step-length limit (reading): a Newton correction that would move a node
   // by more than one cell width h is scaled down to h (a near-singular J, as
@@ -664,6 +683,104 @@ void time_spmv_impl(mpm_scene* s, int reps, double* ms, double* bytes) {
   *bytes = (double)nnzb * B * B * ts + (double)s->nrow * B * ts * 2.0 + (double)s->nrow * 4.0;
 }
 
+// Adjoint of the staged step at its current (converged) iterate; see
+// mpm_adjoint.cu for the equations.  K is left holding J^T.
+template <int D, class T, int B>
+void adjoint_impl(mpm_scene* s, const double* dL_dU, const double* dL_dx, double* gE, double* gPhi,
+                  double* gK) {
+  if (!s->staged) fail(MPM_ERR_STATE, "no converged step staged (run the Newton iterations, then the adjoint)");
+  cudaStream_t st = s->st;
+  ck(cudaMemsetAsync(s->d_err, 0, sizeof(int), st), "memset");
+  assemble_impl<D, T, B>(s);
+  DevMatrix<T> K = matview<T>(s);
+  const int S = stencil_slots(D);
+  const size_t nval = (size_t)s->cap * S * B * B;
+  if (s->kt_cap != s->cap) {
+    s->dfree(s->d_KT);
+    s->d_KT = s->dalloc<T>(nval);
+    s->kt_cap = s->cap;
+  }
+  ck(launch_transpose_blocks<D, T, B>(s->G, K, s->d_node2row, (T*)s->d_KT, s->nrow, st), "transpose");
+  ck(cudaMemcpyAsync(s->d_K, s->d_KT, nval * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy");
+  ck(launch_block_jacobi<D, T, B>(s->G, K, s->nrow, s->d_err, st), "block jacobi");
+  s->launches += 2;
+  // right-hand side: dL/du on the nodes, plus a particle-displacement
+  // gradient mapped with the weights; b = -S g
+  double* d_g = s->dalloc<double>(s->ndof);
+  double* d_b = s->dalloc<double>(s->ndof);
+  if (dL_dU) ck(cudaMemcpyAsync(d_g, dL_dU, s->ndof * sizeof(double), cudaMemcpyHostToDevice, st), "upload");
+  else ck(cudaMemsetAsync(d_g, 0, s->ndof * sizeof(double), st), "memset");
+  double* d_x = nullptr;
+  if (dL_dx && s->np > 0) {
+    d_x = s->dalloc<double>((size_t)s->np * 3);
+    ck(cudaMemcpyAsync(d_x, dL_dx, (size_t)s->np * 3 * sizeof(double), cudaMemcpyHostToDevice, st), "upload");
+    ck(launch_loss_p2g<D, B>(s->P, s->G, d_x, d_g, s->d_err, st), "loss p2g");
+    s->launches += 1;
+  }
+  ck(launch_adjoint_rhs<D, B>(d_g, d_b, s->ndof, s->up ? s->psc : 1.0, st), "rhs");
+  ck(cudaMemsetAsync(s->d_norm, 0, sizeof(double), st), "memset");
+  ck(launch_norm_free<B>(d_b, s->d_rows, s->nrow, s->d_fixed, s->d_norm, st), "norm");
+  ck(cudaMemcpyAsync(s->h_dbl + 4, s->d_norm, sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
+  ck(cudaStreamSynchronize(st), "sync");
+  s->launches += 2;
+  const double bnorm = std::sqrt(s->h_dbl[4]);
+  KrylovVecs<D, T> v = vecview<D, T>(s);
+  int kit = 0, kstat = 0;
+  double kres2 = 0.0;
+  if (bnorm > 0) {
+    s->krhs = d_b;
+    try {
+      krylov_solve<D, T, B>(s, s->mixed ? 1e-6 : 1e-12, bnorm, kit, kstat, kres2);
+    } catch (...) {
+      s->krhs = s->d_r;
+      throw;
+    }
+    s->krhs = s->d_r;
+  } else {
+    ck(cudaMemsetAsync((T*)s->d_vec + s->vpad, 0, s->ndof * sizeof(T), st), "memset");
+  }
+  s->adj_kit = kit;
+  double *d_gE = gE ? s->dalloc<double>(std::max(s->np, 1)) : nullptr;
+  double *d_gP = gPhi ? s->dalloc<double>(std::max(s->np, 1)) : nullptr;
+  double *d_gK = gK ? s->dalloc<double>(s->nmat) : nullptr;
+  if (d_gK) ck(cudaMemsetAsync(d_gK, 0, s->nmat * sizeof(double), st), "memset");
+  ck(launch_param_grad<D, T, B>(s->P, s->G, s->d_mats, s->d_du, v.x, s->up ? s->psc : 1.0, d_gE, d_gP, d_gK,
+                                s->d_err, st),
+     "parameter gradient");
+  s->launches += 1;
+  ck(cudaMemcpyAsync(s->h_int + 2, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
+  ck(cudaStreamSynchronize(st), "sync");
+  if (gE && s->np) ck(cudaMemcpy(gE, d_gE, s->np * sizeof(double), cudaMemcpyDeviceToHost), "download");
+  if (gPhi && s->np) ck(cudaMemcpy(gPhi, d_gP, s->np * sizeof(double), cudaMemcpyDeviceToHost), "download");
+  if (gK) ck(cudaMemcpy(gK, d_gK, s->nmat * sizeof(double), cudaMemcpyDeviceToHost), "download");
+  s->dfree(d_g);
+  s->dfree(d_b);
+  s->dfree(d_x);
+  s->dfree(d_gE);
+  s->dfree(d_gP);
+  s->dfree(d_gK);
+  check_err_bits(s);
+  // a solve that stopped early (breakdown near convergence, the iteration
+  // limit) is accepted when its residual is within a loose bound of the target
+  const double accept = s->mixed ? 1e-5 : 1e-8;
+  if (kstat != 0 && !(std::sqrt(std::max(kres2, 0.0)) <= accept * bnorm))
+    fail(kstat == 1 ? MPM_ERR_KRYLOV_MAXIT : MPM_ERR_KRYLOV_BREAKDOWN, "adjoint Krylov solve failed");
+}
+
+template <int D, class T, int B>
+void particle_increment_impl(mpm_scene* s, double* out) {
+  if (!s->staged) fail(MPM_ERR_STATE, "no load step staged");
+  double* d_o = s->dalloc<double>((size_t)std::max(s->np, 1) * 3);
+  ck(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->st), "memset");
+  ck(launch_particle_increment<D, B>(s->P, s->G, s->d_du, d_o, s->d_err, s->st), "increment");
+  s->launches += 1;
+  ck(cudaMemcpyAsync(s->h_int + 2, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->st), "copy");
+  ck(cudaStreamSynchronize(s->st), "sync");
+  if (s->np) ck(cudaMemcpy(out, d_o, (size_t)s->np * 3 * sizeof(double), cudaMemcpyDeviceToHost), "download");
+  s->dfree(d_o);
+  check_err_bits(s);
+}
+
 // dispatch on (dim, precision, values per node)
 template <template <int, class, int> class F, class... Args>
 void dispatch(mpm_scene* s, Args... args) {
@@ -684,6 +801,14 @@ template <int D, class T, int B> struct CommitF { static void run(mpm_scene* s) 
 template <int D, class T, int B> struct SetDuF { static void run(mpm_scene* s, const double* du) { set_du_impl<D, T, B>(s, du); } };
 template <int D, class T, int B> struct TimeSpmvF {
   static void run(mpm_scene* s, int reps, double* ms, double* bytes) { time_spmv_impl<D, T, B>(s, reps, ms, bytes); }
+};
+template <int D, class T, int B> struct AdjointF {
+  static void run(mpm_scene* s, const double* a, const double* b, double* c, double* d, double* e) {
+    adjoint_impl<D, T, B>(s, a, b, c, d, e);
+  }
+};
+template <int D, class T, int B> struct IncrementF {
+  static void run(mpm_scene* s, double* o) { particle_increment_impl<D, T, B>(s, o); }
 };
 template <int D, class T, int B> struct AssembleF {
   static void run(mpm_scene* s) {
@@ -790,6 +915,7 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
       c.M = q.M;
       c.lmk = q.lambda_cc - q.kappa_cc;
       c.pc0 = q.pc0;
+      c.dkdt_dk = (s->up && q.gamma_w > 0) ? desc->dt / q.gamma_w : 0.0;
       s->hmats.push_back(c);
       if (s->up && (!(q.k_hyd >= 0) || !(q.gamma_w > 0)))
         fail(MPM_ERR_INVALID_ARG, "u-p materials need k_hyd >= 0 and gamma_w > 0");
@@ -896,6 +1022,7 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
     s->d_duprev = s->dalloc<double>(s->ndof);
     s->d_absmax = s->dalloc<unsigned long long>(1);
     s->d_r = s->dalloc<double>(s->ndof);
+    s->krhs = s->d_r;
     s->d_bcval = s->dalloc<double>(s->ndof);
     s->d_grav = s->dalloc<double>(3);
     s->d_norm = s->dalloc<double>(1);
@@ -1225,6 +1352,53 @@ mpm_status mpm_get_particles(const mpm_scene* cs, double* x, double* be, double*
       ck(cudaStreamSynchronize(s->st), "sync");
       ck(cudaMemcpy(tau, d_tau, (size_t)np * 9 * sizeof(double), cudaMemcpyDeviceToHost), "download");
       s->dfree(d_tau);
+    }
+  });
+}
+
+mpm_status mpm_adjoint(mpm_scene* s, const double* dL_dU, const double* dL_dx, double* grad_E, double* grad_phi,
+                       double* grad_k) {
+  if (!s) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] { dispatch<AdjointF>(s, dL_dU, dL_dx, grad_E, grad_phi, grad_k); });
+}
+
+mpm_status mpm_get_particle_increment(const mpm_scene* cs, double* du_p) {
+  mpm_scene* s = const_cast<mpm_scene*>(cs);
+  if (!s || !du_p) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] { dispatch<IncrementF>(s, du_p); });
+}
+
+mpm_status mpm_set_params(mpm_scene* s, const double* E_p, const double* phi_p, const double* k_p) {
+  if (!s) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] {
+    const int np = s->np;
+    for (int p = 0; p < np; ++p) {
+      if (E_p && !(E_p[p] > 0)) fail(MPM_ERR_INVALID_ARG, "E_p must be positive");
+      if (phi_p && !(phi_p[p] >= 0 && phi_p[p] < 90)) fail(MPM_ERR_INVALID_ARG, "phi_p must be in [0, 90)");
+      if (k_p && !(k_p[p] >= 0)) fail(MPM_ERR_INVALID_ARG, "k_p must be >= 0");
+    }
+    if (k_p && !s->up) fail(MPM_ERR_INVALID_ARG, "k_p needs a u-p scene");
+    ck(cudaStreamSynchronize(s->st), "sync");
+    s->staged = false;
+    if (np == 0) return;
+    std::vector<int> orig(np), mat(np);
+    ck(cudaMemcpy(orig.data(), s->P.orig, np * sizeof(int), cudaMemcpyDeviceToHost), "download");
+    ck(cudaMemcpy(mat.data(), s->P.mat, np * sizeof(int), cudaMemcpyDeviceToHost), "download");
+    std::vector<double> h(np);
+    auto up = [&](double* d) {
+      ck(cudaMemcpy(d, h.data(), np * sizeof(double), cudaMemcpyHostToDevice), "upload");
+    };
+    if (E_p) {
+      for (int p = 0; p < np; ++p) h[p] = E_p[orig[p]];
+      up(s->P.Ep);
+    }
+    if (phi_p) {
+      for (int p = 0; p < np; ++p) h[p] = phi_p[orig[p]];
+      up(s->P.phip);
+    }
+    if (k_p) {
+      for (int p = 0; p < np; ++p) h[p] = k_p[orig[p]] * s->hmats[mat[p]].dkdt_dk;
+      up(s->P.kdt);
     }
   });
 }

@@ -21,6 +21,7 @@ struct MatC {
   double phi, psi, coh;    // degrees, degrees, Pa
   double M, lmk;           // Cam-Clay slope, lambda - kappa
   double pc0;
+  double dkdt_dk;          // u-p: d(mobility x time step) / d(hydraulic conductivity) = dt / gamma_w
 };
 
 struct Lame { double mu, lam; };

@@ -239,6 +239,23 @@ template <int D, class T>
 cudaError_t launch_bicgstab_persistent(const DevGrid& G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S,
                                        double* part, unsigned int* bar, int* err, int nblocks, cudaStream_t st);
 
+// adjoint of a converged step (mpm_adjoint.cu)
+template <int D, class T, int B>
+cudaError_t launch_transpose_blocks(const DevGrid& G, DevMatrix<T> K, const int* node2row, T* out, int nrow,
+                                    cudaStream_t st);
+template <int D, int B>
+cudaError_t launch_loss_p2g(const DevParticles& P, const DevGrid& G, const double* dLdx, double* g, int* err,
+                            cudaStream_t st);
+template <int D, int B>
+cudaError_t launch_adjoint_rhs(const double* g, double* b, long long ndof, double psc, cudaStream_t st);
+template <int D, int B>
+cudaError_t launch_particle_increment(const DevParticles& P, const DevGrid& G, const double* U, double* out,
+                                      int* err, cudaStream_t st);
+template <int D, class T, int B>
+cudaError_t launch_param_grad(const DevParticles& P, const DevGrid& G, const MatC* mats, const double* U,
+                              const T* mu, double psc, double* gE, double* gPhi, double* gK, int* err,
+                              cudaStream_t st);
+
 // GMRES(m) with classical Gram-Schmidt applied twice
 constexpr int GMRES_MMAX = 64;
 struct GmresState {

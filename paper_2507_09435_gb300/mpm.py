@@ -106,7 +106,8 @@ _lib = None
 EXPORTS = ["mpm_create_scene", "mpm_set_gravity", "mpm_set_dirichlet", "mpm_begin_step", "mpm_newton_step",
            "mpm_set_du", "mpm_assemble", "mpm_commit_step", "mpm_solve_step", "mpm_get_residual", "mpm_get_du", "mpm_get_mass",
            "mpm_get_counts", "mpm_get_jacobian_bsr", "mpm_get_particles", "mpm_get_pressure",
-           "mpm_set_traction", "mpm_kernel_launches",
+           "mpm_set_traction", "mpm_kernel_launches", "mpm_set_params", "mpm_get_particle_increment",
+           "mpm_adjoint",
            "mpm_time_spmv", "mpm_set_particles", "mpm_residual_norm_noalloc", "mpm_noalloc_last_error",
            "mpm_footprint_bytes",
            "mpm_destroy_scene", "mpm_status_string", "mpm_last_error",
@@ -142,6 +143,9 @@ def lib(build: bool = True):
     L.mpm_get_particles.argtypes = [_P, _D, _D, _D, _D, _D]
     L.mpm_get_pressure.argtypes = [_P, _D]
     L.mpm_set_traction.argtypes = [_P, ctypes.c_int, _I, _D]
+    L.mpm_set_params.argtypes = [_P, _D, _D, _D]
+    L.mpm_get_particle_increment.argtypes = [_P, _D]
+    L.mpm_adjoint.argtypes = [_P, _D, _D, _D, _D, _D]
     L.mpm_kernel_launches.argtypes = [_P, _LL]
     L.mpm_set_particles.argtypes = [_P, _D, _D, _D]
     L.mpm_residual_norm_noalloc.argtypes = [_P, _P, ctypes.c_int, _P, ctypes.c_int, _D, _P]
@@ -350,6 +354,27 @@ def mpm_set_traction(h, particle, f):
     _check(lib().mpm_set_traction(h, int(particle.size), _p(particle, _I), _p(f)), h)
 
 
+def mpm_set_params(h, E_p=None, phi_p=None, k_p=None):
+    _check(lib().mpm_set_params(h, _p(_f64(E_p)), _p(_f64(phi_p)), _p(_f64(k_p))), h)
+
+
+def mpm_get_particle_increment(h, np_):
+    out = np.zeros(np_ * 3)
+    _check(lib().mpm_get_particle_increment(h, _p(out)), h)
+    return out.reshape(np_, 3)
+
+
+def mpm_adjoint(h, np_, nmat, dL_dU=None, dL_dx=None, want_E=True, want_phi=True, want_k=False):
+    """dL/dE_p, dL/dphi_p (np each) and dL/dk per material of the staged,
+    converged step (see include/mpm.h)."""
+    gE = np.zeros(max(np_, 1)) if want_E else None
+    gP = np.zeros(max(np_, 1)) if want_phi else None
+    gK = np.zeros(nmat) if want_k else None
+    x = None if dL_dx is None else _f64(np.asarray(dL_dx, dtype=np.float64).reshape(np_, 3))
+    _check(lib().mpm_adjoint(h, _p(_f64(dL_dU)), _p(x), _p(gE), _p(gP), _p(gK)), h)
+    return (gE[:np_] if gE is not None else None, gP[:np_] if gP is not None else None, gK)
+
+
 def mpm_set_particles(h, be=None, pc=None, F=None):
     _check(lib().mpm_set_particles(h, _p(_f64(be)), _p(_f64(pc)), _p(_f64(F))), h)
 
@@ -469,6 +494,31 @@ class GpuScene:
 
     def pressure(self):
         return mpm_get_pressure(self.h, self.np)
+
+    def particle_increment(self):
+        return mpm_get_particle_increment(self.h, self.np)
+
+    def set_params(self, E_p=None, phi_p=None, k_p=None):
+        mpm_set_params(self.h, E_p, phi_p, k_p)
+
+    def solve_staged(self, step, tol=None, maxit=None):
+        """Begin the step and run Newton iterations to the scene's tolerance
+        without committing (for the adjoint).  Returns the relative residual
+        history."""
+        tol = self.desc.newton_tol if tol is None else tol
+        maxit = self.desc.newton_maxit if maxit is None else maxit
+        self.begin(step)
+        hist = [1.0]
+        for _ in range(maxit):
+            rel = self.newton().rel_residual
+            hist.append(rel)
+            if rel <= tol:
+                return hist
+        raise MPMError(4, f"Newton did not reach {tol} (last {hist[-1]:.3e})")
+
+    def adjoint(self, dL_dU=None, dL_dx=None, want_E=True, want_phi=True, want_k=False):
+        return mpm_adjoint(self.h, self.np, len(self.scene.materials), dL_dU=dL_dU, dL_dx=dL_dx,
+                           want_E=want_E, want_phi=want_phi, want_k=want_k)
 
     def particles(self, **kw):
         return mpm_get_particles(self.h, self.np, **kw)

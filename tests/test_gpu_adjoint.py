@@ -1,0 +1,141 @@
+"""Adjoint of a converged implicit step (mpm_adjoint) against the oracle's
+gradient by its definition (central differences of the oracle's converged
+solve, per parameter), against directional differences of the GPU's own
+solve, for the conductivity of a u-p column, and through the
+torch.autograd wrapper."""
+import numpy as np
+import pytest
+
+from oracle import mpm_oracle as O
+from paper_2507_09435_gb300 import mpm, scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _dp_scene():
+    """A small Drucker-Prager block on a fixed base, compressed from the top
+    by 1 % so that part of it yields."""
+    sc = S.tiny_scene(2, S.MODEL_NH_DP, seed=41, ncell=3, ppc=2, jitter=0.1)
+    nx1, ny1 = sc.n[0] + 1, sc.n[1] + 1
+    nodes = np.arange(sc.nnode)
+    ix, iy = nodes % nx1, (nodes // nx1) % ny1
+    base = nodes[iy <= 3]
+    top = nodes[iy >= 6]
+    dof = np.concatenate([base * 2, base * 2 + 1, top * 2, top * 2 + 1])
+    val = np.concatenate([np.zeros(2 * base.size), np.zeros(top.size), np.full(top.size, -3e-3)])
+    order = np.argsort(dof)
+    step = S.LoadStep(dof[order].astype(np.int64), val[order], (0.0, -9.81, 0.0))
+    return sc, step
+
+
+def test_adjoint_matches_oracle_gradient_fp64():
+    sc, step = _dp_scene()
+    rng = np.random.default_rng(5)
+    c = rng.standard_normal((sc.np, 3))
+    c[:, 2] = 0.0
+
+    def loss(du, dup):
+        return float(np.sum(c * dup))
+
+    gs = mpm.GpuScene(sc, newton_tol=1e-12, newton_maxit=30, forcing=mpm.MPM_FORCING_FIXED, krylov_rtol=1e-13)
+    gs.solve_staged(step)
+    gE, gP, _ = gs.adjoint(dL_dx=c)
+    dup = gs.particle_increment()
+    # the loss on the GPU's increments equals the oracle's at the same state
+    make = lambda: O.OracleScene.from_scene(sc)
+    out = make().solve_step(step.dof, step.value, step.gravity, tol=1e-13, commit=False)
+    orc = make()
+    assert np.abs(dup - O.particle_increments(orc, out["du"])).max() < 1e-9 * np.abs(dup).max()
+    _, _, modes = orc.residual(out["du"], with_mode=True)
+    assert (modes > 0).sum() >= 3, "the step should drive particles plastic"
+    idx = list(range(0, sc.np, max(1, sc.np // 12)))
+    fdE = np.array([O.step_gradient_fd(make, step, loss, "E", p) for p in idx])
+    fdP = np.array([O.step_gradient_fd(make, step, loss, "phi", p) for p in idx])
+    assert np.abs(gE[idx] - fdE).max() <= 1e-5 * np.abs(fdE).max(), (gE[idx], fdE)
+    assert np.abs(gP[idx] - fdP).max() <= 1e-5 * max(np.abs(fdP).max(), 1e-300), (gP[idx], fdP)
+    gs.close()
+
+
+@pytest.mark.parametrize("precision", [mpm.MPM_FP64, mpm.MPM_MIXED])
+def test_adjoint_directional_derivative_footing(precision):
+    """Coarse footing, first settlement step: the adjoint's directional
+    derivative along random E and phi directions against central differences
+    of the GPU's FP64 solve."""
+    sc = S.footing(nx=48, ny=24, h=0.5, nsteps=20, settle_frac=0.1)
+    rng = np.random.default_rng(9)
+    c = rng.standard_normal((sc.np, 3))
+    c[:, 2] = 0.0
+    E0 = np.full(sc.np, sc.materials[0].E)
+    P0 = np.full(sc.np, sc.materials[0].phi)
+    vE = rng.standard_normal(sc.np) * E0
+    vP = rng.standard_normal(sc.np)
+
+    def solve(E, P, prec):
+        gs = mpm.GpuScene(sc, precision=prec, newton_tol=1e-12 if prec == mpm.MPM_FP64 else 1e-9,
+                          newton_maxit=32, forcing=mpm.MPM_FORCING_FIXED,
+                          krylov_rtol=1e-13 if prec == mpm.MPM_FP64 else 1e-7)
+        gs.solve_step(sc.steps[0])          # geostatic step (committed)
+        gs.set_params(E_p=E, phi_p=P)
+        gs.solve_staged(sc.steps[1])
+        return gs
+
+    gs = solve(E0, P0, precision)
+    gE, gP, _ = gs.adjoint(dL_dx=c)
+    gs.close()
+    eps = 1e-6
+    for v, g, which in ((vE, gE, "E"), (vP, gP, "phi")):
+        Lp, Lm = [], []
+        for sgn, acc in ((1.0, Lp), (-1.0, Lm)):
+            E = E0 + sgn * eps * vE if which == "E" else E0
+            P = P0 + sgn * eps * vP if which == "phi" else P0
+            g2 = solve(E, P, mpm.MPM_FP64)
+            acc.append(float(np.sum(c * g2.particle_increment())))
+            g2.close()
+        fd = (Lp[0] - Lm[0]) / (2 * eps)
+        ad = float(np.dot(g, v))
+        tol = 1e-4 if precision == mpm.MPM_FP64 else 1e-3
+        assert abs(ad - fd) <= tol * abs(fd), (which, ad, fd)
+
+
+def test_adjoint_conductivity_terzaghi():
+    """u-p column: dL/dk (per material) for a loss on the nodal pressures and
+    displacements, against the oracle's central difference in log k."""
+    h = 0.5
+    sc = S.terzaghi(ncell=20, dt=0.5 * h * h / 1.8e-6, nsteps=2)
+    B = sc.B
+    rng = np.random.default_rng(3)
+    cU = rng.standard_normal(sc.nnode * B)
+    cU[2::3] *= 1e-3      # pressure entries on the scale of 1/Pa vs 1/m
+
+    def loss(du, dup):
+        return float(np.dot(cU, du))
+
+    gs = mpm.GpuScene(sc, krylov=mpm.MPM_GMRES, newton_tol=1e-11, newton_maxit=30,
+                      forcing=mpm.MPM_FORCING_FIXED, krylov_rtol=1e-13)
+    gs.solve_staged(sc.steps[0], tol=1e-11)
+    _, _, gK = gs.adjoint(dL_dU=cU, want_E=False, want_phi=False, want_k=True)
+    make = lambda: O.OracleScene.from_scene(sc)
+    fd = O.step_gradient_fd(make, sc.steps[0], loss, "k", 0, rel=1e-5, tol=1e-12)
+    k = sc.materials[0].k_hyd
+    assert abs(gK[0] * k - fd) <= 1e-4 * abs(fd), (gK[0] * k, fd)
+    gs.close()
+
+
+def test_autograd_function_matches_adjoint():
+    import torch
+    from paper_2507_09435_gb300.autograd import ImplicitStep
+    sc, step = _dp_scene()
+    gs = mpm.GpuScene(sc, newton_tol=1e-12, newton_maxit=30, forcing=mpm.MPM_FORCING_FIXED, krylov_rtol=1e-13)
+    E = torch.full((sc.np,), sc.materials[0].E, dtype=torch.float64, requires_grad=True)
+    P = torch.full((sc.np,), sc.materials[0].phi, dtype=torch.float64, requires_grad=True)
+    du = ImplicitStep.apply(gs, step, E, P)
+    w = torch.linspace(-1.0, 1.0, du.numel(), dtype=torch.float64).reshape(du.shape)
+    (du * w).sum().backward()
+    c = np.zeros((sc.np, 3))
+    c[:, :2] = w.numpy()
+    gE, gP, _ = gs.adjoint(dL_dx=c)
+    # two adjoint solves agree to their tolerance (atomic summation order differs)
+    assert np.abs(E.grad.numpy() - gE).max() <= 1e-8 * np.abs(gE).max()
+    assert np.abs(P.grad.numpy() - gP).max() <= 1e-8 * np.abs(gP).max()
+    gs.commit()
+    gs.close()
