@@ -256,7 +256,7 @@ def serving_measure(nreq, slots, precision, seed=2507_09435 + 4):
     svc = []
     for d in draws[:ncap]:
         sc, st = S.serving_scene(d)
-        t = sv1.submit(sc, steps=st, precision=precision, newton_maxit=40)
+        t = sv1.submit(sc, steps=st, precision=precision, newton_maxit=32)
         r = sv1.wait(t)
         svc.append(r.t_service_ms)
         sv1.release(t)
@@ -278,7 +278,7 @@ def serving_measure(nreq, slots, precision, seed=2507_09435 + 4):
             time.sleep(due - now)
         else:
             late = max(late, now - due)
-        tickets.append(sv.submit(sc, steps=st, precision=precision, newton_maxit=40))
+        tickets.append(sv.submit(sc, steps=st, precision=precision, newton_maxit=32))
         del sc, st
     res = [sv.wait(t) for t in tickets]
     wall = time.perf_counter() - t0
