@@ -260,6 +260,32 @@ mpm_status mpm_get_particle_increment(const mpm_scene* s, double* du_p);
 mpm_status mpm_adjoint(mpm_scene* s, const double* dL_dU, const double* dL_dx, double* grad_E,
                        double* grad_phi, double* grad_k);
 
+/* Reverse chain through a sequence of load steps.  Step n maps the committed
+ * particle state s_{n-1} = (x, be, pc, F) and the parameters to its converged
+ * increment U_n and to the committed state s_n.  To differentiate a loss of
+ * several steps, record s_{n-1} (mpm_get_particles) and U_n (mpm_get_du) on
+ * the way forward; then, for n = N .. 1: restore s_{n-1} (mpm_set_state),
+ * stage step n (mpm_set_dirichlet, mpm_set_gravity, mpm_begin_step), set its
+ * converged increment (mpm_set_du) and call this.  On entry sbar_* hold the
+ * adjoint dL/ds_n of the end-of-step state (caller order: x np*3, be np*6,
+ * pc np, F np*9; zeros for the last step of a loss on increments only); on
+ * exit they hold dL/ds_{n-1}.  dL_dU / dL_dx are the loss's direct gradients
+ * on this step's increment as in mpm_adjoint.  The parameter gradients are
+ * ADDED to grad_E, grad_phi (np) and grad_k (nmat) (each may be NULL).  The
+ * per-particle partial derivatives of the commit map and of the residual
+ * contribution with respect to the particle state and parameters are central
+ * differences of the FP64 particle update (relative steps 1e-6 to 1e-7); the
+ * transposed solve is as in mpm_adjoint.  Errors as mpm_adjoint. */
+mpm_status mpm_adjoint_step(mpm_scene* s, const double* dL_dU, const double* dL_dx, double* sbar_x,
+                            double* sbar_be, double* sbar_pc, double* sbar_F, double* grad_E,
+                            double* grad_phi, double* grad_k);
+
+/* Overwrite the committed particle state including positions (caller order;
+ * x np*3, then as mpm_set_particles; any pointer may be NULL).  Unstages a
+ * staged step.  MPM_ERR_INVALID_ARG for a position outside the grid
+ * interior or an invalid be / F. */
+mpm_status mpm_set_state(mpm_scene* s, const double* x, const double* be, const double* pc, const double* F);
+
 /* MPM_UP: pore pressure of each particle after the last commit,
  * p_p = sum_i w_ip p_i (caller's order, np values).  MPM_ERR_INVALID_ARG for a
  * single-phase scene. */

@@ -767,6 +767,104 @@ void adjoint_impl(mpm_scene* s, const double* dL_dU, const double* dL_dx, double
     fail(kstat == 1 ? MPM_ERR_KRYLOV_MAXIT : MPM_ERR_KRYLOV_BREAKDOWN, "adjoint Krylov solve failed");
 }
 
+// One step of the reverse chain (see mpm_adjoint_steps.cu): on entry sb
+// holds the adjoint of the end-of-step state (19 per particle, caller order),
+// on exit that of the start-of-step state; the parameter gradients are added
+// to gE, gPhi (np) and gK (nmat).
+template <int D, class T, int B>
+void adjoint_step_impl(mpm_scene* s, const double* dL_dU, const double* dL_dx, double* sb, double* gE, double* gPhi,
+                       double* gK) {
+  if (!s->staged) fail(MPM_ERR_STATE, "no converged step staged (restore the state, stage the step, set du)");
+  cudaStream_t st = s->st;
+  ck(cudaMemsetAsync(s->d_err, 0, sizeof(int), st), "memset");
+  assemble_impl<D, T, B>(s);
+  DevMatrix<T> K = matview<T>(s);
+  const int S = stencil_slots(D);
+  const size_t nval = (size_t)s->cap * S * B * B;
+  if (s->kt_cap != s->cap) {
+    s->dfree(s->d_KT);
+    s->d_KT = s->dalloc<T>(nval);
+    s->kt_cap = s->cap;
+  }
+  ck(launch_transpose_blocks<D, T, B>(s->G, K, s->d_node2row, (T*)s->d_KT, s->nrow, st), "transpose");
+  ck(cudaMemcpyAsync(s->d_K, s->d_KT, nval * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy");
+  ck(launch_block_jacobi<D, T, B>(s->G, K, s->nrow, s->d_err, st), "block jacobi");
+  const size_t np = (size_t)std::max(s->np, 1);
+  double* d_g = s->dalloc<double>(s->ndof);
+  double* d_b = s->dalloc<double>(s->ndof);
+  double* d_sb = s->dalloc<double>(np * 19);
+  double* d_so = s->dalloc<double>(np * 19);
+  double* d_gE = s->dalloc<double>(np);
+  double* d_gP = s->dalloc<double>(np);
+  double* d_gK = s->dalloc<double>(s->nmat);
+  if (dL_dU) ck(cudaMemcpyAsync(d_g, dL_dU, s->ndof * sizeof(double), cudaMemcpyHostToDevice, st), "upload");
+  else ck(cudaMemsetAsync(d_g, 0, s->ndof * sizeof(double), st), "memset");
+  if (s->np > 0) ck(cudaMemcpyAsync(d_sb, sb, (size_t)s->np * 19 * sizeof(double), cudaMemcpyHostToDevice, st), "upload");
+  ck(cudaMemsetAsync(d_gE, 0, np * sizeof(double), st), "memset");
+  ck(cudaMemsetAsync(d_gP, 0, np * sizeof(double), st), "memset");
+  ck(cudaMemsetAsync(d_gK, 0, s->nmat * sizeof(double), st), "memset");
+  double* d_x = nullptr;
+  if (dL_dx && s->np > 0) {
+    d_x = s->dalloc<double>(np * 3);
+    ck(cudaMemcpyAsync(d_x, dL_dx, (size_t)s->np * 3 * sizeof(double), cudaMemcpyHostToDevice, st), "upload");
+    ck(launch_loss_p2g<D, B>(s->P, s->G, d_x, d_g, s->d_err, st), "loss p2g");
+  }
+  const double psc = s->up ? s->psc : 1.0;
+  ck(launch_adj_commit_vjp<D, T, B>(s->P, s->G, s->d_mats, s->d_grav, s->d_du, psc, d_sb, d_g, s->d_err, st),
+     "commit vjp");
+  ck(launch_adjoint_rhs<D, B>(d_g, d_b, s->ndof, psc, st), "rhs");
+  ck(cudaMemsetAsync(s->d_norm, 0, sizeof(double), st), "memset");
+  ck(launch_norm_free<B>(d_b, s->d_rows, s->nrow, s->d_fixed, s->d_norm, st), "norm");
+  ck(cudaMemcpyAsync(s->h_dbl + 4, s->d_norm, sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
+  ck(cudaStreamSynchronize(st), "sync");
+  s->launches += 6;
+  const double bnorm = std::sqrt(s->h_dbl[4]);
+  KrylovVecs<D, T> v = vecview<D, T>(s);
+  int kit = 0, kstat = 0;
+  double kres2 = 0.0;
+  if (bnorm > 0) {
+    s->krhs = d_b;
+    try {
+      krylov_solve<D, T, B>(s, s->mixed ? 1e-6 : 1e-12, bnorm, kit, kstat, kres2);
+    } catch (...) {
+      s->krhs = s->d_r;
+      throw;
+    }
+    s->krhs = s->d_r;
+  } else {
+    ck(cudaMemsetAsync((T*)s->d_vec + s->vpad, 0, s->ndof * sizeof(T), st), "memset");
+  }
+  s->adj_kit = kit;
+  ck(launch_adj_state_vjp<D, T, B>(s->P, s->G, s->d_mats, s->d_grav, s->d_du, v.x, psc, d_sb, d_so, d_gE, d_gP,
+                                   d_gK, s->d_err, st),
+     "state vjp");
+  s->launches += 1;
+  ck(cudaMemcpyAsync(s->h_int + 2, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
+  ck(cudaStreamSynchronize(st), "sync");
+  std::vector<double> h(np);
+  if (s->np > 0) {
+    ck(cudaMemcpy(sb, d_so, (size_t)s->np * 19 * sizeof(double), cudaMemcpyDeviceToHost), "download");
+    if (gE) {
+      ck(cudaMemcpy(h.data(), d_gE, s->np * sizeof(double), cudaMemcpyDeviceToHost), "download");
+      for (int p = 0; p < s->np; ++p) gE[p] += h[p];
+    }
+    if (gPhi) {
+      ck(cudaMemcpy(h.data(), d_gP, s->np * sizeof(double), cudaMemcpyDeviceToHost), "download");
+      for (int p = 0; p < s->np; ++p) gPhi[p] += h[p];
+    }
+  }
+  if (gK) {
+    std::vector<double> hk(s->nmat);
+    ck(cudaMemcpy(hk.data(), d_gK, s->nmat * sizeof(double), cudaMemcpyDeviceToHost), "download");
+    for (int m = 0; m < s->nmat; ++m) gK[m] += hk[m];
+  }
+  for (double* d : {d_g, d_b, d_sb, d_so, d_gE, d_gP, d_gK, d_x}) s->dfree(d);
+  check_err_bits(s);
+  const double accept = s->mixed ? 1e-5 : 1e-8;
+  if (kstat != 0 && !(std::sqrt(std::max(kres2, 0.0)) <= accept * bnorm))
+    fail(kstat == 1 ? MPM_ERR_KRYLOV_MAXIT : MPM_ERR_KRYLOV_BREAKDOWN, "adjoint Krylov solve failed");
+}
+
 template <int D, class T, int B>
 void particle_increment_impl(mpm_scene* s, double* out) {
   if (!s->staged) fail(MPM_ERR_STATE, "no load step staged");
@@ -805,6 +903,11 @@ template <int D, class T, int B> struct TimeSpmvF {
 template <int D, class T, int B> struct AdjointF {
   static void run(mpm_scene* s, const double* a, const double* b, double* c, double* d, double* e) {
     adjoint_impl<D, T, B>(s, a, b, c, d, e);
+  }
+};
+template <int D, class T, int B> struct AdjointStepF {
+  static void run(mpm_scene* s, const double* a, const double* b, double* sb, double* c, double* d, double* e) {
+    adjoint_step_impl<D, T, B>(s, a, b, sb, c, d, e);
   }
 };
 template <int D, class T, int B> struct IncrementF {
@@ -1360,6 +1463,56 @@ mpm_status mpm_adjoint(mpm_scene* s, const double* dL_dU, const double* dL_dx, d
                        double* grad_k) {
   if (!s) return MPM_ERR_INVALID_ARG;
   return guarded(s, [&] { dispatch<AdjointF>(s, dL_dU, dL_dx, grad_E, grad_phi, grad_k); });
+}
+
+mpm_status mpm_adjoint_step(mpm_scene* s, const double* dL_dU, const double* dL_dx, double* sbar_x,
+                            double* sbar_be, double* sbar_pc, double* sbar_F, double* grad_E, double* grad_phi,
+                            double* grad_k) {
+  if (!s || !sbar_x || !sbar_be || !sbar_pc || !sbar_F) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] {
+    const int np = s->np;
+    std::vector<double> sb((size_t)std::max(np, 1) * 19, 0.0);
+    for (int p = 0; p < np; ++p) {
+      double* q = &sb[(size_t)p * 19];
+      for (int a = 0; a < 3; ++a) q[a] = sbar_x[3 * p + a];
+      for (int k = 0; k < 6; ++k) q[3 + k] = sbar_be[6 * p + k];
+      q[9] = sbar_pc[p];
+      for (int k = 0; k < 9; ++k) q[10 + k] = sbar_F[9 * p + k];
+    }
+    dispatch<AdjointStepF>(s, dL_dU, dL_dx, sb.data(), grad_E, grad_phi, grad_k);
+    for (int p = 0; p < np; ++p) {
+      const double* q = &sb[(size_t)p * 19];
+      for (int a = 0; a < 3; ++a) sbar_x[3 * p + a] = q[a];
+      for (int k = 0; k < 6; ++k) sbar_be[6 * p + k] = q[3 + k];
+      sbar_pc[p] = q[9];
+      for (int k = 0; k < 9; ++k) sbar_F[9 * p + k] = q[10 + k];
+    }
+  });
+}
+
+mpm_status mpm_set_state(mpm_scene* s, const double* x, const double* be, const double* pc, const double* F) {
+  if (!s) return MPM_ERR_INVALID_ARG;
+  mpm_status rc = guarded(s, [&] {
+    const int np = s->np, D = s->D;
+    if (!x || np == 0) return;
+    for (int p = 0; p < np; ++p)
+      for (int a = 0; a < D; ++a) {
+        const double sg = (x[3 * p + a] - s->G.o[a]) / s->G.h;
+        const double fb = std::floor(sg - 0.5);
+        if (!(fb >= 0 && fb <= s->G.n[a] - 2)) fail(MPM_ERR_INVALID_ARG, "particle outside the grid interior");
+      }
+    ck(cudaStreamSynchronize(s->st), "sync");
+    s->staged = false;
+    std::vector<int> orig(np);
+    ck(cudaMemcpy(orig.data(), s->P.orig, np * sizeof(int), cudaMemcpyDeviceToHost), "download");
+    std::vector<double> h(np);
+    for (int a = 0; a < D; ++a) {
+      for (int p = 0; p < np; ++p) h[p] = x[3 * orig[p] + a];
+      ck(cudaMemcpy(s->P.x[a], h.data(), np * sizeof(double), cudaMemcpyHostToDevice), "upload");
+    }
+  });
+  if (rc != MPM_OK) return rc;
+  return mpm_set_particles(s, be, pc, F);
 }
 
 mpm_status mpm_get_particle_increment(const mpm_scene* cs, double* du_p) {

@@ -256,6 +256,17 @@ cudaError_t launch_param_grad(const DevParticles& P, const DevGrid& G, const Mat
                               const T* mu, double psc, double* gE, double* gPhi, double* gK, int* err,
                               cudaStream_t st);
 
+// reverse chain through load steps (mpm_adjoint_steps.cu); sbar: 19 per
+// particle in caller order (x 3, b_e 6, p_c 1, F 9)
+template <int D, class T, int B>
+cudaError_t launch_adj_commit_vjp(const DevParticles& P, const DevGrid& G, const MatC* mats, const double* grav,
+                                  const double* U, double psc, const double* sbar, double* g, int* err,
+                                  cudaStream_t st);
+template <int D, class T, int B>
+cudaError_t launch_adj_state_vjp(const DevParticles& P, const DevGrid& G, const MatC* mats, const double* grav,
+                                 const double* U, const T* mu, double psc, const double* sbar, double* sbar_out,
+                                 double* gE, double* gPhi, double* gK, int* err, cudaStream_t st);
+
 // GMRES(m) with classical Gram-Schmidt applied twice
 constexpr int GMRES_MMAX = 64;
 struct GmresState {

@@ -107,7 +107,7 @@ EXPORTS = ["mpm_create_scene", "mpm_set_gravity", "mpm_set_dirichlet", "mpm_begi
            "mpm_set_du", "mpm_assemble", "mpm_commit_step", "mpm_solve_step", "mpm_get_residual", "mpm_get_du", "mpm_get_mass",
            "mpm_get_counts", "mpm_get_jacobian_bsr", "mpm_get_particles", "mpm_get_pressure",
            "mpm_set_traction", "mpm_kernel_launches", "mpm_set_params", "mpm_get_particle_increment",
-           "mpm_adjoint",
+           "mpm_adjoint", "mpm_adjoint_step", "mpm_set_state",
            "mpm_time_spmv", "mpm_set_particles", "mpm_residual_norm_noalloc", "mpm_noalloc_last_error",
            "mpm_footprint_bytes",
            "mpm_destroy_scene", "mpm_status_string", "mpm_last_error",
@@ -146,6 +146,8 @@ def lib(build: bool = True):
     L.mpm_set_params.argtypes = [_P, _D, _D, _D]
     L.mpm_get_particle_increment.argtypes = [_P, _D]
     L.mpm_adjoint.argtypes = [_P, _D, _D, _D, _D, _D]
+    L.mpm_adjoint_step.argtypes = [_P, _D, _D, _D, _D, _D, _D, _D, _D, _D]
+    L.mpm_set_state.argtypes = [_P, _D, _D, _D, _D]
     L.mpm_kernel_launches.argtypes = [_P, _LL]
     L.mpm_set_particles.argtypes = [_P, _D, _D, _D]
     L.mpm_residual_norm_noalloc.argtypes = [_P, _P, ctypes.c_int, _P, ctypes.c_int, _D, _P]
@@ -373,6 +375,24 @@ def mpm_adjoint(h, np_, nmat, dL_dU=None, dL_dx=None, want_E=True, want_phi=True
     x = None if dL_dx is None else _f64(np.asarray(dL_dx, dtype=np.float64).reshape(np_, 3))
     _check(lib().mpm_adjoint(h, _p(_f64(dL_dU)), _p(x), _p(gE), _p(gP), _p(gK)), h)
     return (gE[:np_] if gE is not None else None, gP[:np_] if gP is not None else None, gK)
+
+
+def mpm_adjoint_step(h, np_, sbar, dL_dU=None, dL_dx=None, grads=None):
+    """One step of the reverse chain (include/mpm.h).  `sbar` is a dict of
+    x (np,3), be (np,6), pc (np,), F (np,3,3) arrays, updated in place from
+    dL/ds_n to dL/ds_{n-1}; `grads` a dict of E, phi (np,) and k (nmat,)
+    arrays that the gradients are added to."""
+    for k in ("x", "be", "pc", "F"):
+        sbar[k] = np.ascontiguousarray(sbar[k], dtype=np.float64)
+    x = None if dL_dx is None else _f64(np.asarray(dL_dx, dtype=np.float64).reshape(np_, 3))
+    g = grads or {}
+    _check(lib().mpm_adjoint_step(h, _p(_f64(dL_dU)), _p(x), _p(sbar["x"]), _p(sbar["be"]), _p(sbar["pc"]),
+                                  _p(sbar["F"]), _p(g.get("E")), _p(g.get("phi")), _p(g.get("k"))), h)
+    return sbar
+
+
+def mpm_set_state(h, x=None, be=None, pc=None, F=None):
+    _check(lib().mpm_set_state(h, _p(_f64(x)), _p(_f64(be)), _p(_f64(pc)), _p(_f64(F))), h)
 
 
 def mpm_set_particles(h, be=None, pc=None, F=None):
