@@ -32,7 +32,7 @@ void ck(cudaError_t e, const char* what) {
   }
 }
 constexpr double ACTIVE_REL = 1e-12;
-constexpr int KTPB = 256;
+constexpr int KTPB = KRYLOV_TPB;
 constexpr int GRAPH_CHUNK = 8;   // Krylov iterations per graph launch
 thread_local std::string g_create_err;  // message of the last failed mpm_create_scene
 }  // namespace

@@ -18,7 +18,7 @@
 namespace mpm {
 
 namespace {
-constexpr int GTPB = 256;
+constexpr int GTPB = KRYLOV_TPB;
 
 __device__ __forceinline__ double wsum(double v) {
 #pragma unroll

@@ -132,6 +132,10 @@ __device__ __forceinline__ void precond_apply(const DevMatrix<T>& K, int row, co
   }
 }
 
+// Threads per block of the row-parallel Krylov kernels (one thread per
+// active row; the grids are ceil(rows / KRYLOV_TPB) blocks).
+constexpr int KRYLOV_TPB = 128;
+
 struct KrylovScalars {
   double rho, alpha, omega;
   double acc_rv, acc_ts, acc_tt, acc_rho, acc_rr;

@@ -17,7 +17,7 @@
 namespace mpm {
 
 namespace {
-constexpr int KTPB = 256;
+constexpr int KTPB = KRYLOV_TPB;
 
 template <int D>
 __device__ __forceinline__ long long nbr(long long i, int dx, int dy, int dz, int nx1, int ny1) {

@@ -184,3 +184,48 @@ def test_multistep_adjoint_matches_oracle_gradient_fp64():
     part = gs.particles()
     assert np.abs(part["x"][:, :2] - xN.detach().numpy()).max() == 0.0
     gs.close()
+
+
+def test_slope_multistep_directional_derivative():
+    """Coarse Drucker-Prager slope with per-particle E and phi random fields
+    (the inverse-analysis workload's shape): three gravity-ramp steps, loss on
+    the final positions of the surface particles; the adjoint's directional
+    derivative along random field perturbations against central differences
+    of the GPU's FP64 three-step solve."""
+    import torch
+    from paper_2507_09435_gb300.autograd import ImplicitSteps
+    sc = S.slope(nx=48, ny=24, h=0.5, ppc=3, nsteps=20, found_h=6, body_h=8, crest=20, toe=32)
+    steps = sc.steps[:3]
+    ytop = sc.x[:, 1].max()
+    surf = sc.x[:, 1] > ytop - 0.5 * sc.h
+    rng = np.random.default_rng(23)
+    c = np.zeros((sc.np, 2))
+    c[surf] = rng.standard_normal((surf.sum(), 2))
+    E0, P0 = sc.E_p.copy(), sc.phi_p.copy()
+    vE = 0.1 * E0 * rng.standard_normal(sc.np)
+    vP = 0.1 * P0 * rng.standard_normal(sc.np)
+    kw = dict(newton_tol=1e-11, newton_maxit=32, forcing=mpm.MPM_FORCING_FIXED, krylov_rtol=1e-13)
+
+    def loss(E, P):
+        gs = mpm.GpuScene(sc, **kw)
+        gs.set_params(E_p=E, phi_p=P)
+        for st in steps:
+            gs.solve_step(st)
+        x = gs.particles(tau=False)["x"][:, :2]
+        gs.close()
+        return float(np.sum(c * x))
+
+    gs = mpm.GpuScene(sc, **kw)
+    Et = torch.tensor(E0, requires_grad=True)
+    Pt = torch.tensor(P0, requires_grad=True)
+    xN = ImplicitSteps.apply(gs, steps, Et, Pt)
+    (xN * torch.from_numpy(c)).sum().backward()
+    gs.close()
+    eps = 1e-6
+    for v, g, which in ((vE, Et.grad.numpy(), "E"), (vP, Pt.grad.numpy(), "phi")):
+        if which == "E":
+            fd = (loss(E0 + eps * vE, P0) - loss(E0 - eps * vE, P0)) / (2 * eps)
+        else:
+            fd = (loss(E0, P0 + eps * vP) - loss(E0, P0 - eps * vP)) / (2 * eps)
+        ad = float(np.dot(g, v))
+        assert abs(ad - fd) <= 1e-4 * abs(fd), (which, ad, fd)
