@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--krylov", default="bicgstab", choices=["bicgstab", "gmres"])
     ap.add_argument("--precond", default="auto", choices=["auto", "node", "seg4"],
                     help="block-Jacobi blocks: one node, or four consecutive active nodes")
-    ap.add_argument("--workload", default="footing", choices=["footing", "column3d", "column3d_stated", "serving"])
+    ap.add_argument("--workload", default="footing",
+                    choices=["footing", "column3d", "column3d_stated", "serving", "slope_adjoint"])
     ap.add_argument("--serving", type=int, default=32,
                     help="requests of the serving stream measured beside the main line (0: none); "
                          "--workload serving runs the 512-request stream alone")
@@ -69,6 +70,7 @@ WORKLOADS = {
     "column3d_stated": "column3d_128x128x64_mcc_393k",
     # the serving stream (the reference arm samples its first footing request)
     "serving": "serving_stream_512",
+    "slope_adjoint": "slope_192x96_dp_random_fields",
 }
 
 
@@ -83,6 +85,8 @@ def workload_scene(name="footing"):
     if name == "serving":
         d = next(d for d in scenes.serving_draws(512) if d["kind"] == "dp_footing")
         return scenes.serving_scene(d)[0]
+    if name == "slope_adjoint":
+        return scenes.slope()
     raise ValueError(name)
 
 
@@ -312,6 +316,78 @@ def serving_measure(nreq, slots, precision, seed=2507_09435 + 4):
     }
 
 
+def run_slope_adjoint_line(args):
+    """Inverse-analysis workload: the random-field Drucker-Prager slope
+    (192x96 cells, ~71k particles, per-particle E and phi fields), the first 6
+    of its 20 gravity-ramp steps forward, then the adjoint through them for a
+    surface-displacement misfit; the gradient's directional derivative along a
+    random field perturbation is checked against central differences of two
+    more forward runs."""
+    import torch
+    from paper_2507_09435_gb300 import mpm, scenes as S
+    from paper_2507_09435_gb300.autograd import ImplicitSteps
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    prec = mpm.MPM_MIXED if args.precision == "mixed" else mpm.MPM_FP64
+    sc = S.slope()
+    steps = sc.steps[:6]      # the first 6 of 20 ramp steps (see the slope's reading)
+    surf = sc.x[:, 1] > sc.x[:, 1].max() - 0.5 * sc.h
+    obs = S.slope(seed=2507_09435 + 6)       # "observed" run: a second seeded field
+    kw = dict(precision=prec, newton_tol=1e-8, newton_maxit=32)
+
+    def forward(E, P, record=None):
+        gs = mpm.GpuScene(sc, **kw)
+        gs.set_params(E_p=E, phi_p=P)
+        newton = 0
+        for st in steps:
+            newton += gs.solve_step(st).newton_iters
+        x = gs.particles(tau=False)["x"][:, :2]
+        gs.close()
+        return x, newton
+
+    x_obs, _ = forward(obs.E_p, obs.phi_p)
+    clk = ClockSampler(0)
+    gs = mpm.GpuScene(sc, **kw)
+    E = torch.tensor(sc.E_p, requires_grad=True)
+    P = torch.tensor(sc.phi_p, requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    xN = ImplicitSteps.apply(gs, steps, E, P)
+    t1 = time.perf_counter()
+    d = (xN - torch.from_numpy(x_obs))[torch.from_numpy(surf)]
+    loss = 0.5 * (d * d).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    gs.close()
+    clocks = clk.stop()
+    rng = np.random.default_rng(11)
+    vE = 0.1 * sc.E_p * rng.standard_normal(sc.np)
+    eps = 1e-4
+
+    def L(Ev):
+        x, _ = forward(Ev, sc.phi_p)
+        dd = (x - x_obs)[surf]
+        return 0.5 * float((dd * dd).sum())
+
+    fd = (L(sc.E_p + eps * vE) - L(sc.E_p - eps * vE)) / (2 * eps)
+    ad = float(np.dot(E.grad.numpy(), vE))
+    _, newton = forward(sc.E_p, sc.phi_p)
+    line = {"metric": "adjoint gradient evaluations/s (6-step slope, forward + reverse chain)",
+            "value": 1.0 / (t2 - t0), "unit": "gradients/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": 1e3 * (t2 - t0), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": "slope_192x96_dp_random_fields", "particles": sc.np, "load_steps": len(steps),
+                       "loss": "0.5 |x_N - x_obs|^2 over the surface particles (x_obs: second seeded field)"},
+            "adjoint": {"forward_s": t1 - t0, "backward_s": t2 - t1, "forward_newton_iters": newton,
+                        "directional_derivative": ad, "central_difference": fd,
+                        "relative_difference": abs(ad - fd) / max(abs(fd), 1e-300), "fd_eps": eps},
+            "clocks": clocks, "cpu_baseline": None, "e2e": None, "roofline": None, "gpu_launches": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serving_line(args):
     import torch
     from paper_2507_09435_gb300 import mpm
@@ -346,6 +422,8 @@ def main():
         return run_reference(args)
     if args.workload == "serving":
         return run_serving_line(args)
+    if args.workload == "slope_adjoint":
+        return run_slope_adjoint_line(args)
     import torch
     import torch.distributed as dist
     from paper_2507_09435_gb300 import mpm
