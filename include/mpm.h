@@ -66,7 +66,7 @@ enum { MPM_FP64 = 0, MPM_MIXED = 1 };                       /* precision modes  
 enum { MPM_BICGSTAB = 0, MPM_GMRES = 1 };                   /* Krylov methods    */
 enum { MPM_FORCING_FIXED = 0, MPM_FORCING_EW = 1 };         /* linear tolerances */
 enum { MPM_SOLID = 0, MPM_UP = 1 };                         /* formulations      */
-enum { MPM_PC_AUTO = 0, MPM_PC_NODE = 1, MPM_PC_SEG4 = 2 };  /* preconditioners   */
+enum { MPM_PC_AUTO = 0, MPM_PC_NODE = 1, MPM_PC_SEG4 = 2, MPM_PC_MG = 3 };  /* preconditioners */
 
 typedef struct {
   int dim;                 /* 2 (plane strain) or 3                              */
@@ -100,7 +100,13 @@ typedef struct {
                               B x B diagonal block; MPM_PC_SEG4 the 4B x 4B
                               diagonal block of four consecutive active nodes
                               (row order, mostly x-neighbours); MPM_PC_AUTO
-                              (0): SEG4 for MPM_UP, NODE otherwise            */
+                              (0): SEG4 for MPM_UP, NODE otherwise;
+                              MPM_PC_MG: geometric multigrid V-cycle on the
+                              background grid (every second node per level,
+                              linear interpolation, Galerkin coarse operators
+                              P^T J P, damped block-Jacobi smoothing, dense
+                              coarsest level); BiCGStab only (MPM_GMRES with
+                              MPM_PC_MG is MPM_ERR_INVALID_ARG)               */
 } mpm_scene_desc;
 
 typedef struct {
@@ -219,6 +225,22 @@ mpm_status mpm_get_counts(const mpm_scene* s, int* n_active, long long* nnzb);
  * identity.  Capacity `cap` in blocks; MPM_ERR_INVALID_ARG if too small. */
 mpm_status mpm_get_jacobian_bsr(const mpm_scene* s, long long cap, int* row_node,
                                 long long* row_ptr, int* col_node, double* val);
+
+/* Multigrid hierarchy of the last assembly (MPM_PC_MG), for inspection.
+ * *levels: levels in use (level 0 is the Jacobian itself, the last level is
+ * solved with a dense inverse).  For 1 <= level < *levels: dims[3] the
+ * level's node counts per axis (dims[2] = 1 in 2D), *nrow its active nodes;
+ * when `nodes` is not NULL (room for `cap` rows): nodes[nrow] the active node
+ * indices (x fastest), vals[nrow * S * B * B] the Galerkin operator P^T A P
+ * as stencil blocks (S = 5^dim slots per row, slot (dx+2) + 5(dy+2)
+ * [+ 25(dz+2)] for the neighbour at offset (dx, dy, dz); block row-major;
+ * solver units: u-p pressure rows and columns carry p_scale), fixed[nnode*B]
+ * (may be NULL) the level's prescribed-DOF flags, and *lambda_max (may be
+ * NULL) the power-iteration estimate of lambda_max(D^-1 A) that sets the
+ * smoother damping.  MPM_ERR_STATE without a hierarchy; MPM_ERR_INVALID_ARG
+ * for a level out of range or `cap` too small. */
+mpm_status mpm_get_mg_level(const mpm_scene* s, int level, int* levels, int dims[3], int* nrow, int cap,
+                            int* nodes, double* vals, unsigned char* fixed, double* lambda_max);
 
 /* Particle state in the caller's original order (any pointer may be NULL):
  * x[np*3], be[np*6] elastic left Cauchy-Green (xx,yy,zz,xy,yz,xz),

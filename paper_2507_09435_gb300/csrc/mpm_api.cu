@@ -73,7 +73,6 @@ struct mpm_scene {
   int* h_int = nullptr;           // pinned: ncell, nrow, err, nplastic
   double* h_dbl = nullptr;        // pinned: norm
   cudaGraphExec_t gexec = nullptr;
-  int graph_cap = -1;
   bool use_graph = true;
   cudaEvent_t ev[6]{};
   // step state
@@ -104,6 +103,26 @@ struct mpm_scene {
   void* d_KT = nullptr;            // adjoint: transposed Jacobian scratch
   int kt_cap = -1;
   int adj_kit = 0;                 // Krylov iterations of the last adjoint solve
+  // geometric multigrid preconditioner (MPM_PC_MG): levels 1.. of the
+  // hierarchy (entry 0 unused: level 0 is the scene's own matrix)
+  struct MgHost {
+    int nx1 = 0, ny1 = 0, nz1 = 0;
+    long long nnode = 0, vpad = 0, vlen = 0;
+    int *node2row = nullptr, *rows = nullptr, *flag = nullptr, *pos = nullptr, *nrow_d = nullptr;
+    uint8_t* fixed = nullptr;
+    void *val = nullptr, *dinv = nullptr, *vec = nullptr;
+    int cap = 0, nrow = 0;
+  };
+  bool mg = false;
+  int mg_L = 0;                    // levels in use for the staged step (the last dense)
+  std::vector<MgHost> mgl;
+  void* d_mg_v0 = nullptr;         // level 0: residual and power-iteration scratch (2 vectors)
+  float* d_mg_inv = nullptr;       // coarsest-level dense inverse, transposed
+  double* d_mg_nrm = nullptr;      // power-iteration norms, MG_POWER_IT + 1 per level
+  int* d_mg_err = nullptr;         // singular coarse diagonal blocks (identity used)
+  int* h_mgn = nullptr;            // pinned: active rows per level
+  bool mg_lam = false;             // smoother damping estimated for the staged step
+  std::vector<int> graph_sig;      // capacities the BiCGStab graph was captured with
   std::string err;
 
   // Device memory comes from the stream-ordered pool on the scene's stream:
@@ -156,8 +175,11 @@ void validate_desc(const mpm_scene_desc* d) {
     fail(MPM_ERR_INVALID_ARG, "newton_tol > 0 and 1 <= newton_maxit <= 32 required");
   if (!(d->krylov_rtol > 0) || d->krylov_maxit < 1) fail(MPM_ERR_INVALID_ARG, "bad Krylov settings");
   if (d->formulation != MPM_SOLID && d->formulation != MPM_UP) fail(MPM_ERR_INVALID_ARG, "bad formulation");
-  if (d->precond != MPM_PC_AUTO && d->precond != MPM_PC_NODE && d->precond != MPM_PC_SEG4)
+  if (d->precond != MPM_PC_AUTO && d->precond != MPM_PC_NODE && d->precond != MPM_PC_SEG4 &&
+      d->precond != MPM_PC_MG)
     fail(MPM_ERR_INVALID_ARG, "bad precond");
+  if (d->precond == MPM_PC_MG && d->krylov != MPM_BICGSTAB)
+    fail(MPM_ERR_INVALID_ARG, "the multigrid preconditioner is built for BiCGStab");
   if (d->formulation == MPM_UP) {
     if (d->dim != 2) fail(MPM_ERR_INVALID_ARG, "the u-p formulation is built for dim 2");
     if (!(d->dt > 0)) fail(MPM_ERR_INVALID_ARG, "u-p needs dt > 0");
@@ -188,7 +210,11 @@ size_t footprint(const mpm_scene_desc* d, int np) {
   // active rows are bounded by the nodes the particles can reach
   long long rows = std::min<long long>(nn, (long long)np * (D == 2 ? 9 : 27));
   size_t mat = (size_t)rows * (stencil_slots(D) + 1) * B * B * T;
-  return part + grid + tang + vec + mat + (1 << 20);
+  // multigrid: coarse matrices (a quarter per level in 2D, an eighth in 3D),
+  // coarse grids and vectors, two level-0 scratch vectors
+  size_t mg = 0;
+  if (d->precond == MPM_PC_MG) mg = mat / (D == 2 ? 3 : 7) + (size_t)nn * 12 + vec / 3 + (1 << 20);
+  return part + grid + tang + vec + mat + mg + (1 << 20);
 }
 
 template <class T>
@@ -232,7 +258,7 @@ void ensure_capacity(mpm_scene* s, int nrow) {
     cudaGraphExecDestroy(s->gexec);
     s->gexec = nullptr;
   }
-  s->graph_cap = -1;
+  s->graph_sig.clear();
 }
 
 template <int D>
@@ -320,6 +346,9 @@ void check_err_bits(mpm_scene* s) {
   fail(st, m);
 }
 
+template <int D, int B>
+void mg_structure(mpm_scene* s);
+
 template <int D, class T, int B>
 void begin_step_impl(mpm_scene* s, mpm_newton_report* rep) {
   cudaStream_t st = s->st;
@@ -355,6 +384,7 @@ void begin_step_impl(mpm_scene* s, mpm_newton_report* rep) {
   s->ncell = s->h_int[0];
   s->nrow = s->h_int[1];
   ensure_capacity(s, s->nrow);
+  if (s->mg) mg_structure<D, B>(s);
   // prescribed increments and r^0 (with the tangent for the first iteration)
   ck(cudaMemcpyAsync(s->d_grav, s->grav, 3 * sizeof(double), cudaMemcpyHostToDevice, st), "grav");
   ck(launch_apply_bc(s->d_fixed, s->d_bcval, s->d_node2row, s->d_du, s->ndof, B, st), "bc");
@@ -382,8 +412,187 @@ void begin_step_impl(mpm_scene* s, mpm_newton_report* rep) {
   }
 }
 
+// ---- geometric multigrid hierarchy (csrc/mpm_mg.cu) ----------------------
+// Grids of every coarse level, allocated with the scene (each level has about
+// a quarter (2D) or an eighth (3D) of the nodes of the one above; coarsening
+// stops when every axis has at most 2 nodes, at most 8 nodes in all).
+void mg_create(mpm_scene* s) {
+  s->mgl.assign(1, mpm_scene::MgHost{});
+  int nx = s->G.nx1, ny = s->G.ny1, nz = s->G.nz1;
+  const size_t T = tsize(s);
+  while ((int)s->mgl.size() < MG_MAX_LEVELS && (nx > 2 || ny > 2 || (s->D == 3 && nz > 2))) {
+    mpm_scene::MgHost m;
+    m.nx1 = nx / 2 + 1;
+    m.ny1 = ny / 2 + 1;
+    m.nz1 = s->D == 3 ? nz / 2 + 1 : 1;
+    m.nnode = (long long)m.nx1 * m.ny1 * m.nz1;
+    m.node2row = s->dalloc<int>(m.nnode);
+    m.rows = s->dalloc<int>(m.nnode);
+    m.flag = s->dalloc<int>(m.nnode + 1);
+    m.pos = s->dalloc<int>(m.nnode + 1);
+    m.nrow_d = s->dalloc<int>(1);
+    m.fixed = s->dalloc<uint8_t>(m.nnode * s->B);
+    m.vpad = (2 + 2LL * m.nx1 + (s->D == 3 ? 2LL * m.nx1 * m.ny1 : 0)) * s->B;
+    m.vlen = m.nnode * s->B + 2 * m.vpad;
+    m.vec = s->mixed ? (void*)s->dalloc<float>(3 * m.vlen) : (void*)s->dalloc<double>(3 * m.vlen);
+    ck(cudaMemsetAsync(m.vec, 0, 3 * m.vlen * T, s->st), "memset");
+    ck(cudaMemsetAsync(m.nrow_d, 0, sizeof(int), s->st), "memset");
+    s->mgl.push_back(m);
+    nx = m.nx1;
+    ny = m.ny1;
+    nz = m.nz1;
+  }
+  s->d_mg_v0 = s->mixed ? (void*)s->dalloc<float>(2 * s->vlen) : (void*)s->dalloc<double>(2 * s->vlen);
+  ck(cudaMemsetAsync(s->d_mg_v0, 0, 2 * s->vlen * T, s->st), "memset");
+  s->d_mg_inv = s->dalloc<float>((size_t)MG_DENSE_MAX * MG_DENSE_MAX);
+  s->d_mg_nrm = s->dalloc<double>((size_t)MG_MAX_LEVELS * (MG_POWER_IT + 1));
+  s->d_mg_err = s->dalloc<int>(1);
+  ck(cudaMallocHost(&s->h_mgn, MG_MAX_LEVELS * sizeof(int)), "host alloc");
+}
+
+// Active nodes and prescribed DOFs of every coarse level for the staged step
+// (after the fine rows and prescribed DOFs are set); the hierarchy in use ends
+// at the first level with at most MG_DENSE_MAX unknowns.
+template <int D, int B>
+void mg_structure(mpm_scene* s) {
+  cudaStream_t st = s->st;
+  const int Lmax = (int)s->mgl.size();
+  int fx = s->G.nx1, fy = s->G.ny1, fz = s->G.nz1;
+  const int* n2r = s->d_node2row;
+  const uint8_t* fix = s->d_fixed;
+  for (int l = 1; l < Lmax; ++l) {
+    auto& m = s->mgl[l];
+    ck(launch_mg_flags<D>(fx, fy, fz, n2r, m.nx1, m.ny1, m.nnode, m.flag, st), "mg flags");
+    ck(scan_exclusive(m.flag, m.pos, (int)(m.nnode + 1), s->d_scan_tmp, st), "mg scan");
+    ck(launch_node2row(m.flag, m.pos, m.node2row, m.rows, m.nnode, st), "mg rows");
+    ck(cudaMemcpyAsync(m.nrow_d, m.pos + m.nnode, sizeof(int), cudaMemcpyDeviceToDevice, st), "copy");
+    ck(cudaMemcpyAsync(s->h_mgn + l, m.pos + m.nnode, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
+    ck(launch_mg_fixed<D, B>(fx, fy, fz, n2r, fix, m.nx1, m.ny1, m.nnode, m.fixed, st), "mg fixed");
+    s->launches += 3 + scan_launches(m.nnode + 1);
+    fx = m.nx1;
+    fy = m.ny1;
+    fz = m.nz1;
+    n2r = m.node2row;
+    fix = m.fixed;
+  }
+  ck(cudaStreamSynchronize(st), "sync");
+  s->h_mgn[0] = s->nrow;
+  int L = 0;
+  for (int l = 0; l < Lmax && L == 0; ++l)
+    if ((long long)s->h_mgn[l] * B <= MG_DENSE_MAX) L = l + 1;
+  if (L == 0) fail(MPM_ERR_INVALID_ARG, "grid too large for the multigrid hierarchy");
+  const size_t S = stencil_slots(D), BB = (size_t)B * B;
+  for (int l = 1; l < L; ++l) {
+    auto& m = s->mgl[l];
+    m.nrow = s->h_mgn[l];
+    if (m.nrow > m.cap || !m.val) {
+      const int cap = (int)std::min<long long>(m.nnode, std::max<long long>(64, (long long)(m.nrow * 1.25) + 32));
+      s->dfree(m.val);
+      s->dfree(m.dinv);
+      if (s->mixed) {
+        m.val = s->dalloc<float>((size_t)cap * S * BB);
+        m.dinv = s->dalloc<float>((size_t)(cap + 4) * BB);
+      } else {
+        m.val = s->dalloc<double>((size_t)cap * S * BB);
+        m.dinv = s->dalloc<double>((size_t)(cap + 4) * BB);
+      }
+      m.cap = cap;
+    }
+  }
+  s->mg_L = L;
+  s->mg_lam = false;
+}
+
+template <class T>
+MgApply<T> mg_view(mpm_scene* s) {
+  MgApply<T> a{};
+  a.L = s->mg_L;
+  a.invT = s->d_mg_inv;
+  MgLevel<T>& f = a.lev[0];
+  f.nx1 = s->G.nx1;
+  f.ny1 = s->G.ny1;
+  f.nz1 = s->G.nz1;
+  f.K = matview<T>(s);
+  f.node2row = s->d_node2row;
+  f.fixed = s->d_fixed;
+  f.b = nullptr;
+  f.z = nullptr;
+  f.r = (T*)s->d_mg_v0 + s->vpad;
+  a.caps[0] = s->cap;
+  // single-block tail: from the first coarse level with at most MG_TAIL_ROWS rows
+  a.tail = std::max(a.L - 1, 1);
+  for (int l = 1; l < a.L; ++l)
+    if (s->h_mgn[l] <= MG_TAIL_ROWS) {
+      a.tail = l;
+      break;
+    }
+  for (int l = 1; l < a.L; ++l) {
+    const auto& m = s->mgl[l];
+    MgLevel<T>& c = a.lev[l];
+    c.nx1 = m.nx1;
+    c.ny1 = m.ny1;
+    c.nz1 = m.nz1;
+    c.K.val = (T*)m.val;
+    c.K.dinv = (T*)m.dinv;
+    c.K.cap = m.cap;
+    c.K.rows = m.rows;
+    c.K.nrow = m.nrow_d;
+    c.K.seg = 1;
+    c.node2row = m.node2row;
+    c.fixed = m.fixed;
+    T* v = (T*)m.vec;
+    c.b = v + m.vpad;
+    c.z = v + m.vlen + m.vpad;
+    c.r = v + 2 * m.vlen + m.vpad;
+    a.caps[l] = m.cap;
+  }
+  return a;
+}
+
+// smoother damping w = MG_DAMP / lambda_max(D^-1 A), per level
+constexpr double MG_DAMP = 1.2;
+// BiCGStab iterations per graph launch with the V-cycle (a few iterations
+// per solve: a long chunk would launch many early-returning kernels)
+constexpr int MG_CHUNK = 2;
+
+// Coarse operators, their block inverses, the smoother damping (estimated at
+// the first assembly of a load step) and the coarsest dense inverse, from the
+// assembled level-0 matrix and its block-Jacobi inverse.
 template <int D, class T, int B>
-void build_graph(mpm_scene* s, int nblk) {
+void mg_setup(mpm_scene* s) {
+  if (!s->mg || s->mg_L == 0 || s->nrow == 0) return;
+  cudaStream_t st = s->st;
+  MgApply<T> a = mg_view<T>(s);
+  const int L = a.L;
+  for (int l = 1; l < L; ++l) {
+    ck(launch_mg_galerkin<D, T, B>(a.lev[l - 1], a.lev[l], s->h_mgn[l], st), "galerkin");
+    s->launches += 1;
+    if (l + 1 < L) {
+      ck(launch_block_jacobi<D, T, B>(s->G, a.lev[l].K, s->h_mgn[l], s->d_mg_err, st), "coarse block jacobi");
+      s->launches += 1;
+    }
+  }
+  const int P1 = MG_POWER_IT + 1;
+  if (!s->mg_lam) {
+    for (int l = 0; l + 1 < L; ++l) {
+      T* va = (l == 0) ? (T*)s->d_mg_v0 + s->vpad : a.lev[l].b;
+      T* vb = (l == 0) ? (T*)s->d_mg_v0 + s->vlen + s->vpad : a.lev[l].z;
+      ck(launch_mg_power<D, T, B>(a.lev[l], a.caps[l], va, vb, s->d_mg_nrm + l * P1, MG_POWER_IT, st), "power");
+      s->launches += 1 + MG_POWER_IT;
+    }
+    s->mg_lam = true;
+  }
+  for (int l = 0; l + 1 < L; ++l) {
+    const long long n = (long long)(a.caps[l] + 4) * B * B * (l == 0 ? s->seg : 1);
+    ck(launch_mg_scale<T>(a.lev[l].K.dinv, n, s->d_mg_nrm + l * P1 + MG_POWER_IT, MG_DAMP, st), "scale");
+    s->launches += 1;
+  }
+  ck(launch_mg_dense_inverse<D, T, B>(a.lev[L - 1], s->d_mg_inv, st), "dense inverse");
+  s->launches += 1;
+}
+
+template <int D, class T, int B>
+void build_graph(mpm_scene* s, int nblk, const MgApply<T>* mg, int chunk, const std::vector<int>& sig) {
   if (s->gexec) {
     cudaGraphExecDestroy(s->gexec);
     s->gexec = nullptr;
@@ -392,18 +601,19 @@ void build_graph(mpm_scene* s, int nblk) {
   ck(cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal), "capture");
   DevMatrix<T> K = matview<T>(s);
   KrylovVecs<D, T> v = vecview<D, T>(s);
-  for (int c = 0; c < GRAPH_CHUNK; ++c) launch_bicgstab_iter<D, T, B>(s->G, K, v, s->d_S, nblk, s->st);
+  for (int c = 0; c < chunk; ++c) launch_bicgstab_iter<D, T, B>(s->G, K, v, s->d_S, nblk, s->st, mg);
   ck(cudaStreamEndCapture(s->st, &g), "end capture");
   ck(cudaGraphInstantiate(&s->gexec, g, 0), "instantiate");
   cudaGraphDestroy(g);
-  s->graph_cap = s->cap;
+  s->graph_sig = sig;
 }
+
 
 // Assembly of the per-particle consistent tangents (written by the last
 // residual pass) into the stencil-BSR Jacobian, prescribed rows/columns set
 // to the identity, block-Jacobi inverse.
 template <int D, class T, int B>
-void assemble_impl(mpm_scene* s) {
+void assemble_impl(mpm_scene* s, bool with_mg = true) {
   if (!s->staged) fail(MPM_ERR_STATE, "no load step staged (call mpm_begin_step)");
   cudaStream_t st = s->st;
   DevMatrix<T> K = matview<T>(s);
@@ -412,6 +622,7 @@ void assemble_impl(mpm_scene* s) {
   ck(launch_bc_matrix<D, T, B>(s->G, K, s->d_fixed, s->d_node2row, s->nrow, st), "bc matrix");
   ck(launch_block_jacobi<D, T, B>(s->G, K, s->nrow, s->d_err, st), "block jacobi");
   s->launches += 3;
+  if (with_mg) mg_setup<D, T, B>(s);
 }
 
 // Restarted GMRES(m) on J d = -r to an absolute residual `tol`: cycles of m
@@ -475,8 +686,19 @@ void krylov_solve(mpm_scene* s, double eta, double rnorm, int& kit, int& kstat, 
   if (s->gm > 0) {
     gmres_solve<D, T, B>(s, K, v.x, eta * rnorm, nblk, kit, kstat, kres2);
   } else {
+  const bool use_mg = s->mg && s->mg_L > 0;
+  MgApply<T> mga{};
+  if (use_mg) mga = mg_view<T>(s);
+  const MgApply<T>* mgp = use_mg ? &mga : nullptr;
+  int* d_done = &s->d_S->done;
+  const int chunk = use_mg ? MG_CHUNK : GRAPH_CHUNK;
+  const int per_iter = 4 + (use_mg ? 2 * mg_vcycle_launches(mga.L, mga.tail) : 0);
   ck(launch_bicgstab_init<D, T, B>(K, s->krhs, s->d_fixed, v, s->d_S, tol2, s->desc.krylov_maxit, nblk, st),
      "krylov init");
+  if (use_mg) {
+    ck(launch_mg_vcycle<D, T, B>(mga, v.p, v.phat, d_done, st), "v-cycle");
+    s->launches += mg_vcycle_launches(mga.L, mga.tail);
+  }
   const int pblk = std::min(s->pblocks, std::max(1, (s->nrow * 4 + 511) / 512));
   if (s->pblocks > 0) {
     // whole solve in one cooperative launch
@@ -489,7 +711,10 @@ void krylov_solve(mpm_scene* s, double eta, double rnorm, int& kit, int& kstat, 
     ck(cudaStreamSynchronize(st), "sync");
     check_err_bits(s);
   }
-  if (s->pblocks == 0 && s->use_graph && s->graph_cap != s->cap) build_graph<D, T, B>(s, nblk);
+  std::vector<int> sig = {s->cap, use_mg ? s->mg_L : 0, use_mg ? mga.tail : 0};
+  if (use_mg)
+    for (int l = 1; l < s->mg_L; ++l) sig.push_back(s->mgl[l].cap);
+  if (s->pblocks == 0 && s->use_graph && sig != s->graph_sig) build_graph<D, T, B>(s, nblk, mgp, chunk, sig);
   if (s->pblocks == 0) {
     // graph chunks of GRAPH_CHUNK iterations until the done flag; on a
     // (near) breakdown or the iteration limit, restart from the current x
@@ -500,15 +725,15 @@ void krylov_solve(mpm_scene* s, double eta, double rnorm, int& kit, int& kstat, 
         if (s->use_graph) {
           ck(cudaGraphLaunch(s->gexec, st), "graph launch");
         } else {
-          for (int c = 0; c < GRAPH_CHUNK; ++c)
-            ck(launch_bicgstab_iter<D, T, B>(s->G, K, v, s->d_S, nblk, st), "krylov");
+          for (int c = 0; c < chunk; ++c)
+            ck(launch_bicgstab_iter<D, T, B>(s->G, K, v, s->d_S, nblk, st, mgp), "krylov");
         }
-        launched += GRAPH_CHUNK;
-        s->launches += 4 * GRAPH_CHUNK;
+        launched += chunk;
+        s->launches += (long long)per_iter * chunk;
         ck(cudaMemcpyAsync(s->h_S, s->d_S, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st), "copy S");
         ck(cudaStreamSynchronize(st), "sync");
         if (s->h_S->done) break;
-        if (launched > s->desc.krylov_maxit + 2 * GRAPH_CHUNK) break;   // belt and braces
+        if (launched > s->desc.krylov_maxit + 2 * chunk) break;   // belt and braces
       }
       kit += s->h_S->iter;
       kstat = s->h_S->status;
@@ -520,6 +745,10 @@ void krylov_solve(mpm_scene* s, double eta, double rnorm, int& kit, int& kstat, 
                                        s->desc.krylov_maxit - kit, nblk, st),
          "krylov restart");
       s->launches += 1;
+      if (use_mg) {
+        ck(launch_mg_vcycle<D, T, B>(mga, v.p, v.phat, d_done, st), "v-cycle");
+        s->launches += mg_vcycle_launches(mga.L, mga.tail);
+      }
       ck(cudaMemcpyAsync(s->h_S, s->d_S, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st), "copy S");
       ck(cudaStreamSynchronize(st), "sync");
       if (kstat == 0 && s->h_S->rr_last <= 4.0 * tol2) break;   // true residual within 2x of the tolerance
@@ -691,7 +920,7 @@ void adjoint_impl(mpm_scene* s, const double* dL_dU, const double* dL_dx, double
   if (!s->staged) fail(MPM_ERR_STATE, "no converged step staged (run the Newton iterations, then the adjoint)");
   cudaStream_t st = s->st;
   ck(cudaMemsetAsync(s->d_err, 0, sizeof(int), st), "memset");
-  assemble_impl<D, T, B>(s);
+  assemble_impl<D, T, B>(s, false);
   DevMatrix<T> K = matview<T>(s);
   const int S = stencil_slots(D);
   const size_t nval = (size_t)s->cap * S * B * B;
@@ -703,6 +932,10 @@ void adjoint_impl(mpm_scene* s, const double* dL_dU, const double* dL_dx, double
   ck(launch_transpose_blocks<D, T, B>(s->G, K, s->d_node2row, (T*)s->d_KT, s->nrow, st), "transpose");
   ck(cudaMemcpyAsync(s->d_K, s->d_KT, nval * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy");
   ck(launch_block_jacobi<D, T, B>(s->G, K, s->nrow, s->d_err, st), "block jacobi");
+  // multigrid on the transposed operator (P^T J^T P is the transpose of the
+  // Galerkin operator of J); the smoother damping is estimated again
+  s->mg_lam = false;
+  mg_setup<D, T, B>(s);
   s->launches += 2;
   // right-hand side: dL/du on the nodes, plus a particle-displacement
   // gradient mapped with the weights; b = -S g
@@ -777,7 +1010,7 @@ void adjoint_step_impl(mpm_scene* s, const double* dL_dU, const double* dL_dx, d
   if (!s->staged) fail(MPM_ERR_STATE, "no converged step staged (restore the state, stage the step, set du)");
   cudaStream_t st = s->st;
   ck(cudaMemsetAsync(s->d_err, 0, sizeof(int), st), "memset");
-  assemble_impl<D, T, B>(s);
+  assemble_impl<D, T, B>(s, false);
   DevMatrix<T> K = matview<T>(s);
   const int S = stencil_slots(D);
   const size_t nval = (size_t)s->cap * S * B * B;
@@ -789,6 +1022,10 @@ void adjoint_step_impl(mpm_scene* s, const double* dL_dU, const double* dL_dx, d
   ck(launch_transpose_blocks<D, T, B>(s->G, K, s->d_node2row, (T*)s->d_KT, s->nrow, st), "transpose");
   ck(cudaMemcpyAsync(s->d_K, s->d_KT, nval * sizeof(T), cudaMemcpyDeviceToDevice, st), "copy");
   ck(launch_block_jacobi<D, T, B>(s->G, K, s->nrow, s->d_err, st), "block jacobi");
+  // multigrid on the transposed operator (P^T J^T P is the transpose of the
+  // Galerkin operator of J); the smoother damping is estimated again
+  s->mg_lam = false;
+  mg_setup<D, T, B>(s);
   const size_t np = (size_t)std::max(s->np, 1);
   double* d_g = s->dalloc<double>(s->ndof);
   double* d_b = s->dalloc<double>(s->ndof);
@@ -950,6 +1187,7 @@ void destroy(mpm_scene* s) {
   if (s->h_S) cudaFreeHost(s->h_S);
   if (s->h_int) cudaFreeHost(s->h_int);
   if (s->h_dbl) cudaFreeHost(s->h_dbl);
+  if (s->h_mgn) cudaFreeHost(s->h_mgn);
   for (auto& e : s->ev)
     if (e) cudaEventDestroy(e);
   if (s->own_stream && s->st) cudaStreamDestroy(s->st);
@@ -980,6 +1218,7 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
     // 4-node solves take in the lateral pressure modes that only the small
     // Darcy term controls (node blocks leave them to the Krylov method)
     s->seg = (desc->precond == MPM_PC_SEG4 || (desc->precond == MPM_PC_AUTO && s->up)) ? 4 : 1;
+    s->mg = desc->precond == MPM_PC_MG;
     s->np = np;
     s->nmat = nmat;
     s->nbe = s->D == 2 ? 4 : 6;
@@ -1145,6 +1384,7 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
     else s->d_vec = s->dalloc<double>(9 * s->vlen);
     ck(cudaMemsetAsync(s->d_vec, 0, 9 * s->vlen * T, s->st), "memset");
     s->d_S = s->dalloc<KrylovScalars>(1);
+    if (s->mg) mg_create(s);
     if (desc->krylov == MPM_GMRES) {
       s->gm = desc->gmres_restart > 0 ? std::min(std::max(desc->gmres_restart, 2), GMRES_MMAX) : 30;
       const size_t nv = (size_t)(s->gm + 3) * s->vlen;
@@ -1164,7 +1404,7 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
       int dev = 0;
       ck(cudaGetDevice(&dev), "device");
       const bool want_persistent = env && env[0] == '1';
-      if (want_persistent && desc->krylov == MPM_BICGSTAB && !s->up && s->seg == 1) {
+      if (want_persistent && desc->krylov == MPM_BICGSTAB && !s->up && s->seg == 1 && !s->mg) {
         if (s->D == 2) s->pblocks = s->mixed ? persistent_blocks<2, float>(dev) : persistent_blocks<2, double>(dev);
         else s->pblocks = s->mixed ? persistent_blocks<3, float>(dev) : persistent_blocks<3, double>(dev);
       }
@@ -1401,6 +1641,56 @@ mpm_status mpm_get_jacobian_bsr(const mpm_scene* cs, long long cap, int* row_nod
       }
       row_ptr[r + 1] = nb;
     }
+  });
+}
+
+mpm_status mpm_get_mg_level(const mpm_scene* cs, int level, int* levels, int dims[3], int* nrow, int cap,
+                            int* nodes, double* vals, unsigned char* fixed, double* lambda_max) {
+  mpm_scene* s = const_cast<mpm_scene*>(cs);
+  if (!s || !levels) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] {
+    if (!s->mg || s->mg_L == 0) fail(MPM_ERR_STATE, "no multigrid hierarchy (MPM_PC_MG, after an assembly)");
+    *levels = s->mg_L;
+    if (level == 0 && lambda_max) {
+      ck(cudaStreamSynchronize(s->st), "sync");
+      double n2 = 0;
+      ck(cudaMemcpy(&n2, s->d_mg_nrm + MG_POWER_IT, sizeof(double), cudaMemcpyDeviceToHost), "download");
+      *lambda_max = std::sqrt(n2);
+    }
+    if (level < 1) return;
+    if (level >= s->mg_L) fail(MPM_ERR_INVALID_ARG, "level out of range");
+    const auto& m = s->mgl[level];
+    if (dims) {
+      dims[0] = m.nx1;
+      dims[1] = m.ny1;
+      dims[2] = m.nz1;
+    }
+    if (nrow) *nrow = m.nrow;
+    ck(cudaStreamSynchronize(s->st), "sync");
+    if (lambda_max) {
+      double n2 = 0;
+      ck(cudaMemcpy(&n2, s->d_mg_nrm + (size_t)level * (MG_POWER_IT + 1) + MG_POWER_IT, sizeof(double),
+                    cudaMemcpyDeviceToHost),
+         "download");
+      *lambda_max = std::sqrt(n2);
+    }
+    if (fixed) ck(cudaMemcpy(fixed, m.fixed, m.nnode * s->B, cudaMemcpyDeviceToHost), "download");
+    if (!nodes) return;
+    if (cap < m.nrow || !vals) fail(MPM_ERR_INVALID_ARG, "capacity too small for the level");
+    ck(cudaMemcpy(nodes, m.rows, m.nrow * sizeof(int), cudaMemcpyDeviceToHost), "download");
+    const int S = stencil_slots(s->D), BB = s->B * s->B;
+    const size_t nval = (size_t)m.cap * S * BB;
+    std::vector<double> K(nval);
+    if (s->mixed) {
+      std::vector<float> Kf(nval);
+      ck(cudaMemcpy(Kf.data(), m.val, nval * sizeof(float), cudaMemcpyDeviceToHost), "download");
+      for (size_t q = 0; q < nval; ++q) K[q] = Kf[q];
+    } else {
+      ck(cudaMemcpy(K.data(), m.val, nval * sizeof(double), cudaMemcpyDeviceToHost), "download");
+    }
+    for (int r = 0; r < m.nrow; ++r)
+      for (int sl = 0; sl < S; ++sl)
+        for (int k = 0; k < BB; ++k) vals[((size_t)r * S + sl) * BB + k] = K[((size_t)sl * m.cap + r) * BB + k];
   });
 }
 

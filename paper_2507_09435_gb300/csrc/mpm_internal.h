@@ -132,6 +132,35 @@ __device__ __forceinline__ void precond_apply(const DevMatrix<T>& K, int row, co
   }
 }
 
+// y = K x for one row (node i) of a stencil-BSR matrix: the 5^D neighbour
+// blocks of the row against the neighbours' values of x (x on the padded
+// dense node grid of the matrix's level).  COHERENT: x was written earlier in
+// the same kernel (ordinary loads instead of the read-only path).
+template <int D, class T, int B, bool COHERENT = false>
+__device__ __forceinline__ void stencil_row_product(const DevMatrix<T>& K, int row, long long i, int nx1, int ny1,
+                                                    const T* x, T y[B]) {
+#pragma unroll
+  for (int a = 0; a < B; ++a) y[a] = (T)0;
+  constexpr int ZR = (D == 3) ? 2 : 0;
+  const long long cap = K.cap;
+#pragma unroll
+  for (int dz = -ZR; dz <= ZR; ++dz)
+#pragma unroll
+    for (int dy = -2; dy <= 2; ++dy)
+#pragma unroll
+      for (int dx = -2; dx <= 2; ++dx) {
+        const int slot = (D == 2) ? (dx + 2) + 5 * (dy + 2) : (dx + 2) + 5 * ((dy + 2) + 5 * (dz + 2));
+        const long long j = i + dx + (long long)nx1 * (dy + (long long)ny1 * dz);
+        T xj[B], kb[B * B];
+        ld_node<B, T, COHERENT>(x, j, xj);
+        ld_block<B, T>(&K.val[((long long)slot * cap + row) * (B * B)], kb);
+#pragma unroll
+        for (int a = 0; a < B; ++a)
+#pragma unroll
+          for (int b = 0; b < B; ++b) y[a] += kb[a * B + b] * xj[b];
+      }
+}
+
 // Threads per block of the row-parallel Krylov kernels (one thread per
 // active row; the grids are ceil(rows / KRYLOV_TPB) blocks).
 constexpr int KRYLOV_TPB = 128;
@@ -206,6 +235,55 @@ template <int D>
 cudaError_t launch_norm_free(const double* r, const int* rows, int nrow_host, const uint8_t* fixed,
                              double* out, cudaStream_t st);
 
+// Geometric multigrid preconditioner (mpm_mg.cu).  One level of the
+// hierarchy: the level's grid (nz1 = 1 in 2D), its stencil-BSR matrix (seg 1
+// on the coarse levels; the block inverses pre-multiplied by the smoother's
+// damping), node -> row map, prescribed-DOF flags and three padded vectors.
+template <class T>
+struct MgLevel {
+  int nx1, ny1, nz1;
+  DevMatrix<T> K;
+  const int* node2row;
+  const uint8_t* fixed;
+  T *b, *z, *r;
+};
+constexpr int MG_MAX_LEVELS = 12;
+constexpr int MG_DENSE_MAX = 128;   // unknowns of the coarsest (dense) level
+constexpr int MG_POWER_IT = 8;      // power iterations for lambda_max(D^-1 A)
+constexpr int MG_TAIL_ROWS = 1024;  // coarse levels this small run in one block
+constexpr int MG_TAIL_TPB = 512;
+// A built hierarchy, for the V-cycle launches: levels 0..L-1 (the last
+// dense); levels tail..L-1 (tail >= 1) run inside one single-block kernel,
+// the levels above it one launch per step.
+template <class T>
+struct MgApply {
+  MgLevel<T> lev[MG_MAX_LEVELS];
+  int caps[MG_MAX_LEVELS];
+  int L, tail;
+  const float* invT;
+};
+template <int D>
+cudaError_t launch_mg_flags(int fx, int fy, int fz, const int* n2r_f, int cx, int cy, long long nc, int* flag,
+                            cudaStream_t st);
+template <int D, int B>
+cudaError_t launch_mg_fixed(int fx, int fy, int fz, const int* n2r_f, const uint8_t* fix_f, int cx, int cy,
+                            long long nc, uint8_t* fix_c, cudaStream_t st);
+template <int D, class T, int B>
+cudaError_t launch_mg_galerkin(MgLevel<T> f, MgLevel<T> c, int nrow_c, cudaStream_t st);
+// power iteration on D^-1 A of a level: nrm[k] = ||v_k||^2 (v_k of unit
+// predecessor), so sqrt(nrm[iters]) estimates lambda_max; va, vb scratch
+template <int D, class T, int B>
+cudaError_t launch_mg_power(MgLevel<T> l, int cap, T* va, T* vb, double* nrm, int iters, cudaStream_t st);
+template <class T>
+cudaError_t launch_mg_scale(T* dinv, long long n, const double* nrm, double c, cudaStream_t st);
+template <int D, class T, int B>
+cudaError_t launch_mg_dense_inverse(MgLevel<T> c, float* invT, cudaStream_t st);
+// z0 = V-cycle(b0) given the first smoothing sweep already in z0; levels
+// 0..L-1, the last dense; kernels return at once while *done is set
+template <int D, class T, int B>
+cudaError_t launch_mg_vcycle(const MgApply<T>& mg, const T* b0, T* z0, const int* done, cudaStream_t st);
+int mg_vcycle_launches(int L, int tail);
+
 // Krylov
 template <int D, class T>
 struct KrylovVecs {
@@ -214,9 +292,11 @@ struct KrylovVecs {
 template <int D, class T, int B = D>
 cudaError_t launch_bicgstab_init(DevMatrix<T> K, const double* res, const uint8_t* fixed, KrylovVecs<D, T> v,
                                  KrylovScalars* S, double tol2, int maxit, int nblk, cudaStream_t st);
+// one BiCGStab iteration; with `mg`, each preconditioner application is the
+// V-cycle (the fused block-Jacobi step being its first smoothing sweep)
 template <int D, class T, int B = D>
 cudaError_t launch_bicgstab_iter(const DevGrid& G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S,
-                                 int nblk, cudaStream_t st);
+                                 int nblk, cudaStream_t st, const MgApply<T>* mg = nullptr);
 template <int D, class T, int B = D>
 cudaError_t launch_bicgstab_restart(const DevGrid& G, DevMatrix<T> K, const double* res, const uint8_t* fixed,
                                     KrylovVecs<D, T> v, KrylovScalars* S, double tol2, int maxit, int nblk,

@@ -24,32 +24,6 @@ __device__ __forceinline__ long long nbr(long long i, int dx, int dy, int dz, in
   return i + dx + (long long)nx1 * (dy + (long long)ny1 * dz);
 }
 
-// y = K x for one row (node i).
-template <int D, class T, int B>
-__device__ __forceinline__ void spmv_row(const DevMatrix<T>& K, int row, long long i, int nx1, int ny1,
-                                         const T* __restrict__ x, T y[B]) {
-#pragma unroll
-  for (int a = 0; a < B; ++a) y[a] = (T)0;
-  constexpr int ZR = (D == 3) ? 2 : 0;
-  const long long cap = K.cap;
-#pragma unroll
-  for (int dz = -ZR; dz <= ZR; ++dz)
-#pragma unroll
-    for (int dy = -2; dy <= 2; ++dy)
-#pragma unroll
-      for (int dx = -2; dx <= 2; ++dx) {
-        const int slot = (D == 2) ? (dx + 2) + 5 * (dy + 2) : (dx + 2) + 5 * ((dy + 2) + 5 * (dz + 2));
-        const long long j = nbr<D>(i, dx, dy, dz, nx1, ny1);
-        T xj[B], kb[B * B];
-        ld_node<B, T, false>(x, j, xj);
-        ld_block<B, T>(&K.val[((long long)slot * cap + row) * (B * B)], kb);
-#pragma unroll
-        for (int a = 0; a < B; ++a)
-#pragma unroll
-          for (int b = 0; b < B; ++b) y[a] += kb[a * B + b] * xj[b];
-      }
-}
-
 __device__ __forceinline__ double wsum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -163,7 +137,7 @@ __global__ void __launch_bounds__(KTPB) k_bicg_B(DevGrid G, DevMatrix<T> K, Kryl
   if (row < *K.nrow) {
     const long long i = K.rows[row];
     T y[B];
-    spmv_row<D, T, B>(K, row, i, G.nx1, G.ny1, v.phat, y);
+    stencil_row_product<D, T, B>(K, row, i, G.nx1, G.ny1, v.phat, y);
 #pragma unroll
     for (int a = 0; a < B; ++a) {
       v.v[i * B + a] = y[a];
@@ -230,7 +204,7 @@ __global__ void __launch_bounds__(KTPB) k_bicg_D(DevGrid G, DevMatrix<T> K, Kryl
   if (row < *K.nrow) {
     const long long i = K.rows[row];
     T y[B];
-    spmv_row<D, T, B>(K, row, i, G.nx1, G.ny1, v.shat, y);
+    stencil_row_product<D, T, B>(K, row, i, G.nx1, G.ny1, v.shat, y);
 #pragma unroll
     for (int a = 0; a < B; ++a) {
       const long long d = i * B + a;
@@ -298,7 +272,7 @@ __global__ void __launch_bounds__(KTPB) k_bicg_restart(DevGrid G, DevMatrix<T> K
   if (row < *K.nrow) {
     const long long i = K.rows[row];
     T y[B], r[B], z[B];
-    spmv_row<D, T, B>(K, row, i, G.nx1, G.ny1, v.x, y);
+    stencil_row_product<D, T, B>(K, row, i, G.nx1, G.ny1, v.x, y);
 #pragma unroll
     for (int a = 0; a < B; ++a) {
       const long long d = i * B + a;
@@ -348,11 +322,14 @@ cudaError_t launch_bicgstab_init(DevMatrix<T> K, const double* res, const uint8_
 
 template <int D, class T, int B>
 cudaError_t launch_bicgstab_iter(const DevGrid& G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S,
-                                 int nblk, cudaStream_t st) {
+                                 int nblk, cudaStream_t st, const MgApply<T>* mg) {
   k_bicg_B<D, T, B><<<nblk, KTPB, 0, st>>>(G, K, v, S);
   k_bicg_C<D, T, B><<<nblk, KTPB, 0, st>>>(K, v, S);
+  // multigrid: C left the first smoothing sweep in shat; the V-cycle completes it
+  if (mg) launch_mg_vcycle<D, T, B>(*mg, v.s, v.shat, &S->done, st);
   k_bicg_D<D, T, B><<<nblk, KTPB, 0, st>>>(G, K, v, S);
   k_bicg_A<D, T, B><<<nblk, KTPB, 0, st>>>(K, v, S);
+  if (mg) launch_mg_vcycle<D, T, B>(*mg, v.p, v.phat, &S->done, st);
   return cudaGetLastError();
 }
 // max |d| over the free displacement DOFs of the active rows (the first D of
@@ -413,7 +390,7 @@ __global__ void __launch_bounds__(KTPB) k_spmv(DevGrid G, DevMatrix<T> K, const 
   if (row >= *K.nrow) return;
   const long long i = K.rows[row];
   T v[B];
-  spmv_row<D, T, B>(K, row, i, G.nx1, G.ny1, x, v);
+  stencil_row_product<D, T, B>(K, row, i, G.nx1, G.ny1, x, v);
 #pragma unroll
   for (int a = 0; a < B; ++a) y[i * B + a] = v[a];
 }
@@ -448,7 +425,7 @@ cudaError_t launch_update_du(DevMatrix<T> K, const T* x, const uint8_t* fixed, d
                                                   KrylovVecs<D, T>, KrylovScalars*, double, int, int,   \
                                                   cudaStream_t);                                        \
   template cudaError_t launch_bicgstab_iter<D, T, B>(const DevGrid&, DevMatrix<T>, KrylovVecs<D, T>,       \
-                                                  KrylovScalars*, int, cudaStream_t);                   \
+                                                  KrylovScalars*, int, cudaStream_t, const MgApply<T>*); \
   template cudaError_t launch_bicgstab_restart<D, T, B>(const DevGrid&, DevMatrix<T>, const double*,       \
                                                      const uint8_t*, KrylovVecs<D, T>, KrylovScalars*,  \
                                                      double, int, int, cudaStream_t);                   \

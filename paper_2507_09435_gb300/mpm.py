@@ -22,7 +22,7 @@ MPM_FP64, MPM_MIXED = 0, 1
 MPM_BICGSTAB, MPM_GMRES = 0, 1
 MPM_FORCING_FIXED, MPM_FORCING_EW = 0, 1
 MPM_SOLID, MPM_UP = 0, 1
-MPM_PC_AUTO, MPM_PC_NODE, MPM_PC_SEG4 = 0, 1, 2
+MPM_PC_AUTO, MPM_PC_NODE, MPM_PC_SEG4, MPM_PC_MG = 0, 1, 2, 3
 
 STATUS = {
     0: "MPM_OK", 1: "MPM_ERR_INVALID_ARG", 2: "MPM_ERR_OOM", 3: "MPM_ERR_CUDA",
@@ -105,7 +105,7 @@ _lib = None
 # every symbol declared in include/mpm.h
 EXPORTS = ["mpm_create_scene", "mpm_set_gravity", "mpm_set_dirichlet", "mpm_begin_step", "mpm_newton_step",
            "mpm_set_du", "mpm_assemble", "mpm_commit_step", "mpm_solve_step", "mpm_get_residual", "mpm_get_du", "mpm_get_mass",
-           "mpm_get_counts", "mpm_get_jacobian_bsr", "mpm_get_particles", "mpm_get_pressure",
+           "mpm_get_counts", "mpm_get_jacobian_bsr", "mpm_get_mg_level", "mpm_get_particles", "mpm_get_pressure",
            "mpm_set_traction", "mpm_kernel_launches", "mpm_set_params", "mpm_get_particle_increment",
            "mpm_adjoint", "mpm_adjoint_step", "mpm_set_state",
            "mpm_time_spmv", "mpm_set_particles", "mpm_residual_norm_noalloc", "mpm_noalloc_last_error",
@@ -140,6 +140,8 @@ def lib(build: bool = True):
     L.mpm_get_mass.argtypes = [_P, _D]
     L.mpm_get_counts.argtypes = [_P, _I, _LL]
     L.mpm_get_jacobian_bsr.argtypes = [_P, ctypes.c_longlong, _I, _LL, _I, _D]
+    L.mpm_get_mg_level.argtypes = [_P, ctypes.c_int, _I, _I, _I, ctypes.c_int, _I, _D,
+                                   ctypes.POINTER(ctypes.c_ubyte), _D]
     L.mpm_get_particles.argtypes = [_P, _D, _D, _D, _D, _D]
     L.mpm_get_pressure.argtypes = [_P, _D]
     L.mpm_set_traction.argtypes = [_P, ctypes.c_int, _I, _D]
@@ -312,6 +314,32 @@ def mpm_get_counts(h):
     nb = ctypes.c_longlong(0)
     _check(lib().mpm_get_counts(h, ctypes.byref(na), ctypes.byref(nb)), h)
     return na.value, nb.value
+
+
+def mpm_get_mg_level(h, level, dim, B):
+    """Coarse level `level` >= 1 of the multigrid hierarchy: dict with levels,
+    dims, nodes, vals[nrow, 5**dim, B, B], fixed[nnode*B], lambda_max."""
+    levels = ctypes.c_int(0)
+    if level == 0:
+        lam = ctypes.c_double(0.0)
+        _check(lib().mpm_get_mg_level(h, 0, ctypes.byref(levels), None, None, 0, None, None, None,
+                                      ctypes.byref(lam)), h)
+        return dict(levels=levels.value, lambda_max=lam.value)
+    dims = np.zeros(3, dtype=np.int32)
+    nrow = ctypes.c_int(0)
+    _check(lib().mpm_get_mg_level(h, level, ctypes.byref(levels), _p(dims, _I), ctypes.byref(nrow), 0, None,
+                                  None, None, None), h)
+    n = nrow.value
+    S = 5 ** dim
+    nodes = np.zeros(max(n, 1), dtype=np.int32)
+    vals = np.zeros(max(n, 1) * S * B * B)
+    fixed = np.zeros(int(np.prod(dims)) * B, dtype=np.uint8)
+    lam = ctypes.c_double(0.0)
+    _check(lib().mpm_get_mg_level(h, level, ctypes.byref(levels), _p(dims, _I), ctypes.byref(nrow), n,
+                                  _p(nodes, _I), _p(vals), fixed.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)),
+                                  ctypes.byref(lam)), h)
+    return dict(levels=levels.value, dims=dims, nodes=nodes[:n], vals=vals[:n * S * B * B].reshape(n, S, B, B),
+                fixed=fixed.astype(bool), lambda_max=lam.value)
 
 
 def mpm_get_jacobian_bsr(h, dim):
@@ -511,6 +539,9 @@ class GpuScene:
 
     def jacobian_bsr(self):
         return mpm_get_jacobian_bsr(self.h, self.B)
+
+    def mg_level(self, level):
+        return mpm_get_mg_level(self.h, level, self.dim, self.B)
 
     def pressure(self):
         return mpm_get_pressure(self.h, self.np)

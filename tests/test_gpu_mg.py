@@ -1,0 +1,304 @@
+"""Geometric multigrid preconditioner (precond MPM_PC_MG) on the GPU.
+
+* The coarse operators are the Galerkin products P^T A P of the level above,
+  with P the per-axis linear interpolation from every second node (rows of
+  prescribed fine DOFs zero) -- checked block by block against the same
+  product formed with scipy from the exported fine Jacobian.
+* Converged load steps with the multigrid preconditioner match the oracle
+  (the same increment bar as the block-Jacobi parity tests), in 2D, 3D and
+  for the coupled u-p formulation.
+* On the footing the V-cycle cuts the BiCGStab iterations per Newton
+  iteration by a large factor at the same Newton convergence.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import mpm_oracle as O
+from paper_2507_09435_gb300 import mpm, scenes as S
+
+from parity_util import DU_TOL, du_error, fixed_mask
+from test_gpu_parity import _run_parity
+
+pytestmark = pytest.mark.gpu
+
+
+def _prolongation(fine_dims, coarse_dims, B, keep):
+    """P (fine DOFs x coarse DOFs): per-axis weights 1 (coincident node) or
+    1/2 (odd fine node), per component; rows where `keep` is False are zero."""
+    mats = []
+    for n1, nc in zip(fine_dims, coarse_dims):
+        rows, cols, vals = [], [], []
+        for i in range(n1):
+            for J in (i // 2, (i + 1) // 2) if i % 2 else (i // 2,):
+                rows.append(i)
+                cols.append(J)
+                vals.append(1.0 if i % 2 == 0 else 0.5)
+        mats.append(sp.csr_matrix((vals, (rows, cols)), shape=(n1, nc)))
+    P = mats[0]
+    for m in mats[1:]:
+        P = sp.kron(m, P)          # x fastest
+    P = sp.kron(P, sp.eye(B)).tocsr()
+    return sp.diags(keep.astype(float)) @ P
+
+
+def _bsr_to_csr(row_node, row_ptr, col_node, val, nnode, B):
+    rows, cols, vals = [], [], []
+    for r, n in enumerate(row_node):
+        for k in range(row_ptr[r], row_ptr[r + 1]):
+            m = col_node[k]
+            for a in range(B):
+                for b in range(B):
+                    rows.append(n * B + a)
+                    cols.append(m * B + b)
+                    vals.append(val[k, a, b])
+    N = nnode * B
+    return sp.csr_matrix((vals, (rows, cols)), shape=(N, N))
+
+
+def _level_to_csr(lev, dims, B, dim):
+    nodes, vals = lev["nodes"], lev["vals"]
+    nx, ny = int(dims[0]), int(dims[1])
+    N = int(np.prod(dims)) * B
+    rows, cols, v = [], [], []
+    for r, n in enumerate(nodes):
+        ix, iy, iz = n % nx, (n // nx) % ny, n // (nx * ny)
+        for s in range(5 ** dim):
+            dx, dy, dz = s % 5 - 2, (s // 5) % 5 - 2, (s // 25 - 2) if dim == 3 else 0
+            jx, jy, jz = ix + dx, iy + dy, iz + dz
+            if not (0 <= jx < nx and 0 <= jy < ny and 0 <= jz < int(dims[2])):
+                assert np.all(vals[r, s] == 0.0)
+                continue
+            m = jx + nx * (jy + ny * jz)
+            for a in range(B):
+                for b in range(B):
+                    if vals[r, s, a, b] != 0.0:
+                        rows.append(n * B + a)
+                        cols.append(m * B + b)
+                        v.append(vals[r, s, a, b])
+    return sp.csr_matrix((v, (rows, cols)), shape=(N, N))
+
+
+def _check_galerkin(sc, gs, st, tol):
+    d, B = sc.dim, sc.B
+    fixed = fixed_mask(sc, st)
+    M = gs.mass()
+    active = M > 1e-12 * sc.mass.max()
+    A = _bsr_to_csr(*gs.jacobian_bsr(), sc.nnode, B)
+    if B > d:
+        # the hierarchy is built in solver units: pressure rows and columns
+        # carry p_scale (the identity entries of prescribed DOFs stay 1)
+        psc = O.OracleScene.from_scene(sc).p_scale
+        w = np.ones(A.shape[0])
+        w[d::B] = psc
+        wf = np.where(fixed, 1.0, w)
+        A = (sp.diags(wf) @ A @ sp.diags(wf)).tocsr()
+    dims = [sc.n[a] + 1 for a in range(d)] + ([1] if d == 2 else [])
+    act, fix = active, fixed
+    info = gs.mg_level(0)
+    L = info["levels"]
+    assert L >= 3, L
+    assert np.isfinite(info["lambda_max"]) and info["lambda_max"] >= 0.9
+    for l in range(1, L):
+        lev = gs.mg_level(l)
+        cd = [int(x) for x in lev["dims"]]
+        assert cd[:d] == [n // 2 + 1 for n in dims[:d]]
+        keep = np.repeat(act, B) & ~fix
+        P = _prolongation(dims[:d], cd[:d], B, keep)
+        Ac = (P.T @ A @ P).tocsr()
+        # coarse activity and prescribed DOFs follow from the fine level
+        Pn = _prolongation(dims[:d], cd[:d], 1, act)
+        act_c = np.asarray((abs(Pn).T @ np.ones(Pn.shape[0])) > 0).ravel()
+        assert set(lev["nodes"].tolist()) == set(np.nonzero(act_c)[0].tolist()), l
+        free_c = np.asarray((abs(P).T @ keep.astype(float)) > 0).ravel()
+        fix_c = ~free_c
+        assert np.array_equal(lev["fixed"].reshape(-1, B)[act_c], fix_c.reshape(-1, B)[act_c]), l
+        Ac = Ac + sp.diags((fix_c & np.repeat(act_c, B)).astype(float))
+        G = _level_to_csr(lev, cd, B, d)
+        rows = (lev["nodes"][:, None] * B + np.arange(B)[None, :]).ravel()
+        Ad = Ac[rows].toarray()
+        Gd = G[rows].toarray()
+        scale = np.abs(Ad).max(axis=1, keepdims=True) + 1e-300
+        err = float((np.abs(Gd - Ad) / scale).max())
+        assert err < tol, (l, err)
+        assert np.isfinite(lev["lambda_max"]) or l == L - 1
+        # next level from the GPU's own operator
+        A, dims, act, fix = G, cd, act_c, fix_c
+    return L
+
+
+@pytest.mark.parametrize("precision,tol", [(mpm.MPM_FP64, 1e-12), (mpm.MPM_MIXED, 2e-6)])
+def test_galerkin_levels_footing(precision, tol):
+    sc = S.footing(nx=48, ny=24, h=0.5, nsteps=20, settle_frac=0.1)
+    gs = mpm.GpuScene(sc, precision=precision, newton_tol=1e-10, precond=mpm.MPM_PC_MG)
+    gs.solve_step(sc.steps[0])
+    st = sc.steps[1]
+    gs.begin(st)
+    gs.newton()
+    gs.assemble()
+    _check_galerkin(sc, gs, st, tol)
+    gs.close()
+
+
+def test_galerkin_levels_column_3d():
+    sc = S.column_collapse_3d(nx=16, ny=16, nz=12, h=0.1, col=(6, 6, 8), nsteps=3, pc_mean=-8e3, E=1e6)
+    gs = mpm.GpuScene(sc, precision=mpm.MPM_FP64, newton_tol=1e-10, precond=mpm.MPM_PC_MG)
+    st = sc.steps[0]
+    gs.begin(st)
+    gs.assemble()
+    _check_galerkin(sc, gs, st, 1e-12)
+    gs.close()
+
+
+def test_galerkin_levels_terzaghi_up():
+    sc = S.terzaghi(ncell=40, dt=5e4, nsteps=3)
+    gs = mpm.GpuScene(sc, precision=mpm.MPM_FP64, newton_tol=1e-10, precond=mpm.MPM_PC_MG)
+    st = sc.steps[0]
+    gs.begin(st)
+    gs.assemble()
+    _check_galerkin(sc, gs, st, 1e-12)
+    gs.close()
+
+
+def test_multigrid_block_matches_oracle():
+    _run_parity(S.block_compression(nsteps=3), 3, jac_every_step=False, precond=mpm.MPM_PC_MG)
+
+
+def test_multigrid_footing_matches_oracle():
+    sc = S.footing(nx=48, ny=24, h=0.5, nsteps=20, settle_frac=0.1)
+    _run_parity(sc, 4, jac_every_step=False, expect_plastic=True, precond=mpm.MPM_PC_MG)
+
+
+def test_multigrid_column_3d_matches_oracle():
+    sc = S.column_collapse_3d(nx=12, ny=12, nz=12, h=0.1, col=(4, 4, 6), nsteps=3, pc_mean=-8e3, E=1e6)
+    _run_parity(sc, 1, jac_every_step=False, expect_plastic=True, precond=mpm.MPM_PC_MG)
+
+
+def test_multigrid_oedometer_3d_matches_oracle():
+    _run_parity(S.oedometer_3d(), 2, jac_every_step=False, expect_plastic=True, precond=mpm.MPM_PC_MG)
+
+
+def _tiny_block(nsteps=3, strain=2e-3):
+    """2x2-cell Neo-Hookean block (16 particles) on a 6x6 grid: 25 active
+    nodes, 50 unknowns -- within the dense level (at most 128 unknowns)."""
+    n, h = (6, 6, 0), 1.0 / 6
+    x = S.lattice(S.box_cells((2, 2), (4, 4)), h, 2, 2)
+    mat = S.Material(model=S.MODEL_NH, E=1e6, nu=0.3, rho=1000.0)
+    vol = np.full(x.shape[0], h * h / 4)
+    sc = S.Scene("tiny_block", 2, n, h, (0.0, 0.0, 0.0), x, vol, vol * mat.rho, np.zeros(x.shape[0], np.int32),
+                 [mat])
+    nx1 = n[0] + 1
+    bot = [(ix + nx1 * iy) * 2 + 1 for iy in range(0, 3) for ix in range(nx1)]
+    top = [(ix + nx1 * iy) * 2 + 1 for iy in range(4, 7) for ix in range(nx1)]
+    left = [(ix + nx1 * iy) * 2 for iy in range(nx1) for ix in range(0, 3)]
+    dof = np.array(bot + top + left, dtype=np.int64)
+    val = np.concatenate([np.zeros(len(bot)), np.full(len(top), -strain * 2 * h), np.zeros(len(left))])
+    sc.steps = [S.LoadStep(dof, val, (0.0, 0.0, 0.0)) for _ in range(nsteps)]
+    return sc
+
+
+def test_multigrid_dense_only_level():
+    """A grid small enough that the fine level itself is the dense level
+    (nrow * B <= 128 unknowns): the preconditioner is the inverse up to FP32
+    rounding, so BiCGStab needs at most a few iterations per Newton
+    iteration, and the steps match the oracle."""
+    sc = _tiny_block()
+    gs = mpm.GpuScene(sc, precision=mpm.MPM_FP64, newton_tol=1e-12, forcing=mpm.MPM_FORCING_FIXED,
+                      krylov_rtol=1e-12, precond=mpm.MPM_PC_MG)
+    orc = O.OracleScene.from_scene(sc)
+    for st in sc.steps:
+        gs.begin(st)
+        assert mpm.mpm_get_counts(gs.h)[0] * sc.B <= 128
+        assert gs.mg_level(0)["levels"] == 1
+        its = []
+        for _ in range(6):
+            nr = gs.newton()
+            its.append(nr.krylov_iters)
+            if nr.rel_residual <= 1e-12:
+                break
+        assert nr.rel_residual <= 1e-12
+        assert max(its) <= 4, its
+        out = orc.solve_step(st.dof, st.value, st.gravity, tol=1e-13)
+        assert du_error(gs.du(), out["du"]) < DU_TOL
+        gs.commit()
+    gs.close()
+
+
+def test_multigrid_footing_iterations_and_solution():
+    """Mixed precision footing (64x32 grid): the same load steps with node
+    block-Jacobi and with the V-cycle converge to the same particle positions
+    within the Newton tolerance, with at least 5x fewer BiCGStab iterations."""
+    sc = S.footing(nx=64, ny=32, h=0.4, nsteps=20, settle_frac=0.1)
+    res = {}
+    for pc in (mpm.MPM_PC_NODE, mpm.MPM_PC_MG):
+        gs = mpm.GpuScene(sc, precision=mpm.MPM_MIXED, newton_tol=1e-8, precond=pc)
+        kit = nit = 0
+        for st in sc.steps[:4]:
+            rep = gs.solve_step(st)
+            assert rep.converged, (pc, rep.status)
+            kit += rep.krylov_iters_total
+            nit += rep.newton_iters
+        res[pc] = (gs.particles()["x"], kit / nit)
+        gs.close()
+    xb, kb = res[mpm.MPM_PC_NODE]
+    xm, km = res[mpm.MPM_PC_MG]
+    x0 = np.zeros_like(xb)
+    x0[:, :2] = sc.x[:, :2]
+    disp = np.abs(xb - x0).max()
+    assert np.abs(xm - xb).max() <= 1e-5 * disp, np.abs(xm - xb).max() / disp
+    assert km * 5 <= kb, (km, kb)
+
+
+def test_multigrid_terzaghi_matches_oracle():
+    h = 0.5
+    sc = S.terzaghi(ncell=20, dt=0.5 * h * h / 1.8e-6, nsteps=4)
+    B = sc.B
+    orc = O.OracleScene.from_scene(sc)
+    gs = mpm.GpuScene(sc, newton_tol=1e-12, newton_maxit=30, forcing=mpm.MPM_FORCING_FIXED, krylov_rtol=1e-13,
+                      krylov_maxit=20000, precond=mpm.MPM_PC_MG)
+    for k, st in enumerate(sc.steps):
+        gs.begin(st)
+        rel, best, it = 1.0, 1.0, 0
+        while rel > 1e-13 and it < 30:
+            rel = gs.newton().rel_residual
+            it += 1
+            if it >= 3 and rel > 0.5 * best:
+                break
+            best = min(best, rel)
+        assert min(rel, best) <= 1e-11, (k, rel)
+        out = orc.solve_step(st.dof, st.value, st.gravity, tol=1e-13, maxit=30)
+        assert du_error(gs.du(), out["du"], B, 2) < DU_TOL, k
+        gs.commit()
+    gs.close()
+
+
+def test_multigrid_adjoint_matches_block_jacobi():
+    """The adjoint solve with the V-cycle built on J^T gives the same
+    per-particle gradients as with block-Jacobi."""
+    sc = S.footing(nx=48, ny=24, h=0.5, nsteps=20, settle_frac=0.1)
+    rng = np.random.default_rng(5)
+    w = rng.standard_normal((sc.np, 3))
+    w[:, 2] = 0.0
+    out = {}
+    for pc in (mpm.MPM_PC_NODE, mpm.MPM_PC_MG):
+        gs = mpm.GpuScene(sc, precision=mpm.MPM_FP64, newton_tol=1e-12, forcing=mpm.MPM_FORCING_FIXED,
+                          krylov_rtol=1e-13, krylov_maxit=20000, precond=pc)
+        gs.solve_step(sc.steps[0])
+        st = sc.steps[1]
+        gs.begin(st)
+        for _ in range(30):
+            if gs.newton().rel_residual <= 1e-12:
+                break
+        gE, gP, _ = gs.adjoint(dL_dx=w)
+        out[pc] = {"E": gE, "phi": gP}
+        gs.close()
+    gb, gm = out[mpm.MPM_PC_NODE], out[mpm.MPM_PC_MG]
+    for key in ("E", "phi"):
+        a, b = np.asarray(gb[key]), np.asarray(gm[key])
+        assert np.abs(a - b).max() <= 1e-7 * np.abs(a).max(), key
+
+
+def test_multigrid_rejects_gmres():
+    sc = S.block_compression(nsteps=1)
+    with pytest.raises(mpm.MPMError):
+        mpm.GpuScene(sc, krylov=mpm.MPM_GMRES, precond=mpm.MPM_PC_MG)
