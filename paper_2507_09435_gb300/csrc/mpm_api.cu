@@ -519,7 +519,7 @@ MgApply<T> mg_view(mpm_scene* s) {
   f.z = nullptr;
   f.r = (T*)s->d_mg_v0 + s->vpad;
   a.caps[0] = s->cap;
-  // single-block tail: from the first coarse level with at most MG_TAIL_ROWS rows
+  // cluster tail: from the first coarse level with at most MG_TAIL_ROWS rows
   a.tail = std::max(a.L - 1, 1);
   for (int l = 1; l < a.L; ++l)
     if (s->h_mgn[l] <= MG_TAIL_ROWS) {
@@ -688,7 +688,10 @@ void krylov_solve(mpm_scene* s, double eta, double rnorm, int& kit, int& kstat, 
   } else {
   const bool use_mg = s->mg && s->mg_L > 0;
   MgApply<T> mga{};
-  if (use_mg) mga = mg_view<T>(s);
+  if (use_mg) {
+    mga = mg_view<T>(s);
+    mga.cluster = mg_tail_cluster<D, T, B>();
+  }
   const MgApply<T>* mgp = use_mg ? &mga : nullptr;
   int* d_done = &s->d_S->done;
   const int chunk = use_mg ? MG_CHUNK : GRAPH_CHUNK;
@@ -711,7 +714,7 @@ void krylov_solve(mpm_scene* s, double eta, double rnorm, int& kit, int& kstat, 
     ck(cudaStreamSynchronize(st), "sync");
     check_err_bits(s);
   }
-  std::vector<int> sig = {s->cap, use_mg ? s->mg_L : 0, use_mg ? mga.tail : 0};
+  std::vector<int> sig = {s->cap, use_mg ? s->mg_L : 0, use_mg ? mga.tail : 0, use_mg ? mga.cluster : 0};
   if (use_mg)
     for (int l = 1; l < s->mg_L; ++l) sig.push_back(s->mgl[l].cap);
   if (s->pblocks == 0 && s->use_graph && sig != s->graph_sig) build_graph<D, T, B>(s, nblk, mgp, chunk, sig);

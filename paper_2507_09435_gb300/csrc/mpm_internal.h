@@ -250,18 +250,21 @@ struct MgLevel {
 constexpr int MG_MAX_LEVELS = 12;
 constexpr int MG_DENSE_MAX = 128;   // unknowns of the coarsest (dense) level
 constexpr int MG_POWER_IT = 8;      // power iterations for lambda_max(D^-1 A)
-constexpr int MG_TAIL_ROWS = 1024;  // coarse levels this small run in one block
+constexpr int MG_TAIL_ROWS = 16384; // coarse levels this small run inside one cluster
 constexpr int MG_TAIL_TPB = 512;
 // A built hierarchy, for the V-cycle launches: levels 0..L-1 (the last
-// dense); levels tail..L-1 (tail >= 1) run inside one single-block kernel,
-// the levels above it one launch per step.
+// dense); levels tail..L-1 (tail >= 1) run inside one kernel of one
+// thread-block cluster of `cluster` blocks, the levels above it one launch
+// per step.
 template <class T>
 struct MgApply {
   MgLevel<T> lev[MG_MAX_LEVELS];
   int caps[MG_MAX_LEVELS];
-  int L, tail;
+  int L, tail, cluster;
   const float* invT;
 };
+template <int D, class T, int B>
+int mg_tail_cluster();
 template <int D>
 cudaError_t launch_mg_flags(int fx, int fy, int fz, const int* n2r_f, int cx, int cy, long long nc, int* flag,
                             cudaStream_t st);

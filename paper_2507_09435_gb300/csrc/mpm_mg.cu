@@ -22,17 +22,22 @@
 // * coarsest level (at most MG_DENSE_MAX unknowns): a dense inverse by
 //   Gauss-Jordan elimination with partial pivoting in shared memory;
 // * the levels with at most MG_TAIL_ROWS rows run, with the dense solve,
-//   inside one single-block kernel (block barriers between the steps); the
-//   levels above take one launch per step (residual, restriction with the
-//   coarse level's first sweep, prolongation, post-smoothing).
+//   inside one kernel of one thread-block cluster (cluster barriers between
+//   the steps); the levels above take one launch per step (residual,
+//   restriction with the coarse level's first sweep, prolongation,
+//   post-smoothing).
 // The V-cycle is a fixed linear operator, so it serves as the right
 // preconditioner of BiCGStab.  Every apply kernel returns at once when the
 // Krylov solve is done (the graph chunks of iterations run to their end).
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "mpm_internal.h"
 
 namespace mpm {
+
+namespace cg = cooperative_groups;
 
 namespace {
 constexpr int MTPB = KRYLOV_TPB;
@@ -510,35 +515,53 @@ __global__ void __launch_bounds__(MTPB) k_mg_smooth(MgLevel<T> l, const T* b, co
   row_smooth<D, T, B, false>(l, row, b, zin, zout, live);
 }
 
-// Levels mg.tail .. L-1 of the V-cycle in one block: the coarse levels are
-// too small to fill the GPU, so their steps run back to back separated by
-// block barriers instead of one launch each.  On entry level `tail` holds its
+// Levels mg.tail .. L-1 of the V-cycle in one thread-block cluster: the
+// coarse levels are too small to fill the GPU, so their steps run back to
+// back, separated by cluster barriers (release/acquire at cluster scope, which
+// makes the global-memory writes of one step visible to every block of the
+// cluster), instead of one launch each.  On entry level `tail` holds its
 // right-hand side and first smoothing sweep (written by the restriction
 // above); on exit its corrected, post-smoothed z.  Coarse levels use node
-// blocks, so the smoother needs no warp exchange.
+// blocks, so the smoother needs no warp exchange.  Every block reads the
+// same done flag, so either all return or none does.
 template <int D, class T, int B>
 __global__ void __launch_bounds__(MG_TAIL_TPB) k_mg_tail(const __grid_constant__ MgApply<T> mg, const int* done) {
   if (is_done(done)) return;
+  cg::cluster_group cl = cg::this_cluster();
   __shared__ float bv[MG_DENSE_MAX];
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x, ts = gridDim.x * blockDim.x;
   const int L = mg.L, l0 = mg.tail;
   for (int l = l0; l + 1 < L; ++l) {
     const MgLevel<T>& f = mg.lev[l];
     const MgLevel<T>& c = mg.lev[l + 1];
     const int nf = *f.K.nrow, nc = *c.K.nrow;
-    for (int row = threadIdx.x; row < nf; row += blockDim.x) row_residual<D, T, B, true>(f, row, f.b, f.z, f.r);
-    __syncthreads();
-    for (int row = threadIdx.x; row < nc; row += blockDim.x) row_restrict<D, T, B>(f, f.r, c, row, l + 2 < L);
-    __syncthreads();
+    for (int row = t0; row < nf; row += ts) row_residual<D, T, B, true>(f, row, f.b, f.z, f.r);
+    cl.sync();
+    for (int row = t0; row < nc; row += ts) row_restrict<D, T, B>(f, f.r, c, row, l + 2 < L);
+    cl.sync();
   }
-  block_dense_apply<T, B>(mg.lev[L - 1], mg.invT, mg.lev[L - 1].b, mg.lev[L - 1].z, bv);
+  {
+    const MgLevel<T>& c = mg.lev[L - 1];
+    const int n = *c.K.nrow * B;
+    if (n > 0 && n <= MG_DENSE_MAX) {
+      for (int k = threadIdx.x; k < n; k += blockDim.x) bv[k] = (float)c.b[(long long)c.K.rows[k / B] * B + k % B];
+      __syncthreads();
+      for (int k = t0; k < n; k += ts) {
+        float s = 0.0f;
+        for (int j = 0; j < n; ++j) s += mg.invT[j * n + k] * bv[j];
+        c.z[(long long)c.K.rows[k / B] * B + k % B] = (T)s;
+      }
+    }
+    cl.sync();
+  }
   for (int l = L - 2; l >= l0; --l) {
     const MgLevel<T>& f = mg.lev[l];
     const MgLevel<T>& c = mg.lev[l + 1];
     const int nf = *f.K.nrow;
-    for (int row = threadIdx.x; row < nf; row += blockDim.x) row_prolong<D, T, B>(f, f.z, c, f.r, row);
-    __syncthreads();
-    for (int row = threadIdx.x; row < nf; row += blockDim.x) row_smooth<D, T, B, true>(f, row, f.b, f.r, f.z, 0u);
-    __syncthreads();
+    for (int row = t0; row < nf; row += ts) row_prolong<D, T, B>(f, f.z, c, f.r, row);
+    cl.sync();
+    for (int row = t0; row < nf; row += ts) row_smooth<D, T, B, true>(f, row, f.b, f.r, f.z, 0u);
+    cl.sync();
   }
 }
 
@@ -618,7 +641,21 @@ cudaError_t launch_mg_vcycle(const MgApply<T>& mg, const T* b0, T* z0, const int
     k_mg_restrict<D, T, B><<<nblk_rows(mg.caps[l + 1]), MTPB, 0, st>>>(lev[l], lev[l].r, lev[l + 1],
                                                                        (l + 2 < L) ? 1 : 0, done);
   }
-  k_mg_tail<D, T, B><<<1, MG_TAIL_TPB, 0, st>>>(mg, done);
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)mg.cluster);
+    cfg.blockDim = dim3(MG_TAIL_TPB);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)mg.cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_mg_tail<D, T, B>, mg, done);
+    if (e != cudaSuccess) return e;
+  }
   // up from the tail: prolongation into the residual buffer, post-smoothing
   for (int l = l0 - 1; l >= 0; --l) {
     const T* b = (l == 0) ? b0 : lev[l].b;
@@ -627,6 +664,33 @@ cudaError_t launch_mg_vcycle(const MgApply<T>& mg, const T* b0, T* z0, const int
     k_mg_smooth<D, T, B><<<nblk_rows(mg.caps[l]), MTPB, 0, st>>>(lev[l], b, lev[l].r, z, done);
   }
   return cudaGetLastError();
+}
+
+// Blocks of the tail cluster: 16 (a non-portable cluster size) where the
+// device can co-schedule such a cluster of the tail kernel, else 8.
+template <int D, class T, int B>
+int mg_tail_cluster() {
+  static int c = 0;
+  if (c) return c;
+  int size = 8;
+  if (cudaFuncSetAttribute(k_mg_tail<D, T, B>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(MG_TAIL_TPB);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 16;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_mg_tail<D, T, B>, &cfg) == cudaSuccess && nclusters >= 1)
+      size = 16;
+  }
+  cudaGetLastError();
+  c = size;
+  return c;
 }
 
 int mg_vcycle_launches(int L, int tail) {
@@ -638,7 +702,8 @@ int mg_vcycle_launches(int L, int tail) {
   template cudaError_t launch_mg_galerkin<D, T, B>(MgLevel<T>, MgLevel<T>, int, cudaStream_t);                \
   template cudaError_t launch_mg_power<D, T, B>(MgLevel<T>, int, T*, T*, double*, int, cudaStream_t);         \
   template cudaError_t launch_mg_dense_inverse<D, T, B>(MgLevel<T>, float*, cudaStream_t);                    \
-  template cudaError_t launch_mg_vcycle<D, T, B>(const MgApply<T>&, const T*, T*, const int*, cudaStream_t);
+  template cudaError_t launch_mg_vcycle<D, T, B>(const MgApply<T>&, const T*, T*, const int*, cudaStream_t); \
+  template int mg_tail_cluster<D, T, B>();
 MPM_MG_INST(2, float, 2)
 MPM_MG_INST(2, double, 2)
 MPM_MG_INST(3, float, 3)
