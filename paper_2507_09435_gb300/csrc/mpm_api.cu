@@ -516,7 +516,7 @@ MgApply<T> mg_view(mpm_scene* s) {
   f.node2row = s->d_node2row;
   f.fixed = s->d_fixed;
   f.b = nullptr;
-  f.z = nullptr;
+  f.z = (T*)s->d_mg_v0 + s->vlen + s->vpad;   // smoothing scratch
   f.r = (T*)s->d_mg_v0 + s->vpad;
   a.caps[0] = s->cap;
   // cluster tail: from the first coarse level with at most MG_TAIL_ROWS rows

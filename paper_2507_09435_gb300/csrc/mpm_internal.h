@@ -251,6 +251,7 @@ constexpr int MG_MAX_LEVELS = 12;
 constexpr int MG_DENSE_MAX = 128;   // unknowns of the coarsest (dense) level
 constexpr int MG_POWER_IT = 8;      // power iterations for lambda_max(D^-1 A)
 constexpr int MG_TAIL_ROWS = 16384; // coarse levels this small run inside one cluster
+constexpr int MG_NU0 = 2;           // smoothing sweeps per side on the finest level
 constexpr int MG_TAIL_TPB = 512;
 // A built hierarchy, for the V-cycle launches: levels 0..L-1 (the last
 // dense); levels tail..L-1 (tail >= 1) run inside one kernel of one

@@ -16,9 +16,10 @@
 //   one node, so the product again couples coarse nodes up to two apart: every
 //   level has the same stencil-BSR layout and the same row kernels;
 // * a coarse DOF none of whose fine DOFs is free becomes an identity row;
-// * smoother: one sweep of damped block Jacobi before and after the coarse
-//   correction, z += w D^-1 (b - A z), with w = c / lambda_max(D^-1 A) from a
-//   power iteration (the block inverses are stored pre-multiplied by w);
+// * smoother: damped block Jacobi, z += w D^-1 (b - A z), with
+//   w = c / lambda_max(D^-1 A) from a power iteration (the block inverses are
+//   stored pre-multiplied by w); MG_NU0 sweeps before and after the coarse
+//   correction on the finest level, one on the coarse levels;
 // * coarsest level (at most MG_DENSE_MAX unknowns): a dense inverse by
 //   Gauss-Jordan elimination with partial pivoting in shared memory;
 // * the levels with at most MG_TAIL_ROWS rows run, with the dense solve,
@@ -633,10 +634,19 @@ cudaError_t launch_mg_vcycle(const MgApply<T>& mg, const T* b0, T* z0, const int
     return cudaGetLastError();
   }
   const int l0 = std::min(std::max(mg.tail, 1), L - 1);
+  // level 0: MG_NU0 smoothing sweeps before and after the coarse correction
+  // (the first pre-sweep is fused into the Krylov kernel that produced z0);
+  // lev[0].z is a scratch vector there
+  const T* zc0 = z0;
+  for (int k = 1; k < MG_NU0; ++k) {
+    T* dst = (k & 1) ? lev[0].z : z0;
+    k_mg_smooth<D, T, B><<<nblk_rows(mg.caps[0]), MTPB, 0, st>>>(lev[0], b0, zc0, dst, done);
+    zc0 = dst;
+  }
   // down to the tail: residual, restriction (+ the next level's first sweep)
   for (int l = 0; l < l0; ++l) {
     const T* b = (l == 0) ? b0 : lev[l].b;
-    const T* z = (l == 0) ? z0 : lev[l].z;
+    const T* z = (l == 0) ? zc0 : lev[l].z;
     k_mg_residual<D, T, B><<<nblk_rows(mg.caps[l]), MTPB, 0, st>>>(lev[l], b, z, lev[l].r, done);
     k_mg_restrict<D, T, B><<<nblk_rows(mg.caps[l + 1]), MTPB, 0, st>>>(lev[l], lev[l].r, lev[l + 1],
                                                                        (l + 2 < L) ? 1 : 0, done);
@@ -657,11 +667,19 @@ cudaError_t launch_mg_vcycle(const MgApply<T>& mg, const T* b0, T* z0, const int
     if (e != cudaSuccess) return e;
   }
   // up from the tail: prolongation into the residual buffer, post-smoothing
-  for (int l = l0 - 1; l >= 0; --l) {
-    const T* b = (l == 0) ? b0 : lev[l].b;
-    T* z = (l == 0) ? z0 : lev[l].z;
-    k_mg_prolong<D, T, B><<<nblk_rows(mg.caps[l]), MTPB, 0, st>>>(lev[l], z, lev[l + 1], lev[l].r, done);
-    k_mg_smooth<D, T, B><<<nblk_rows(mg.caps[l]), MTPB, 0, st>>>(lev[l], b, lev[l].r, z, done);
+  for (int l = l0 - 1; l >= 1; --l) {
+    k_mg_prolong<D, T, B><<<nblk_rows(mg.caps[l]), MTPB, 0, st>>>(lev[l], lev[l].z, lev[l + 1], lev[l].r, done);
+    k_mg_smooth<D, T, B><<<nblk_rows(mg.caps[l]), MTPB, 0, st>>>(lev[l], lev[l].b, lev[l].r, lev[l].z, done);
+  }
+  k_mg_prolong<D, T, B><<<nblk_rows(mg.caps[0]), MTPB, 0, st>>>(lev[0], zc0, lev[1], lev[0].r, done);
+  {
+    // sweeps r -> (z scratch -> r ...) -> z0, the last one into z0
+    const T* src = lev[0].r;
+    for (int k = 0; k < MG_NU0; ++k) {
+      T* dst = (k == MG_NU0 - 1) ? z0 : ((src == lev[0].r) ? lev[0].z : lev[0].r);
+      k_mg_smooth<D, T, B><<<nblk_rows(mg.caps[0]), MTPB, 0, st>>>(lev[0], b0, src, dst, done);
+      src = dst;
+    }
   }
   return cudaGetLastError();
 }
@@ -695,7 +713,7 @@ int mg_tail_cluster() {
 
 int mg_vcycle_launches(int L, int tail) {
   if (L <= 1) return 1;
-  return 4 * std::min(std::max(tail, 1), L - 1) + 1;
+  return 4 * std::min(std::max(tail, 1), L - 1) + 1 + 2 * (MG_NU0 - 1);
 }
 
 #define MPM_MG_INST(D, T, B)                                                                                   \
