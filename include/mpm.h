@@ -242,6 +242,21 @@ mpm_status mpm_get_jacobian_bsr(const mpm_scene* s, long long cap, int* row_node
 mpm_status mpm_get_mg_level(const mpm_scene* s, int level, int* levels, int dims[3], int* nrow, int cap,
                             int* nodes, double* vals, unsigned char* fixed, double* lambda_max);
 
+/* Device-pointer variants: the caller's DEVICE buffers (for example the data
+ * pointers of CUDA tensors on the scene's device), written on the scene's
+ * stream without synchronising the host (order later work on that stream, or
+ * synchronise it, before reading).  Same layouts and units as the host calls:
+ * d_du and d_r hold nnode*B doubles (u-p pressure in physical units), d_x
+ * np*3 doubles in the caller's particle order (z = 0 in 2D).  The scene's
+ * own device memory is never handed out. */
+mpm_status mpm_get_du_dev(const mpm_scene* s, double* d_du);
+mpm_status mpm_get_residual_dev(const mpm_scene* s, double* d_r);
+mpm_status mpm_get_positions_dev(const mpm_scene* s, double* d_x);
+/* mpm_set_dirichlet with the DOF indices (int64) and values in device memory;
+ * synchronises the scene's stream to report an index outside [0, nnode*B)
+ * (MPM_ERR_INVALID_ARG; the out-of-range entries are skipped). */
+mpm_status mpm_set_dirichlet_dev(mpm_scene* s, int n, const long long* d_dof, const double* d_value);
+
 /* Particle state in the caller's original order (any pointer may be NULL):
  * x[np*3], be[np*6] elastic left Cauchy-Green (xx,yy,zz,xy,yz,xz),
  * pc[np] preconsolidation, F[np*9] deformation gradient (row-major),

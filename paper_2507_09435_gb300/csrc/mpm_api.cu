@@ -1551,6 +1551,51 @@ mpm_status mpm_get_du(const mpm_scene* cs, double* du) {
   });
 }
 
+mpm_status mpm_get_du_dev(const mpm_scene* cs, double* d_du) {
+  mpm_scene* s = const_cast<mpm_scene*>(cs);
+  if (!s || !d_du) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] {
+    ck(launch_du_out(s->d_du, d_du, s->ndof, s->B, s->D, s->psc, s->st), "du out");
+    s->launches += 1;
+  });
+}
+
+mpm_status mpm_get_residual_dev(const mpm_scene* cs, double* d_r) {
+  mpm_scene* s = const_cast<mpm_scene*>(cs);
+  if (!s || !d_r) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] {
+    ck(launch_residual_out(s->d_r, s->d_fixed, s->d_node2row, d_r, s->ndof, s->B, s->D, s->psc, s->st),
+       "residual out");
+    s->launches += 1;
+  });
+}
+
+mpm_status mpm_get_positions_dev(const mpm_scene* cs, double* d_x) {
+  mpm_scene* s = const_cast<mpm_scene*>(cs);
+  if (!s || !d_x) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] {
+    ck(launch_positions_out(s->P, s->D, d_x, s->st), "positions out");
+    s->launches += 1;
+  });
+}
+
+mpm_status mpm_set_dirichlet_dev(mpm_scene* s, int n, const long long* d_dof, const double* d_value) {
+  if (!s) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] {
+    if (n < 0 || (n > 0 && (!d_dof || !d_value))) fail(MPM_ERR_INVALID_ARG, "dirichlet arrays");
+    ck(cudaMemsetAsync(s->d_fixed, 0, s->ndof, s->st), "memset");
+    ck(cudaMemsetAsync(s->d_bcval, 0, s->ndof * sizeof(double), s->st), "memset");
+    ck(cudaMemsetAsync(s->d_nplastic, 0, sizeof(int), s->st), "memset");
+    ck(launch_dirichlet_in(n, d_dof, d_value, s->d_fixed, s->d_bcval, s->ndof, s->B, s->D, s->psc, s->d_nplastic,
+                           s->st),
+       "dirichlet in");
+    s->launches += 1;
+    ck(cudaMemcpyAsync(s->h_int + 3, s->d_nplastic, sizeof(int), cudaMemcpyDeviceToHost, s->st), "copy");
+    ck(cudaStreamSynchronize(s->st), "sync");
+    if (s->h_int[3] != 0) fail(MPM_ERR_INVALID_ARG, "dirichlet dof out of range");
+  });
+}
+
 mpm_status mpm_get_mass(const mpm_scene* cs, double* mass) {
   mpm_scene* s = const_cast<mpm_scene*>(cs);
   if (!s || !mass) return MPM_ERR_INVALID_ARG;

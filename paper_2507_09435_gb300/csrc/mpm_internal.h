@@ -288,6 +288,15 @@ template <int D, class T, int B>
 cudaError_t launch_mg_vcycle(const MgApply<T>& mg, const T* b0, T* z0, const int* done, cudaStream_t st);
 int mg_vcycle_launches(int L, int tail);
 
+// device-pointer getters and Dirichlet setter (mpm_devio.cu)
+cudaError_t launch_du_out(const double* du, double* out, long long ndof, int B, int D, double psc,
+                          cudaStream_t st);
+cudaError_t launch_residual_out(const double* r, const uint8_t* fixed, const int* node2row, double* out,
+                                long long ndof, int B, int D, double psc, cudaStream_t st);
+cudaError_t launch_positions_out(const DevParticles& P, int D, double* out, cudaStream_t st);
+cudaError_t launch_dirichlet_in(int n, const long long* dof, const double* value, uint8_t* fixed, double* bcval,
+                                long long ndof, int B, int D, double psc, int* bad, cudaStream_t st);
+
 // Krylov
 template <int D, class T>
 struct KrylovVecs {

@@ -106,6 +106,7 @@ _lib = None
 EXPORTS = ["mpm_create_scene", "mpm_set_gravity", "mpm_set_dirichlet", "mpm_begin_step", "mpm_newton_step",
            "mpm_set_du", "mpm_assemble", "mpm_commit_step", "mpm_solve_step", "mpm_get_residual", "mpm_get_du", "mpm_get_mass",
            "mpm_get_counts", "mpm_get_jacobian_bsr", "mpm_get_mg_level", "mpm_get_particles", "mpm_get_pressure",
+           "mpm_get_du_dev", "mpm_get_residual_dev", "mpm_get_positions_dev", "mpm_set_dirichlet_dev",
            "mpm_set_traction", "mpm_kernel_launches", "mpm_set_params", "mpm_get_particle_increment",
            "mpm_adjoint", "mpm_adjoint_step", "mpm_set_state",
            "mpm_time_spmv", "mpm_set_particles", "mpm_residual_norm_noalloc", "mpm_noalloc_last_error",
@@ -143,6 +144,10 @@ def lib(build: bool = True):
     L.mpm_get_mg_level.argtypes = [_P, ctypes.c_int, _I, _I, _I, ctypes.c_int, _I, _D,
                                    ctypes.POINTER(ctypes.c_ubyte), _D]
     L.mpm_get_particles.argtypes = [_P, _D, _D, _D, _D, _D]
+    L.mpm_get_du_dev.argtypes = [_P, _P]
+    L.mpm_get_residual_dev.argtypes = [_P, _P]
+    L.mpm_get_positions_dev.argtypes = [_P, _P]
+    L.mpm_set_dirichlet_dev.argtypes = [_P, ctypes.c_int, _P, _P]
     L.mpm_get_pressure.argtypes = [_P, _D]
     L.mpm_set_traction.argtypes = [_P, ctypes.c_int, _I, _D]
     L.mpm_set_params.argtypes = [_P, _D, _D, _D]
@@ -314,6 +319,40 @@ def mpm_get_counts(h):
     nb = ctypes.c_longlong(0)
     _check(lib().mpm_get_counts(h, ctypes.byref(na), ctypes.byref(nb)), h)
     return na.value, nb.value
+
+
+def _dev_ptr(t, n, dtype):
+    """Data pointer of a contiguous CUDA tensor of `n` elements of `dtype`."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous() and t.dtype == dtype and t.numel() >= n):
+        raise ValueError(f"need a contiguous CUDA {dtype} tensor of at least {n} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def mpm_get_du_dev(h, out, ndof):
+    import torch
+    _check(lib().mpm_get_du_dev(h, _dev_ptr(out, ndof, torch.float64)), h)
+    return out
+
+
+def mpm_get_residual_dev(h, out, ndof):
+    import torch
+    _check(lib().mpm_get_residual_dev(h, _dev_ptr(out, ndof, torch.float64)), h)
+    return out
+
+
+def mpm_get_positions_dev(h, out, np_):
+    import torch
+    _check(lib().mpm_get_positions_dev(h, _dev_ptr(out, 3 * np_, torch.float64)), h)
+    return out
+
+
+def mpm_set_dirichlet_dev(h, dof, value):
+    import torch
+    n = int(dof.numel())
+    if int(value.numel()) != n:
+        raise ValueError("dof and value lengths differ")
+    _check(lib().mpm_set_dirichlet_dev(h, n, _dev_ptr(dof, n, torch.int64), _dev_ptr(value, n, torch.float64)), h)
 
 
 def mpm_get_mg_level(h, level, dim, B):
@@ -542,6 +581,19 @@ class GpuScene:
 
     def mg_level(self, level):
         return mpm_get_mg_level(self.h, level, self.dim, self.B)
+
+    # device-tensor variants (work on the scene's stream, no host sync)
+    def du_into(self, out):
+        return mpm_get_du_dev(self.h, out, self.ndof)
+
+    def residual_into(self, out):
+        return mpm_get_residual_dev(self.h, out, self.ndof)
+
+    def positions_into(self, out):
+        return mpm_get_positions_dev(self.h, out, self.np)
+
+    def set_dirichlet_dev(self, dof, value):
+        mpm_set_dirichlet_dev(self.h, dof, value)
 
     def pressure(self):
         return mpm_get_pressure(self.h, self.np)
