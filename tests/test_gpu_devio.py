@@ -25,10 +25,16 @@ def _scenes():
     return [S.footing(nx=48, ny=24, h=0.5, nsteps=20, settle_frac=0.1), S.terzaghi(ncell=20, dt=5e4, nsteps=3)]
 
 
+def _kw(sc):
+    # the u-p column is solved with GMRES(30), as in its parity tests
+    return dict(precision=mpm.MPM_FP64, newton_tol=1e-10, newton_maxit=30,
+                krylov=mpm.MPM_GMRES if sc.formulation == "up" else mpm.MPM_BICGSTAB)
+
+
 @pytest.mark.parametrize("k", [0, 1])
 def test_device_getters_match_host(k):
     sc = _scenes()[k]
-    gs = mpm.GpuScene(sc, precision=mpm.MPM_FP64, newton_tol=1e-10)
+    gs = mpm.GpuScene(sc, **_kw(sc))
     gs.solve_step(sc.steps[0])
     gs.begin(sc.steps[1])
     gs.newton()
@@ -53,7 +59,7 @@ def test_dirichlet_dev_stages_the_same_step(k):
     sc = _scenes()[k]
     out = []
     for use_dev in (False, True):
-        gs = mpm.GpuScene(sc, precision=mpm.MPM_FP64, newton_tol=1e-10)
+        gs = mpm.GpuScene(sc, **_kw(sc))
         for st in sc.steps[:2]:
             if use_dev:
                 gs.set_dirichlet_dev(torch.as_tensor(np.asarray(st.dof, dtype=np.int64), device="cuda:0"),
@@ -65,7 +71,11 @@ def test_dirichlet_dev_stages_the_same_step(k):
             assert rep.converged
         out.append(gs.particles()["x"])
         gs.close()
-    assert np.array_equal(out[0], out[1])
+    # the two runs differ only by the summation order of FP64 atomics, which
+    # the Newton iterations carry to about their tolerance
+    x0 = np.zeros_like(out[0])
+    x0[:, :sc.dim] = sc.x[:, :sc.dim]
+    assert np.abs(out[0] - out[1]).max() <= 1e-8 * np.abs(out[0] - x0).max()
 
 
 def test_dirichlet_dev_rejects_out_of_range_index():
@@ -82,15 +92,17 @@ def test_dirichlet_dev_rejects_out_of_range_index():
 
 
 def test_residual_reproducible_and_assembly_bitwise():
+    """Two scenes in the same state, the same increment: the residuals agree to
+    FP64 summation order (node sums use atomics), the assembled Jacobians bit
+    for bit (owner-computes assembly, no atomics)."""
     sc = S.footing(nx=48, ny=24, h=0.5, nsteps=20, settle_frac=0.1)
     res = []
     for _ in range(2):
         gs = mpm.GpuScene(sc, precision=mpm.MPM_MIXED, newton_tol=1e-8)
-        gs.solve_step(sc.steps[0])
         gs.begin(sc.steps[1])
         rng = np.random.default_rng(7)
         du = gs.du()
-        du = du + 1e-4 * rng.standard_normal(du.shape) * (np.abs(du).max() + 1e-3)
+        du = du + 1e-5 * rng.standard_normal(du.shape)
         gs.set_du(du)
         gs.assemble()
         res.append((gs.residual(), gs.jacobian_bsr()))
