@@ -35,6 +35,21 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+def reduce_over_ranks(t, counts, world, device="cpu"):
+    """Whole-job aggregate of a timed region over the ranks (replicas): the
+    slowest rank's time and each count summed over ranks.  `t` is this rank's
+    time, `counts` a list of its counts; with world == 1 they pass through."""
+    import torch
+    tt = torch.tensor([float(t)] + [float(c) for c in counts], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        tmax = tt[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        return float(tmax[0]), [float(v) for v in tt[1:]]
+    return float(tt[0]), [float(v) for v in tt[1:]]
+
+
 METRIC = "Newton iters/s"
 UNIT = "newton_iters/s"
 WORKLOAD = "footing_256x128_dp"
@@ -506,15 +521,7 @@ def main():
     launches = mpm.mpm_kernel_launches(gs.h) - L0
     barrier()
     clocks = clk.stop()
-    tt = torch.tensor([t_ms, float(newton), float(krylov)], dtype=torch.float64, device=dev)
-    if world > 1:
-        tmax = tt[:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        t_all = float(tmax[0])
-    else:
-        t_all = float(tt[0])
-    newton_all, krylov_all = float(tt[1]), float(tt[2])
+    t_all, (newton_all, krylov_all) = reduce_over_ranks(t_ms, [newton, krylov], world, dev)
     value = newton_all / (t_all / 1e3)
 
     # ---- dominant kernel: the Krylov iteration, timed live -------------------
@@ -581,13 +588,8 @@ def main():
             n_e += rep.newton_iters
             h2d = pin_dof[idx].numel() * 8 + pin_val[idx].numel() * 8 + 24
             d2h = out["x"].nbytes + out["tau"].nbytes
-        tv = torch.tensor([t_e, float(n_e)], dtype=torch.float64, device=dev)
-        if world > 1:
-            tm = tv[:1].clone()
-            dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-            dist.all_reduce(tv, op=dist.ReduceOp.SUM)
-            t_e = float(tm[0])
-        e2e = {"value": float(tv[1]) / t_e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        t_e, (n_e_all,) = reduce_over_ranks(t_e, [n_e], world, dev)
+        e2e = {"value": n_e_all / t_e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h),
                "call": "mpm_set_dirichlet + mpm_set_gravity + mpm_solve_step + mpm_get_particles(x, tau)"}
         gs2.close()
