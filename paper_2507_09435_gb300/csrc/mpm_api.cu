@@ -748,15 +748,17 @@ void krylov_solve(mpm_scene* s, double eta, double rnorm, int& kit, int& kstat, 
                                        s->desc.krylov_maxit - kit, nblk, st),
          "krylov restart");
       s->launches += 1;
-      if (use_mg) {
-        ck(launch_mg_vcycle<D, T, B>(mga, v.p, v.phat, d_done, st), "v-cycle");
-        s->launches += mg_vcycle_launches(mga.L, mga.tail);
-      }
       ck(cudaMemcpyAsync(s->h_S, s->d_S, sizeof(KrylovScalars), cudaMemcpyDeviceToHost, st), "copy S");
       ck(cudaStreamSynchronize(st), "sync");
       if (kstat == 0 && s->h_S->rr_last <= 4.0 * tol2) break;   // true residual within 2x of the tolerance
       kstat = 0;
       s->restarts += 1;
+      // the restart's search direction, preconditioned by the V-cycle (the
+      // restart kernel applied only its first smoothing sweep)
+      if (use_mg) {
+        ck(launch_mg_vcycle<D, T, B>(mga, v.p, v.phat, d_done, st), "v-cycle");
+        s->launches += mg_vcycle_launches(mga.L, mga.tail);
+      }
     }
   } else {
     kit = s->h_S->iter;
@@ -802,21 +804,21 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
   // step-length limit (reading): a Newton correction that would move a node
   // by more than one cell width h is scaled down to h (a near-singular J, as
   // at the onset of a mechanism, otherwise yields astronomically large steps)
+  // (the limit is applied on the device by the update kernel; the host reads
+  // max |d| back with the new residual norm, without a synchronisation of its own)
   ck(launch_absmax<D, T, B>(K, v.x, s->d_fixed, s->d_absmax, nblk, st), "absmax");
-  ck(cudaMemcpyAsync(s->h_dbl + 2, s->d_absmax, sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
-  ck(cudaStreamSynchronize(st), "sync");
-  const double xmax = s->h_dbl[2];
-  double step = 1.0;
-  if (!std::isfinite(xmax)) step = 0.0;
-  else if (xmax > s->G.h) step = s->G.h / xmax;
-  if (step < 1.0) s->limited += 1;
   ck(cudaMemcpyAsync(s->d_duprev, s->d_du, s->ndof * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy du");
-  ck(launch_step_du<D, T, B>(K, v.x, s->d_fixed, s->d_duprev, s->d_du, step, nblk, st), "update");
+  ck(launch_step_du<D, T, B>(K, v.x, s->d_fixed, s->d_duprev, s->d_du, 1.0, nblk, st, s->d_absmax, s->G.h),
+     "update");
+  ck(cudaMemcpyAsync(s->h_dbl + 2, s->d_absmax, sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
   s->launches += 3;   // Krylov init + absmax + update
   cudaEventRecord(s->ev[2], st);
   residual_pass<D, T, B>(s, 1);
   cudaEventRecord(s->ev[3], st);
   ck(cudaStreamSynchronize(st), "sync");
+  const double xmax = s->h_dbl[2];
+  const bool limited = !std::isfinite(xmax) || xmax > s->G.h;
+  if (limited) s->limited += 1;
   // a full step that drives a return map out of its domain (or to a
   // non-finite state), or that does not decrease ||r|| while ||r|| is still
   // well above the tolerance (a backtracking line search on the residual
@@ -829,7 +831,8 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
   };
   for (int half = 1; half <= 4 && need_halving(); ++half) {
     ck(cudaMemsetAsync(s->d_err, 0, sizeof(int), st), "memset");
-    ck(launch_step_du<D, T, B>(K, v.x, s->d_fixed, s->d_duprev, s->d_du, step * std::ldexp(1.0, -half), nblk, st),
+    ck(launch_step_du<D, T, B>(K, v.x, s->d_fixed, s->d_duprev, s->d_du, std::ldexp(1.0, -half), nblk, st,
+                               s->d_absmax, s->G.h),
        "step");
     s->launches += 1;
     residual_pass<D, T, B>(s, 1);

@@ -321,7 +321,8 @@ template <int D, class T, int B = D>
 cudaError_t launch_spmv(const DevGrid& G, DevMatrix<T> K, const T* x, T* y, int nblk, cudaStream_t st);
 template <int D, class T, int B = D>
 cudaError_t launch_step_du(DevMatrix<T> K, const T* x, const uint8_t* fixed, const double* base, double* du,
-                           double alpha, int nblk, cudaStream_t st);
+                           double alpha, int nblk, cudaStream_t st, const unsigned long long* absmax = nullptr,
+                           double hlim = 0.0);
 template <int D, class T, int B = D>
 cudaError_t launch_absmax(DevMatrix<T> K, const T* x, const uint8_t* fixed, unsigned long long* out, int nblk,
                           cudaStream_t st);

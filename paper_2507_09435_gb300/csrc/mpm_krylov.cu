@@ -362,24 +362,37 @@ cudaError_t launch_absmax(DevMatrix<T> K, const T* x, const uint8_t* fixed, unsi
   return cudaGetLastError();
 }
 
-// du = base + alpha d on the free DOFs (the halved step of a Newton iteration
-// whose full step drove a return map out of its domain).
+// du = base + alpha * step * d on the free DOFs.  step is the Newton
+// step-length limit read from the device: with xmax = max |d| over the free
+// displacement DOFs (k_absmax), step = hlim / xmax when xmax > hlim, 0 when
+// xmax is not finite, else 1 (absmax == nullptr: step = 1).  The halved steps
+// of a Newton iteration whose full step drove a return map out of its domain
+// pass alpha = 2^-k.
+__device__ __forceinline__ double step_limit(const unsigned long long* absmax, double hlim) {
+  if (!absmax) return 1.0;
+  const double xmax = __longlong_as_double((long long)*absmax);
+  if (!(xmax <= 1.7976931348623157e308)) return 0.0;
+  return (xmax > hlim) ? hlim / xmax : 1.0;
+}
 template <int D, class T, int B>
 __global__ void k_step_du(DevMatrix<T> K, const T* __restrict__ x, const uint8_t* __restrict__ fixed,
-                          const double* __restrict__ base, double* du, double alpha) {
+                          const double* __restrict__ base, double* du, double alpha,
+                          const unsigned long long* absmax, double hlim) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= *K.nrow) return;
+  const double a = alpha * step_limit(absmax, hlim);
   const long long i = K.rows[row];
 #pragma unroll
-  for (int a = 0; a < B; ++a) {
-    const long long d = i * B + a;
-    if (!fixed[d]) du[d] = base[d] + alpha * (double)x[d];
+  for (int c = 0; c < B; ++c) {
+    const long long d = i * B + c;
+    if (!fixed[d]) du[d] = base[d] + a * (double)x[d];
   }
 }
 template <int D, class T, int B>
 cudaError_t launch_step_du(DevMatrix<T> K, const T* x, const uint8_t* fixed, const double* base, double* du,
-                           double alpha, int nblk, cudaStream_t st) {
-  k_step_du<D, T, B><<<nblk, KTPB, 0, st>>>(K, x, fixed, base, du, alpha);
+                           double alpha, int nblk, cudaStream_t st, const unsigned long long* absmax,
+                           double hlim) {
+  k_step_du<D, T, B><<<nblk, KTPB, 0, st>>>(K, x, fixed, base, du, alpha, absmax, hlim);
   return cudaGetLastError();
 }
 
@@ -435,7 +448,7 @@ cudaError_t launch_update_du(DevMatrix<T> K, const T* x, const uint8_t* fixed, d
   template cudaError_t launch_absmax<D, T, B>(DevMatrix<T>, const T*, const uint8_t*, unsigned long long*, int, \
                                            cudaStream_t);                                                  \
   template cudaError_t launch_step_du<D, T, B>(DevMatrix<T>, const T*, const uint8_t*, const double*, double*, \
-                                            double, int, cudaStream_t);
+                                            double, int, cudaStream_t, const unsigned long long*, double);
 MPM_KRYLOV_INST(2, float, 2)
 MPM_KRYLOV_INST(2, double, 2)
 MPM_KRYLOV_INST(3, float, 3)
