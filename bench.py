@@ -548,8 +548,9 @@ def main():
     if args.krylov == "gmres":
         kname = "GMRES(m) cycle kernels (k_gmres_spmv/orth1/orth2/norm/update, one CUDA graph per cycle)"
     elif args.precond == "mg":
-        kname = ("BiCGStab iteration with two multigrid V-cycles (k_bicg_B/C/D/A, per-level k_mg_residual/"
-                 "restrict/prolong/smooth, single-block k_mg_tail; CUDA graph of 2 iterations)")
+        kname = ("BiCGStab iteration with two multigrid V-cycles (k_bicg_B/C/D/A, finest-level k_mg_smooth/"
+                 "residual/restrict/prolong, coarse levels in k_mg_tail on one thread-block cluster; CUDA graph "
+                 "of 2 iterations)")
     elif os.environ.get("MPM_KRYLOV_PERSISTENT", "0") == "1":
         kname = "k_bicg_persistent (whole BiCGStab solve, one cooperative launch per Newton iteration)"
     else:
