@@ -72,6 +72,8 @@ def parse():
                     help="requests of the serving stream measured beside the main line (0: none); "
                          "--workload serving runs the 512-request stream alone")
     ap.add_argument("--slots", type=int, default=4, help="serving worker slots")
+    ap.add_argument("--serving-precond", default="mg", choices=["auto", "mg"],
+                    help="preconditioner of the serving requests (auto: block-Jacobi)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -278,7 +280,7 @@ def run_reference(args):
 # serving stream: continuous batching through the native server
 # ----------------------------------------------------------------------------
 
-def serving_measure(nreq, slots, precision, seed=2507_09435 + 4):
+def serving_measure(nreq, slots, precision, seed=2507_09435 + 4, precond="auto"):
     """Requests of the serving stream (kinds uniform over elastic block /
     Drucker-Prager footing / u-p Terzaghi column, grid cells log-uniform in
     [1e3, 6e4], 10-40 load steps) arriving as a Poisson process at 0.8 x the
@@ -286,6 +288,7 @@ def serving_measure(nreq, slots, precision, seed=2507_09435 + 4):
     `slots` workers with admission by device footprint.  Latency = submit to
     done (queueing included); throughput over the whole run."""
     from paper_2507_09435_gb300 import mpm, scenes as S
+    pc = mpm.MPM_PC_MG if precond == "mg" else mpm.MPM_PC_AUTO
     draws = S.serving_draws(nreq, seed=seed)
     # single-stream capacity on a sample of the stream
     ncap = min(8, nreq)
@@ -293,7 +296,7 @@ def serving_measure(nreq, slots, precision, seed=2507_09435 + 4):
     svc = []
     for d in draws[:ncap]:
         sc, st = S.serving_scene(d)
-        t = sv1.submit(sc, steps=st, precision=precision, newton_maxit=32)
+        t = sv1.submit(sc, steps=st, precision=precision, newton_maxit=32, precond=pc)
         r = sv1.wait(t)
         svc.append(r.t_service_ms)
         sv1.release(t)
@@ -315,7 +318,7 @@ def serving_measure(nreq, slots, precision, seed=2507_09435 + 4):
             time.sleep(due - now)
         else:
             late = max(late, now - due)
-        tickets.append(sv.submit(sc, steps=st, precision=precision, newton_maxit=32))
+        tickets.append(sv.submit(sc, steps=st, precision=precision, newton_maxit=32, precond=pc))
         del sc, st
     res = [sv.wait(t) for t in tickets]
     wall = time.perf_counter() - t0
@@ -345,7 +348,8 @@ def serving_measure(nreq, slots, precision, seed=2507_09435 + 4):
         "peak_running": stats.peak_running, "peak_footprint_bytes": int(stats.peak_in_use),
         "budget_bytes": int(stats.budget),
         "precision": "mixed" if precision == mpm.MPM_MIXED else "fp64",
-        "krylov": "BiCGStab; block-Jacobi per node (solid) or per 4-node row segment (u-p)",
+        "krylov": ("BiCGStab; multigrid V-cycle" if precond == "mg" else
+                   "BiCGStab; block-Jacobi per node (solid) or per 4-node row segment (u-p)"),
     }
 
 
@@ -430,7 +434,7 @@ def run_serving_line(args):
         return 0
     prec = mpm.MPM_MIXED if args.precision == "mixed" else mpm.MPM_FP64
     clk = ClockSampler(0)
-    s = serving_measure(512, args.slots, prec)
+    s = serving_measure(512, args.slots, prec, precond=args.serving_precond)
     clocks = clk.stop()
     line = {"metric": "served Newton iters/s with p50/p99 request latency", "value": s["newton_iters_per_s"],
             "unit": UNIT, "n_gpus": 1, "steps": s["requests"], "warmup": 0,
@@ -607,7 +611,7 @@ def main():
 
     serving = None
     if rank == 0 and args.serving > 0:
-        serving = serving_measure(args.serving, args.slots, prec)
+        serving = serving_measure(args.serving, args.slots, prec, precond=args.serving_precond)
 
     if rank == 0:
         n_gpus = world

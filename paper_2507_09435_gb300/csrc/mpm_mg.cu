@@ -33,6 +33,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "mpm_internal.h"
 
@@ -688,8 +689,8 @@ cudaError_t launch_mg_vcycle(const MgApply<T>& mg, const T* b0, T* z0, const int
 // device can co-schedule such a cluster of the tail kernel, else 8.
 template <int D, class T, int B>
 int mg_tail_cluster() {
-  static int c = 0;
-  if (c) return c;
+  static std::atomic<int> c{0};   // scenes of several host threads (serving) may ask at once
+  if (const int v = c.load()) return v;
   int size = 8;
   if (cudaFuncSetAttribute(k_mg_tail<D, T, B>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
     cudaLaunchConfig_t cfg = {};
@@ -707,8 +708,8 @@ int mg_tail_cluster() {
       size = 16;
   }
   cudaGetLastError();
-  c = size;
-  return c;
+  c.store(size);
+  return size;
 }
 
 int mg_vcycle_launches(int L, int tail) {
