@@ -89,3 +89,32 @@ def test_failed_request_does_not_stop_the_server():
     st = sv.stats()
     assert st.failed == 1 and st.completed == 2
     sv.close()
+
+
+def test_multigrid_requests_same_alone_and_in_the_mix():
+    """Requests preconditioned by the multigrid V-cycle (the bench's serving
+    setting), mixed precision: every request converges, concurrently on
+    several streams (CUDA graphs captured per worker thread, cluster launches
+    on each stream) as alone, to within the Newton tolerance."""
+    kw = dict(precision=mpm.MPM_MIXED, newton_tol=1e-8, newton_maxit=32, precond=mpm.MPM_PC_MG)
+    mix = _mix()
+    alone = []
+    for sc, st in mix:
+        sv = mpm.Server(slots=1)
+        t = sv.submit(sc, steps=st, **kw)
+        r = sv.wait(t)
+        assert r.status == mpm.MPM_OK, (sc.name, mpm.STATUS.get(r.status))
+        alone.append(sv.particles(t)[0])
+        sv.close()
+    sv = mpm.Server(slots=4)
+    tickets = [sv.submit(sc, steps=st, **kw) for sc, st in mix]
+    res = [sv.wait(t) for t in tickets]
+    assert sv.stats().peak_running >= 2
+    for (sc, st), t, r, xa in zip(mix, tickets, res, alone):
+        assert r.status == mpm.MPM_OK, (sc.name, mpm.STATUS.get(r.status))
+        x = sv.particles(t)[0]
+        x0 = np.zeros_like(x)
+        x0[:, :sc.dim] = sc.x[:, :sc.dim]
+        disp = max(np.abs(xa - x0).max(), 1e-300)
+        assert np.abs(x - xa).max() <= 1e-5 * disp, sc.name
+    sv.close()
