@@ -97,7 +97,10 @@ def test_multigrid_requests_same_alone_and_in_the_mix():
     several streams (CUDA graphs captured per worker thread, cluster launches
     on each stream) as alone, to within the Newton tolerance."""
     kw = dict(precision=mpm.MPM_MIXED, newton_tol=1e-8, newton_maxit=32, precond=mpm.MPM_PC_MG)
-    mix = _mix()
+    # the solid requests of the mix, and u-p columns as the serving stream
+    # draws them (16 cells wide; a one-cell-wide column coarsens to two nodes
+    # across, where the V-cycle's coarse levels carry little of the problem)
+    mix = _mix()[:4] + [S.serving_scene(dict(kind="up_terzaghi", cells=c, nsteps=3)) for c in (1024, 2048)]
     alone = []
     for sc, st in mix:
         sv = mpm.Server(slots=1)
