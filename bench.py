@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--slots", type=int, default=4, help="serving worker slots")
     ap.add_argument("--serving-precond", default="mg", choices=["auto", "mg"],
                     help="preconditioner of the serving requests (auto: block-Jacobi)")
+    ap.add_argument("--serving-terzaghi", default="full", choices=["layer", "full"],
+                    help="u-p requests: c_v dt/h^2 = 10 with N <= 256 (layer), or steps spanning T in [0, 1] "
+                         "with N <= 512 (full)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -280,7 +283,7 @@ def run_reference(args):
 # serving stream: continuous batching through the native server
 # ----------------------------------------------------------------------------
 
-def serving_measure(nreq, slots, precision, seed=2507_09435 + 4, precond="auto"):
+def serving_measure(nreq, slots, precision, seed=2507_09435 + 4, precond="auto", consolidation="layer"):
     """Requests of the serving stream (kinds uniform over elastic block /
     Drucker-Prager footing / u-p Terzaghi column, grid cells log-uniform in
     [1e3, 6e4], 10-40 load steps) arriving as a Poisson process at 0.8 x the
@@ -295,7 +298,7 @@ def serving_measure(nreq, slots, precision, seed=2507_09435 + 4, precond="auto")
     sv1 = mpm.Server(slots=1)
     svc = []
     for d in draws[:ncap]:
-        sc, st = S.serving_scene(d)
+        sc, st = S.serving_scene(d, consolidation)
         t = sv1.submit(sc, steps=st, precision=precision, newton_maxit=32, precond=pc)
         r = sv1.wait(t)
         svc.append(r.t_service_ms)
@@ -312,7 +315,7 @@ def serving_measure(nreq, slots, precision, seed=2507_09435 + 4, precond="auto")
     late = 0.0
     for d, g in zip(draws, gaps):
         due += g
-        sc, st = S.serving_scene(d)
+        sc, st = S.serving_scene(d, consolidation)
         now = time.perf_counter() - t0
         if now < due:
             time.sleep(due - now)
@@ -434,7 +437,7 @@ def run_serving_line(args):
         return 0
     prec = mpm.MPM_MIXED if args.precision == "mixed" else mpm.MPM_FP64
     clk = ClockSampler(0)
-    s = serving_measure(512, args.slots, prec, precond=args.serving_precond)
+    s = serving_measure(512, args.slots, prec, precond=args.serving_precond, consolidation=args.serving_terzaghi)
     clocks = clk.stop()
     line = {"metric": "served Newton iters/s with p50/p99 request latency", "value": s["newton_iters_per_s"],
             "unit": UNIT, "n_gpus": 1, "steps": s["requests"], "warmup": 0,
@@ -611,7 +614,8 @@ def main():
 
     serving = None
     if rank == 0 and args.serving > 0:
-        serving = serving_measure(args.serving, args.slots, prec, precond=args.serving_precond)
+        serving = serving_measure(args.serving, args.slots, prec, precond=args.serving_precond,
+                                  consolidation=args.serving_terzaghi)
 
     if rank == 0:
         n_gpus = world

@@ -504,7 +504,7 @@ def serving_draws(n: int, seed: int = SEED_BASE + 4, cells_lo: float = 1e3, cell
     return [dict(kind=SERVING_KINDS[k], cells=float(c), nsteps=int(s)) for k, c, s in zip(kinds, cells, steps)]
 
 
-def serving_scene(d) -> Tuple[Scene, list]:
+def serving_scene(d, consolidation: str = "layer") -> Tuple[Scene, list]:
     """The scene and load steps of one serving request descriptor.
     elastic block: square grid of ~cells cells, block on a quarter of it,
     1 % strain over the steps; footing: nx = 2 ny with nx*ny ~ cells, h = 0.1,
@@ -514,7 +514,9 @@ def serving_scene(d) -> Tuple[Scene, list]:
     k = 1e-9 m/s, time step c_v dt / h^2 = 10 (the early, boundary-layer part of
     the consolidation: with block-Jacobi Krylov the u-p system is solved
     reliably near that ratio, while steps spanning T in [0, 1] give ratios in
-    the thousands, a pressure problem that wants a multilevel preconditioner)."""
+    the thousands, a pressure problem that wants a multilevel preconditioner).
+    consolidation="full": N = cells/16 clipped to [64, 512] and the load steps
+    spanning T = c_v t / H^2 in [0, 1] (c_v dt / h^2 = N^2 / nsteps)."""
     kind, cells, ns = d["kind"], d["cells"], d["nsteps"]
     if kind == "elastic_block":
         ng = max(32, int(round(np.sqrt(cells) / 16)) * 16)
@@ -528,12 +530,13 @@ def serving_scene(d) -> Tuple[Scene, list]:
         B = 2 * ny * 0.1 / 12.8
         sc = footing(nx=2 * ny, ny=ny, h=0.1, nsteps=ns - 1, B=B, settle_frac=0.001 * (ns - 1))
         return sc, sc.steps
-    N = int(np.clip(round(cells / 16.0), 64, 256))
+    full = consolidation == "full"
+    N = int(np.clip(round(cells / 16.0), 64, 512 if full else 256))
     lam = mu = 600e3
     k_hyd = 1e-9
     cv = k_hyd / 9810.0 * (lam + 2 * mu)
     hh = 10.0 / N
-    dt = 10.0 * hh * hh / cv
+    dt = (10.0 * 10.0 / (cv * ns)) if full else 10.0 * hh * hh / cv
     sc = terzaghi(ncell=N, ncell_x=16, k_hyd=k_hyd, dt=dt, nsteps=ns)
     return sc, sc.steps
 
