@@ -509,14 +509,13 @@ def serving_scene(d, consolidation: str = "layer") -> Tuple[Scene, list]:
     elastic block: square grid of ~cells cells, block on a quarter of it,
     1 % strain over the steps; footing: nx = 2 ny with nx*ny ~ cells, h = 0.1,
     B = nx h / 12.8, settlement 0.001 B per step after the geostatic step; Terzaghi: a
-    column 16 cells wide and N = cells/16 (clipped to [64, 256]: taller columns
-    need the multilevel preconditioner too) high,
-    k = 1e-9 m/s, time step c_v dt / h^2 = 10 (the early, boundary-layer part of
-    the consolidation: with block-Jacobi Krylov the u-p system is solved
-    reliably near that ratio, while steps spanning T in [0, 1] give ratios in
-    the thousands, a pressure problem that wants a multilevel preconditioner).
-    consolidation="full": N = cells/16 clipped to [64, 512] and the load steps
-    spanning T = c_v t / H^2 in [0, 1] (c_v dt / h^2 = N^2 / nsteps)."""
+    column 16 cells wide, k = 1e-9 m/s, and
+    * consolidation="full": N = cells/16 clipped to [64, 512] cells high, the
+      load steps spanning T = c_v t / H^2 in [0, 1] (c_v dt / h^2 = N^2 /
+      nsteps, up to about 17,000; solved with the multigrid V-cycle);
+    * consolidation="layer": N clipped to [64, 256], c_v dt / h^2 = 10 (the
+      early, boundary-layer part of the consolidation, which block-Jacobi
+      Krylov solves reliably)."""
     kind, cells, ns = d["kind"], d["cells"], d["nsteps"]
     if kind == "elastic_block":
         ng = max(32, int(round(np.sqrt(cells) / 16)) * 16)
