@@ -358,8 +358,8 @@ __global__ void __launch_bounds__(1024) k_mg_dense_inverse(MgLevel<T> c, float* 
 }
 
 // ---- one row of each V-cycle step (used by the per-level kernels and by the
-// single-block tail; COH: the input vector was written earlier in the same
-// kernel, so it is read with ordinary loads)
+// cluster tail; COH: the input vector was written earlier in the same kernel,
+// so it is read with ordinary loads)
 
 // r = b - A z
 template <int D, class T, int B, bool COH>
@@ -453,8 +453,9 @@ __device__ __forceinline__ void row_smooth(const MgLevel<T>& l, int row, const T
   for (int a = 0; a < B; ++a) zout[i * B + a] = zin[i * B + a] + z[a];
 }
 
-// z = A^-1 b on the dense level, by one block (any size >= 1 thread); bv is
-// shared scratch of MG_DENSE_MAX entries.  Ends with a block barrier.
+// z = A^-1 b on the dense level (L == 1: the finest level itself), by one
+// block; bv is shared scratch of MG_DENSE_MAX entries.  Ends with a block
+// barrier.
 template <class T, int B>
 __device__ __forceinline__ void block_dense_apply(const MgLevel<T>& c, const float* invT, const T* b, T* z,
                                                   float* bv) {
