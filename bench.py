@@ -30,7 +30,12 @@ import sys
 import tempfile
 import time
 
-import numpy as np
+# The oracle legs (cpu_baseline, --impl reference) are reported as one host
+# core: keep numpy's BLAS thread pool to one thread (set before numpy loads).
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
