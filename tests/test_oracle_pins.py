@@ -9,7 +9,9 @@ oracle would fail it.
 * Zero-strain tangent equals the isotropic elasticity tensor (closed form).
 * Per-particle tangent against central differences of the oracle's own
   stress, elastic, plastic, apex and repeated-eigenvalue states.
-* Return maps: consistency f = 0, flow rule, hardening law.
+* Return maps: consistency f = 0, flow rule, hardening law; at small strain
+  both tend, at first order, to the textbook returns of linear elasticity
+  (Drucker-Prager radial return, Cam-Clay in p-q invariants).
 * P2G: linear and angular momentum balance of the internal force; gravity
   sums to the total weight (a transposed dF^-T breaks the angular balance).
 * Global Jacobian against the coloured central-difference Jacobian, and the
@@ -368,3 +370,100 @@ def test_self_weight_bar_converges_to_closed_form(oracle):
     assert (np.log2(errs[:-1] / errs[1:]) > 0.6).all()
     assert errs[-1] < 0.04
     assert herr[-1] < 0.06 and herr[-1] < herr[0]
+
+
+# ---------------------------------------------------------------- small-strain limits
+# At strains of size d, Neo-Hookean principal Kirchhoff stresses
+# mu (exp(2 eps) - 1) + lam tr eps differ from linear (Hencky) ones
+# 2 mu eps + lam tr eps by O(d) relative, so the log-strain return maps must
+# approach the textbook small-strain returns of linear elasticity at first
+# order in d.  Those are written here from their own derivation in stress
+# invariants (no principal-space local Newton), so a sign, a factor of the
+# invariants or the direction of hardening that is wrong in the oracle shows
+# up as an O(1) difference.
+
+def _hencky_dp_return(etr, mu, lam, eta, etab, xi, c):
+    """Radial return for Drucker-Prager with linear elasticity: the deviatoric
+    direction is kept, sqrt(J2) drops by mu dg, p by K etab dg, and
+    f_tr - (mu + K eta etab) dg = 0 (de Souza Neto et al., Sec. 8.3)."""
+    K = lam + 2.0 * mu / 3.0
+    ev = etr.sum()
+    e_dev = etr - ev / 3.0
+    s_tr = 2.0 * mu * e_dev
+    rJ2 = np.sqrt(0.5 * (s_tr ** 2).sum())
+    p_tr = K * ev
+    f_tr = rJ2 + eta * p_tr - xi * c
+    dg = f_tr / (mu + K * eta * etab)
+    eps = etr - dg * (s_tr / (2.0 * rJ2) + etab / 3.0)
+    return eps, dg
+
+
+def _small_strain_mcc_return(etr, mu, lam, M, lmk, pcn):
+    """Modified Cam-Clay return with linear elasticity in (p, q): q scales by
+    1 / (1 + 6 mu dg / M^2), p = p_tr - K dg (2p - pc), pc = pcn
+    exp(-dg (2p - pc) / (lambda - kappa)), f(p, q, pc) = 0 (Borja and Lee
+    1990, invariant form), solved with a library root finder."""
+    from scipy.optimize import fsolve
+    K = lam + 2.0 * mu / 3.0
+    ev = etr.sum()
+    e_dev = etr - ev / 3.0
+    s_tr = 2.0 * mu * e_dev
+    q_tr = np.sqrt(1.5 * (s_tr ** 2).sum())
+    p_tr = K * ev
+
+    def eqs(z):
+        dg, p, pc = z[0] / abs(pcn), z[1] * abs(pcn), z[2] * abs(pcn)
+        q = q_tr / (1.0 + 6.0 * mu * dg / M ** 2)
+        return [(q * q / M ** 2 + p * (p - pc)) / pcn ** 2,
+                (p - p_tr + K * dg * (2 * p - pc)) / abs(pcn),
+                (pc - pcn * np.exp(-dg * (2 * p - pc) / lmk)) / abs(pcn)]
+
+    z, _, ok, msg = fsolve(eqs, [1e-12, p_tr / abs(pcn), pcn / abs(pcn)], xtol=1e-14, full_output=True)
+    assert ok == 1, msg
+    dg, p, pc = z[0] / abs(pcn), z[1] * abs(pcn), z[2] * abs(pcn)
+    s = s_tr / (1.0 + 6.0 * mu * dg / M ** 2)
+    eps = etr - dg * (3.0 * s / M ** 2 + (2.0 * p - pc) / 3.0)
+    return eps, dg, pc
+
+
+def test_dp_return_tends_to_the_small_strain_radial_return(oracle):
+    E, nu = 1e6, 0.3
+    mu, lam = _lame(E, nu)
+    tp = np.tan(np.radians(30.0))
+    eta, xi = 3 * tp / np.sqrt(9 + 12 * tp ** 2), 3 / np.sqrt(9 + 12 * tp ** 2)
+    direction = np.array([0.8, -1.0, 0.1])          # mostly deviatoric, slight dilation
+    for psi in (0.0, 10.0):
+        ts = np.tan(np.radians(psi))
+        etab = 3 * ts / np.sqrt(9 + 12 * ts ** 2)
+        errs = []
+        for d in (1e-3, 1e-4, 1e-5):
+            etr = d * direction
+            K = lam + 2 * mu / 3
+            rJ2 = np.sqrt(0.5 * ((2 * mu * (etr - etr.sum() / 3)) ** 2).sum())
+            c = (0.5 * rJ2 + eta * K * etr.sum()) / xi     # trial f = half of sqrt(J2)
+            p = _mat(S.MODEL_NH_DP, E=E, nu=nu, c=c, psi=psi)
+            eps, _, mode, _, dg = oracle.return_map(S.MODEL_NH_DP, p, etr)
+            assert mode == 1
+            eps_l, dg_l = _hencky_dp_return(etr, mu, lam, eta, etab, xi, c)
+            errs.append(max(abs(dg - dg_l) / dg_l, np.abs(eps - eps_l).max() / d))
+        errs = np.array(errs)
+        assert errs[0] < 0.01
+        assert (errs[1:] < 0.2 * errs[:-1]).all()        # first order in d
+
+
+def test_mcc_return_tends_to_the_small_strain_invariant_return(oracle):
+    E, nu, M, lmk = 1e6, 0.3, 1.2, 0.08
+    mu, lam = _lame(E, nu)
+    direction = np.array([-1.0, -0.4, -0.2])         # compression with shear
+    errs = []
+    for d in (1e-3, 1e-4, 1e-5):
+        etr = d * direction
+        pcn = -0.4 * E * d                            # on the scale of the trial stress: plastic
+        p = _mat(S.MODEL_NH_MCC, E=E, nu=nu, M=M, lambda_cc=0.1, kappa_cc=0.1 - lmk)
+        eps, pc, mode, _, dg = oracle.return_map(S.MODEL_NH_MCC, p, etr, pcn)
+        assert mode == 1
+        eps_l, dg_l, pc_l = _small_strain_mcc_return(etr, mu, lam, M, lmk, pcn)
+        errs.append(max(abs(dg - dg_l) / dg_l, np.abs(eps - eps_l).max() / d, abs(pc - pc_l) / abs(pcn)))
+    errs = np.array(errs)
+    assert errs[0] < 0.01
+    assert (errs[1:] < 0.2 * errs[:-1]).all()
