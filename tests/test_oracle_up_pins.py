@@ -9,6 +9,8 @@ Sec. 4.4 one-dimensional consolidation), no GPU.
   pressure-pressure block).
 * Discrete flux energy: with du = 0, sum_i p_i r_p,i = sum_p kdt V_p |grad p_p|^2
   >= 0 (the sign and the quadratic form of the Darcy term).
+* Finite strain: the Darcy rows are unchanged by a superposed rigid rotation
+  and scale by s1 / s2 under a stretch s1 across and s2 along the flow.
 * Terzaghi (Sec. 4.4): pore pressure and settlement converge to the series
   solution p/p0 = sum 2/M sin(M z/H) exp(-M^2 T) and s = s_inf U(T) as the
   column is refined (time step proportional to h^2).
@@ -95,6 +97,54 @@ def test_up_flux_energy_identity(oracle):
         rhs += kdt[p] * orc.V0[p] * float(G @ G)
     assert rhs > 0
     assert abs(lhs - rhs) <= 1e-12 * rhs
+
+
+def _flux_rows(orc, sc, dF, pnode):
+    """Mass-balance rows of the Darcy term alone at a uniform deformation dF
+    (an affine nodal increment, which G2P reproduces exactly) and nodal
+    pressures pnode: the rows at pnode minus the rows at zero pressure (the
+    volume-change part does not depend on the pressure)."""
+    X = sc.node_coords()[:, :2]
+    U = np.zeros(sc.nnode * 3)
+    u = X @ (dF - np.eye(2)).T
+    U[0::3], U[1::3] = u[:, 0], u[:, 1]
+    r0, _ = orc.residual(U)
+    U[2::3] = pnode
+    r1, M = orc.residual(U)
+    return (r1 - r0)[2::3], M
+
+
+def test_up_darcy_flux_is_objective_and_scales_with_the_deformed_geometry(oracle):
+    """Darcy's law holds in the deformed configuration.  (1) A superposed
+    rigid rotation leaves every flux row unchanged.  (2) Stretching the body by
+    s1 across and s2 along a uniform reference pressure gradient widens the
+    flow section by s1 and lengthens the flow path by s2, so every flux row
+    scales by s1 / s2 (a dropped volume ratio, a single inverse deformation
+    gradient in place of dF^-1 dF^-T, or the gradient pushed the wrong way
+    fails one of these)."""
+    sc = _up_tiny(S.MODEL_NH, seed=31)
+    orc = oracle.OracleScene.from_scene(sc)
+    X = sc.node_coords()[:, :2]
+    rng = np.random.default_rng(32)
+    p_rand = rng.standard_normal(sc.nnode) * 1e4
+    F_ref, M = _flux_rows(orc, sc, np.eye(2), p_rand)
+    act = M > 0
+    scale = np.abs(F_ref[act]).max()
+    assert scale > 0
+    th = 0.7
+    R = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+    F_rot, _ = _flux_rows(orc, sc, R, p_rand)
+    assert np.abs(F_rot - F_ref)[act].max() <= 1e-12 * scale
+    s1, s2 = 1.1, 0.9
+    for axis in (0, 1):
+        g = 1e4 / sc.h
+        p_lin = g * X[:, axis]
+        F0, _ = _flux_rows(orc, sc, np.eye(2), p_lin)
+        dF = np.diag([s2, s1]) if axis == 0 else np.diag([s1, s2])   # s2 along the gradient
+        F1, _ = _flux_rows(orc, sc, dF, p_lin)
+        ref = np.abs(F0[act]).max()
+        assert ref > 0
+        assert np.abs(F1 - (s1 / s2) * F0)[act].max() <= 1e-12 * ref
 
 
 def _terzaghi_series(z, T, H, nterms=400):
