@@ -373,7 +373,11 @@ mpm_status mpm_residual_norm_noalloc(const double* r, const int* rows, int nrow,
 /* Message of the last failed mpm_residual_norm_noalloc call on this thread. */
 const char* mpm_noalloc_last_error(void);
 
-/* Device memory a scene of this size would take (for admission control). */
+/* Device memory a scene of this size would take (for admission control): an
+ * upper bound over particles, grid, tangents, Krylov vectors (the GMRES(m)
+ * basis included), the stencil-BSR Jacobian with its block-Jacobi inverses
+ * and the multigrid levels; the adjoint's transposed Jacobian is not
+ * included.  Host arithmetic only.  MPM_ERR_INVALID_ARG for a bad desc. */
 mpm_status mpm_footprint_bytes(const mpm_scene_desc* desc, int np, size_t* out);
 
 void mpm_destroy_scene(mpm_scene* s);

@@ -207,9 +207,17 @@ size_t footprint(const mpm_scene_desc* d, int np) {
   size_t tang = (size_t)np * B * NPHI * B * NPHI * T;
   long long pad = 2 + 2LL * (d->n[0] + 1) + (D == 3 ? 2LL * (d->n[0] + 1) * (d->n[1] + 1) : 0);
   size_t vec = 9 * (size_t)(nn + 2 * pad) * B * T;
-  // active rows are bounded by the nodes the particles can reach
+  // GMRES(m): the m + 3 basis and work vectors beside the nine BiCGStab ones
+  if (d->krylov == MPM_GMRES) {
+    const int m = d->gmres_restart > 0 ? std::min(std::max(d->gmres_restart, 2), GMRES_MMAX) : 30;
+    vec += (size_t)(m + 3) * (size_t)(nn + 2 * pad) * B * T;
+  }
+  // active rows are bounded by the nodes the particles can reach; the
+  // block-Jacobi inverses take one B x B block per row, or four for the
+  // 4-row segments (the u-p default)
   long long rows = std::min<long long>(nn, (long long)np * (D == 2 ? 9 : 27));
-  size_t mat = (size_t)rows * (stencil_slots(D) + 1) * B * B * T;
+  const int seg = (d->precond == MPM_PC_SEG4 || (d->precond == MPM_PC_AUTO && B > D)) ? 4 : 1;
+  size_t mat = (size_t)rows * (stencil_slots(D) + seg) * B * B * T;
   // multigrid: coarse matrices (a quarter per level in 2D, an eighth in 3D),
   // coarse grids and vectors, two level-0 scratch vectors
   size_t mg = 0;

@@ -49,6 +49,27 @@ def test_host_only_calls():
         mpm.mpm_footprint_bytes(bad, 10)
 
 
+def test_footprint_counts_the_krylov_and_preconditioner_storage():
+    """Admission footprint: the GMRES(m) basis (m + 3 vectors beside the nine
+    BiCGStab ones) and the 4-row-segment block inverses of u-p scenes are
+    counted; FP32 Jacobian and vectors take less than FP64."""
+    n, B = (64, 64), 2
+    nn = 65 * 65
+    pad = 2 + 2 * 65
+    bi = mpm.mpm_footprint_bytes(mpm.make_desc(2, n, 0.1, precision=mpm.MPM_MIXED), 4096)
+    for m in (10, 30):
+        gm = mpm.mpm_footprint_bytes(mpm.make_desc(2, n, 0.1, precision=mpm.MPM_MIXED, krylov=mpm.MPM_GMRES,
+                                                   gmres_restart=m), 4096)
+        assert gm - bi == (m + 3) * (nn + 2 * pad) * B * 4
+    f64 = mpm.mpm_footprint_bytes(mpm.make_desc(2, n, 0.1, precision=mpm.MPM_FP64), 4096)
+    assert f64 > bi
+    up = dict(precision=mpm.MPM_MIXED, formulation=mpm.MPM_UP, dt=1.0)
+    seg = mpm.mpm_footprint_bytes(mpm.make_desc(2, n, 0.1, precond=mpm.MPM_PC_SEG4, **up), 4096)
+    node = mpm.mpm_footprint_bytes(mpm.make_desc(2, n, 0.1, precond=mpm.MPM_PC_NODE, **up), 4096)
+    auto = mpm.mpm_footprint_bytes(mpm.make_desc(2, n, 0.1, precond=mpm.MPM_PC_AUTO, **up), 4096)
+    assert seg - node == nn * 3 * 9 * 4 and auto == seg
+
+
 def test_compute_without_gpu_fails_loudly():
     import torch
     if torch.cuda.is_available():
