@@ -73,7 +73,7 @@ def lib():
         L.orc_return_map.argtypes = [ctypes.c_int, _D, _D, ctypes.c_double, _D, _D, _I, _D, _D]
         L.orc_particle.argtypes = [ctypes.c_int, _D, _D, ctypes.c_double, _D, ctypes.c_double,
                                    _D, _D, _D, _I, _D, _D]
-        L.orc_residual.argtypes = [_I, _D, _D, ctypes.c_int, _D, _D, _D, _I, _D, _D, _D, _D,
+        L.orc_residual.argtypes = [_I, _D, _D, ctypes.c_int, _D, _D, _D, _I, _D, _D, _D, _D, _D,
                                    _D, _D, _I, _D]
         L.orc_jacobian.argtypes = [_I, _D, ctypes.c_int, _D, _D, _I, _D, _D, _D, _D,
                                    ctypes.c_long, _L, _L, _D]
@@ -236,8 +236,8 @@ class OracleScene:
         else:
             rc = lib().orc_residual(_p(self.gi, _I), _p(self.gd), _p(_f64(self.gravity)), self.np,
                                     _p(self.x), _p(self.V0), _p(self.m), _p(self.model, _I),
-                                    _p(self.params), _p(self.be), _p(self.pc), _p(du), _p(r), _p(M),
-                                    _p(mode, _I), _p(rabs) if with_scale else None)
+                                    _p(self.params), _p(self.be), _p(self.pc), _p(self.fext), _p(du), _p(r),
+                                    _p(M), _p(mode, _I), _p(rabs) if with_scale else None)
         if rc:
             raise OracleError(f"residual failed ({rc})")
         out = (r, M)

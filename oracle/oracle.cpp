@@ -729,15 +729,18 @@ int orc_particle(int model, const double* params, const double* be6, double pcn,
 }
 
 // Global residual r = f_int - f_ext on the dense node grid (nnode*dim) and
-// nodal mass M_i = sum_p w_ip m_p (paper's mapping equation).  Returns 0,
-// -1 (particle outside the grid) or a constitutive failure code.  When
-// `mode_out` is given the per-particle mode is written there; when `rabs` is
-// given it receives sum_p |contribution| per DOF (the scale against which
-// the rounding of r is judged).
+// nodal mass M_i = sum_p w_ip m_p (paper's mapping equation).  f_ext spreads
+// each particle's weight m_p g and the force it carries, fext (3 per
+// particle, nullable: the traction term of the paper's discrete external
+// force, read as a traction times the particle's share of the loaded face),
+// with w_ip.  Returns 0, -1 (particle outside the grid) or a constitutive
+// failure code.  When `mode_out` is given the per-particle mode is written
+// there; when `rabs` is given it receives sum_p |contribution| per DOF (the
+// scale against which the rounding of r is judged).
 int orc_residual(const int* gi, const double* gd, const double* grav, int np, const double* x,
                  const double* V0, const double* m, const int* model, const double* params,
-                 const double* be, const double* pc, const double* du, double* r, double* mass,
-                 int* mode_out, double* rabs) {
+                 const double* be, const double* pc, const double* fext, const double* du, double* r,
+                 double* mass, int* mode_out, double* rabs) {
   Grid G = make_grid(gi, gd);
   long nn = G.nnode();
   std::fill(r, r + nn * G.dim, 0.0);
@@ -760,8 +763,9 @@ int orc_residual(const int* gi, const double* gd, const double* grav, int np, co
       for (int a = 0; a < G.dim; ++a) {
         double f = 0;
         for (int c = 0; c < G.dim; ++c) f += o.P[a][c] * S.g[l][c];
-        r[i * G.dim + a] += f - S.w[l] * m[p] * grav[a];
-        if (rabs) rabs[i * G.dim + a] += std::fabs(f) + std::fabs(S.w[l] * m[p] * grav[a]);
+        const double fe = S.w[l] * (m[p] * grav[a] + (fext ? fext[3 * p + a] : 0.0));
+        r[i * G.dim + a] += f - fe;
+        if (rabs) rabs[i * G.dim + a] += std::fabs(f) + std::fabs(fe);
       }
     }
   }

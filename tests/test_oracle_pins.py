@@ -13,7 +13,8 @@ oracle would fail it.
   both tend, at first order, to the textbook returns of linear elasticity
   (Drucker-Prager radial return, Cam-Clay in p-q invariants).
 * P2G: linear and angular momentum balance of the internal force; gravity
-  sums to the total weight (a transposed dF^-T breaks the angular balance).
+  sums to the total weight; particle forces keep their sum and moment (a
+  transposed dF^-T breaks the angular balance).
 * Global Jacobian against the coloured central-difference Jacobian, and the
   coloured difference equal, bit for bit, to one-DOF-at-a-time differences
   (the paper's sparse = dense Jacobian check, Sec. 4.3).
@@ -275,6 +276,25 @@ def test_internal_force_momentum_balance(oracle, dim, model):
     fg = (r2 - r).reshape(-1, dim).sum(0)
     assert np.allclose(-fg, sc.mass.sum() * g[:dim], rtol=1e-13)
     assert abs(M2.sum() - sc.mass.sum()) < 1e-13 * sc.mass.sum()
+    # particle forces (the traction reading): spread by w_ip, they sum to the
+    # total applied force and carry its moment about the origin (the B-spline
+    # weights reproduce linear fields)
+    orc.gravity = np.zeros(3)
+    fp = np.zeros((sc.np, 3))
+    fp[:, :dim] = RNG.standard_normal((sc.np, dim)) * 1e3
+    orc.fext[:] = fp
+    r3, _ = orc.residual(du)
+    ft = -(r3 - r).reshape(-1, dim)
+    assert np.allclose(ft.sum(0), fp[:, :dim].sum(0), rtol=1e-12, atol=1e-12 * np.abs(fp).sum())
+    X = sc.node_coords()[:, :dim]
+    xp = sc.x[:, :dim]
+    if dim == 2:
+        m_nodes = (X[:, 0] * ft[:, 1] - X[:, 1] * ft[:, 0]).sum()
+        m_parts = (xp[:, 0] * fp[:, 1] - xp[:, 1] * fp[:, 0]).sum()
+    else:
+        m_nodes = np.cross(X, ft).sum(0)
+        m_parts = np.cross(xp, fp[:, :3]).sum(0)
+    assert np.allclose(m_nodes, m_parts, rtol=1e-11, atol=1e-11 * np.abs(fp).sum() * np.abs(xp).max())
 
 
 # ---------------------------------------------------------------- global Jacobian
