@@ -259,9 +259,11 @@ def run_reference(args):
     if rank != 0:
         return 0
     sc = workload_scene(args.workload)
-    for _ in range(max(0, min(args.warmup, 1))):
-        pass  # the oracle has no warm-up state; each step is an independent bounded sample
     sub, scale, what = cpu_sample_scene(sc, args.workload)
+    # the oracle keeps no state between samples: one untimed sample warms the
+    # library loads and caches, whatever W is
+    if args.warmup > 0:
+        oracle_newton_sample(sub)
     times, iters, kits = [], 0, 0
     for _ in range(args.steps):
         t, n, k = oracle_newton_sample(sub)

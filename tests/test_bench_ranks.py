@@ -1,10 +1,13 @@
 """The bench's multi-rank path (replicas only: no collective on the data
 path) on CPU with two gloo ranks: the whole-job aggregate takes the slowest
-rank's time and sums the ranks' iteration counts."""
+rank's time and sums the ranks' iteration counts.  The oracle (reference)
+arm prints its one line on rank 0 only."""
 import os
 import socket
 
 import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 torch = pytest.importorskip("torch")
 import torch.distributed as dist  # noqa: E402
@@ -49,3 +52,33 @@ def test_reduce_over_two_gloo_ranks():
 def test_single_rank_passes_through():
     import bench
     assert bench.reduce_over_ranks(2.5, [3, 4], 1) == (2.5, [3.0, 4.0])
+
+
+def _bench(env_extra, *args):
+    import subprocess
+    import sys
+    env = dict(os.environ, **env_extra)
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], capture_output=True,
+                          text=True, env=env, timeout=600)
+
+
+def test_reference_arm_prints_one_line_on_rank_zero_only():
+    """The oracle arm under a multi-rank launch: ranks other than 0 exit 0
+    without work or output; rank 0 prints one JSON line with the contract's
+    keys and a one-core CPU baseline of the same sample."""
+    import json
+    quiet = _bench({"RANK": "1", "WORLD_SIZE": "2"}, "--impl", "reference", "--gpus", "2", "--steps", "1",
+                   "--warmup", "0")
+    assert quiet.returncode == 0 and quiet.stdout.strip() == ""
+    r = _bench({"RANK": "0", "WORLD_SIZE": "1"}, "--impl", "reference", "--steps", "1", "--warmup", "0")
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["cores"] == 1 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["cpu_baseline"]["value"] == line["value"] == line["e2e"]["value"]
+    assert line["config"]["workload"] == "footing_256x128_dp"
