@@ -609,9 +609,9 @@ def main():
                "call": "mpm_set_dirichlet + mpm_set_gravity + mpm_solve_step + mpm_get_particles(x, tau)"}
         gs2.close()
 
-    # ---- CPU baseline: the oracle on a bounded sample ------------------------
+    # ---- CPU baseline: the oracle on a bounded sample (N = 1 runs only) -------
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sub, scale, what = cpu_sample_scene(sc, args.workload)
         t, n, k = oracle_newton_sample(sub)
         cpu = {"value": n / (t * scale), "unit": UNIT, "cores": 1, "kind": "oracle",
