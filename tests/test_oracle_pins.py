@@ -298,7 +298,8 @@ def test_internal_force_momentum_balance(oracle, dim, model):
 
 
 # ---------------------------------------------------------------- global Jacobian
-JAC_CASES = [(2, S.MODEL_NH, 0.02), (2, S.MODEL_NH_DP, 0.03), (3, S.MODEL_NH_MCC, 0.01)]
+JAC_CASES = [(2, S.MODEL_NH, 0.02), (2, S.MODEL_NH_DP, 0.03), (3, S.MODEL_NH, 0.02), (3, S.MODEL_NH_DP, 0.03),
+             (3, S.MODEL_NH_MCC, 0.01)]
 
 
 @pytest.mark.parametrize("dim,model,amp", JAC_CASES)
