@@ -15,6 +15,8 @@ oracle would fail it.
 * P2G: linear and angular momentum balance of the internal force; gravity
   sums to the total weight; particle forces keep their sum and moment (a
   transposed dF^-T breaks the angular balance).
+* Residual of a Neo-Hookean body = gradient of its total potential (energy
+  density and B-spline kinematics written again in the test).
 * Global Jacobian against the coloured central-difference Jacobian, and the
   coloured difference equal, bit for bit, to one-DOF-at-a-time differences
   (the paper's sparse = dense Jacobian check, Sec. 4.3).
@@ -488,3 +490,76 @@ def test_mcc_return_tends_to_the_small_strain_invariant_return(oracle):
     errs = np.array(errs)
     assert errs[0] < 0.01
     assert (errs[1:] < 0.2 * errs[:-1]).all()
+
+
+# ---------------------------------------------------------------- residual as an energy gradient
+def _bspline_1d(x, h):
+    """Textbook quadratic B-spline on a uniform grid: the three node indices
+    from floor(x/h - 1/2), their weights N(xi) and derivatives dN/dx."""
+    base = int(np.floor(x / h - 0.5))
+    idx = np.arange(base, base + 3)
+    xi = x / h - idx
+    a = np.abs(xi)
+    N = np.where(a < 0.5, 0.75 - xi * xi, 0.5 * (1.5 - a) ** 2)
+    dN = np.where(a < 0.5, -2.0 * xi, -(1.5 - a) * np.sign(xi)) / h
+    return idx, N, dN
+
+
+def _nh_total_potential(sc, du, grav):
+    """Total potential of a fresh Neo-Hookean body (b_e = 1 at the start of
+    the step): sum_p V0_p psi(dF_p) - sum_p m_p g . u(x_p), with
+    psi = mu/2 (tr b - 3) - mu ln J + lam/2 (ln J)^2 and dF_p from the
+    textbook B-spline gradients (plane strain: dF_zz = 1)."""
+    _, params, _ = sc.particle_params()
+    d = sc.dim
+    U = du.reshape(-1, d)
+    nx1, ny1 = sc.n[0] + 1, sc.n[1] + 1
+    total = 0.0
+    for p in range(sc.np):
+        E, nu = params[p, 0], params[p, 1]
+        mu, lam = _lame(E, nu)
+        ax = [_bspline_1d(sc.x[p, a] - sc.origin[a], sc.h) for a in range(d)]
+        dF = np.eye(3)
+        up = np.zeros(d)
+        for combo in np.ndindex(*(3,) * d):
+            node = ax[0][0][combo[0]] + nx1 * ax[1][0][combo[1]]
+            if d == 3:
+                node += nx1 * ny1 * ax[2][0][combo[2]]
+            w = np.prod([ax[a][1][combo[a]] for a in range(d)])
+            gw = np.array([ax[a][2][combo[a]] * np.prod([ax[b][1][combo[b]] for b in range(d) if b != a])
+                           for a in range(d)])
+            dF[:d, :d] += np.outer(U[node], gw)
+            up += w * U[node]
+        J = np.linalg.det(dF)
+        b = dF @ dF.T
+        psi = 0.5 * mu * (np.trace(b) - 3.0) - mu * np.log(J) + 0.5 * lam * np.log(J) ** 2
+        total += sc.vol0[p] * psi - sc.mass[p] * float(grav[:d] @ up)
+    return total
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_neo_hookean_residual_is_the_gradient_of_the_total_potential(oracle, dim):
+    """For a hyperelastic body the discrete residual is the gradient of the
+    total potential (stored energy minus the work of gravity), computed here
+    from the energy density with its own B-spline kinematics: a transposed
+    dF^-T, a wrong stress formula, a dropped volume or a wrong gravity sign
+    breaks it."""
+    sc = S.tiny_scene(dim, S.MODEL_NH, seed=41, ncell=3 if dim == 2 else 2)
+    orc = oracle.OracleScene.from_scene(sc)
+    g = np.array([0.4, -9.81, 0.7 if dim == 3 else 0.0])
+    orc.gravity = g
+    du = S.random_increment(sc, 0.03, seed=42)
+    r, M = orc.residual(du)
+    rng = np.random.default_rng(43)
+    for _ in range(3):
+        v = rng.standard_normal(du.size) * sc.h
+        eps = 1e-6
+        dPi = (_nh_total_potential(sc, du + eps * v, g) - _nh_total_potential(sc, du - eps * v, g)) / (2 * eps)
+        assert abs(dPi - r @ v) <= 1e-7 * np.abs(r).max() * np.abs(v).sum() / np.sqrt(v.size)
+    # one DOF at a time on the busiest node
+    i = int(np.argmax(M))
+    for a in range(dim):
+        e = np.zeros(du.size)
+        e[i * dim + a] = sc.h
+        dPi = (_nh_total_potential(sc, du + 1e-6 * e, g) - _nh_total_potential(sc, du - 1e-6 * e, g)) / 2e-6
+        assert abs(dPi - r[i * dim + a] * sc.h) <= 1e-7 * abs(r[i * dim + a] * sc.h) + 1e-9 * np.abs(r).max() * sc.h
