@@ -563,3 +563,26 @@ def test_neo_hookean_residual_is_the_gradient_of_the_total_potential(oracle, dim
         e[i * dim + a] = sc.h
         dPi = (_nh_total_potential(sc, du + 1e-6 * e, g) - _nh_total_potential(sc, du - 1e-6 * e, g)) / 2e-6
         assert abs(dPi - r[i * dim + a] * sc.h) <= 1e-7 * abs(r[i * dim + a] * sc.h) + 1e-9 * np.abs(r).max() * sc.h
+
+
+def test_cam_clay_newton_converges_quadratically_once_yielding(oracle):
+    """The consistent tangent makes Newton quadratic once the plastic set is
+    fixed (the paper's observation for its plastic examples, Sec. 4.1-4.2):
+    on the Cam-Clay oedometer, whose particles all yield after the first
+    steps, e_{k+1} <= C e_k^2 with a modest C until the rounding floor.  A
+    continuum (non-consistent) tangent gives a linear rate and fails this."""
+    sc = S.oedometer_3d(model=S.MODEL_NH_MCC)
+    orc = oracle.OracleScene.from_scene(sc)
+    checked = 0
+    for k, st in enumerate(sc.steps):
+        out = orc.solve_step(st.dof, st.value, st.gravity, tol=1e-13, commit=False)
+        assert out["converged"] and out["iters"] <= 5
+        _, _, modes = orc.residual(out["du"], with_mode=True)
+        if (modes > 0).mean() == 1.0:
+            h = out["hist"]
+            for a, b in zip(h[1:], h[2:]):
+                if a * a > 1e-12:      # above the rounding floor of about 5e-14
+                    assert b <= 1.0 * a * a, (k, h)
+                    checked += 1
+        orc.commit(out["du"])
+    assert checked >= 4
