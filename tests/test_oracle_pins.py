@@ -565,13 +565,16 @@ def test_neo_hookean_residual_is_the_gradient_of_the_total_potential(oracle, dim
         assert abs(dPi - r[i * dim + a] * sc.h) <= 1e-7 * abs(r[i * dim + a] * sc.h) + 1e-9 * np.abs(r).max() * sc.h
 
 
-def test_cam_clay_newton_converges_quadratically_once_yielding(oracle):
+@pytest.mark.parametrize("model,kw", [(S.MODEL_NH_MCC, {}), (S.MODEL_NH_DP, dict(c=100.0, nu=0.2, prestrain=0.0))],
+                         ids=["cam_clay", "drucker_prager"])
+def test_plastic_newton_converges_quadratically_once_yielding(oracle, model, kw):
     """The consistent tangent makes Newton quadratic once the plastic set is
     fixed (the paper's observation for its plastic examples, Sec. 4.1-4.2):
-    on the Cam-Clay oedometer, whose particles all yield after the first
-    steps, e_{k+1} <= C e_k^2 with a modest C until the rounding floor.  A
-    continuum (non-consistent) tangent gives a linear rate and fails this."""
-    sc = S.oedometer_3d(model=S.MODEL_NH_MCC)
+    on oedometers whose particles all yield (Cam-Clay after the first steps;
+    Drucker-Prager with a low Poisson ratio and no pre-compression),
+    e_{k+1} <= e_k^2 until the rounding floor.  A continuum (non-consistent)
+    tangent gives a linear rate and fails this."""
+    sc = S.oedometer_3d(model=model, **kw)
     orc = oracle.OracleScene.from_scene(sc)
     checked = 0
     for k, st in enumerate(sc.steps):
