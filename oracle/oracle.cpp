@@ -16,7 +16,9 @@
 //     logarithmic strain (the paper defers the models to textbooks, Sec. 2.1);
 //   * the internal force f_int,i = sum_p V0_p tau_p dF_p^-T grad w_ip (the
 //     paper's f_int,p = (sym grad w_p)^T : sigma_p V_p with sigma V = tau V0)
-//     and gravity f_ext,i = sum_p w_ip m_p g;
+//     and the external force f_ext,i = sum_p w_ip (m_p g + f_p): gravity plus
+//     the force a particle carries (the traction term, read as a traction
+//     times the particle's share of the loaded face);
 //   * the residual r = f_int - f_ext (paper Eq. for r(u^{n+1}));
 //   * the Jacobian J = dr/du (paper Eq. for J^{n+1,k}) as its exact
 //     derivative: the per-particle tangent A_p = dP_p/d(dF_p) obtained by
