@@ -6,6 +6,8 @@ tests/golden/, each citing its table or section; no GPU).
   coloured difference Jacobian with the table's b = 5 equals one-DOF-at-a-time
   differences bit for bit, and one colour fewer per axis (b = 4) mixes
   columns (a wrong stencil reach or a wrong colouring fails one of these).
+* Sec. 4.3: the sparse (coloured) and dense difference Jacobians agree below
+  the printed relative Frobenius bound of 1e-15.
 * Sec. 4.2: on the bar under self-weight every load step reaches a relative
   residual of 1e-11 within four Newton iterations (a wrong tangent term
   slows Newton to a linear rate and fails this).
@@ -71,6 +73,10 @@ def test_table1_block_size_is_the_smallest_collision_free_colouring(oracle):
     Jp = oracle.fd_jacobian_plain(orc, du, eps, act)
     Jb = oracle.fd_jacobian_colored(orc, du, eps, b=b_tab)
     assert np.array_equal(Jb[:, act], Jp)
+    # Sec. 4.3: sparse and dense Jacobians agree to below 1e-15 in relative
+    # Frobenius norm (here they agree bit for bit)
+    bound = _kv("sec43_sparse_dense_jacobian.txt")["relative_frobenius_error_below"]
+    assert np.linalg.norm(Jb[:, act] - Jp) / np.linalg.norm(Jp) < bound
     Jless = oracle.fd_jacobian_colored(orc, du, eps, b=b_tab - 1)
     scale = np.abs(Jp).max()
     assert np.abs(Jless[:, act] - Jp).max() > 1e-3 * scale
