@@ -550,12 +550,18 @@ def main():
     B = sc.dim
     bytes_iter = 2 * spmv_bytes + 19 * na * B * tsz + 2 * na * B * B * tsz
     if args.precond == "mg":
-        # V-cycle: per level a residual and a smoothing product (2 stencil
-        # products), the block inverses and 6 vector passes; the coarse
-        # levels add 1/3 (2D: 1/4 per level) or 1/7 (3D: 1/8 per level)
-        lvl = 2 * spmv_bytes + 6 * na * B * tsz + na * B * B * tsz
-        vcyc = lvl * (4.0 / 3.0 if sc.dim == 2 else 8.0 / 7.0)
-        bytes_iter = 2 * spmv_bytes + 19 * na * B * tsz + 2 * vcyc
+        # Two V-cycles per iteration.  Finest level (two smoothing sweeps per
+        # side, the first fused into the Krylov kernel that produces its
+        # input): three sweeps and one residual with a stencil product, four
+        # reads of the block inverses, and about 8 vector passes (the sweeps'
+        # and the residual's right-hand sides, restriction, prolongation).
+        # Each coarse level: a first sweep without a product, a residual and a
+        # post-sweep product, two block-inverse reads and 6 vector passes, on
+        # 1/4 (2D) or 1/8 (3D) of the rows of the level above.
+        vec, dinv = na * B * tsz, na * B * B * tsz
+        fine = 4 * spmv_bytes + 4 * dinv + 8 * vec
+        coarse = (2 * spmv_bytes + 2 * dinv + 6 * vec) * (1.0 / 3.0 if sc.dim == 2 else 1.0 / 7.0)
+        bytes_iter = 2 * spmv_bytes + 19 * na * B * tsz + 2 * (fine + coarse)
     peaks, src = read_peaks()
     t_kry_s = phase[3] * 1e-3
     achieved = (krylov / max(newton, 1)) * newton * bytes_iter / max(t_kry_s, 1e-12) / 1e9
