@@ -556,6 +556,9 @@ def test_neo_hookean_residual_is_the_gradient_of_the_total_potential(oracle, dim
         eps = 1e-6
         dPi = (_nh_total_potential(sc, du + eps * v, g) - _nh_total_potential(sc, du - eps * v, g)) / (2 * eps)
         assert abs(dPi - r @ v) <= 1e-7 * np.abs(r).max() * np.abs(v).sum() / np.sqrt(v.size)
+    # the Jacobian is then the Hessian of that potential: symmetric
+    J = orc.jacobian(du).toarray()
+    assert np.abs(J - J.T).max() <= 1e-12 * np.abs(J).max()
     # one DOF at a time on the busiest node
     i = int(np.argmax(M))
     for a in range(dim):
