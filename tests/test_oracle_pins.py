@@ -592,3 +592,25 @@ def test_plastic_newton_converges_quadratically_once_yielding(oracle, model, kw)
                     checked += 1
         orc.commit(out["du"])
     assert checked >= 4
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_associative_drucker_prager_jacobian_is_symmetric(oracle, dim):
+    """With associative flow (psi = phi), no hardening and an elastic law with
+    a potential in principal log strain, the return map is the stationarity
+    condition of an incremental potential, so the consistent tangent, and the
+    global Jacobian, is symmetric, apex states included (Simo 1992).  The
+    non-associative case (psi = 0) is not: a wrong flow direction or a
+    transposed term of the spectral tangent breaks the first, the second
+    shows the check can fail."""
+    sc = S.tiny_scene(dim, S.MODEL_NH_DP, seed=7, ncell=3 if dim == 2 else 2)
+    du = S.random_increment(sc, 0.03, seed=8)
+    sc.materials[0].psi = sc.materials[0].phi
+    orc = oracle.OracleScene.from_scene(sc)
+    _, _, modes = orc.residual(du, with_mode=True)
+    assert (modes == 1).sum() >= 10 and (modes == 2).sum() >= 10
+    J = orc.jacobian(du).toarray()
+    assert np.abs(J - J.T).max() <= 1e-13 * np.abs(J).max()
+    sc.materials[0].psi = 0.0
+    J0 = oracle.OracleScene.from_scene(sc).jacobian(du).toarray()
+    assert np.abs(J0 - J0.T).max() > 1e-2 * np.abs(J0).max()
