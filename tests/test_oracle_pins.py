@@ -614,3 +614,42 @@ def test_associative_drucker_prager_jacobian_is_symmetric(oracle, dim):
     sc.materials[0].psi = 0.0
     J0 = oracle.OracleScene.from_scene(sc).jacobian(du).toarray()
     assert np.abs(J0 - J0.T).max() > 1e-2 * np.abs(J0).max()
+
+
+def _rotation(rng):
+    q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+    q = q @ np.diag(np.sign(np.diag(r)))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+@pytest.mark.parametrize("case", [c for c in TANGENT_CASES if c[0] in
+                                  ("nh_random", "dp_plastic", "dp_apex", "dp_plastic_prestrained",
+                                   "mcc_compaction", "mcc_prestrained")], ids=lambda c: c[0])
+def test_constitutive_update_is_objective(oracle, case):
+    """A rigid rotation R superposed on the increment (dF -> R dF) rotates
+    the Kirchhoff stress and the elastic left Cauchy-Green tensor (R . R^T),
+    leaves the mode and the hardening variable unchanged, and transforms
+    P = V0 tau dF^-T to R P and the tangent dP/d(dF) to
+    R_ai A_icje R_bj.  A frame-dependent step anywhere in the spectral return
+    map or its tangent fails this."""
+    _, model, kw, be_spec, pcn, dF_spec, mode = case
+    rng = np.random.default_rng(77)
+    p = _mat(model, **kw)
+    be6 = np.array([1, 1, 1, 0, 0, 0.0]) if be_spec == "eye" else _spd6(0.01)
+    dF = _make_dF(dF_spec)
+    R = _rotation(rng)
+    o = oracle.particle(model, p, be6, pcn, dF, V0=0.3)
+    oR = oracle.particle(model, p, be6, pcn, R @ dF, V0=0.3)
+    assert oR["mode"] == o["mode"] == mode
+    s = np.abs(o["tau"]).max()
+    assert np.abs(oR["tau"] - R @ o["tau"] @ R.T).max() <= 1e-10 * s
+    assert np.abs(oR["P"] - R @ o["P"]).max() <= 1e-10 * np.abs(o["P"]).max()
+
+    def full(b6):
+        return np.array([[b6[0], b6[3], b6[5]], [b6[3], b6[1], b6[4]], [b6[5], b6[4], b6[2]]])
+    assert np.abs(full(oR["be"]) - R @ full(o["be"]) @ R.T).max() <= 1e-12
+    assert abs(oR["pc"] - o["pc"]) <= 1e-12 * abs(o["pc"]) + 1e-300
+    A_rot = np.einsum("ai,icje,bj->acbe", R, o["A"], R)
+    assert np.abs(oR["A"] - A_rot).max() <= 1e-9 * np.abs(o["A"]).max()
