@@ -9,6 +9,8 @@ Sec. 4.4 one-dimensional consolidation), no GPU.
   pressure-pressure block).
 * Discrete flux energy: with du = 0, sum_i p_i r_p,i = sum_p kdt V_p |grad p_p|^2
   >= 0 (the sign and the quadratic form of the Darcy term).
+* Volume change: under a uniform dilation with zero pressure the mass-balance
+  rows sum to (J - 1) sum_p V_p.
 * Finite strain: the Darcy rows are unchanged by a superposed rigid rotation
   and scale by s1 / s2 under a stretch s1 across and s2 along the flow.
 * Terzaghi (Sec. 4.4): pore pressure and settlement converge to the series
@@ -135,6 +137,15 @@ def test_up_darcy_flux_is_objective_and_scales_with_the_deformed_geometry(oracle
     R = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
     F_rot, _ = _flux_rows(orc, sc, R, p_rand)
     assert np.abs(F_rot - F_ref)[act].max() <= 1e-12 * scale
+    # the volume-change part of the mass balance: with zero pressure and a
+    # uniform dilation the rows sum (partition of unity) to (J - 1) sum_p V_p
+    e = 0.01
+    Xd = sc.node_coords()[:, :2]
+    U = np.zeros(sc.nnode * 3)
+    U[0::3], U[1::3] = e * Xd[:, 0], e * Xd[:, 1]
+    r_vol, _ = orc.residual(U)
+    J = (1 + e) ** 2
+    assert abs(r_vol[2::3].sum() - (J - 1) * sc.vol0.sum()) <= 1e-13 * (J - 1) * sc.vol0.sum() * 10
     s1, s2 = 1.1, 0.9
     for axis in (0, 1):
         g = 1e4 / sc.h
