@@ -9,6 +9,8 @@ Sec. 4.4 one-dimensional consolidation), no GPU.
   pressure-pressure block).
 * Discrete flux energy: with du = 0, sum_i p_i r_p,i = sum_p kdt V_p |grad p_p|^2
   >= 0 (the sign and the quadratic form of the Darcy term).
+* Pore-pressure term: under a uniform dilation a uniform pressure p0 adds
+  momentum rows with zero sum and virial -p0 (current volume) 1.
 * Volume change: under a uniform dilation with zero pressure the mass-balance
   rows sum to (J - 1) sum_p V_p.
 * Finite strain: the Darcy rows are unchanged by a superposed rigid rotation
@@ -99,6 +101,30 @@ def test_up_flux_energy_identity(oracle):
         rhs += kdt[p] * orc.V0[p] * float(G @ G)
     assert rhs > 0
     assert abs(lhs - rhs) <= 1e-12 * rhs
+
+
+def test_up_pore_pressure_virial(oracle):
+    """A uniform pore pressure p0 in a body under a uniform dilation
+    (1 + e) adds the momentum rows of the total-stress term -p J dF^-T; their
+    virial sum_i x_i (x) dr_i over the current node positions is
+    -p0 times the current volume times the identity (positive pressure in
+    compression, scaled by J, pushed forward by dF^-T: a sign, a dropped J or
+    a missing dF^-T fails it)."""
+    sc = _up_tiny(S.MODEL_NH, seed=41)
+    orc = oracle.OracleScene.from_scene(sc)
+    X = sc.node_coords()[:, :2]
+    e, p0 = 0.02, 3e4
+    U = np.zeros(sc.nnode * 3)
+    U[0::3], U[1::3] = e * X[:, 0], e * X[:, 1]
+    r0, _ = orc.residual(U)
+    U[2::3] = p0
+    r1, _ = orc.residual(U)
+    dr = (r1 - r0).reshape(-1, 3)[:, :2]
+    x = (1 + e) * X
+    vir = x.T @ dr
+    ref = -p0 * (1 + e) ** 2 * sc.vol0.sum()
+    assert np.abs(vir - ref * np.eye(2)).max() <= 1e-12 * abs(ref)
+    assert np.abs(dr.sum(axis=0)).max() <= 1e-12 * np.abs(dr).sum()
 
 
 def _flux_rows(orc, sc, dF, pnode):
