@@ -653,3 +653,23 @@ def test_constitutive_update_is_objective(oracle, case):
     assert abs(oR["pc"] - o["pc"]) <= 1e-12 * abs(o["pc"]) + 1e-300
     A_rot = np.einsum("ai,icje,bj->acbe", R, o["A"], R)
     assert np.abs(oR["A"] - A_rot).max() <= 1e-9 * np.abs(o["A"]).max()
+
+
+@pytest.mark.parametrize("dim,model", [(2, S.MODEL_NH), (2, S.MODEL_NH_DP), (3, S.MODEL_NH_MCC)])
+def test_internal_force_virial_equals_the_kirchhoff_stress_sum(oracle, dim, model):
+    """For any increment, sum_i (X_i + du_i) (x) f_int,i = sum_p V0_p tau_p:
+    the B-spline gradients reproduce dF exactly, and P = V0 tau dF^-T.  It
+    ties the residual to the stress the update reports (a wrong sign, scale or
+    transposition of P between the two fails it)."""
+    sc = S.tiny_scene(dim, model, seed=51, ncell=3 if dim == 2 else 2)
+    orc = oracle.OracleScene.from_scene(sc)
+    orc.gravity = np.zeros(3)
+    du = S.random_increment(sc, 0.02, seed=52)
+    r, _ = orc.residual(du)
+    x = sc.node_coords()[:, :dim] + du.reshape(-1, dim)
+    vir = x.T @ r.reshape(-1, dim)
+    tau, modes = orc.stresses(du)
+    ref = np.einsum("p,pab->ab", orc.V0, tau)[:dim, :dim]
+    assert np.abs(vir - ref).max() <= 1e-11 * np.abs(ref).max()
+    if model != S.MODEL_NH:
+        assert (modes > 0).any()
