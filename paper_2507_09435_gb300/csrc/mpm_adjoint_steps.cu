@@ -38,7 +38,7 @@ struct LocalOut {
 
 // One evaluation of the particle's commit map and residual contribution.
 template <int D, class T, int B>
-__device__ bool local_eval(const DevGrid& G, const MatC& mc, double V0, double m, const double grav[3],
+__device__ __noinline__ bool local_eval(const DevGrid& G, const MatC& mc, double V0, double m, const double grav[3],
                            const double fe[3], const double* __restrict__ U, const T* __restrict__ mu, double psc,
                            const double* sb, const LocalZ& z, LocalOut& out) {
   Spline1 sp[3];
