@@ -1,18 +1,26 @@
 #!/usr/bin/env python
 """Benchmark of the implicit-MPM Newton step on one GB300 (or N replicas).
 
-Workload (default): 2D plane-strain rigid-footing bearing capacity, 256x128
-grid (h = 0.1 m), 128,016 particles (2x2 per cell), Neo-Hookean +
-non-associative Drucker-Prager (phi 30 deg, psi 0, c 5 kPa, E 1e7 Pa,
-nu 0.3), gravity, displacement-controlled footing; FP64 residual / return
-map / Newton check, FP32 Jacobian and BiCGStab (mixed mode).
+Workload (default): 3D granular column under a gravity ramp, 128x128x64
+grid (h = 0.1 m), a 72x72x48-cell column at 8 particles per cell (1,990,656
+particles), Neo-Hookean + modified Cam-Clay (M 1.2, lambda 0.1, kappa 0.02,
+pc0 lognormal about -100 kPa), 27-node stencil, 3x3 blocks, 125 blocks per
+row; FP64 residual / return map / Newton check, FP32 Jacobian and
+block-Jacobi BiCGStab (mixed mode).
 
 A bench "step" is one load step: sort + pattern, Newton iterations
 (residual + Jacobian + Krylov + update) to a relative residual of 1e-8,
 commit.  The metric is Newton iterations per second; particle-updates/s =
-particles x Newton iterations / s.  The first warm-up step is the geostatic
-step; the timed steps are footing increments.  L2 is flushed (256 MiB write)
-between timed steps, outside the per-step CUDA-event windows.
+particles x Newton iterations / s.  W warm-up steps run on a scene of their
+own; the timed run then solves load steps 0..K-1 of the ramp on a fresh
+scene (steps past the ramp's end hold the full load).  L2 is flushed (256
+MiB write) between timed steps, outside the per-step CUDA-event windows.
+
+Beside the headline: the last --fp64-steps timed load steps solved again by
+the plain FP64 GPU path from the same committed state (mixed vs FP64), an
+end-to-end leg through the C ABI with host buffers, the 2D footing
+(256x128, 128,016 particles, Drucker-Prager, multigrid V-cycle), the FP64
+oracle on a bounded sample (cpu_baseline) and the serving stream.
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
 build) on the same workload, one bounded sample per step.
@@ -71,8 +79,12 @@ def parse():
     ap.add_argument("--precond", default=None, choices=["auto", "node", "seg4", "mg"],
                     help="node / seg4: block-Jacobi blocks of one node or four consecutive active nodes; "
                          "mg: geometric multigrid V-cycle; default: mg for the 2D footing, auto otherwise")
-    ap.add_argument("--workload", default="footing",
+    ap.add_argument("--workload", default="column3d",
                     choices=["footing", "column3d", "column3d_stated", "serving", "slope_adjoint"])
+    ap.add_argument("--fp64-steps", type=int, default=3,
+                    help="the last N timed load steps are solved again by the plain FP64 GPU path from the "
+                         "same committed state (0: none)")
+    ap.add_argument("--no-footing", action="store_true", help="skip the 2D footing line beside the main one")
     ap.add_argument("--serving", type=int, default=32,
                     help="requests of the serving stream measured beside the main line (0: none); "
                          "--workload serving runs the 512-request stream alone")
@@ -92,13 +104,19 @@ def parse():
     return args
 
 
+# ncu-measured DRAM traffic of one Krylov iteration per workload /
+# precision / preconditioner (bytes; the profile that gives each is named
+# beside it); None where no capture of the current kernels exists
+TRAFFIC = {}
+
 WORKLOADS = {
-    # the 2D footing: the headline workload
+    # the 2D footing (reported beside the headline)
     "footing": "footing_256x128_dp",
     # the 3D modified Cam-Clay column under a gravity ramp: ~2M particles
-    # (72x72x48-cell column, 8 per cell) and the stated 32x32x48-cell column
-    "column3d": "column3d_128x128x64_mcc_2M",
-    "column3d_stated": "column3d_128x128x64_mcc_393k",
+    # (72x72x48-cell column, 8 per cell; the headline throughput workload)
+    # and the stated 32x32x48-cell column
+    "column3d": "mcc3d_2M",
+    "column3d_stated": "mcc3d_stated_393k",
     # the serving stream (the reference arm samples its first footing request)
     "serving": "serving_stream_512",
     "slope_adjoint": "slope_192x96_dp_random_fields",
@@ -124,11 +142,14 @@ def workload_scene(name="footing"):
 def config(args, sc):
     if args.workload in ("footing", "serving"):
         extra = {"ppc": 4, "model": "neo-hookean + drucker-prager (phi 30, psi 0, c 5 kPa)",
-                 "step": "one load step (footing increment 4 mm)"}
+                 "step": "one load step (geostatic step, then footing increments of 4 mm)"}
     else:
-        extra = {"ppc": 8, "model": "neo-hookean + modified cam-clay (M 1.2, lambda 0.1, kappa 0.02, "
-                                    "pc0 lognormal sigma 0.1 about -100 kPa)",
-                 "step": "one load step of a 20-step gravity ramp"}
+        cells = {"column3d": [72, 72, 48], "column3d_stated": [32, 32, 48]}[args.workload]
+        extra = {"ppc": 8, "column_cells": cells,
+                 "model": "neo-hookean + modified cam-clay (M 1.2, lambda 0.1, kappa 0.02, "
+                          "pc0 lognormal sigma 0.1 about -100 kPa)",
+                 "step": "one load step of a 20-step gravity ramp 0 -> g (timed steps 0..K-1 of the ramp "
+                         "on a fresh scene after W warm-up steps on another)"}
     return {"workload": WORKLOADS[args.workload], "grid": [int(v) for v in sc.n[:sc.dim]], "h": sc.h,
             "particles": sc.np, **extra, "precision": args.precision, "krylov": args.krylov,
             "precond": args.precond,
@@ -463,6 +484,92 @@ def run_serving_line(args):
 # GPU arm
 # ----------------------------------------------------------------------------
 
+def _events_step(gs, st, stream, flush):
+    """One load step on `gs`, L2 flushed before it, timed by CUDA events on
+    the scene's stream (the flush is outside the event window)."""
+    import torch
+    with torch.cuda.stream(stream):
+        flush.zero_()
+    stream.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rep = gs.solve_step(st)
+    e1.record(stream)
+    e1.synchronize()
+    return {"ms": e0.elapsed_time(e1), "newton": rep.newton_iters, "krylov": rep.krylov_iters_total,
+            "phase": np.array([rep.t_setup_ms, rep.t_residual_ms, rep.t_assembly_ms, rep.t_krylov_ms]),
+            "rel": rep.rel_residual}
+
+
+def _summary(recs):
+    ms = sum(r["ms"] for r in recs)
+    newton = sum(r["newton"] for r in recs)
+    krylov = sum(r["krylov"] for r in recs)
+    n = max(len(recs), 1)
+    return {"value": newton / (ms / 1e3) if ms > 0 else 0.0, "unit": UNIT, "ms_per_step": ms / n,
+            "newton_iters_per_step": newton / n, "krylov_iters_per_newton": krylov / max(newton, 1),
+            "rel_residual_max": max((r["rel"] for r in recs), default=0.0),
+            "phase_ms_per_step": dict(zip(("setup", "residual", "assembly", "krylov"),
+                                          [float(v) / n for v in sum((r["phase"] for r in recs), np.zeros(4))]))}
+
+
+def fp64_arm(sc, schedule, s0, k_end, snap, x_mixed_end, mixed_recs, args, stream, flush):
+    """The same load steps s0..k_end-1 solved with the FP64 Jacobian and
+    Krylov (the plain FP64 GPU path), from the mixed run's committed state at
+    step s0 (checkpoint/resume through mpm_set_state); one untimed solve of
+    step s0 first warms the FP64 scene's buffers and graphs.  Returns its
+    throughput beside the mixed path's on the same steps, and the mixed
+    result's stated error against it."""
+    from paper_2507_09435_gb300 import mpm
+    pc = {"auto": mpm.MPM_PC_AUTO, "node": mpm.MPM_PC_NODE, "seg4": mpm.MPM_PC_SEG4,
+          "mg": mpm.MPM_PC_MG}[args.precond]
+    kry = mpm.MPM_BICGSTAB if args.krylov == "bicgstab" else mpm.MPM_GMRES
+    g64 = mpm.GpuScene(sc, precision=mpm.MPM_FP64, krylov=kry, stream=stream.cuda_stream, newton_tol=1e-8,
+                       precond=pc, krylov_maxit=50000)
+    mpm.mpm_set_state(g64.h, x=snap["x"], be=snap["be"], pc=snap["pc"], F=snap["F"])
+    g64.solve_step(schedule(s0))
+    mpm.mpm_set_state(g64.h, x=snap["x"], be=snap["be"], pc=snap["pc"], F=snap["F"])
+    recs = [_events_step(g64, schedule(k), stream, flush) for k in range(s0, k_end)]
+    x64 = g64.particles(be=False, pc=False, F=False, tau=False)["x"]
+    g64.close()
+    out = _summary(recs)
+    mix = _summary(mixed_recs[s0:k_end])
+    disp = float(np.abs(x64 - snap["x"]).max())
+    out.update({
+        "steps": [int(s0), int(k_end - 1)],
+        "start": "the mixed run's committed state before the first of these steps (mpm_set_state)",
+        "mixed_same_steps": {k: mix[k] for k in ("value", "ms_per_step", "newton_iters_per_step",
+                                                 "krylov_iters_per_newton", "rel_residual_max")},
+        "mixed_speedup_per_load_step": mix["ms_per_step"] and out["ms_per_step"] / mix["ms_per_step"],
+        "mixed_newton_iters_per_s_ratio": out["value"] and mix["value"] / out["value"],
+        "mixed_error_vs_fp64": {"max_abs_x_diff_m": float(np.abs(x_mixed_end - x64).max()),
+                                "displacement_scale_m": disp,
+                                "relative": float(np.abs(x_mixed_end - x64).max()) / max(disp, 1e-300)},
+    })
+    return out
+
+
+def footing_extra(args, stream, flush, nwarm=2, nsteps=8):
+    """The C2 footing (256x128, 128,016 particles, NH + Drucker-Prager, mixed,
+    V-cycle preconditioned BiCGStab): geostatic step and one increment
+    untimed, then `nsteps` timed footing increments on the same scene."""
+    from paper_2507_09435_gb300 import mpm
+    sc = workload_scene("footing")
+    gs = mpm.GpuScene(sc, precision=mpm.MPM_MIXED, stream=stream.cuda_stream, newton_tol=1e-8,
+                      precond=mpm.MPM_PC_MG, krylov_maxit=50000)
+    for k in range(nwarm):
+        gs.solve_step(sc.steps[k])
+    recs = [_events_step(gs, sc.steps[min(k, len(sc.steps) - 1)], stream, flush)
+            for k in range(nwarm, nwarm + nsteps)]
+    gs.close()
+    out = _summary(recs)
+    out.update({"workload": WORKLOADS["footing"], "particles": sc.np, "precision": "mixed",
+                "preconditioner": "multigrid V-cycle", "steps_timed": nsteps,
+                "note": "matrix (about 13.6 MB FP32) is L2-resident: latency-bound, not an HBM fraction"})
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -492,58 +599,60 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     pc = {"auto": mpm.MPM_PC_AUTO, "node": mpm.MPM_PC_NODE, "seg4": mpm.MPM_PC_SEG4,
           "mg": mpm.MPM_PC_MG}[args.precond]
-    gs = mpm.GpuScene(sc, precision=prec, krylov=kry, stream=stream.cuda_stream, newton_tol=1e-8, precond=pc,
-                      krylov_maxit=50000)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     steps = sc.steps
-    k_next = 0
 
-    def next_step():
-        nonlocal k_next
-        st = steps[min(k_next, len(steps) - 1)]
-        k_next += 1
-        return st
+    def schedule(k):
+        # the load-step schedule; steps past its end hold the last load
+        return steps[min(k, len(steps) - 1)]
+
+    def new_scene(precision=prec):
+        return mpm.GpuScene(sc, precision=precision, krylov=kry, stream=stream.cuda_stream, newton_tol=1e-8,
+                            precond=pc, krylov_maxit=50000)
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(max(args.warmup, 1)):
-        rep = gs.solve_step(next_step())
+    # warm-up: the first W steps of the schedule on a scene of their own, so
+    # that the timed run solves the schedule from its first load step
+    gw = new_scene()
+    for k in range(max(args.warmup, 1)):
+        gw.solve_step(schedule(k))
+    gw.close()
 
-    # ---- device-timed region -------------------------------------------------
+    # ---- device-timed region: load steps 0..K-1 of the schedule ------------
+    n64 = 0 if (args.precision == "fp64" or args.fp64_steps <= 0) else min(args.fp64_steps, args.steps)
+    s0 = args.steps - n64
+    gs = new_scene()
+    snap = None
     barrier()
     clk = ClockSampler(torch.cuda.current_device())
     L0 = mpm.mpm_kernel_launches(gs.h)
-    t_ms, newton, krylov = 0.0, 0, 0
-    phase = np.zeros(4)
-    for _ in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        stream.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        rep = gs.solve_step(next_step())
-        e1.record(stream)
-        e1.synchronize()
-        t_ms += e0.elapsed_time(e1)
-        newton += rep.newton_iters
-        krylov += rep.krylov_iters_total
-        phase += [rep.t_setup_ms, rep.t_residual_ms, rep.t_assembly_ms, rep.t_krylov_ms]
+    recs = []
+    for k in range(args.steps):
+        if n64 and k == s0:
+            # checkpoint for the FP64 arm (outside the event windows)
+            snap = gs.particles(tau=False)
+        recs.append(_events_step(gs, schedule(k), stream, flush))
     launches = mpm.mpm_kernel_launches(gs.h) - L0
     barrier()
     clocks = clk.stop()
+    t_ms = sum(r["ms"] for r in recs)
+    newton = sum(r["newton"] for r in recs)
+    krylov = sum(r["krylov"] for r in recs)
+    phase = sum((r["phase"] for r in recs), np.zeros(4))
     t_all, (newton_all, krylov_all) = reduce_over_ranks(t_ms, [newton, krylov], world, dev)
     value = newton_all / (t_all / 1e3)
+    x_mixed_end = gs.particles(be=False, pc=False, F=False, tau=False)["x"] if n64 else None
 
     # ---- dominant kernel: the Krylov iteration, timed live -------------------
     # achieved = algorithmic bytes of all timed Krylov iterations / the
     # CUDA-event time of the Krylov phases.  Bytes per iteration: two stencil-BSR products (present
     # blocks + input/output vectors + row list) + 19 vector passes of the
     # BLAS-1 phases + two block-Jacobi applications.
-    gs.begin(next_step())
+    gs.begin(schedule(args.steps))
     na, _ = mpm.mpm_get_counts(gs.h)
     spmv_ms, spmv_bytes = mpm.mpm_time_spmv(gs.h, 200)
     tsz = 4 if args.precision == "mixed" else 8
@@ -564,7 +673,7 @@ def main():
         bytes_iter = 2 * spmv_bytes + 19 * na * B * tsz + 2 * (fine + coarse)
     peaks, src = read_peaks()
     t_kry_s = phase[3] * 1e-3
-    achieved = (krylov / max(newton, 1)) * newton * bytes_iter / max(t_kry_s, 1e-12) / 1e9
+    achieved = krylov * bytes_iter / max(t_kry_s, 1e-12) / 1e9
     if args.krylov == "gmres":
         kname = "GMRES(m) cycle kernels (k_gmres_spmv/orth1/orth2/norm/update, one CUDA graph per cycle)"
     elif args.precond == "mg":
@@ -578,42 +687,54 @@ def main():
                  "CUDA graph of 8 iterations)")
     roof = {"kernel": kname,
             "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
-            "bytes_per_iteration": bytes_iter, "us_per_iteration": 1e6 * t_kry_s / max(krylov, 1),
+            "frac": achieved / peaks["hbm_gbs"], "traffic": TRAFFIC.get((args.workload, args.precision,
+                                                                          args.precond)),
+            "peak_source": src, "bytes_per_iteration": bytes_iter,
+            "us_per_iteration": 1e6 * t_kry_s / max(krylov, 1),
             "spmv_alone": {"kernel": "k_spmv", "ms_per_launch": spmv_ms, "bytes_per_launch": spmv_bytes,
-                           "gbs": spmv_bytes / (spmv_ms * 1e-3) / 1e9},
-            "note": ("2D footing matrix (about 13.6 MB FP32) is L2-resident; HBM fraction is not the bound here"
+                           "gbs": spmv_bytes / (spmv_ms * 1e-3) / 1e9,
+                           "frac": spmv_bytes / (spmv_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]},
+            "note": ("2D matrix is L2-resident; HBM fraction is not the bound here"
                      if sc.dim == 2 else "3D matrix exceeds L2 (129 MB): HBM-bound")}
+    gs.close()
+
+    # ---- the plain FP64 GPU path on the last timed steps ---------------------
+    fp64 = None
+    if n64 and snap is not None:
+        fp64 = fp64_arm(sc, schedule, s0, args.steps, snap, x_mixed_end, recs, args, stream, flush)
 
     # ---- end to end through the C ABI with host buffers ----------------------
     e2e = None
     if not args.no_e2e:
-        pin_dof = [torch.from_numpy(np.asarray(s.dof, dtype=np.int64)).pin_memory() for s in steps]
-        pin_val = [torch.from_numpy(np.asarray(s.value, dtype=np.float64)).pin_memory() for s in steps]
-        gs2 = mpm.GpuScene(sc, precision=prec, krylov=kry, stream=stream.cuda_stream, newton_tol=1e-8, precond=pc,
-                           krylov_maxit=50000)
-        gs2.solve_step(steps[0])
+        ke = max(1, args.steps // 2)
+        pin_dof = [torch.from_numpy(np.asarray(schedule(k).dof, dtype=np.int64)).pin_memory()
+                   for k in range(ke + 1)]
+        pin_val = [torch.from_numpy(np.asarray(schedule(k).value, dtype=np.float64)).pin_memory()
+                   for k in range(ke + 1)]
+        gs2 = new_scene()
+        gs2.solve_step(schedule(0))
         h2d = d2h = 0
         t_e, n_e = 0.0, 0
-        kk = 1
-        for _ in range(max(1, args.steps // 2)):
-            idx = min(kk, len(steps) - 1)
-            kk += 1
+        for k in range(1, ke + 1):
             barrier()
             t0 = time.perf_counter()
-            mpm.mpm_set_dirichlet(gs2.h, pin_dof[idx].numpy(), pin_val[idx].numpy())
-            mpm.mpm_set_gravity(gs2.h, steps[idx].gravity)
+            mpm.mpm_set_dirichlet(gs2.h, pin_dof[k].numpy(), pin_val[k].numpy())
+            mpm.mpm_set_gravity(gs2.h, schedule(k).gravity)
             rep = mpm.mpm_solve_step(gs2.h)
             out = gs2.particles(be=False, pc=False, F=False)
             t_e += time.perf_counter() - t0
             n_e += rep.newton_iters
-            h2d = pin_dof[idx].numel() * 8 + pin_val[idx].numel() * 8 + 24
+            h2d = pin_dof[k].numel() * 8 + pin_val[k].numel() * 8 + 24
             d2h = out["x"].nbytes + out["tau"].nbytes
         t_e, (n_e_all,) = reduce_over_ranks(t_e, [n_e], world, dev)
         e2e = {"value": n_e_all / t_e, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h),
+               "d2h_bytes_per_step": int(d2h), "steps": [1, ke],
                "call": "mpm_set_dirichlet + mpm_set_gravity + mpm_solve_step + mpm_get_particles(x, tau)"}
         gs2.close()
+
+    footing = None
+    if rank == 0 and args.workload != "footing" and not args.no_footing:
+        footing = footing_extra(args, stream, flush)
 
     # ---- CPU baseline: the oracle on a bounded sample (N = 1 runs only) -------
     cpu = None
@@ -640,12 +761,12 @@ def main():
                 "particle_updates_per_s": value * sc.np,
                 "krylov_iters_per_newton": krylov_all / max(newton_all, 1.0),
                 "newton_iters_per_step": newton_all / (args.steps * n_gpus),
+                "rel_residual_max": max(r["rel"] for r in recs),
                 "phase_ms_per_step": {"setup": phase[0] / args.steps, "residual": phase[1] / args.steps,
                                       "assembly": phase[2] / args.steps, "krylov": phase[3] / args.steps},
-                "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "clocks": clocks, "serving": serving}
+                "gpu_launches": int(launches), "roofline": roof, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clocks, "footing": footing, "serving": serving}
         print(json.dumps(line), flush=True)
-    gs.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

@@ -332,6 +332,14 @@ mpm_status mpm_get_pressure(const mpm_scene* s, double* pp);
  * inside CUDA-graph launches). */
 mpm_status mpm_kernel_launches(const mpm_scene* s, long long* out);
 
+/* Newton globalisation counters of this scene since it was created:
+ * *limited Newton corrections scaled down by the step-length limit (a node
+ * moved by more than one cell width h), *halvings halved steps (a return map
+ * left its domain, a state became non-finite or inverted, or the residual
+ * norm did not decrease).  Either pointer may be NULL.  The paper's Newton
+ * (Sec. 2.2) takes full steps; these safeguards are this library's. */
+mpm_status mpm_get_newton_counters(const mpm_scene* s, long long* limited, long long* halvings);
+
 /* Time the Jacobian-vector product kernel of the staged step's assembled
  * Jacobian: `reps` launches on the scene's stream between CUDA events.
  * ms_per_launch: average duration; bytes_per_launch: algorithmic bytes of

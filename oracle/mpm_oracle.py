@@ -13,6 +13,9 @@ Newton loop of the paper's Sec. 2.2:
   solved by a sparse direct factorisation (SciPy's SuperLU, a library step);
 * stop when ||r^k|| / ||r^0|| <= tol (paper's convergence criterion), with
   r^0 taken after the prescribed boundary increment is applied;
+* the correction is globalised (a reading: the paper takes full steps):
+  limited to one cell width h per node, halved up to four times when the
+  residual cannot be evaluated or does not decrease (``_globalised_update``);
 * commit of the particle state after convergence.
 
 Readings (the paper is silent on these):
@@ -309,13 +312,15 @@ class OracleScene:
         hist = [1.0]
         it = 0
         conv = r0 == 0.0
+        disp = np.tile(np.arange(self.B) < self.dim, self.nnode)[fidx]
+        rk = r0
         while not conv and it < maxit:
             J = self.jacobian(du)[fidx][:, fidx].tocsc()
             delta = spla.spsolve(J, -r[fidx])
-            du[fidx] += delta
-            r, M = self.residual(du)
+            du, r, M = self._globalised_update(du, fidx, delta, disp, rk, r0, tol, wn, free)
             it += 1
-            rel = np.linalg.norm((wn * r)[free]) / r0
+            rk = np.linalg.norm((wn * r)[free])
+            rel = rk / r0
             hist.append(rel)
             conv = rel <= tol
         out = dict(du=du, hist=np.array(hist), iters=it, converged=bool(conv), r0=r0,
@@ -323,6 +328,45 @@ class OracleScene:
         if commit:
             self.commit(du)
         return out
+
+    def _globalised_update(self, du, fidx, delta, disp, rk, r0, tol, wn, free):
+        """Apply the Newton correction `delta` (over the free DOFs `fidx`) with
+        the globalisation reading (the paper's Newton of Sec. 2.2 takes full
+        steps; it states no safeguard):
+        * step-length limit: when the largest displacement component of the
+          correction exceeds one cell width h, the correction is scaled so
+          that it equals h (a non-finite correction becomes zero);
+        * a step whose residual cannot be evaluated because a return map
+          leaves its domain or a particle's deformation stops being
+          invertible, or whose residual norm is not below (1 - 1e-4) times the
+          current one while that is above 10 tol ||r0||, is halved, at most
+          four times; the fourth halving is taken whatever its residual.
+        Returns the new increment, its residual and the nodal mass."""
+        xmax = float(np.abs(delta[disp]).max()) if disp.any() else 0.0
+        lim = 0.0 if not np.isfinite(xmax) else (self.h / xmax if xmax > self.h else 1.0)
+        base = du.copy()
+
+        def trial(alpha):
+            d = base.copy()
+            d[fidx] += (alpha * lim) * delta
+            try:
+                r, M = self.residual(d)
+            except OracleError as e:
+                if "(-1)" in str(e):
+                    raise           # a particle's support left the grid
+                return d, None, None
+            return d, r, M
+
+        d, r, M = trial(1.0)
+        for half in range(1, 5):
+            if r is not None:
+                rnew = np.linalg.norm((wn * r)[free])
+                if rnew < (1.0 - 1e-4) * rk or rk <= 10.0 * tol * r0:
+                    break
+            d, r, M = trial(2.0 ** -half)
+        if r is None:
+            raise OracleError("residual failed after four step halvings")
+        return d, r, M
 
     def commit(self, du):
         if self.formulation == "up":

@@ -1494,6 +1494,13 @@ mpm_status mpm_kernel_launches(const mpm_scene* s, long long* out) {
   return MPM_OK;
 }
 
+mpm_status mpm_get_newton_counters(const mpm_scene* s, long long* limited, long long* halvings) {
+  if (!s) return MPM_ERR_INVALID_ARG;
+  if (limited) *limited = s->limited;
+  if (halvings) *halvings = s->halvings;
+  return MPM_OK;
+}
+
 mpm_status mpm_solve_step(mpm_scene* s, mpm_step_report* rep) {
   if (!s) return MPM_ERR_INVALID_ARG;
   mpm_step_report local{};

@@ -15,7 +15,8 @@ from parity_util import (DU_TOL, JAC_TOL_FP64, JAC_TOL_MIXED, RES_TOL, du_error,
 pytestmark = pytest.mark.gpu
 
 
-def _run_parity(sc, nsteps, precision=mpm.MPM_FP64, jac_every_step=True, expect_plastic=False, **kw):
+def _run_parity(sc, nsteps, precision=mpm.MPM_FP64, jac_every_step=True, expect_plastic=False,
+                expect_globalised=False, **kw):
     orc = O.OracleScene.from_scene(sc)
     gs = mpm.GpuScene(sc, precision=precision, newton_tol=1e-12, newton_maxit=30,
                       forcing=mpm.MPM_FORCING_FIXED, krylov_rtol=1e-13 if precision == mpm.MPM_FP64 else 1e-6,
@@ -38,18 +39,18 @@ def _run_parity(sc, nsteps, precision=mpm.MPM_FP64, jac_every_step=True, expect_
         # kappa(J) times the stopping tolerance
         it = 0
         rel, best = 1.0, 1.0
-        while rel > 1e-13 and it < 30:
+        while rel > 1e-13 and it < 40:
             nr = gs.newton()
             it += 1
             rel = nr.rel_residual
             saw_plastic |= nr.n_plastic > 0
             assert residual_error(gs, orc, gs.du(), fixed) < RES_TOL
-            if it >= 4 and rel > 0.5 * best:
+            if rel < 1e-10 and rel > 0.5 * best:
                 break   # at the rounding floor
             best = min(best, rel)
         assert rel <= 1e-12, (k, rel)
         du_g = gs.du()
-        out = orc.solve_step(st.dof, st.value, st.gravity, tol=1e-13, maxit=30)
+        out = orc.solve_step(st.dof, st.value, st.gravity, tol=1e-13, maxit=40)
         assert out["hist"][-1] <= 1e-12, out["hist"]   # 1e-13 or the oracle's own rounding floor
         assert du_error(du_g, out["du"]) < DU_TOL, (k, du_error(du_g, out["du"]))
         gs.commit()
@@ -62,6 +63,9 @@ def _run_parity(sc, nsteps, precision=mpm.MPM_FP64, jac_every_step=True, expect_
             assert np.abs(part["pc"] - orc.pc).max() < 1e-6 * np.abs(orc.pc).max()
     if expect_plastic:
         assert saw_plastic
+    if expect_globalised:
+        limited, halvings = mpm.mpm_get_newton_counters(gs.h)
+        assert limited + halvings > 0, (limited, halvings)
     gs.close()
 
 
@@ -89,9 +93,35 @@ def test_block_compression_matches_homogeneous_closed_form():
 
 def test_footing_coarse_fp64_plastic():
     """Coarsened footing (46x22 soil cells, 4,048 particles): geostatic step
-    plus footing steps large enough to drive Drucker-Prager particles plastic."""
+    plus footing steps of 0.5 cm that drive Drucker-Prager particles plastic."""
     sc = S.footing(nx=48, ny=24, h=0.5, nsteps=20, settle_frac=0.1)
     _run_parity(sc, 4, jac_every_step=True, expect_plastic=True)
+
+
+def test_footing_coarse_fp64_large_increments():
+    """The coarse footing pushed 4 cm per step (8 % of a cell), geostatic step
+    plus three increments.  The first increment takes about two dozen Newton
+    iterations on both sides, most of them scaled by the step-length limit or
+    halved: the globalised, strongly plastic regime, compared iterate by
+    iterate (residual) and at convergence (Jacobian, increment, state).  The
+    fourth increment (16 cm in all) meets the bearing-failure mechanism: there
+    neither side converges, and the GPU reports it without committing."""
+    sc = S.footing(nx=48, ny=24, h=0.5, nsteps=5, settle_frac=0.1)
+    _run_parity(sc, 4, jac_every_step=True, expect_plastic=True, expect_globalised=True)
+    orc = O.OracleScene.from_scene(sc)
+    for st in sc.steps[:4]:
+        assert orc.solve_step(st.dof, st.value, st.gravity, tol=1e-12, maxit=40)["converged"]
+    st = sc.steps[4]
+    assert not orc.solve_step(st.dof, st.value, st.gravity, tol=1e-8, maxit=30, commit=False)["converged"]
+    gs = mpm.GpuScene(sc, precision=mpm.MPM_FP64, newton_tol=1e-8, newton_maxit=30)
+    for s_ in sc.steps[:4]:
+        assert gs.solve_step(s_).converged
+    x_before = gs.particles(be=False, pc=False, F=False, tau=False)["x"]
+    gs.set_step(st)
+    rep = mpm.mpm_solve_step(gs.h, check=False)
+    assert rep.status != 0 and not rep.converged
+    assert np.array_equal(gs.particles(be=False, pc=False, F=False, tau=False)["x"], x_before)
+    gs.close()
 
 
 @pytest.mark.parametrize("krylov", [mpm.MPM_BICGSTAB, mpm.MPM_GMRES])
@@ -139,15 +169,19 @@ def test_random_states(dim, model, amp, precision):
     assert residual_error(gs, orc, du, fixed) < RES_TOL
     gs.assemble()
     ej, ng, no = jacobian_error(gs, orc, du, fixed)
-    assert ej < (JAC_TOL_FP64 if precision == mpm.MPM_FP64 else JAC_TOL_MIXED) * (10 if model else 1)
+    assert ej < (JAC_TOL_FP64 if precision == mpm.MPM_FP64 else JAC_TOL_MIXED), ej
     gs.close()
 
 
 def test_column_3d_mcc_fp64():
-    """Small 3D modified Cam-Clay column (4x4x6 cells, 768 particles): first
-    step of a gravity ramp with a low preconsolidation so that it yields."""
-    sc = S.column_collapse_3d(nx=12, ny=12, nz=12, h=0.1, col=(4, 4, 6), nsteps=3, pc_mean=-8e3, E=1e6)
-    _run_parity(sc, 1, jac_every_step=True, expect_plastic=True)
+    """Small 3D modified Cam-Clay column (4x4x6 cells, 768 particles): the
+    first three steps of a six-step gravity ramp with a low preconsolidation,
+    so that the plastic zone grows from 1 to 22 to about 150 particles.  (The
+    same column under 20 g, or carried past half of g, has no equilibrium:
+    the unconfined Cam-Clay column collapses and Newton stalls on both
+    sides.)"""
+    sc = S.column_collapse_3d(nx=12, ny=12, nz=12, h=0.1, col=(4, 4, 6), nsteps=6, pc_mean=-1.2e4, E=1e6)
+    _run_parity(sc, 3, jac_every_step=True, expect_plastic=True)
 
 
 def test_oedometer_3d_mcc_fp64():

@@ -57,7 +57,7 @@ def test_up_random_states(model, precision):
     gs.assemble()
     ej, ng, no = jacobian_error(gs, orc, U, fixed)
     assert ng == no
-    assert ej < (JAC_TOL_FP64 if precision == mpm.MPM_FP64 else JAC_TOL_MIXED) * (10 if model else 1), ej
+    assert ej < (JAC_TOL_FP64 if precision == mpm.MPM_FP64 else JAC_TOL_MIXED), ej
     gs.close()
 
 

@@ -343,7 +343,7 @@ def test_block_compression_homogeneous_closed_form_and_quadratic_newton(oracle):
     orc = oracle.OracleScene.from_scene(sc)
     mu, lam = _lame(1e6, 0.3)
     for k, st in enumerate(sc.steps):
-        out = orc.solve_step(st.dof, st.value, st.gravity, tol=1e-12)
+        out = orc.solve_step(st.dof, st.value, st.gravity, tol=1e-12, globalise=False)
         assert out["converged"] and out["iters"] <= 4
         h = out["hist"]
         for a, b in zip(h[1:-1], h[2:]):
@@ -379,7 +379,7 @@ def test_self_weight_bar_converges_to_closed_form(oracle):
         orc = oracle.OracleScene.from_scene(sc)
         Y = sc.x[:, 1] - sc.meta["y_base"]
         for st in sc.steps:
-            out = orc.solve_step(st.dof, st.value, st.gravity, tol=1e-11)
+            out = orc.solve_step(st.dof, st.value, st.gravity, tol=1e-11, globalise=False)
             assert out["converged"] and out["iters"] <= 6
         tau, _ = orc.stresses()
         J = np.linalg.det(orc.F.reshape(-1, 3, 3))
@@ -581,7 +581,7 @@ def test_plastic_newton_converges_quadratically_once_yielding(oracle, model, kw)
     orc = oracle.OracleScene.from_scene(sc)
     checked = 0
     for k, st in enumerate(sc.steps):
-        out = orc.solve_step(st.dof, st.value, st.gravity, tol=1e-13, commit=False)
+        out = orc.solve_step(st.dof, st.value, st.gravity, tol=1e-13, commit=False, globalise=False)
         assert out["converged"] and out["iters"] <= 5
         _, _, modes = orc.residual(out["du"], with_mode=True)
         if (modes > 0).mean() == 1.0:
@@ -673,3 +673,19 @@ def test_internal_force_virial_equals_the_kirchhoff_stress_sum(oracle, dim, mode
     assert np.abs(vir - ref).max() <= 1e-11 * np.abs(ref).max()
     if model != S.MODEL_NH:
         assert (modes > 0).any()
+
+
+def test_globalised_newton_reaches_the_plain_newton_root(oracle):
+    """The step-length limit and the step halving change the Newton path, not
+    its end point: on the bar under self-weight (large compaction, where the
+    limit is active) both forms converge to the same increment, and on the
+    block both take the same full steps."""
+    for sc in (S.self_weight_column(4), S.block_compression()):
+        a = oracle.OracleScene.from_scene(sc)
+        b = oracle.OracleScene.from_scene(sc)
+        for st in sc.steps[:3]:
+            oa = a.solve_step(st.dof, st.value, st.gravity, tol=1e-12, globalise=False)
+            ob = b.solve_step(st.dof, st.value, st.gravity, tol=1e-12, globalise=True)
+            assert oa["converged"] and ob["converged"]
+            scale = np.abs(oa["du"]).max()
+            assert np.abs(oa["du"] - ob["du"]).max() <= 1e-9 * scale
