@@ -360,20 +360,29 @@ mpm_status mpm_set_particles(mpm_scene* s, const double* be, const double* pc, c
  * a host framework owns every device allocation, or a loop that forbids
  * allocation after start-up.
  *   r      device pointer, nnode*dim FP64 residual on the dense node grid
- *   rows   device pointer, nrow int32 node indices (the rows to include)
+ *   rows   device pointer, nrow int32 node indices (the rows to include);
+ *          each rows[k] must lie in [0, nnode): the call cannot check this
+ *          (it is not given nnode), and an index outside is an out-of-bounds
+ *          device read (undefined behaviour)
  *   fixed  device pointer, nnode*dim uint8 prescribed-DOF flags (1 = skip)
- *   out_norm  host pointer, receives sqrt(sum of r^2 over the free DOFs)
+ *   dim    values per node, 2 or 3 (a 2D u-p residual has 3: u_x, u_y, p)
+ *   out_norm  host pointer, receives sqrt(sum of r^2 over the free DOFs);
+ *          nrow = 0 gives 0
  *   stream cudaStream_t to run on (NULL = legacy default stream); the call
- *          synchronises this stream before returning.
+ *          synchronises this stream and copies the result to the host, so
+ *          it must not be called on a stream that is being captured into a
+ *          CUDA graph (that would invalidate the capture).
  * Its only scratch is a file-scope device array of 8192 FP64 partial sums
  * (64 KiB per GPU that loads the library, held until exit), so nrow is
  * limited to 8192*256 = 2,097,152 rows; larger nrow returns
  * MPM_ERR_INVALID_ARG.  No cudaMalloc, cudaFree or allocating library call is
  * made.  The first call on a device looks up that array's device address with
- * cudaGetSymbolAddress (once per device, with that device current): make that
- * first call before any stream capture.  Every call shares the array, so
- * calls that overlap on the GPU race; order them on one stream or with events.
- * Errors: MPM_ERR_INVALID_ARG, MPM_ERR_CUDA; message from
+ * cudaGetSymbolAddress (once per device, with that device current).  Every
+ * call shares the array, so calls that overlap on the GPU race; order them on
+ * one stream or with events.
+ * Errors: MPM_ERR_INVALID_ARG, MPM_ERR_CUDA (a launch or copy failed, or a
+ * CUDA error was already pending on this thread from earlier work: the call
+ * then reports and clears it without launching); message from
  * mpm_noalloc_last_error. */
 mpm_status mpm_residual_norm_noalloc(const double* r, const int* rows, int nrow,
                                      const unsigned char* fixed, int dim, double* out_norm,

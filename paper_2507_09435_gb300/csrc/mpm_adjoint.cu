@@ -182,33 +182,30 @@ __global__ void __launch_bounds__(ATPB) k_param_grad(DevParticles P, DevGrid G, 
   const MatC mc = mats[P.mat[p]];
   const double V0 = P.vol0[p], E = P.Ep[p], phi = P.phip[p], pcn = P.pc[p];
   const int o = P.orig[p];
-  // central differences of the stress in E and phi (the pressure part of the
-  // u-p stress does not depend on either)
-  auto contract = [&](double Ea, double pa, double& out) -> bool {
-    PState s2 = st;
-    if (constitutive<D>(mc, Ea, pa, pcn, V0, s2)) return false;
-    double v = 0.0;
-    for (int a = 0; a < D; ++a)
-      for (int c = 0; c < D; ++c) v += Lam[a][c] * s2.P[a][c];
-    out = v;
-    return true;
-  };
+  // dL/dtheta = -lambda^T dr/dtheta; per particle dr_i/dtheta = (dP/dtheta) grad w_ip
+  // with dP/dtheta = V0 (dtau/dtheta) dF^-T (the pressure part of the u-p
+  // stress depends on neither E nor phi), dtau/dtheta written out by
+  // param_dtau (no finite differences)
   bool ok = true;
-  if (gE) {
-    const double dE = 1e-6 * E;
-    double vp = 0, vm = 0;
-    ok = ok && contract(E + dE, phi, vp) && contract(E - dE, phi, vm);
-    gE[o] = -(vp - vm) / (2.0 * dE);
-  }
-  if (gPhi) {
-    double g = 0.0;
-    if (mc.model == MODEL_NH_DP) {
-      const double dp = 1e-6 * fmax(fabs(phi), 1.0);
-      double vp = 0, vm = 0;
-      ok = ok && contract(E, phi + dp, vp) && contract(E, phi - dp, vm);
-      g = -(vp - vm) / (2.0 * dp);
+  if (gE || gPhi) {
+    PState s2 = st;
+    double dtE[3][3], dtP[3][3];
+    ok = constitutive<D>(mc, E, phi, pcn, V0, s2) == 0 && param_dtau<D>(mc, E, phi, pcn, s2, dtE, dtP);
+    if (ok) {
+      double vE = 0.0, vP = 0.0;
+      for (int a = 0; a < D; ++a)
+        for (int c = 0; c < D; ++c) {
+          double pe = 0.0, pp = 0.0;
+          for (int k = 0; k < 3; ++k) {
+            pe += dtE[a][k] * s2.Fi[c][k];
+            pp += dtP[a][k] * s2.Fi[c][k];
+          }
+          vE += Lam[a][c] * V0 * pe;
+          vP += Lam[a][c] * V0 * pp;
+        }
+      if (gE) gE[o] = -vE;
+      if (gPhi) gPhi[o] = (mc.model == MODEL_NH_DP) ? -vP : 0.0;
     }
-    gPhi[o] = g;
   }
   if (gK && B > D && P.kdt) {
     // fl = kdt V^n det(dF) dF^-1 dF^-T grad p: linear in kdt, hence in k

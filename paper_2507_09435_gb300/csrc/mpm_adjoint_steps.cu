@@ -12,8 +12,10 @@
 // scaled residual, mu its adjoint) with respect to the position (through the
 // B-spline weights and gradients), b_e, p_c, F, E, phi, kdt and, for pass A,
 // an offset added to dF and to the particle increment (whose derivatives are
-// mapped to the nodes with grad w_ip and w_ip).  The derivatives are central
-// differences of the FP64 particle update (relative steps of 1e-6 to 1e-7).
+// mapped to the nodes with grad w_ip and w_ip).  The derivatives in E, phi
+// and kdt are written out (local_param_grad); those in the particle state
+// and in the dF / increment offsets are central differences of the FP64
+// particle update (relative steps of 1e-6 to 1e-7).
 #include "mpm_internal.h"
 
 namespace mpm {
@@ -36,23 +38,25 @@ struct LocalOut {
   double f;  // -mu . rhat_p
 };
 
-// One evaluation of the particle's commit map and residual contribution.
-template <int D, class T, int B>
-__device__ __noinline__ bool local_eval(const DevGrid& G, const MatC& mc, double V0, double m, const double grav[3],
-                           const double fe[3], const double* __restrict__ U, const T* __restrict__ mu, double psc,
-                           const double* sb, const LocalZ& z, LocalOut& out) {
-  Spline1 sp[3];
+// The particle's G2P at its local inputs: B-spline weights about the base
+// node, dF = 1 + dFx + sum_i U_i (x) grad w_ip, the particle increment
+// u_p = dux + sum_i w_ip U_i, and for u-p the pressure and its gradient;
+// b_e of the start of the step into st.  Returns false if the support
+// leaves the grid.
+template <int D, int B>
+__device__ bool local_g2p(const DevGrid& G, const double* __restrict__ U, double psc, const LocalZ& z,
+                          Spline1 sp[3], long long& nb, PState& st, double up[3], double& pp, double Gp[3]) {
   for (int a = 0; a < D; ++a) sp[a] = spline1((z.x[a] - G.o[a]) / G.h);
   if (D == 2) { sp[2].base = 0; sp[2].N[0] = 1.0; sp[2].dN[0] = 0.0; }
   for (int a = 0; a < D; ++a)
     if (sp[a].base < 0 || sp[a].base > G.n[a] - 2) return false;
-  const long long nb = sp[0].base + (long long)G.nx1 * (sp[1].base + (long long)G.ny1 * sp[2].base);
+  nb = sp[0].base + (long long)G.nx1 * (sp[1].base + (long long)G.ny1 * sp[2].base);
   const int KZ = (D == 3) ? 3 : 1;
-  PState st;
   for (int a = 0; a < 3; ++a)
     for (int c = 0; c < 3; ++c) st.F[a][c] = ((a == c) ? 1.0 : 0.0) + z.dFx[a][c];
-  double up[3] = {z.dux[0], z.dux[1], z.dux[2]};
-  double pp = 0.0, Gp[3] = {0, 0, 0};
+  for (int a = 0; a < 3; ++a) up[a] = z.dux[a];
+  pp = 0.0;
+  Gp[0] = Gp[1] = Gp[2] = 0.0;
   for (int kz = 0; kz < KZ; ++kz)
     for (int ky = 0; ky < 3; ++ky)
       for (int kx = 0; kx < 3; ++kx) {
@@ -81,6 +85,20 @@ __device__ __noinline__ bool local_eval(const DevGrid& G, const MatC& mc, double
   } else {
     st.bn[1][2] = st.bn[2][1] = st.bn[0][2] = st.bn[2][0] = 0.0;
   }
+  return true;
+}
+
+// One evaluation of the particle's commit map and residual contribution.
+template <int D, class T, int B>
+__device__ __noinline__ bool local_eval(const DevGrid& G, const MatC& mc, double V0, double m, const double grav[3],
+                           const double fe[3], const double* __restrict__ U, const T* __restrict__ mu, double psc,
+                           const double* sb, const LocalZ& z, LocalOut& out) {
+  Spline1 sp[3];
+  long long nb;
+  PState st;
+  double up[3], pp, Gp[3];
+  if (!local_g2p<D, B>(G, U, psc, z, sp, nb, st, up, pp, Gp)) return false;
+  const int KZ = (D == 3) ? 3 : 1;
   if (constitutive<D>(mc, z.E, z.phi, z.pc, V0, st)) return false;
   // sbar . Phi: x' = x + u_p, b_e', p_c', F' = dF F
   double h = 0.0;
@@ -139,6 +157,106 @@ __device__ __noinline__ bool local_eval(const DevGrid& G, const MatC& mc, double
         }
       }
   out.f = -s;
+  return true;
+}
+
+// Derivatives of q = sbar . Phi_p - mu . rhat_p with respect to E, phi and
+// kdt, written out (no differences): E and phi reach the commit map through
+// the returned principal log strains, b_e' = Q diag(exp(2 eps)) Q^T and
+// p_c' = p_c exp(-sum(eps^tr - eps) / (lambda - kappa)) (Cam-Clay), and the
+// residual through P = V0 tau dF^-T (param_dtau); kdt enters the u-p Darcy
+// term fl = kdt V det(dF) dF^-1 dF^-T grad p linearly.
+template <int D, class T, int B>
+__device__ __noinline__ bool local_param_grad(const DevGrid& G, const MatC& mc, double V0,
+                                              const double* __restrict__ U, const T* __restrict__ mu, double psc,
+                                              const double* sb, const LocalZ& z, double& qE, double& qP,
+                                              double& qK) {
+  Spline1 sp[3];
+  long long nb;
+  PState st;
+  double up[3], pp, Gp[3];
+  qE = qP = qK = 0.0;
+  if (!local_g2p<D, B>(G, U, psc, z, sp, nb, st, up, pp, Gp)) return false;
+  if (constitutive<D>(mc, z.E, z.phi, z.pc, V0, st)) return false;
+  double dtE[3][3], dtP[3][3], deps[3][2];
+  if (!param_dtau<D>(mc, z.E, z.phi, z.pc, st, dtE, dtP, deps)) return false;
+  // commit map
+  if (st.mode != 0) {
+    double dbE[3][3], dbP[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        double e = 0.0, f = 0.0;
+        for (int A = 0; A < 3; ++A) {
+          const double c = 2.0 * exp(2.0 * st.eps[A]) * st.Q[i][A] * st.Q[j][A];
+          e += c * deps[A][0];
+          f += c * deps[A][1];
+        }
+        dbE[i][j] = e;
+        dbP[i][j] = f;
+      }
+    const int ii[6] = {0, 1, 2, 0, 1, 0}, jj[6] = {0, 1, 2, 1, 2, 2};
+    const int nbe = (D == 2) ? 4 : 6;
+    for (int k = 0; k < nbe; ++k) {
+      qE += sb[3 + k] * dbE[ii[k]][jj[k]];
+      qP += sb[3 + k] * dbP[ii[k]][jj[k]];
+    }
+    if (mc.model == MODEL_NH_MCC) {
+      const double f = st.pc / mc.lmk;
+      qE += sb[9] * f * (deps[0][0] + deps[1][0] + deps[2][0]);
+      qP += sb[9] * f * (deps[0][1] + deps[1][1] + deps[2][1]);
+    }
+  }
+  if (!mu) return true;
+  // residual: d rhat_i = (V0 dtau dF^-T) grad w_ip on the momentum rows; the
+  // Darcy part of the mass-balance rows for kdt
+  double dPE[3][3], dPP[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) {
+      double e = 0.0, f = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        e += dtE[a][k] * st.Fi[c][k];
+        f += dtP[a][k] * st.Fi[c][k];
+      }
+      dPE[a][c] = V0 * e;
+      dPP[a][c] = V0 * f;
+    }
+  double Xt[3] = {0.0, 0.0, 0.0}, Vnew = 0.0;
+  if (B > D) {
+    Vnew = V0 * det3(z.F) * det3(st.F);
+    const double (&X)[3][3] = st.Fi;
+    double t[3];
+    for (int k = 0; k < 3; ++k) t[k] = X[0][k] * Gp[0] + X[1][k] * Gp[1] + X[2][k] * Gp[2];
+    for (int c = 0; c < 3; ++c) Xt[c] = X[c][0] * t[0] + X[c][1] * t[1] + X[c][2] * t[2];
+  }
+  const int KZ = (D == 3) ? 3 : 1;
+  double sE = 0.0, sP = 0.0, sK = 0.0;
+  for (int kz = 0; kz < KZ; ++kz)
+    for (int ky = 0; ky < 3; ++ky)
+      for (int kx = 0; kx < 3; ++kx) {
+        const long long node = nb + kx + (long long)G.nx1 * (ky + (long long)G.ny1 * kz);
+        double g[3];
+        g[0] = sp[0].dN[kx] * sp[1].N[ky] * sp[2].N[kz] * G.ih;
+        g[1] = sp[0].N[kx] * sp[1].dN[ky] * sp[2].N[kz] * G.ih;
+        g[2] = sp[0].N[kx] * sp[1].N[ky] * sp[2].dN[kz] * G.ih;
+        for (int a = 0; a < D; ++a) {
+          double re = 0.0, rp = 0.0;
+          for (int c = 0; c < D; ++c) {
+            re += dPE[a][c] * g[c];
+            rp += dPP[a][c] * g[c];
+          }
+          const double m = (double)mu[node * B + a];
+          sE += m * re;
+          sP += m * rp;
+        }
+        if (B > D) {
+          double qk = 0.0;
+          for (int c = 0; c < D; ++c) qk += Vnew * Xt[c] * g[c];
+          sK += (double)mu[node * B + D] * psc * qk;
+        }
+      }
+  qE -= sE;
+  qP -= sP;
+  qK -= sK;
   return true;
 }
 
@@ -294,26 +412,14 @@ __global__ void __launch_bounds__(VTPB) k_adj_state_vjp(DevParticles P, DevGrid 
     }
     so[dst] = d;
   }
-  if (gE && ok) {
-    const double e = 1e-6 * z0.E;
-    LocalZ zp = z0, zm = z0;
-    zp.E += e;
-    zm.E -= e;
-    gE[o] += (q(zp, ok) - q(zm, ok)) / (2.0 * e);
-  }
-  if (gPhi && ok && mc.model == MODEL_NH_DP) {
-    const double e = 1e-6 * fmax(fabs(z0.phi), 1.0);
-    LocalZ zp = z0, zm = z0;
-    zp.phi += e;
-    zm.phi -= e;
-    gPhi[o] += (q(zp, ok) - q(zm, ok)) / (2.0 * e);
-  }
-  if (gK && ok && B > D && z0.kdt > 0.0) {
-    const double e = 1e-6 * z0.kdt;
-    LocalZ zp = z0, zm = z0;
-    zp.kdt += e;
-    zm.kdt -= e;
-    atomicAdd(&gK[P.mat[p]], (q(zp, ok) - q(zm, ok)) / (2.0 * e) * mc.dkdt_dk);
+  if ((gE || gPhi || (gK && B > D && z0.kdt > 0.0)) && ok) {
+    double qE, qP, qK;
+    ok = local_param_grad<D, T, B>(G, mc, V0, U, mu, psc, sb, z0, qE, qP, qK);
+    if (ok) {
+      if (gE) gE[o] += qE;
+      if (gPhi && mc.model == MODEL_NH_DP) gPhi[o] += qP;
+      if (gK && B > D && z0.kdt > 0.0) atomicAdd(&gK[P.mat[p]], qK * mc.dkdt_dk);
+    }
   }
   if (!ok) atomicOr(err, ERRF_RETURN);
 }

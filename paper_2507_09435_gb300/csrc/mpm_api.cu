@@ -626,7 +626,8 @@ void assemble_impl(mpm_scene* s, bool with_mg = true) {
   cudaStream_t st = s->st;
   DevMatrix<T> K = matview<T>(s);
   // every block of every active row is stored by the assembly (no zero fill)
-  ck(launch_assemble<D, T, B>(s->P, s->G, s->d_cstart, s->d_node2row, (const T*)s->d_A, K, st), "assemble");
+  ck(launch_assemble<D, T, B>(s->P, s->G, s->d_cstart, s->d_node2row, (const T*)s->d_A, K, s->nrow, st),
+     "assemble");
   ck(launch_bc_matrix<D, T, B>(s->G, K, s->d_fixed, s->d_node2row, s->nrow, st), "bc matrix");
   ck(launch_block_jacobi<D, T, B>(s->G, K, s->nrow, s->d_err, st), "block jacobi");
   s->launches += 3;

@@ -197,6 +197,7 @@ __device__ __forceinline__ void eig_jacobi(const double b[3][3], double lam[3], 
 struct ReturnOut {
   double eps[3];
   double deps[3][3];   // d eps_A / d eps^tr_B
+  double x3;           // the converged plastic multiplier unknown (x[3])
   double pc;
   int mode;            // 0 elastic, 1 plastic, 2 DP apex
   bool ok;
@@ -355,6 +356,7 @@ __device__ inline void local_newton(double mu, double lam, double eta, double xi
       for (int j = 0; j < 3; ++j) rhs[i][j] = -Je[i][j];
   }
   if (!solve4<3>(J, rhs)) { o.ok = false; return; }
+  o.x3 = x[3];
 #pragma unroll
   for (int A = 0; A < 3; ++A) {
     o.eps[A] = x[A];
@@ -385,6 +387,7 @@ __device__ inline void dp_return(double mu, double lam, double eta, double xi, d
         if (fabs(de) <= 1e-16 * (1.0 + fabs(e))) break;
       }
       o.ok = it < 60;
+      o.x3 = 0.0;
 #pragma unroll
       for (int A = 0; A < 3; ++A) {
         o.eps[A] = e;
@@ -419,6 +422,7 @@ struct PState {
   // principal data of a plastic particle (for the tangent)
   double lam[3], Q[3][3], tp[3], D[3][3];
   double mu, lamL;
+  double eps[3], x3;   // converged principal log strains and multiplier unknown
 };
 
 // Constitutive update of one particle given dF, bn, material; fills
@@ -492,6 +496,9 @@ __device__ inline int constitutive(const MatC& mc, double E_p, double phi_p, dou
     }
     if (!ro.ok) return ERRF_RETURN;
     st.mode = ro.mode;
+    st.x3 = ro.x3;
+#pragma unroll
+    for (int A = 0; A < 3; ++A) st.eps[A] = ro.eps[A];
     if (mc.model == MODEL_NH_MCC) st.pc = ro.pc;
     double th = ro.eps[0] + ro.eps[1] + ro.eps[2];
     double Ex[3];
@@ -533,6 +540,129 @@ __device__ inline int constitutive(const MatC& mc, double E_p, double phi_p, dou
     for (int j = 0; j < 3; ++j)
       st.P[i][j] = V0 * (st.tau[i][0] * st.Fi[j][0] + st.tau[i][1] * st.Fi[j][1] + st.tau[i][2] * st.Fi[j][2]);
   return 0;
+}
+
+// Derivatives of the Kirchhoff stress of `constitutive` (same dF and
+// start-of-step state, already evaluated into st) with respect to the
+// particle's Young's modulus E and friction angle phi (degrees):
+//  * E enters only through mu = E m and lam = E l, so at fixed principal log
+//    strains tau is proportional to E: elastic d tau / dE = tau / E;
+//  * phi enters only through the Drucker-Prager constants eta(phi), xi(phi);
+//  * on a return the converged local unknowns x = (eps_1..3, x3) solve
+//    R(x; theta) = 0 (dp_eval / mcc_eval), hence dx/dtheta = -J^-1 dR/dtheta
+//    with J = dR/dx at the root, and d tau_A = sum_B C_AB d eps_B +
+//    (tau_A / E) dE with C_AB = d tau_A / d eps_B; the principal directions
+//    (those of the trial b) do not depend on E or phi;
+//  * the DP apex state tau = (xi c / eta) 1 depends on phi alone.
+// With t = tan phi and S = sqrt(9 + 12 t^2): d eta/dt = 27/S^3,
+// d xi/dt = -36 t/S^3, d(xi/eta)/dt = -1/t^2, dt/dphi = (1 + t^2) pi/180.
+// `deps` (may be null) receives the principal log-strain derivatives
+// d eps_A / dE and d eps_A / dphi (zero on the elastic branch, where eps is
+// the trial strain; at the apex, from mu (e^{2e} - 1) + 3 lam e = xi c / eta).
+// Returns false if the local system is singular.
+template <int DIM>
+__device__ inline bool param_dtau(const MatC& mc, double E_p, double phi_p, double pcn, const PState& st,
+                                  double dtE[3][3], double dtP[3][3], double (*deps)[2] = nullptr) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      dtE[i][j] = (st.mode == 0) ? st.tau[i][j] / E_p : 0.0;
+      dtP[i][j] = 0.0;
+    }
+  if (deps)
+#pragma unroll
+    for (int A = 0; A < 3; ++A) deps[A][0] = deps[A][1] = 0.0;
+  if (st.mode == 0) return true;
+  const double deg = 0.017453292519943295;
+  if (st.mode == 2) {
+    // apex (Drucker-Prager only, eta > 0)
+    const double t = tan(phi_p * deg);
+    const double d = -mc.coh / (t * t) * (1.0 + t * t) * deg;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dtP[i][i] = d;
+    if (deps) {
+      const double ex = exp(2.0 * st.eps[0]);
+      const double ge = 2.0 * st.mu * ex + 3.0 * st.lamL;
+      const double pa = st.tp[0];
+#pragma unroll
+      for (int A = 0; A < 3; ++A) {
+        deps[A][0] = -(pa / E_p) / ge;
+        deps[A][1] = d / ge;
+      }
+    }
+    return true;
+  }
+  const double mu = st.mu, lam = st.lamL;
+  const double etr[3] = {0.5 * log(st.lam[0]), 0.5 * log(st.lam[1]), 0.5 * log(st.lam[2])};
+  const double x[4] = {st.eps[0], st.eps[1], st.eps[2], st.x3};
+  double R[4], J[4][4], b[4][2];
+  const double p = (st.tp[0] + st.tp[1] + st.tp[2]) * (1.0 / 3.0);
+  if (mc.model == MODEL_NH_DP) {
+    double eta, xi, etab, xb;
+    dp_consts(phi_p, eta, xi);
+    dp_consts(mc.psi, etab, xb);
+    dp_eval(mu, lam, eta, xi, etab, mc.coh, etr, x, R, J);
+    const double t = tan(phi_p * deg);
+    const double S = sqrt(9.0 + 12.0 * t * t), iS3 = 1.0 / (S * S * S);
+    const double dt = (1.0 + t * t) * deg;
+    const double deta = 27.0 * iS3 * dt, dxi = -36.0 * t * iS3 * dt;
+#pragma unroll
+    for (int A = 0; A < 3; ++A) { b[A][0] = 0.0; b[A][1] = 0.0; }
+    b[3][0] = -(xi * mc.coh) / (E_p * mu);
+    b[3][1] = -(deta * p - dxi * mc.coh) / mu;
+  } else {
+    double Je[4][3], pc;
+    mcc_eval(mu, lam, mc.M, mc.lmk, pcn, etr, x, R, J, Je, pc);
+    const double iM2 = 1.0 / (mc.M * mc.M), isc = 1.0 / fabs(pcn);
+    double q2 = 0.0;
+#pragma unroll
+    for (int A = 0; A < 3; ++A) q2 += 1.5 * (st.tp[A] - p) * (st.tp[A] - p);
+#pragma unroll
+    for (int A = 0; A < 3; ++A) {
+      // m_A + pc/3 = 3 s_A / M^2 + 2p/3 is proportional to E
+      const double mA = 3.0 * (st.tp[A] - p) * iM2 + 2.0 * p * (1.0 / 3.0);
+      b[A][0] = -x[3] * isc * mA / E_p;
+      b[A][1] = 0.0;
+    }
+    b[3][0] = -(2.0 * q2 * iM2 + 2.0 * p * p - p * pc) * isc * isc / E_p;
+    b[3][1] = 0.0;
+  }
+  if (!solve4<2>(J, b)) return false;
+  if (deps)
+#pragma unroll
+    for (int A = 0; A < 3; ++A) {
+      deps[A][0] = b[A][0];
+      deps[A][1] = b[A][1];
+    }
+  double dA[3][2];
+#pragma unroll
+  for (int A = 0; A < 3; ++A) {
+    double sE = st.tp[A] / E_p, sP = 0.0;
+#pragma unroll
+    for (int B = 0; B < 3; ++B) {
+      const double C = ((A == B) ? 2.0 * mu * exp(2.0 * x[A]) : 0.0) + lam;
+      sE += C * b[B][0];
+      sP += C * b[B][1];
+    }
+    dA[A][0] = sE;
+    dA[A][1] = sP;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double e = 0.0, f = 0.0;
+#pragma unroll
+      for (int A = 0; A < 3; ++A) {
+        const double qq = st.Q[i][A] * st.Q[j][A];
+        e += dA[A][0] * qq;
+        f += dA[A][1] * qq;
+      }
+      dtE[i][j] = e;
+      dtP[i][j] = f;
+    }
+  return true;
 }
 
 // Consistent tangent A[a][c][b][e] = dP_ac / d dF_be for a,c,b,e < DIM,

@@ -220,7 +220,11 @@ cudaError_t launch_stress_out(const DevParticles& P, const DevGrid& G, const Mat
 
 template <int D, class T, int B = D>
 cudaError_t launch_assemble(const DevParticles& P, const DevGrid& G, const int* cstart, const int* node2row,
-                            const T* A, DevMatrix<T> K, cudaStream_t st);
+                            const T* A, DevMatrix<T> K, int nrow_host, cudaStream_t st);
+// 3D single-phase rows, one warp per row (mpm_assemble3d.cu)
+template <class T>
+cudaError_t launch_assemble_rows3(const DevParticles& P, const DevGrid& G, const int* cstart, const T* A,
+                                  DevMatrix<T> K, int nrow_host, cudaStream_t st);
 template <int D, class T, int B = D>
 cudaError_t launch_bc_matrix(const DevGrid& G, DevMatrix<T> K, const uint8_t* fixed, const int* node2row,
                              int nrow_host, cudaStream_t st);

@@ -466,8 +466,6 @@ template <int D, class T, int B>
 struct AsmCfg;
 template <> struct AsmCfg<2, float, 2>  { static constexpr int TX = 16, TY = 8, TZ = 1, CHP = 64; };
 template <> struct AsmCfg<2, double, 2> { static constexpr int TX = 8,  TY = 8, TZ = 1, CHP = 64; };
-template <> struct AsmCfg<3, float, 3>  { static constexpr int TX = 4,  TY = 2, TZ = 2, CHP = 32; };
-template <> struct AsmCfg<3, double, 3> { static constexpr int TX = 2,  TY = 2, TZ = 2, CHP = 16; };
 template <> struct AsmCfg<2, float, 3>  { static constexpr int TX = 8,  TY = 8, TZ = 1, CHP = 64; };
 template <> struct AsmCfg<2, double, 3> { static constexpr int TX = 8,  TY = 4, TZ = 1, CHP = 32; };
 constexpr int ASM_TPB = 256;
@@ -513,7 +511,7 @@ __global__ void __launch_bounds__(ASM_TPB) k_assemble(DevParticles P, DevGrid G,
   using L = AsmSmem<D, T, B>;
   constexpr int TX = L::TX, TY = L::TY, TZ = L::TZ, CHP = L::CHP, NN = L::NN, S = L::S;
   constexpr int D2 = L::D2, D4 = L::D4, NT = L::NT, AST = L::AST, NPHI = L::NPHI;
-  static_assert(D == 2 || B == D, "3D assembly is written for the single-phase blocks");
+  static_assert(D == 2, "3D rows are assembled by k_assemble_rows3");
   extern __shared__ __align__(16) unsigned char smem[];
   T* acc = reinterpret_cast<T*>(smem + L::acc);    // [NT][S][D2]
   T* sA = reinterpret_cast<T*>(smem + L::sA);      // [CHP][AST]
@@ -617,94 +615,43 @@ __global__ void __launch_bounds__(ASM_TPB) k_assemble(DevParticles P, DevGrid G,
           const int ky = iy - cy, kz = (D == 3) ? iz - cz : 0;
           const int il = kx + 3 * ky + 9 * kz;   // i among the cell's nodes
           T* arow = acc + (size_t)l_i * S * D2;
-          if constexpr (D == 3) {
-            // lane j = node of the cell.  Particles go in batches of UB:
-            // lanes 0..26 first form U = g_i . A of every particle of the
-            // batch (independent products), then each lane contracts them
-            // with its own g_j.
-            const int j = lane;
-            const int ua = lane / 9, ub = (lane / 3) % 3, ue = lane % 3;
-            T k9[9];
+          // lane = j + 9 * sub: node j of the cell, particles sub, sub+3, ...
+          const int j = lane % 9, sub = lane / 9;
+          T kb[D2];
 #pragma unroll
-            for (int e = 0; e < 9; ++e) k9[e] = (T)0;
-            T* su = sU + warp * (ASM_UB * 28);
-            for (int qb0 = qa; qb0 < qb; qb0 += ASM_UB) {
-              const int nb = min(ASM_UB, qb - qb0);
-              if (lane < 27) {
+          for (int e = 0; e < D2; ++e) kb[e] = (T)0;
+          if (lane < 27) {
+            for (int q = qa + sub; q < qb; q += 3) {
+              T gi[4], gj[4], aq[AST];
+              lds4(sG + (q * NN + il) * 4, gi);
+              lds4(sG + (q * NN + j) * 4, gj);
 #pragma unroll
-                for (int k = 0; k < ASM_UB; ++k) {
-                  if (k < nb) {
-                    const int q = qb0 + k;
-                    T gi[4];
-                    lds4(sG + (q * NN + il) * 4, gi);
-                    const T* aq = sA + q * AST + ua * 27 + ub * 3 + ue;
-                    su[k * 28 + lane] = gi[0] * aq[0] + gi[1] * aq[9] + gi[2] * aq[18];
-                  }
+              for (int v = 0; v < AST / 4; ++v) lds4(sA + q * AST + 4 * v, aq + 4 * v);
+#pragma unroll
+              for (int a = 0; a < B; ++a)
+#pragma unroll
+                for (int b = 0; b < B; ++b) {
+                  T s = (T)0;
+#pragma unroll
+                  for (int c = 0; c < NPHI; ++c)
+#pragma unroll
+                    for (int e = 0; e < NPHI; ++e) s += gi[c] * aq[((a * NPHI + c) * B + b) * NPHI + e] * gj[e];
+                  kb[a * B + b] += s;
                 }
-              }
-              __syncwarp();
-              if (j < 27) {
-#pragma unroll
-                for (int k = 0; k < ASM_UB; ++k) {
-                  if (k < nb) {
-                    T gj[4];
-                    lds4(sG + ((qb0 + k) * NN + j) * 4, gj);
-                    T u[28];
-#pragma unroll
-                    for (int v = 0; v < 7; ++v) lds4(su + k * 28 + 4 * v, u + 4 * v);
-#pragma unroll
-                    for (int ab = 0; ab < 9; ++ab)
-                      k9[ab] += u[ab * 3 + 0] * gj[0] + u[ab * 3 + 1] * gj[1] + u[ab * 3 + 2] * gj[2];
-                  }
-                }
-              }
-              __syncwarp();
             }
-            if (j < 27) {
-              const int jx = j % 3, jy = (j / 3) % 3, jz = j / 9;
-              T* blk = arow + slot_of<3>(jx - kx, jy - ky, jz - kz) * D2;
+          }
 #pragma unroll
-              for (int ab = 0; ab < 9; ++ab) atomicAdd(blk + ab, k9[ab]);
-            }
-          } else {
-            // lane = j + 9 * sub: node j of the cell, particles sub, sub+3, ...
-            const int j = lane % 9, sub = lane / 9;
-            T kb[D2];
+          for (int e = 0; e < D2; ++e) {
+            // lanes j, j + 9, j + 18 hold the three particle subsets of node j
+            const T v9 = __shfl_sync(0xffffffffu, kb[e], (lane + 9) & 31);
+            const T v18 = __shfl_sync(0xffffffffu, kb[e], (lane + 18) & 31);
+            kb[e] += v9 + v18;
+          }
+          if (lane < 9) {
+            const int jx = j % 3, jy = j / 3;
+            T* blk = arow + slot_of<2>(jx - kx, jy - ky, 0) * D2;
 #pragma unroll
-            for (int e = 0; e < D2; ++e) kb[e] = (T)0;
-            if (lane < 27) {
-              for (int q = qa + sub; q < qb; q += 3) {
-                T gi[4], gj[4], aq[AST];
-                lds4(sG + (q * NN + il) * 4, gi);
-                lds4(sG + (q * NN + j) * 4, gj);
-#pragma unroll
-                for (int v = 0; v < AST / 4; ++v) lds4(sA + q * AST + 4 * v, aq + 4 * v);
-#pragma unroll
-                for (int a = 0; a < B; ++a)
-#pragma unroll
-                  for (int b = 0; b < B; ++b) {
-                    T s = (T)0;
-#pragma unroll
-                    for (int c = 0; c < NPHI; ++c)
-#pragma unroll
-                      for (int e = 0; e < NPHI; ++e) s += gi[c] * aq[((a * NPHI + c) * B + b) * NPHI + e] * gj[e];
-                    kb[a * B + b] += s;
-                  }
-              }
-            }
-#pragma unroll
-            for (int e = 0; e < D2; ++e) {
-              // lanes j, j + 9, j + 18 hold the three particle subsets of node j
-              const T v9 = __shfl_sync(0xffffffffu, kb[e], (lane + 9) & 31);
-              const T v18 = __shfl_sync(0xffffffffu, kb[e], (lane + 18) & 31);
-              kb[e] += v9 + v18;
-            }
-            if (lane < 9) {
-              const int jx = j % 3, jy = j / 3;
-              T* blk = arow + slot_of<2>(jx - kx, jy - ky, 0) * D2;
-#pragma unroll
-              for (int e = 0; e < D2; ++e) atomicAdd(blk + e, kb[e]);
-            }
+            for (int e = 0; e < D2; ++e) atomicAdd(blk + e, kb[e]);
           }
         }
       }
@@ -721,7 +668,11 @@ __global__ void __launch_bounds__(ASM_TPB) k_assemble(DevParticles P, DevGrid G,
 
 template <int D, class T, int B>
 cudaError_t launch_assemble(const DevParticles& P, const DevGrid& G, const int* cstart, const int* node2row,
-                            const T* A, DevMatrix<T> K, cudaStream_t st) {
+                            const T* A, DevMatrix<T> K, int nrow_host, cudaStream_t st) {
+  if constexpr (D == 3) {
+    static_assert(B == 3, "3D assembly is written for the single-phase blocks");
+    return launch_assemble_rows3<T>(P, G, cstart, A, K, nrow_host, st);
+  } else {
   using L = AsmSmem<D, T, B>;
   if (P.np == 0) return cudaSuccess;
   static_assert(L::bytes <= 227 * 1024, "assembly tile exceeds shared memory");
@@ -734,6 +685,7 @@ cudaError_t launch_assemble(const DevParticles& P, const DevGrid& G, const int* 
   if (nt > 0x7fffffffLL) return cudaErrorInvalidValue;
   k_assemble<D, T, B><<<(unsigned)nt, ASM_TPB, L::bytes, st>>>(P, G, cstart, node2row, A, K, ntx, nty);
   return cudaGetLastError();
+  }
 }
 
 // Prescribed DOFs: their rows and columns become the identity.
@@ -966,7 +918,7 @@ MPM_INST_DT(3, double)
 
 #define MPM_INST_DTB(D, T, B)                                                                           \
   template cudaError_t launch_assemble<D, T, B>(const DevParticles&, const DevGrid&, const int*, const int*, \
-                                                const T*, DevMatrix<T>, cudaStream_t);                   \
+                                                const T*, DevMatrix<T>, int, cudaStream_t);              \
   template cudaError_t launch_bc_matrix<D, T, B>(const DevGrid&, DevMatrix<T>, const uint8_t*, const int*, \
                                                  int, cudaStream_t);                                     \
   template cudaError_t launch_block_jacobi<D, T, B>(const DevGrid&, DevMatrix<T>, int, int*, cudaStream_t);

@@ -118,7 +118,7 @@ extern "C" mpm_status mpm_residual_norm_noalloc(const double* r, const int* rows
     return MPM_ERR_INVALID_ARG;
   }
   if (!out_norm || (dim != 2 && dim != 3) || nrow < 0 || (nrow > 0 && (!r || !rows || !fixed))) {
-    g_noalloc_err = "invalid argument (need device r, rows, fixed, a host out_norm, dim 2 or 3)";
+    g_noalloc_err = "invalid argument (need device r, rows, fixed, a host out_norm, 2 or 3 values per node)";
     return MPM_ERR_INVALID_ARG;
   }
   mpm_status st;
@@ -126,15 +126,32 @@ extern "C" mpm_status mpm_residual_norm_noalloc(const double* r, const int* rows
   if (!scratch) return st;
   cudaStream_t s = (cudaStream_t)stream;
   const int nblk = (nrow + NOALLOC_TPB - 1) / NOALLOC_TPB;
-  if (nblk > 0) k_norm_partials<<<nblk, NOALLOC_TPB, 0, s>>>(r, rows, nrow, fixed, dim, scratch);
-  k_norm_total<<<1, NOALLOC_TPB, 0, s>>>(scratch, nblk);
+  // An error left pending by earlier, unrelated work on this thread is
+  // reported (and cleared) here, named as such, before anything is launched.
   cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    g_noalloc_err = std::string("CUDA error pending from earlier work on this thread: ") + cudaGetErrorString(e);
+    return MPM_ERR_CUDA;
+  }
+  if (nblk > 0) {
+    k_norm_partials<<<nblk, NOALLOC_TPB, 0, s>>>(r, rows, nrow, fixed, dim, scratch);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      g_noalloc_err = std::string("launch of k_norm_partials failed: ") + cudaGetErrorString(e);
+      return MPM_ERR_CUDA;
+    }
+  }
+  k_norm_total<<<1, NOALLOC_TPB, 0, s>>>(scratch, nblk);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    g_noalloc_err = std::string("launch of k_norm_total failed: ") + cudaGetErrorString(e);
+    return MPM_ERR_CUDA;
+  }
   double total = 0.0;
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&total, scratch + NOALLOC_MAX_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, s);
+  e = cudaMemcpyAsync(&total, scratch + NOALLOC_MAX_BLOCKS, sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
-    g_noalloc_err = std::string("CUDA error: ") + cudaGetErrorString(e);
+    g_noalloc_err = std::string("CUDA error reading the norm back: ") + cudaGetErrorString(e);
     return MPM_ERR_CUDA;
   }
   *out_norm = sqrt(total);

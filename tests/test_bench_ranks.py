@@ -81,4 +81,4 @@ def test_reference_arm_prints_one_line_on_rank_zero_only():
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["cpu_baseline"]["cores"] == 1 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["cpu_baseline"]["value"] == line["value"] == line["e2e"]["value"]
-    assert line["config"]["workload"] == "footing_256x128_dp"
+    assert line["config"]["workload"] == "mcc3d_2M"
