@@ -85,7 +85,7 @@ def parse():
                     help="the last N timed load steps are solved again by the plain FP64 GPU path from the "
                          "same committed state (0: none)")
     ap.add_argument("--no-footing", action="store_true", help="skip the 2D footing line beside the main one")
-    ap.add_argument("--serving", type=int, default=32,
+    ap.add_argument("--serving", type=int, default=512,
                     help="requests of the serving stream measured beside the main line (0: none); "
                          "--workload serving runs the 512-request stream alone")
     ap.add_argument("--slots", type=int, default=4, help="serving worker slots")
@@ -103,6 +103,17 @@ def parse():
         args.precond = "mg" if args.workload == "footing" and args.krylov == "bicgstab" else "auto"
     return args
 
+
+# FP64 operations of one residual + tangent pass (k_particles, mode 1) per
+# particle, from ncu's executed-instruction counters (2 per DFMA, 1 per DADD /
+# DMUL) on the workload named beside each (profiles/k_particles_*.md); the
+# count depends on the fraction of particles on a return-map branch
+FP64_FLOP_PER_PARTICLE = {
+    # profiles/k_particles_column3d_393k_mixed.md: 891 M per launch on the
+    # 393k column's first load step (nearly all particles elastic); plastic
+    # returns add operations, so later ramp steps are undercounted
+    "column3d": 2266, "column3d_stated": 2266,
+}
 
 # ncu-measured DRAM traffic of one Krylov iteration per workload /
 # precision / preconditioner (bytes; the profile that gives each is named
@@ -127,10 +138,14 @@ def workload_scene(name="footing"):
     from paper_2507_09435_gb300 import scenes
     if name == "footing":
         return scenes.footing(nx=256, ny=128, h=0.1, ppc=2, nsteps=50)
+    # the quasi-static Cam-Clay column has no equilibrium past about 0.85 g
+    # (2M particles) or 0.7 g (393k): a collapse mechanism forms and Newton
+    # stalls; the timed ramp stops short of it (0 -> 0.75 g and 0 -> 0.6 g
+    # over 20 load steps)
     if name == "column3d":
-        return scenes.column_collapse_3d(col=(72, 72, 48))
+        return scenes.column_collapse_3d(col=(72, 72, 48), g=0.75 * 9.81)
     if name == "column3d_stated":
-        return scenes.column_collapse_3d(col=(32, 32, 48))
+        return scenes.column_collapse_3d(col=(32, 32, 48), g=0.6 * 9.81)
     if name == "serving":
         d = next(d for d in scenes.serving_draws(512) if d["kind"] == "dp_footing")
         return scenes.serving_scene(d)[0]
@@ -148,8 +163,9 @@ def config(args, sc):
         extra = {"ppc": 8, "column_cells": cells,
                  "model": "neo-hookean + modified cam-clay (M 1.2, lambda 0.1, kappa 0.02, "
                           "pc0 lognormal sigma 0.1 about -100 kPa)",
-                 "step": "one load step of a 20-step gravity ramp 0 -> g (timed steps 0..K-1 of the ramp "
-                         "on a fresh scene after W warm-up steps on another)"}
+                 "step": "one load step of a 20-step gravity ramp 0 -> %.2f g (the column collapses past "
+                         "about %.2f g; timed steps 0..K-1 of the ramp on a fresh scene after W warm-up steps "
+                         "on another)" % ((0.75, 0.85) if args.workload == "column3d" else (0.6, 0.7))}
     return {"workload": WORKLOADS[args.workload], "grid": [int(v) for v in sc.n[:sc.dim]], "h": sc.h,
             "particles": sc.np, **extra, "precision": args.precision, "krylov": args.krylov,
             "precond": args.precond,
@@ -372,7 +388,8 @@ def serving_measure(nreq, slots, precision, seed=2507_09435 + 4, precond="auto",
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "mean": float(lat.mean())},
         "service_ms": {"p50": float(np.percentile(svt, 50)), "p99": float(np.percentile(svt, 99))},
-        "latency_p50_ms_by_kind": {k: float(np.percentile(v, 50)) for k, v in kinds.items()},
+        "latency_ms_by_kind": {k: {"n": len(v), "p50": float(np.percentile(v, 50)),
+                                   "p99": float(np.percentile(v, 99))} for k, v in kinds.items()},
         "failures_by_kind": fails,
         "throughput_requests_per_s": len(ok) / wall, "newton_iters_per_s": newton / wall,
         "wall_s": wall, "max_arrival_lag_s": late,
@@ -386,11 +403,12 @@ def serving_measure(nreq, slots, precision, seed=2507_09435 + 4, precond="auto",
 
 def run_slope_adjoint_line(args):
     """Inverse-analysis workload: the random-field Drucker-Prager slope
-    (192x96 cells, ~71k particles, per-particle E and phi fields), the first 6
-    of its 20 gravity-ramp steps forward, then the adjoint through them for a
-    surface-displacement misfit; the gradient's directional derivative along a
-    random field perturbation is checked against central differences of two
-    more forward runs."""
+    (192x96 cells, ~71k particles, per-particle E and phi fields), all 20
+    gravity-ramp steps forward, then the adjoint through them for a
+    surface-displacement misfit.  The gradient's directional derivative along
+    a random E perturbation is checked against central differences
+    (eps = 1e-6) of two FP64 forward runs, for the timed gradient (the
+    configured precision) and for an FP64 adjoint."""
     import torch
     from paper_2507_09435_gb300 import mpm, scenes as S
     from paper_2507_09435_gb300.autograd import ImplicitSteps
@@ -399,13 +417,17 @@ def run_slope_adjoint_line(args):
         return 0
     prec = mpm.MPM_MIXED if args.precision == "mixed" else mpm.MPM_FP64
     sc = S.slope()
-    steps = sc.steps[:6]      # the first 6 of 20 ramp steps (see the slope's reading)
+    steps = sc.steps
     surf = sc.x[:, 1] > sc.x[:, 1].max() - 0.5 * sc.h
     obs = S.slope(seed=2507_09435 + 6)       # "observed" run: a second seeded field
-    kw = dict(precision=prec, newton_tol=1e-8, newton_maxit=32)
+    # multigrid V-cycle preconditioning (forward and the transposed adjoint
+    # solves): block-Jacobi BiCGStab breaks down on J^T late in the ramp
+    kw = dict(precision=prec, newton_tol=1e-8, newton_maxit=32, precond=mpm.MPM_PC_MG)
+    kw64 = dict(precision=mpm.MPM_FP64, newton_tol=1e-11, newton_maxit=32, forcing=mpm.MPM_FORCING_FIXED,
+                krylov_rtol=1e-13, precond=mpm.MPM_PC_MG)
 
-    def forward(E, P, record=None):
-        gs = mpm.GpuScene(sc, **kw)
+    def forward(E, P, k=kw):
+        gs = mpm.GpuScene(sc, **k)
         gs.set_params(E_p=E, phi_p=P)
         newton = 0
         for st in steps:
@@ -415,42 +437,53 @@ def run_slope_adjoint_line(args):
         return x, newton
 
     x_obs, _ = forward(obs.E_p, obs.phi_p)
+
+    def gradient(k):
+        gs = mpm.GpuScene(sc, **k)
+        E = torch.tensor(sc.E_p, requires_grad=True)
+        P = torch.tensor(sc.phi_p, requires_grad=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xN = ImplicitSteps.apply(gs, steps, E, P)
+        t1 = time.perf_counter()
+        d = (xN - torch.from_numpy(x_obs))[torch.from_numpy(surf)]
+        loss = 0.5 * (d * d).sum()
+        loss.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        gs.close()
+        return E.grad.numpy(), P.grad.numpy(), t0, t1, t2
+
+    gradient(kw)   # warm-up (buffers, graphs)
     clk = ClockSampler(0)
-    gs = mpm.GpuScene(sc, **kw)
-    E = torch.tensor(sc.E_p, requires_grad=True)
-    P = torch.tensor(sc.phi_p, requires_grad=True)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    xN = ImplicitSteps.apply(gs, steps, E, P)
-    t1 = time.perf_counter()
-    d = (xN - torch.from_numpy(x_obs))[torch.from_numpy(surf)]
-    loss = 0.5 * (d * d).sum()
-    loss.backward()
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
-    gs.close()
+    gE, gP, t0, t1, t2 = gradient(kw)
     clocks = clk.stop()
+    gE64, _, _, _, _ = gradient(kw64)
     rng = np.random.default_rng(11)
     vE = 0.1 * sc.E_p * rng.standard_normal(sc.np)
-    eps = 1e-4
+    eps = 1e-6
 
     def L(Ev):
-        x, _ = forward(Ev, sc.phi_p)
+        x, _ = forward(Ev, sc.phi_p, kw64)
         dd = (x - x_obs)[surf]
         return 0.5 * float((dd * dd).sum())
 
     fd = (L(sc.E_p + eps * vE) - L(sc.E_p - eps * vE)) / (2 * eps)
-    ad = float(np.dot(E.grad.numpy(), vE))
+    ad = float(np.dot(gE, vE))
+    ad64 = float(np.dot(gE64, vE))
     _, newton = forward(sc.E_p, sc.phi_p)
-    line = {"metric": "adjoint gradient evaluations/s (6-step slope, forward + reverse chain)",
-            "value": 1.0 / (t2 - t0), "unit": "gradients/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+    line = {"metric": "adjoint gradient evaluations/s (20-step slope, forward + reverse chain)",
+            "value": 1.0 / (t2 - t0), "unit": "gradients/s", "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": 1e3 * (t2 - t0), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64+f32" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": {"workload": "slope_192x96_dp_random_fields", "particles": sc.np, "load_steps": len(steps),
                        "loss": "0.5 |x_N - x_obs|^2 over the surface particles (x_obs: second seeded field)"},
             "adjoint": {"forward_s": t1 - t0, "backward_s": t2 - t1, "forward_newton_iters": newton,
-                        "directional_derivative": ad, "central_difference": fd,
-                        "relative_difference": abs(ad - fd) / max(abs(fd), 1e-300), "fd_eps": eps},
+                        "directional_derivative": ad, "directional_derivative_fp64_adjoint": ad64,
+                        "central_difference_fp64": fd, "fd_eps": eps,
+                        "relative_difference": abs(ad - fd) / max(abs(fd), 1e-300),
+                        "relative_difference_fp64_adjoint": abs(ad64 - fd) / max(abs(fd), 1e-300),
+                        "gradient_phi_norm": float(np.linalg.norm(gP))},
             "clocks": clocks, "cpu_baseline": None, "e2e": None, "roofline": None, "gpu_launches": None}
     print(json.dumps(line), flush=True)
     return 0
@@ -615,6 +648,10 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
+    # measured arithmetic peaks of this device (FP64 and FP32 FMA chains)
+    fma64 = mpm.mpm_fma_peak(mpm.MPM_FP64)
+    fma32 = mpm.mpm_fma_peak(mpm.MPM_MIXED)
+
     # warm-up: the first W steps of the schedule on a scene of their own, so
     # that the timed run solves the schedule from its first load step
     gw = new_scene()
@@ -698,6 +735,33 @@ def main():
                      if sc.dim == 2 else "3D matrix exceeds L2 (129 MB): HBM-bound")}
     gs.close()
 
+    # ---- ALU-bound kernels against the measured FMA peaks --------------------
+    # assembly (FP32 in mixed mode): per particle 27 rows x (81 + 27 x 27)
+    # multiply-adds in 3D (U = G_i A, then U G_j), 81 node pairs x 16 in 2D;
+    # the residual pass: the FP64 operation count per particle of the profile
+    n_asm = newton   # one assembly per Newton iteration
+    fma_asm = (27 * (81 + 27 * 27)) if sc.dim == 3 else 81 * 16
+    t_asm_s = phase[2] * 1e-3
+    asm_tf = 2.0 * fma_asm * sc.np * n_asm / max(t_asm_s, 1e-12) / 1e12
+    alu = {"fp64_tflops": fma64, "fp32_tflops": fma32,
+           "how": "mpm_fma_peak: 8 independent FMA chains per thread, 8 blocks of 256 per SM, CUDA events",
+           "assembly": {"kernel": "k_assemble_rows3" if sc.dim == 3 else "k_assemble", "bound": "alu",
+                        "achieved_tflops": asm_tf,
+                        "peak_tflops": fma32 if args.precision == "mixed" else fma64,
+                        "frac": asm_tf / (fma32 if args.precision == "mixed" else fma64),
+                        "flop_per_particle": 2 * fma_asm,
+                        "note": "assembly phase time (assembly + identity rows + block inverses) per Newton "
+                                "iteration"}}
+    fpp = FP64_FLOP_PER_PARTICLE.get(args.workload)
+    if fpp:
+        # residual passes: one per Newton iteration plus the first of each step
+        t_res_s = phase[1] * 1e-3
+        res_tf = fpp * sc.np * (newton + args.steps) / max(t_res_s, 1e-12) / 1e12
+        alu["residual"] = {"kernel": "k_particles (G2P, constitutive update, P2G, tangent; FP64)",
+                           "bound": "alu", "achieved_tflops": res_tf, "peak_tflops": fma64,
+                           "frac": res_tf / fma64, "flop_per_particle": fpp,
+                           "note": "FP64 operations per particle from the committed ncu profile"}
+
     # ---- the plain FP64 GPU path on the last timed steps ---------------------
     fp64 = None
     if n64 and snap is not None:
@@ -764,7 +828,8 @@ def main():
                 "rel_residual_max": max(r["rel"] for r in recs),
                 "phase_ms_per_step": {"setup": phase[0] / args.steps, "residual": phase[1] / args.steps,
                                       "assembly": phase[2] / args.steps, "krylov": phase[3] / args.steps},
-                "gpu_launches": int(launches), "roofline": roof, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "roofline": roof, "alu_roofline": alu, "fp64": fp64,
+                "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks, "footing": footing, "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -340,6 +340,14 @@ mpm_status mpm_kernel_launches(const mpm_scene* s, long long* out);
  * (Sec. 2.2) takes full steps; these safeguards are this library's. */
 mpm_status mpm_get_newton_counters(const mpm_scene* s, long long* limited, long long* halvings);
 
+/* Measured arithmetic peak of the current device (a measurement helper; the
+ * paper has no counterpart): fused multiply-add throughput in TFLOP/s (2
+ * flops per FMA) of a kernel of independent FMA chains timed with CUDA
+ * events, FP64 (precision MPM_FP64) or FP32 (MPM_MIXED).  The FP64 residual
+ * pass and the FP32 assembly are reported against it.  Synchronises the
+ * device; allocates 8 bytes.  Errors: MPM_ERR_INVALID_ARG, MPM_ERR_CUDA. */
+mpm_status mpm_fma_peak(int precision, double* tflops);
+
 /* Time the Jacobian-vector product kernel of the staged step's assembled
  * Jacobian: `reps` launches on the scene's stream between CUDA events.
  * ms_per_launch: average duration; bytes_per_launch: algorithmic bytes of

@@ -44,7 +44,7 @@ import scipy.sparse.linalg as spla
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "_build", "liboracle.so")
-ACTIVE_REL = 1e-12
+ACTIVE_REL = 1e-4
 
 _D = ctypes.POINTER(ctypes.c_double)
 _I = ctypes.POINTER(ctypes.c_int)
@@ -292,8 +292,9 @@ class OracleScene:
         return w
 
     # ---- Newton (paper Sec. 2.2) ------------------------------------------
-    def solve_step(self, dof, value, gravity, tol=1e-12, maxit=25, commit=True):
-        """One load step.  Returns dict(du, hist, iters, converged, r0)."""
+    def solve_step(self, dof, value, gravity, tol=1e-12, maxit=25, commit=True, globalise=True):
+        """One load step.  Returns dict(du, hist, iters, converged, r0).
+        ``globalise=False`` takes the paper's plain full Newton steps."""
         self.gravity = _f64(gravity).copy()
         N = self.ndof
         wn = self.norm_weights()
@@ -317,7 +318,11 @@ class OracleScene:
         while not conv and it < maxit:
             J = self.jacobian(du)[fidx][:, fidx].tocsc()
             delta = spla.spsolve(J, -r[fidx])
-            du, r, M = self._globalised_update(du, fidx, delta, disp, rk, r0, tol, wn, free)
+            if globalise:
+                du, r, M = self._globalised_update(du, fidx, delta, disp, rk, r0, tol, wn, free)
+            else:
+                du[fidx] += delta
+                r, M = self.residual(du)
             it += 1
             rk = np.linalg.norm((wn * r)[free])
             rel = rk / r0

@@ -31,7 +31,12 @@ void ck(cudaError_t e, const char* what) {
          std::string(what) + ": " + cudaGetErrorString(e));
   }
 }
-constexpr double ACTIVE_REL = 1e-12;
+// Active nodes: nodal mass above this fraction of the largest particle mass
+// (a node reached only by the far tail of a particle's B-spline, a distance t
+// inside its support edge, has mass ~ t^2 m / 2 and stiffness ~ t^2 but moves
+// the particle's dF at O(1): below t of about 0.014 such a node makes J
+// nearly singular and stalls Newton; it is left out of the step instead).
+constexpr double ACTIVE_REL = 1e-4;
 constexpr int KTPB = KRYLOV_TPB;
 constexpr int GRAPH_CHUNK = 8;   // Krylov iterations per graph launch
 thread_local std::string g_create_err;  // message of the last failed mpm_create_scene
@@ -101,6 +106,7 @@ struct mpm_scene {
   double* d_fail = nullptr;        // first constitutive failure record of a pass
   double* d_part = nullptr;        // per-block partial sums of its reductions
   void* d_KT = nullptr;            // adjoint: transposed Jacobian scratch
+  unsigned* d_pmask = nullptr;     // per-row slot-presence bits of the Jacobian pattern
   int kt_cap = -1;
   int adj_kit = 0;                 // Krylov iterations of the last adjoint solve
   // geometric multigrid preconditioner (MPM_PC_MG): levels 1.. of the
@@ -217,7 +223,7 @@ size_t footprint(const mpm_scene_desc* d, int np) {
   // 4-row segments (the u-p default)
   long long rows = std::min<long long>(nn, (long long)np * (D == 2 ? 9 : 27));
   const int seg = (d->precond == MPM_PC_SEG4 || (d->precond == MPM_PC_AUTO && B > D)) ? 4 : 1;
-  size_t mat = (size_t)rows * (stencil_slots(D) + seg) * B * B * T;
+  size_t mat = (size_t)rows * ((stencil_slots(D) + seg) * B * B * T + pmask_words(D) * 4);
   // multigrid: coarse matrices (a quarter per level in 2D, an eighth in 3D),
   // coarse grids and vectors, two level-0 scratch vectors
   size_t mg = 0;
@@ -229,6 +235,7 @@ template <class T>
 DevMatrix<T> matview(mpm_scene* s) {
   DevMatrix<T> K;
   K.val = (T*)s->d_K;
+  K.pmask = s->d_pmask;
   K.dinv = (T*)s->d_dinv;
   K.cap = s->cap;
   K.rows = s->d_rows;
@@ -251,9 +258,12 @@ void ensure_capacity(mpm_scene* s, int nrow) {
   int cap = std::max<int>(1024, (int)std::min<long long>(s->nnode, (long long)(nrow * 1.25) + 64));
   s->dfree(s->d_K);
   s->dfree(s->d_dinv);
+  s->dfree(s->d_pmask);
   s->d_K = nullptr;
   s->d_dinv = nullptr;
+  s->d_pmask = nullptr;
   const size_t S = stencil_slots(s->D), DD = (size_t)s->B * s->B;
+  s->d_pmask = s->dalloc<unsigned>((size_t)cap * pmask_words(s->D));
   if (s->mixed) {
     s->d_K = s->dalloc<float>((size_t)cap * S * DD);
     s->d_dinv = s->dalloc<float>((size_t)(cap + 4) * DD * s->seg);
@@ -392,6 +402,9 @@ void begin_step_impl(mpm_scene* s, mpm_newton_report* rep) {
   s->ncell = s->h_int[0];
   s->nrow = s->h_int[1];
   ensure_capacity(s, s->nrow);
+  ck(launch_pattern_bits<D>(s->G, s->d_rows, s->nrow, s->d_node2row, s->d_count, s->d_pmask, st),
+     "pattern bits");
+  s->launches += 1;
   if (s->mg) mg_structure<D, B>(s);
   // prescribed increments and r^0 (with the tangent for the first iteration)
   ck(cudaMemcpyAsync(s->d_grav, s->grav, 3 * sizeof(double), cudaMemcpyHostToDevice, st), "grav");
@@ -541,6 +554,7 @@ MgApply<T> mg_view(mpm_scene* s) {
     c.ny1 = m.ny1;
     c.nz1 = m.nz1;
     c.K.val = (T*)m.val;
+    c.K.pmask = nullptr;   // coarse levels: every slot read
     c.K.dinv = (T*)m.dinv;
     c.K.cap = m.cap;
     c.K.rows = m.rows;

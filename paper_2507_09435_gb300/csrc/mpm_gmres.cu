@@ -46,25 +46,7 @@ __device__ __forceinline__ void block_add_n(double* acc, int n, double* out) {
 template <int D, class T, int B>
 __device__ __forceinline__ void spmv(const DevMatrix<T>& K, int row, long long i, int nx1, int ny1, const T* x,
                                      T y[B]) {
-#pragma unroll
-  for (int a = 0; a < B; ++a) y[a] = (T)0;
-  constexpr int ZR = (D == 3) ? 2 : 0;
-#pragma unroll
-  for (int dz = -ZR; dz <= ZR; ++dz)
-#pragma unroll
-    for (int dy = -2; dy <= 2; ++dy)
-#pragma unroll
-      for (int dx = -2; dx <= 2; ++dx) {
-        const int slot = (D == 2) ? (dx + 2) + 5 * (dy + 2) : (dx + 2) + 5 * ((dy + 2) + 5 * (dz + 2));
-        const long long j = i + dx + (long long)nx1 * (dy + (long long)ny1 * dz);
-        T xj[B], kb[B * B];
-        ld_node<B, T, false>(x, j, xj);
-        ld_block<B, T>(&K.val[((long long)slot * K.cap + row) * (B * B)], kb);
-#pragma unroll
-        for (int a = 0; a < B; ++a)
-#pragma unroll
-          for (int b = 0; b < B; ++b) y[a] += kb[a * B + b] * xj[b];
-      }
+  stencil_row_product<D, T, B>(K, row, i, nx1, ny1, x, y);
 }
 
 enum { GS_OK = 0, GS_MAXIT = 1, GS_BREAKDOWN = 2 };

@@ -48,6 +48,9 @@ struct DevGrid {
 template <class T>
 struct DevMatrix {
   T* val;
+  const unsigned* pmask;  // per row PMASK_WORDS(D) words, bit s set when slot s can be
+                          // nonzero (the node pair shares an occupied cell); null: read
+                          // every slot (absent slots hold zeros either way)
   T* dinv;          // block-Jacobi inverse: seg == 1: dinv[row*B*B + a*B + b], the
                     // node's diagonal block; seg == 4: dinv[(s*4B + i)*4B + j], the
                     // inverse of the 4B x 4B diagonal block of rows 4s..4s+3
@@ -132,10 +135,31 @@ __device__ __forceinline__ void precond_apply(const DevMatrix<T>& K, int row, co
   }
 }
 
+// Words of the per-row slot-presence mask.
+constexpr int pmask_words(int D) { return D == 2 ? 1 : 4; }
+
+// The row's slot-presence words (all ones without a mask).
+template <int D>
+__device__ __forceinline__ void load_pmask(const unsigned* pmask, int row, unsigned pm[pmask_words(D)]) {
+  constexpr int PW = pmask_words(D);
+  if (pmask) {
+    if constexpr (PW == 4) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(pmask) + row);
+      pm[0] = v.x; pm[1] = v.y; pm[2] = v.z; pm[3] = v.w;
+    } else {
+      pm[0] = __ldg(pmask + row);
+    }
+  } else {
+#pragma unroll
+    for (int w = 0; w < PW; ++w) pm[w] = ~0u;
+  }
+}
+
 // y = K x for one row (node i) of a stencil-BSR matrix: the 5^D neighbour
 // blocks of the row against the neighbours' values of x (x on the padded
-// dense node grid of the matrix's level).  COHERENT: x was written earlier in
-// the same kernel (ordinary loads instead of the read-only path).
+// dense node grid of the matrix's level); slots absent from the row's
+// presence mask are not read.  COHERENT: x was written earlier in the same
+// kernel (ordinary loads instead of the read-only path).
 template <int D, class T, int B, bool COHERENT = false>
 __device__ __forceinline__ void stencil_row_product(const DevMatrix<T>& K, int row, long long i, int nx1, int ny1,
                                                     const T* x, T y[B]) {
@@ -143,6 +167,8 @@ __device__ __forceinline__ void stencil_row_product(const DevMatrix<T>& K, int r
   for (int a = 0; a < B; ++a) y[a] = (T)0;
   constexpr int ZR = (D == 3) ? 2 : 0;
   const long long cap = K.cap;
+  unsigned pm[pmask_words(D)];
+  load_pmask<D>(K.pmask, row, pm);
 #pragma unroll
   for (int dz = -ZR; dz <= ZR; ++dz)
 #pragma unroll
@@ -150,10 +176,20 @@ __device__ __forceinline__ void stencil_row_product(const DevMatrix<T>& K, int r
 #pragma unroll
       for (int dx = -2; dx <= 2; ++dx) {
         const int slot = (D == 2) ? (dx + 2) + 5 * (dy + 2) : (dx + 2) + 5 * ((dy + 2) + 5 * (dz + 2));
+        // absent slots: predicated off (no load is issued), not branched
+        // around, so that the loads of all slots stay in flight together
+        const bool on = (pm[slot >> 5] >> (slot & 31)) & 1u;
         const long long j = i + dx + (long long)nx1 * (dy + (long long)ny1 * dz);
         T xj[B], kb[B * B];
-        ld_node<B, T, COHERENT>(x, j, xj);
-        ld_block<B, T>(&K.val[((long long)slot * cap + row) * (B * B)], kb);
+        if (on) {
+          ld_node<B, T, COHERENT>(x, j, xj);
+          ld_block<B, T>(&K.val[((long long)slot * cap + row) * (B * B)], kb);
+        } else {
+#pragma unroll
+          for (int b = 0; b < B; ++b) xj[b] = (T)0;
+#pragma unroll
+          for (int b = 0; b < B * B; ++b) kb[b] = (T)0;
+        }
 #pragma unroll
         for (int a = 0; a < B; ++a)
 #pragma unroll
@@ -223,8 +259,8 @@ cudaError_t launch_assemble(const DevParticles& P, const DevGrid& G, const int* 
                             const T* A, DevMatrix<T> K, int nrow_host, cudaStream_t st);
 // 3D single-phase rows, one warp per row (mpm_assemble3d.cu)
 template <class T>
-cudaError_t launch_assemble_rows3(const DevParticles& P, const DevGrid& G, const int* cstart, const T* A,
-                                  DevMatrix<T> K, int nrow_host, cudaStream_t st);
+cudaError_t launch_assemble_rows3(const DevParticles& P, const DevGrid& G, const int* cstart, const int* node2row,
+                                  const T* A, DevMatrix<T> K, int nrow_host, cudaStream_t st);
 template <int D, class T, int B = D>
 cudaError_t launch_bc_matrix(const DevGrid& G, DevMatrix<T> K, const uint8_t* fixed, const int* node2row,
                              int nrow_host, cudaStream_t st);
@@ -233,6 +269,10 @@ cudaError_t launch_block_jacobi(const DevGrid& G, DevMatrix<T> K, int nrow_host,
 template <int D>
 cudaError_t launch_pattern_count(const DevGrid& G, const int* rows, int nrow_host, const int* node2row,
                                  const int* count, int* mask, cudaStream_t st);
+// the same pattern as per-row slot-presence bits (pmask_words(D) per row)
+template <int D>
+cudaError_t launch_pattern_bits(const DevGrid& G, const int* rows, int nrow_host, const int* node2row,
+                                const int* count, unsigned* bits, cudaStream_t st);
 
 // free-DOF residual norm^2 into *out (device double, accumulated)
 template <int D>

@@ -658,11 +658,17 @@ __global__ void __launch_bounds__(ASM_TPB) k_assemble(DevParticles P, DevGrid G,
     }
   __syncthreads();
   // store the tile's rows: all S slots, slot-major so that the rows of one
-  // x-line of nodes land contiguously in each slot plane
+  // x-line of nodes land contiguously in each slot plane; blocks coupling to
+  // an inactive node (below the activity threshold, not an unknown of the
+  // step) are stored as zeros
   for (int t = tid; t < NT * S * D2; t += ASM_TPB) {
     const int ab = t % D2, l = (t / D2) % NT, slot = t / (D2 * NT);
     const int row = srow[l];
-    if (row >= 0) K.val[((long long)slot * K.cap + row) * D2 + ab] = acc[((size_t)l * S + slot) * D2 + ab];
+    if (row < 0) continue;
+    const int jx = tx0 + l % TX + slot % 5 - 2, jy = ty0 + (l / TX) % TY + slot / 5 - 2;
+    const bool live = jx >= 0 && jy >= 0 && jx < G.nx1 && jy < G.ny1 &&
+                      node2row[jx + (long long)G.nx1 * jy] >= 0;
+    K.val[((long long)slot * K.cap + row) * D2 + ab] = live ? acc[((size_t)l * S + slot) * D2 + ab] : (T)0;
   }
 }
 
@@ -671,7 +677,7 @@ cudaError_t launch_assemble(const DevParticles& P, const DevGrid& G, const int* 
                             const T* A, DevMatrix<T> K, int nrow_host, cudaStream_t st) {
   if constexpr (D == 3) {
     static_assert(B == 3, "3D assembly is written for the single-phase blocks");
-    return launch_assemble_rows3<T>(P, G, cstart, A, K, nrow_host, st);
+    return launch_assemble_rows3<T>(P, G, cstart, node2row, A, K, nrow_host, st);
   } else {
   using L = AsmSmem<D, T, B>;
   if (P.np == 0) return cudaSuccess;
@@ -818,6 +824,33 @@ cudaError_t launch_block_jacobi(const DevGrid& G, DevMatrix<T> K, int nrow_host,
   return cudaGetLastError();
 }
 
+// Is block (i, i + offset of `slot`) structurally present: the neighbour is
+// an active node and the pair shares an occupied cell (base node)?
+template <int D>
+__device__ bool pattern_hit(const DevGrid& G, int ix, int iy, int iz, int slot, const int* __restrict__ node2row,
+                            const int* __restrict__ count) {
+  int dx = slot % 5 - 2, dy = (slot / 5) % 5 - 2, dz = (D == 3) ? slot / 25 - 2 : 0;
+  int j3[3] = {ix + dx, iy + dy, iz + dz};
+  int i3[3] = {ix, iy, iz};
+  bool inside = j3[0] >= 0 && j3[1] >= 0 && j3[0] < G.nx1 && j3[1] < G.ny1 &&
+                (D == 2 || (j3[2] >= 0 && j3[2] < G.nz1));
+  if (!inside) return false;
+  long long j = j3[0] + (long long)G.nx1 * (j3[1] + (long long)G.ny1 * j3[2]);
+  if (node2row[j] < 0) return false;
+  int lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) {
+    if (a < D) {
+      lo[a] = max(max(i3[a], j3[a]) - 2, 0);
+      hi[a] = min(min(i3[a], j3[a]), G.n[a] - 2);
+    } else { lo[a] = 0; hi[a] = 0; }
+  }
+  for (int cz = lo[2]; cz <= hi[2]; ++cz)
+    for (int cy = lo[1]; cy <= hi[1]; ++cy)
+      for (int cx = lo[0]; cx <= hi[0]; ++cx)
+        if (count[cx + (long long)G.nx1 * (cy + (long long)G.ny1 * cz)] > 0) return true;
+  return false;
+}
+
 // Structurally present blocks: mask[row*S + slot] = 1 when the neighbour node
 // is active and the two nodes share at least one occupied base cell.
 template <int D>
@@ -829,28 +862,25 @@ __global__ void k_pattern_count(DevGrid G, const int* __restrict__ rows, int nro
   if (row >= nrow) return;
   int i = rows[row];
   int ix = i % G.nx1, iy = (i / G.nx1) % G.ny1, iz = i / (G.nx1 * G.ny1);
-  for (int slot = 0; slot < S; ++slot) {
-    int dx = slot % 5 - 2, dy = (slot / 5) % 5 - 2, dz = (D == 3) ? slot / 25 - 2 : 0;
-    int j3[3] = {ix + dx, iy + dy, iz + dz};
-    int i3[3] = {ix, iy, iz};
-    bool inside = j3[0] >= 0 && j3[1] >= 0 && j3[0] < G.nx1 && j3[1] < G.ny1 &&
-                  (D == 2 || (j3[2] >= 0 && j3[2] < G.nz1));
-    if (!inside) continue;
-    long long j = j3[0] + (long long)G.nx1 * (j3[1] + (long long)G.ny1 * j3[2]);
-    if (node2row[j] < 0) continue;
-    int lo[3], hi[3];
-    for (int a = 0; a < 3; ++a) {
-      if (a < D) {
-        lo[a] = max(max(i3[a], j3[a]) - 2, 0);
-        hi[a] = min(min(i3[a], j3[a]), G.n[a] - 2);
-      } else { lo[a] = 0; hi[a] = 0; }
+  for (int slot = 0; slot < S; ++slot)
+    if (pattern_hit<D>(G, ix, iy, iz, slot, node2row, count)) mask[(long long)row * S + slot] = 1;
+}
+
+template <int D>
+__global__ void k_pattern_bits(DevGrid G, const int* __restrict__ rows, int nrow,
+                               const int* __restrict__ node2row, const int* __restrict__ count, unsigned* bits) {
+  constexpr int S = (D == 2) ? 25 : 125, PW = pmask_words(D);
+  int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nrow) return;
+  int i = rows[row];
+  int ix = i % G.nx1, iy = (i / G.nx1) % G.ny1, iz = i / (G.nx1 * G.ny1);
+  for (int w = 0; w < PW; ++w) {
+    unsigned word = 0u;
+    for (int b = 0; b < 32; ++b) {
+      const int slot = 32 * w + b;
+      if (slot < S && pattern_hit<D>(G, ix, iy, iz, slot, node2row, count)) word |= 1u << b;
     }
-    bool hit = false;
-    for (int cz = lo[2]; cz <= hi[2] && !hit; ++cz)
-      for (int cy = lo[1]; cy <= hi[1] && !hit; ++cy)
-        for (int cx = lo[0]; cx <= hi[0] && !hit; ++cx)
-          hit = count[cx + (long long)G.nx1 * (cy + (long long)G.ny1 * cz)] > 0;
-    if (hit) mask[(long long)row * S + slot] = 1;
+    bits[(long long)row * PW + w] = word;
   }
 }
 template <int D>
@@ -858,6 +888,14 @@ cudaError_t launch_pattern_count(const DevGrid& G, const int* rows, int nrow_hos
                                  const int* count, int* mask, cudaStream_t st) {
   if (nrow_host == 0) return cudaSuccess;
   k_pattern_count<D><<<nblocks(nrow_host), TPB, 0, st>>>(G, rows, nrow_host, node2row, count, mask);
+  return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_pattern_bits(const DevGrid& G, const int* rows, int nrow_host, const int* node2row,
+                                const int* count, unsigned* bits, cudaStream_t st) {
+  if (nrow_host == 0) return cudaSuccess;
+  k_pattern_bits<D><<<nblocks(nrow_host), TPB, 0, st>>>(G, rows, nrow_host, node2row, count, bits);
   return cudaGetLastError();
 }
 
@@ -902,6 +940,8 @@ cudaError_t launch_norm_free(const double* r, const int* rows, int nrow_host, co
                                             cudaStream_t);                                               \
   template cudaError_t launch_pattern_count<D>(const DevGrid&, const int*, int, const int*, const int*,  \
                                                int*, cudaStream_t);                                      \
+  template cudaError_t launch_pattern_bits<D>(const DevGrid&, const int*, int, const int*, const int*,   \
+                                              unsigned*, cudaStream_t);                                  \
   template cudaError_t launch_norm_free<D>(const double*, const int*, int, const uint8_t*, double*,      \
                                            cudaStream_t);
 MPM_INST_D(2)

@@ -104,8 +104,11 @@ __device__ __forceinline__ void spmv_part(const DevMatrix<T>& K, int row, long l
   for (int a = 0; a < D; ++a) y[a] = (T)0;
   const T* base = K.val + (long long)row * (D * D);
   const long long plane = (long long)K.cap * (D * D);
+  unsigned pm[pmask_words(D)];
+  load_pmask<D>(K.pmask, row, pm);
 #pragma unroll 4
   for (int slot = sub; slot < S; slot += RSPLIT) {
+    if (!((pm[slot >> 5] >> (slot & 31)) & 1u)) continue;
     T xj[D], kb[D * D];
     ld_node<D, T, true>(x, i + s_off[slot], xj);
     ld_block<D, T>(base + slot * plane, kb);

@@ -106,7 +106,7 @@ EXPORTS = ["mpm_create_scene", "mpm_set_gravity", "mpm_set_dirichlet", "mpm_begi
            "mpm_set_du", "mpm_assemble", "mpm_commit_step", "mpm_solve_step", "mpm_get_residual", "mpm_get_du", "mpm_get_mass",
            "mpm_get_counts", "mpm_get_jacobian_bsr", "mpm_get_mg_level", "mpm_get_particles", "mpm_get_pressure",
            "mpm_get_du_dev", "mpm_get_residual_dev", "mpm_get_positions_dev", "mpm_set_dirichlet_dev",
-           "mpm_set_traction", "mpm_kernel_launches", "mpm_get_newton_counters", "mpm_set_params", "mpm_get_particle_increment",
+           "mpm_set_traction", "mpm_kernel_launches", "mpm_get_newton_counters", "mpm_fma_peak", "mpm_set_params", "mpm_get_particle_increment",
            "mpm_adjoint", "mpm_adjoint_step", "mpm_set_state",
            "mpm_time_spmv", "mpm_set_particles", "mpm_residual_norm_noalloc", "mpm_noalloc_last_error",
            "mpm_footprint_bytes",
@@ -156,6 +156,7 @@ def lib(build: bool = True):
     L.mpm_set_state.argtypes = [_P, _D, _D, _D, _D]
     L.mpm_kernel_launches.argtypes = [_P, _LL]
     L.mpm_get_newton_counters.argtypes = [_P, _LL, _LL]
+    L.mpm_fma_peak.argtypes = [ctypes.c_int, _D]
     L.mpm_set_particles.argtypes = [_P, _D, _D, _D]
     L.mpm_residual_norm_noalloc.argtypes = [_P, _P, ctypes.c_int, _P, ctypes.c_int, _D, _P]
     L.mpm_noalloc_last_error.argtypes = []
@@ -490,6 +491,16 @@ def mpm_get_newton_counters(h):
     hal = ctypes.c_longlong(0)
     _check(lib().mpm_get_newton_counters(h, ctypes.byref(lim), ctypes.byref(hal)), h)
     return int(lim.value), int(hal.value)
+
+
+def mpm_fma_peak(precision):
+    """Measured FMA throughput of the current device in TFLOP/s (MPM_FP64 or
+    MPM_MIXED for FP32)."""
+    out = ctypes.c_double(0)
+    rc = lib().mpm_fma_peak(int(precision), ctypes.byref(out))
+    if rc != MPM_OK:
+        raise MPMError(rc, "mpm_fma_peak failed")
+    return out.value
 
 
 def mpm_time_spmv(h, reps):

@@ -18,6 +18,8 @@ above is taken per kind: residual scales per row kind, Jacobian scales per
 """
 import numpy as np
 
+from oracle import mpm_oracle as O
+
 RES_TOL = 1e-10
 JAC_TOL_FP64 = 1e-10
 JAC_TOL_MIXED = 1e-5
@@ -86,27 +88,27 @@ def jacobian_error(gs, orc, du, fixed):
             G[(int(row_node[r]), int(col_node[k]))] = val[k]
     bi, bj, bv = orc.jacobian_blocks(du)
     _, M = orc.residual(du)
-    act_node = M > 1e-12 * orc.m.max()
-    O = {(int(i), int(j)): v for i, j, v in zip(bi, bj, bv) if act_node[i] and act_node[j]}
-    O = _bc_blocks(O, fixed, dim)
-    keys = set(G) | set(O)
+    act_node = M > O.ACTIVE_REL * orc.m.max()
+    Ob = {(int(i), int(j)): v for i, j, v in zip(bi, bj, bv) if act_node[i] and act_node[j]}
+    Ob = _bc_blocks(Ob, fixed, dim)
+    keys = set(G) | set(Ob)
     zero = np.zeros((dim, dim))
     worst = 0.0
     if dim == orc.dim:
         row_scale = {}
-        for (i, j), B in O.items():
+        for (i, j), B in Ob.items():
             row_scale[i] = max(row_scale.get(i, 0.0), float(np.abs(B).max()))
         for key in keys:
             i = key[0]
             g = G.get(key, zero)
-            o = O.get(key, zero)
+            o = Ob.get(key, zero)
             sc = row_scale.get(i, 1.0)
             worst = max(worst, float(np.abs(g - o).max() / sc))
-        return worst, len(G), len(O)
+        return worst, len(G), len(Ob)
     # u-p: scale per (block row, row component, column kind)
     kd = kinds(dim, orc.dim)
     row_scale = {}
-    for (i, j), B in O.items():
+    for (i, j), B in Ob.items():
         for a in range(dim):
             for kb in (0, 1):
                 v = float(np.abs(B[a, kd == kb]).max())
@@ -114,7 +116,7 @@ def jacobian_error(gs, orc, du, fixed):
     for key in keys:
         i = key[0]
         g = G.get(key, zero)
-        o = O.get(key, zero)
+        o = Ob.get(key, zero)
         for a in range(dim):
             for b in range(dim):
                 sc = row_scale.get((i, a, kd[b]), 0.0)
@@ -123,7 +125,7 @@ def jacobian_error(gs, orc, du, fixed):
                     worst = max(worst, d / sc)
                 elif d > 0:
                     worst = np.inf
-    return worst, len(G), len(O)
+    return worst, len(G), len(Ob)
 
 
 def du_error(du_g, du_o, B=None, dim=None):

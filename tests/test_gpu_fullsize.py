@@ -44,7 +44,7 @@ def _check_sampled(sc, gs, step, nodes, jac_tol=JAC_TOL_MIXED):
     r_g = gs.residual()
     r_o, M, rabs = orc.residual(du, with_scale=True)
     Mg = gs.mass()
-    act = Mg[nodes] > 1e-12 * sc.mass.max()
+    act = Mg[nodes] > O.ACTIVE_REL * sc.mass.max()
     nodes = nodes[act]
     dofs = (nodes[:, None] * d + np.arange(d)[None, :]).ravel()
     free = dofs[~fixed[dofs]]
@@ -56,7 +56,7 @@ def _check_sampled(sc, gs, step, nodes, jac_tol=JAC_TOL_MIXED):
     rows = {int(n): r for r, n in enumerate(row_node)}
     bi, bj, bv = orc.jacobian_blocks(du)
     want = set(int(n) for n in nodes)
-    Ob = {(int(i), int(j)): v for i, j, v in zip(bi, bj, bv) if int(i) in want and Mg[int(j)] > 1e-12 * sc.mass.max()}
+    Ob = {(int(i), int(j)): v for i, j, v in zip(bi, bj, bv) if int(i) in want and Mg[int(j)] > O.ACTIVE_REL * sc.mass.max()}
     Ob = _bc_blocks(Ob, fixed, d)
     worst = 0.0
     for n in nodes:
@@ -78,7 +78,7 @@ def test_footing_full_size_sampled_parity():
     st = sc.steps[0]
     gs.begin(st)
     M = gs.mass()
-    active = np.nonzero(M > 1e-12 * sc.mass.max())[0]
+    active = np.nonzero(M > O.ACTIVE_REL * sc.mass.max())[0]
     nodes = rng.choice(active, size=48, replace=False)
     assert _check_sampled(sc, gs, st, nodes) >= 40
     gs.newton()
@@ -94,7 +94,7 @@ def test_column3d_2M_sampled_parity():
     st = sc.steps[0]
     gs.begin(st)
     M = gs.mass()
-    active = np.nonzero(M > 1e-12 * sc.mass.max())[0]
+    active = np.nonzero(M > O.ACTIVE_REL * sc.mass.max())[0]
     nodes = rng.choice(active, size=24, replace=False)
     assert _check_sampled(sc, gs, st, nodes, JAC_TOL_MIXED) >= 20
     gs.newton()

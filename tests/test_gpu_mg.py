@@ -83,7 +83,7 @@ def _check_galerkin(sc, gs, st, tol):
     d, B = sc.dim, sc.B
     fixed = fixed_mask(sc, st)
     M = gs.mass()
-    active = M > 1e-12 * sc.mass.max()
+    active = M > O.ACTIVE_REL * sc.mass.max()
     A = _bsr_to_csr(*gs.jacobian_bsr(), sc.nnode, B)
     if B > d:
         # the hierarchy is built in solver units: pressure rows and columns
