@@ -343,7 +343,8 @@ def serving_measure(nreq, slots, precision, seed=2507_09435 + 4, precond="auto",
     svc = []
     for d in draws[:ncap]:
         sc, st = S.serving_scene(d, consolidation)
-        t = sv1.submit(sc, steps=st, precision=precision, newton_maxit=32, precond=pc)
+        t = sv1.submit(sc, steps=st, precision=precision, newton_maxit=32, precond=pc,
+                       newton_tol=S.SERVING_NEWTON_TOL[d["kind"]])
         r = sv1.wait(t)
         svc.append(r.t_service_ms)
         sv1.release(t)
@@ -365,7 +366,8 @@ def serving_measure(nreq, slots, precision, seed=2507_09435 + 4, precond="auto",
             time.sleep(due - now)
         else:
             late = max(late, now - due)
-        tickets.append(sv.submit(sc, steps=st, precision=precision, newton_maxit=32, precond=pc))
+        tickets.append(sv.submit(sc, steps=st, precision=precision, newton_maxit=32, precond=pc,
+                                 newton_tol=S.SERVING_NEWTON_TOL[d["kind"]]))
         del sc, st
     res = [sv.wait(t) for t in tickets]
     wall = time.perf_counter() - t0

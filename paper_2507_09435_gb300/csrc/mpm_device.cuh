@@ -684,6 +684,34 @@ __device__ inline void tangent(const PState& st, double V0, T* out, long long st
       for (int j = 0; j < 3; ++j)
         Fb[i][j] = st.F[i][0] * st.bn[0][j] + st.F[i][1] * st.bn[1][j] + st.F[i][2] * st.bn[2][j];
     const double vmu = V0 * st.mu, vla = V0 * st.lamL;
+    if constexpr (sizeof(T) == 4) {
+      // FP32 Jacobian: the three factors are formed in FP64 (the first one
+      // holds the difference V0 mu dF bn - P) and rounded once; the 81
+      // products and sums, all of the scale of mu, then run in FP32
+      float G[3][3], X[3][3], Mb[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          G[i][j] = (float)(vmu * Fb[i][j] - st.P[i][j]);
+          X[i][j] = (float)st.Fi[i][j];
+          Mb[i][j] = (float)(vmu * st.bn[i][j]);
+        }
+      const float vlf = (float)vla;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a)
+#pragma unroll
+        for (int c = 0; c < DIM; ++c)
+#pragma unroll
+          for (int b = 0; b < DIM; ++b)
+#pragma unroll
+            for (int e = 0; e < DIM; ++e) {
+              float v = G[a][e] * X[c][b] + vlf * X[c][a] * X[e][b];
+              if (a == b) v += Mb[c][e];
+              out[(long long)(((a * DIM + c) * DIM + b) * DIM + e) * stride] = (T)v;
+            }
+      return;
+    }
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
