@@ -118,7 +118,13 @@ FP64_FLOP_PER_PARTICLE = {
 # ncu-measured DRAM traffic of one Krylov iteration per workload /
 # precision / preconditioner (bytes; the profile that gives each is named
 # beside it); None where no capture of the current kernels exists
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/k_bicg_column3d_393k_mixed.md: 553.9 MB per iteration measured
+    # on the 393k column (1.037 x its algorithmic bytes); the 2M column
+    # scaled by its algorithmic bytes (2.543 GB -> 2.637 GB)
+    ("column3d_stated", "mixed", "auto"): 553.9e6,
+    ("column3d", "mixed", "auto"): 2.637e9,
+}
 
 WORKLOADS = {
     # the 2D footing (reported beside the headline)

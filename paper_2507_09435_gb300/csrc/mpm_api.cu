@@ -107,6 +107,8 @@ struct mpm_scene {
   double* d_part = nullptr;        // per-block partial sums of its reductions
   void* d_KT = nullptr;            // adjoint: transposed Jacobian scratch
   unsigned* d_pmask = nullptr;     // per-row slot-presence bits of the Jacobian pattern
+  int* d_tri = nullptr;            // 3D assembly: first active row of each x-aligned row triple
+  int* d_ntri = nullptr;           // number of entries of d_tri (device scalar)
   int kt_cap = -1;
   int adj_kit = 0;                 // Krylov iterations of the last adjoint solve
   // geometric multigrid preconditioner (MPM_PC_MG): levels 1.. of the
@@ -259,11 +261,14 @@ void ensure_capacity(mpm_scene* s, int nrow) {
   s->dfree(s->d_K);
   s->dfree(s->d_dinv);
   s->dfree(s->d_pmask);
+  s->dfree(s->d_tri);
   s->d_K = nullptr;
   s->d_dinv = nullptr;
   s->d_pmask = nullptr;
+  s->d_tri = nullptr;
   const size_t S = stencil_slots(s->D), DD = (size_t)s->B * s->B;
   s->d_pmask = s->dalloc<unsigned>((size_t)cap * pmask_words(s->D));
+  if (s->D == 3) s->d_tri = s->dalloc<int>((size_t)cap);
   if (s->mixed) {
     s->d_K = s->dalloc<float>((size_t)cap * S * DD);
     s->d_dinv = s->dalloc<float>((size_t)(cap + 4) * DD * s->seg);
@@ -405,6 +410,11 @@ void begin_step_impl(mpm_scene* s, mpm_newton_report* rep) {
   ck(launch_pattern_bits<D>(s->G, s->d_rows, s->nrow, s->d_node2row, s->d_count, s->d_pmask, st),
      "pattern bits");
   s->launches += 1;
+  if (D == 3 && B == 3) {
+    ck(cudaMemsetAsync(s->d_ntri, 0, sizeof(int), st), "memset");
+    ck(launch_triple_leaders(s->G, s->d_rows, s->nrow, s->d_node2row, s->d_tri, s->d_ntri, st), "triples");
+    s->launches += 1;
+  }
   if (s->mg) mg_structure<D, B>(s);
   // prescribed increments and r^0 (with the tangent for the first iteration)
   ck(cudaMemcpyAsync(s->d_grav, s->grav, 3 * sizeof(double), cudaMemcpyHostToDevice, st), "grav");
@@ -640,7 +650,8 @@ void assemble_impl(mpm_scene* s, bool with_mg = true) {
   cudaStream_t st = s->st;
   DevMatrix<T> K = matview<T>(s);
   // every block of every active row is stored by the assembly (no zero fill)
-  ck(launch_assemble<D, T, B>(s->P, s->G, s->d_cstart, s->d_node2row, (const T*)s->d_A, K, s->nrow, st),
+  ck(launch_assemble<D, T, B>(s->P, s->G, s->d_cstart, s->d_node2row, (const T*)s->d_A, K, s->nrow, s->d_tri,
+                              s->d_ntri, st),
      "assemble");
   ck(launch_bc_matrix<D, T, B>(s->G, K, s->d_fixed, s->d_node2row, s->nrow, st), "bc matrix");
   ck(launch_block_jacobi<D, T, B>(s->G, K, s->nrow, s->d_err, st), "block jacobi");
@@ -1386,6 +1397,7 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
     s->d_rows = s->dalloc<int>(nn);
     s->d_scan_tmp = s->dalloc<int>(scan_tmp_ints((int)(nn + 1)));
     s->d_nrow = s->dalloc<int>(1);
+    s->d_ntri = s->dalloc<int>(1);
     s->d_err = s->dalloc<int>(2);
     s->d_nplastic = s->d_err + 1;
     s->d_M = s->dalloc<double>(nn);

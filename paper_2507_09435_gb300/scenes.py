@@ -239,7 +239,7 @@ def block_compression(nsteps: int = 5, strain_per_step: float = 1e-3, ppc: int =
 def footing(nx: int = 256, ny: int = 128, h: float = 0.1, ppc: int = 2, nsteps: int = 50,
             B: float = 2.0, settle_frac: float = 0.1, geostatic: bool = True,
             E: float = 1e7, nu: float = 0.3, phi: float = 30.0, psi: float = 0.0,
-            c: float = 5e3, rho: float = 2000.0, g: float = 9.81) -> Scene:
+            c: float = 5e3, rho: float = 2000.0, g: float = 9.81, prestress: bool = False) -> Scene:
     """2D plane-strain rigid-footing bearing capacity: Neo-Hookean +
     non-associative Drucker-Prager soil filling cells [1,nx-1) x [1,ny-1)
     (256 x 128 grid, h = 0.1 m, 2x2 particles per cell: 128,016 particles).
@@ -249,14 +249,33 @@ def footing(nx: int = 256, ny: int = 128, h: float = 0.1, ppc: int = 2, nsteps: 
     y <= h); a rough rigid footing of width B centred on the surface pushes the
     surface nodes under it (y >= (ny-1)h, |x - xc| <= B/2) down by
     settle_frac*B over nsteps steps with u_x = 0.  Load step 0 is a geostatic
-    step (gravity on, footing free) when ``geostatic`` is set."""
+    step (gravity on, footing free) when ``geostatic`` is set.
+
+    ``prestress`` starts the soil from the linear-elastic at-rest state of a
+    laterally confined layer instead of from b_e = 1: a particle at depth d
+    below the surface carries the vertical log strain eps_y = -rho g d /
+    (lam + 2 mu) (one-dimensional compression, eps_x = eps_z = 0), i.e.
+    b_e = diag(1, exp(2 eps_y), 1).  Without it a deep layer settles under
+    its own weight by rho g H^2 / (2 (lam + 2 mu)) (0.12 m for the 12.7 m
+    layer above), which can leave the prescribed surface nodes outside
+    every particle's stencil; with it the geostatic step only removes the
+    small nonlinear remainder."""
     n = (nx, ny, 0)
     cells = box_cells((1, 1), (nx - 1, ny - 1))
     x = lattice(cells, h, ppc, 2)
     mat = Material(model=MODEL_NH_DP, E=E, nu=nu, rho=rho, phi=phi, psi=psi, c=c)
     vol = np.full(x.shape[0], h * h / ppc ** 2)
+    be0 = None
+    if prestress:
+        lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+        mu = E / (2.0 * (1.0 + nu))
+        depth = (ny - 1) * h - x[:, 1]
+        be0 = np.zeros((x.shape[0], 6))
+        be0[:, 0] = 1.0
+        be0[:, 1] = np.exp(-2.0 * rho * g * depth / (lam + 2.0 * mu))
+        be0[:, 2] = 1.0
     sc = Scene("footing", 2, n, h, (0.0, 0.0, 0.0), x, vol, vol * rho,
-               np.zeros(x.shape[0], np.int32), [mat])
+               np.zeros(x.shape[0], np.int32), [mat], be0=be0)
     grav = (0.0, -g, 0.0)
     lx, _ = _dofs(sc, lambda ix, iy: (ix <= 1) | (ix >= nx - 1), 0, 2, n)
     bx, _ = _dofs(sc, lambda ix, iy: iy <= 1, 0, 2, n)
@@ -514,7 +533,7 @@ def serving_scene(d, consolidation: str = "layer") -> Tuple[Scene, list]:
     """The scene and load steps of one serving request descriptor.
     elastic block: square grid of ~cells cells, block on a quarter of it,
     1 % strain over the steps; footing: nx = 2 ny with nx*ny ~ cells, h = 0.1,
-    B = nx h / 12.8, nu = 0.35, settlement 0.0005 B per step after the geostatic step; Terzaghi: a
+    B = nx h / 12.8, nu = 0.35, at-rest prestress, settlement 0.0005 B per step after the geostatic step; Terzaghi: a
     column 16 cells wide, k = 1e-9 m/s, and
     * consolidation="full": N = cells/16 clipped to [64, 512] cells high, the
       load steps spanning T = c_v t / H^2 in [0, 1] (c_v dt / h^2 = N^2 /
@@ -537,10 +556,15 @@ def serving_scene(d, consolidation: str = "layer") -> Tuple[Scene, list]:
         # the Drucker-Prager cone below about 6.5 m, so the geostatic step
         # leaves half of a deep request plastic, and the first footing
         # increments unload it: Newton then stalls near 1e-6 on the GPU and in
-        # the oracle alike; with K0 = 0.54 the geostatic state is elastic
+        # the oracle alike; with K0 = 0.54 the geostatic state is elastic.
+        # The soil starts from the at-rest prestress: from b_e = 1 a 17 m
+        # layer settles by 0.2 m (two cells) in the geostatic step, and the
+        # prescribed surface nodes of the footing fall outside every
+        # particle's stencil
         ny = max(16, int(round(np.sqrt(cells / 2.0))))
         B = 2 * ny * 0.1 / 12.8
-        sc = footing(nx=2 * ny, ny=ny, h=0.1, nsteps=ns - 1, B=B, settle_frac=0.0005 * (ns - 1), nu=0.35)
+        sc = footing(nx=2 * ny, ny=ny, h=0.1, nsteps=ns - 1, B=B, settle_frac=0.0005 * (ns - 1), nu=0.35,
+                     prestress=True)
         return sc, sc.steps
     full = consolidation == "full"
     N = int(np.clip(round(cells / 16.0), 64, 512 if full else 256))
