@@ -107,6 +107,7 @@ struct mpm_scene {
   double* d_part = nullptr;        // per-block partial sums of its reductions
   void* d_KT = nullptr;            // adjoint: transposed Jacobian scratch
   unsigned* d_pmask = nullptr;     // per-row slot-presence bits of the Jacobian pattern
+  double* d_red = nullptr;         // Krylov reduction slots (krylov_red_slots(cap))
   int* d_tri = nullptr;            // 3D assembly: first active row of each x-aligned row triple
   int* d_ntri = nullptr;           // number of entries of d_tri (device scalar)
   int kt_cap = -1;
@@ -222,10 +223,11 @@ size_t footprint(const mpm_scene_desc* d, int np) {
   }
   // active rows are bounded by the nodes the particles can reach; the
   // block-Jacobi inverses take one B x B block per row, or four for the
-  // 4-row segments (the u-p default)
+  // 4-row segments (the u-p default); per row also the presence mask, the
+  // 3D row-triple list and (under a byte) the Krylov reduction slots
   long long rows = std::min<long long>(nn, (long long)np * (D == 2 ? 9 : 27));
   const int seg = (d->precond == MPM_PC_SEG4 || (d->precond == MPM_PC_AUTO && B > D)) ? 4 : 1;
-  size_t mat = (size_t)rows * ((stencil_slots(D) + seg) * B * B * T + pmask_words(D) * 4);
+  size_t mat = (size_t)rows * ((stencil_slots(D) + seg) * B * B * T + pmask_words(D) * 4 + (D == 3 ? 4 : 0) + 1);
   // multigrid: coarse matrices (a quarter per level in 2D, an eighth in 3D),
   // coarse grids and vectors, two level-0 scratch vectors
   size_t mg = 0;
@@ -252,6 +254,7 @@ KrylovVecs<D, T> vecview(mpm_scene* s) {
   KrylovVecs<D, T> v;
   T** f[9] = {&v.x, &v.r, &v.rhat, &v.p, &v.phat, &v.v, &v.s, &v.shat, &v.t};
   for (int k = 0; k < 9; ++k) *f[k] = b + k * s->vlen + s->vpad;
+  v.red = s->d_red;
   return v;
 }
 
@@ -262,13 +265,16 @@ void ensure_capacity(mpm_scene* s, int nrow) {
   s->dfree(s->d_dinv);
   s->dfree(s->d_pmask);
   s->dfree(s->d_tri);
+  s->dfree(s->d_red);
   s->d_K = nullptr;
   s->d_dinv = nullptr;
   s->d_pmask = nullptr;
   s->d_tri = nullptr;
+  s->d_red = nullptr;
   const size_t S = stencil_slots(s->D), DD = (size_t)s->B * s->B;
   s->d_pmask = s->dalloc<unsigned>((size_t)cap * pmask_words(s->D));
   if (s->D == 3) s->d_tri = s->dalloc<int>((size_t)cap);
+  s->d_red = s->dalloc<double>((size_t)krylov_red_slots(cap));
   if (s->mixed) {
     s->d_K = s->dalloc<float>((size_t)cap * S * DD);
     s->d_dinv = s->dalloc<float>((size_t)(cap + 4) * DD * s->seg);

@@ -209,6 +209,16 @@ struct KrylovScalars {
   // merged-reduction BiCGStab: rho of the previous iteration and the extra
   // dot products (s,s), (rhat,s), (rhat,t), (v,v); (rhat,rhat) of the start
   double rho_old, acc_ss, acc_rs, acc_rt, acc_vv, rhat2;
+  // blocks of the current kernel that have stored their partial sums (the
+  // last one adds them up and resets it)
+  unsigned int ticket;
+  // merged BiCGStab, set once per kernel by the last block of the grid sum:
+  // beta and the FP32 copies of alpha, omega and beta; the stop decision
+  // for the next iteration (0: go on, else 1 + status) and the breakdown
+  // flag of the (rhat, v) test
+  double beta;
+  float alpha_f, omega_f, beta_f;
+  int next_stop, c_break;
 };
 
 // ---- host launchers (stream-ordered, no synchronisation) ----------------
@@ -354,7 +364,10 @@ cudaError_t launch_dirichlet_in(int n, const long long* dof, const double* value
 template <int D, class T>
 struct KrylovVecs {
   T *x, *r, *rhat, *p, *phat, *v, *s, *shat, *t;
+  double* red;   // reduction slots: 3 per block of the row grid (krylov_red_slots)
 };
+// slots of KrylovVecs::red for a matrix of row capacity cap
+inline long long krylov_red_slots(long long cap) { return 3 * ((cap + KRYLOV_TPB - 1) / KRYLOV_TPB); }
 template <int D, class T, int B = D>
 cudaError_t launch_bicgstab_init(DevMatrix<T> K, const double* res, const uint8_t* fixed, KrylovVecs<D, T> v,
                                  KrylovScalars* S, double tol2, int maxit, int nblk, cudaStream_t st);

@@ -24,55 +24,178 @@ __device__ __forceinline__ long long nbr(long long i, int dx, int dy, int dz, in
   return i + dx + (long long)nx1 * (dy + (long long)ny1 * dz);
 }
 
-__device__ __forceinline__ double wsum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
+// Accumulator of a dot product.  For FP64 vectors a double; for FP32
+// vectors a double-float pair (hi + lo, about 48 significant bits): each
+// product enters exactly (Dekker's product by a fused multiply-add) and each
+// sum is Knuth's error-free two-sum, so the sums keep FP64-level accuracy
+// while running on the FP32 pipe (the FP64 pipe has 1/64 of its rate here).
+// The explicit _rn intrinsics keep the compiler from contracting or
+// reassociating the error terms.
+template <class T>
+struct Acc;
+template <>
+struct Acc<double> {
+  double v;
+  __device__ static Acc zero() { return {0.0}; }
+  __device__ void add_prod(double a, double b) { v = fma(a, b, v); }
+  __device__ void add(const Acc& o) { v += o.v; }
+  __device__ Acc shfl_xor(int o) const { return {__shfl_xor_sync(0xffffffffu, v, o)}; }
+  __device__ double value() const { return v; }
+  __device__ static Acc load_l2(const Acc* p) { return {__ldcg(&p->v)}; }
+};
+template <>
+struct Acc<float> {
+  float hi, lo;
+  __device__ static Acc zero() { return {0.0f, 0.0f}; }
+  // (hi, lo) += (x, xe)
+  __device__ void add2(float x, float xe) {
+    const float s = __fadd_rn(hi, x);
+    const float bv = __fadd_rn(s, -hi);
+    const float e = __fadd_rn(__fadd_rn(hi, -__fadd_rn(s, -bv)), __fadd_rn(x, -bv));
+    const float t = __fadd_rn(e, __fadd_rn(lo, xe));
+    hi = __fadd_rn(s, t);
+    lo = __fadd_rn(t, -__fadd_rn(hi, -s));
+  }
+  __device__ void add_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    add2(p, __fmaf_rn(a, b, -p));
+  }
+  __device__ void add(const Acc& o) { add2(o.hi, o.lo); }
+  __device__ Acc shfl_xor(int o) const {
+    return {__shfl_xor_sync(0xffffffffu, hi, o), __shfl_xor_sync(0xffffffffu, lo, o)};
+  }
+  __device__ double value() const { return (double)hi + (double)lo; }
+  __device__ static Acc load_l2(const Acc* p) {
+    const float2 u = __ldcg(reinterpret_cast<const float2*>(p));
+    return {u.x, u.y};
+  }
+};
+static_assert(sizeof(Acc<float>) == sizeof(double) && sizeof(Acc<double>) == sizeof(double),
+              "one reduction slot per accumulator");
 
-// Block-reduce NV partial sums and add them atomically to out[k].
-template <int NV>
-__device__ __forceinline__ void block_accumulate(double v[NV], double* const out[NV]) {
-  __shared__ double sh[NV][KTPB / 32];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = wsum(v[k]);
+// Sums of NV per-thread accumulators over the whole grid, in an order fixed
+// by the grid alone (the result does not depend on the order in which the
+// blocks run): each block stores its NV block sums in red[k * gridDim.x +
+// block] and takes a ticket; the block that takes the last ticket adds the
+// stored sums in block order (strided over its threads, then a fixed tree)
+// and resets the ticket for the next kernel.  Returns true in every thread
+// of that last block, with the sums in out[] of its thread 0.  Every block
+// of the grid calls this exactly once.
+template <class T, int NV>
+__device__ __forceinline__ bool grid_sum(Acc<T> v[NV], double* red_raw, unsigned int* ticket, double out[NV]) {
+  constexpr int NW = KTPB / 32;
+  constexpr int RU = 8;   // loads per sum in flight in the last block
+  __shared__ Acc<T> sh[NV][NW];
+  __shared__ int last;
+  Acc<T>* red = reinterpret_cast<Acc<T>*>(red_raw);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k].add(v[k].shfl_xor(o));
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) sh[k][w] = v[k];
   }
   __syncthreads();
-  if (w == 0) {
+  const int nb = gridDim.x;
+  if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-      double t = (lane < KTPB / 32) ? sh[k][lane] : 0.0;
-      t = wsum(t);
-      if (lane == 0 && t != 0.0) atomicAdd(out[k], t);
+      Acc<T> t = sh[k][0];
+#pragma unroll
+      for (int q = 1; q < NW; ++q) t.add(sh[k][q]);
+      red[k * nb + blockIdx.x] = t;
     }
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == (unsigned)(nb - 1));
   }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  Acc<T> t[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) t[k] = Acc<T>::zero();
+  for (int q0 = threadIdx.x; q0 < nb; q0 += KTPB * RU) {
+    Acc<T> l[NV][RU];
+#pragma unroll
+    for (int u = 0; u < RU; ++u) {
+      const int q = q0 + u * KTPB;
+#pragma unroll
+      for (int k = 0; k < NV; ++k) l[k][u] = (q < nb) ? Acc<T>::load_l2(&red[k * nb + q]) : Acc<T>::zero();
+    }
+#pragma unroll
+    for (int u = 0; u < RU; ++u)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) t[k].add(l[k][u]);
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t[k].add(t[k].shfl_xor(o));
+  __syncthreads();   // sh is reused
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k][w] = t[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      Acc<T> u = sh[k][0];
+#pragma unroll
+      for (int q = 1; q < NW; ++q) u.add(sh[k][q]);
+      out[k] = u.value();
+    }
+    *ticket = 0u;
+  }
+  return true;
 }
 
 enum { KS_OK = 0, KS_MAXIT = 1, KS_BREAKDOWN = 2 };
+
+// Stop decision taken once per iteration from the reduced scalars (0: go
+// on; else 1 + the status): converged, iteration limit, or breakdown (a
+// non-finite residual norm, or a zero rho or omega).
+__device__ __forceinline__ int stop_code(double rr, int it, int maxit, double tol2, bool bad) {
+  if (rr <= tol2) return 1 + KS_OK;
+  if (it >= maxit) return 1 + KS_MAXIT;
+  if (!(rr == rr) || bad) return 1 + KS_BREAKDOWN;
+  return 0;
+}
+
+// The working-precision copy of a scalar of the iteration.
+template <class T>
+__device__ __forceinline__ T scal(double d, float f) {
+  if constexpr (sizeof(T) == 4) return f;
+  else return d;
+}
 }  // namespace
 
 // ------------------------------------------------------------------ BiCGStab
 // Right-preconditioned BiCGStab (van der Vorst 1992) on J d = b, d0 = 0, in a
 // merged-reduction form with four kernels per iteration:
-//   B: v = J phat, (rhat, v)
-//   C: alpha = rho/(rhat,v); s = r - alpha v; shat = M^-1 s; (s,s), (rhat,s)
-//   D: t = J shat; (t,s), (t,t), (rhat,t)
-//   A: omega = (t,s)/(t,t); x += alpha phat + omega shat; r = s - omega t;
-//      rho' = (rhat,s) - omega (rhat,t); ||r||^2 = (s,s) - 2 omega (t,s) +
-//      omega^2 (t,t); beta = (rho'/rho)(alpha/omega); p = r + beta (p - omega v);
-//      phat = M^-1 p.
+//   B: v = J phat, (rhat, v); then alpha = rho / (rhat, v)
+//   C: s = r - alpha v; shat = M^-1 s; (s,s), (rhat,s)
+//   D: t = J shat; (t,s), (t,t), (rhat,t); then omega = (t,s)/(t,t),
+//      rho' = (rhat,s) - omega (rhat,t), ||r||^2 = (s,s) - 2 omega (t,s) +
+//      omega^2 (t,t), beta = (rho'/rho)(alpha/omega)
+//   A: x += alpha phat + omega shat; r = s - omega t;
+//      p = r + beta (p - omega v); phat = M^-1 p.
 // The two dot products of the classical form's last step follow from the
 // ones already reduced, so the update and the next search direction share one
-// pass.  (FP32 products are exact in FP64 and summed in FP64, which keeps the
-// cancellation in ||r||^2 harmless at the linear tolerances used.)
-// A kernel's lead thread never writes a field that other blocks of the same
-// kernel read: rho is read in C and written in A; C copies it to rho_old,
-// which A reads; iter is read in B and advanced in D; each accumulator is
-// zeroed in a kernel that neither produces nor consumes it.
+// pass.  The scalars ("then ...") are computed once, by the thread that
+// finishes the kernel's grid sum, which also takes the stop decision for the
+// next iteration; the row kernels only read their FP32 copies.  (The dot
+// products keep FP64-level accuracy, see Acc, which keeps the cancellation in
+// ||r||^2 harmless at the linear tolerances used.)
+// Every field of the scalars is written in one kernel and read only in later
+// kernels, except the stop fields (done, status), which block 0 sets when
+// the whole grid returns at once.
+
+// The start of an iteration's kernels: the solve is over (every kernel of a
+// graph chunk then returns at once).
+__device__ __forceinline__ bool bicg_over(KrylovScalars* S) { return S->done != 0; }
 
 // init: r = b, rhat = b, x = 0, p = r, phat = M^-1 r; rho = (rhat, r),
 // rr_last = (r, r).
@@ -83,7 +206,7 @@ __global__ void __launch_bounds__(KTPB) k_bicg_init(DevMatrix<T> K, const double
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   const int nrow = *K.nrow;
   const unsigned live = __ballot_sync(0xffffffffu, row < nrow);
-  double acc[2] = {0.0, 0.0};
+  Acc<T> acc[1] = {Acc<T>::zero()};
   if (row < nrow) {
     const long long i = K.rows[row];
     T b[B], z[B];
@@ -95,16 +218,14 @@ __global__ void __launch_bounds__(KTPB) k_bicg_init(DevMatrix<T> K, const double
       v.rhat[d] = b[a];
       v.p[d] = b[a];
       v.x[d] = (T)0;
-      acc[0] += (double)b[a] * (double)b[a];
+      acc[0].add_prod(b[a], b[a]);
     }
     precond_apply<B, T>(K, row, b, z, live);
 #pragma unroll
     for (int a = 0; a < B; ++a) v.phat[i * B + a] = z[a];
-    acc[1] = acc[0];
   }
-  double acc3[3] = {acc[0], acc[1], acc[0]};
-  double* outs[3] = {&S->rr_last, &S->rho, &S->rhat2};
-  block_accumulate<3>(acc3, outs);
+  double out[1];
+  const bool last = grid_sum<T, 1>(acc, v.red, &S->ticket, out);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     S->alpha = 1.0;
     S->omega = 1.0;
@@ -114,26 +235,28 @@ __global__ void __launch_bounds__(KTPB) k_bicg_init(DevMatrix<T> K, const double
     S->done = 0;
     S->status = KS_OK;
   }
+  if (last && threadIdx.x == 0) {
+    S->rr_last = out[0];
+    S->rho = out[0];
+    S->rhat2 = out[0];
+    S->next_stop = stop_code(out[0], 0, maxit, tol2, false);
+  }
 }
 
-// B: convergence / limit test, then v = J phat and (rhat, v).
+// B: stop test, then v = J phat and (rhat, v), (v, v); alpha.
 template <int D, class T, int B>
 __global__ void __launch_bounds__(KTPB) k_bicg_B(DevGrid G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
-  if (S->done) return;
-  const double rr = S->rr_last;
-  const int it = S->iter;
-  const bool conv = rr <= S->tol2;
-  const bool maxed = it >= S->maxit;
-  const bool bad = !(rr == rr) || (it > 0 && (S->rho == 0.0 || S->omega == 0.0));
-  if (conv || maxed || bad) {
+  if (bicg_over(S)) return;
+  const int ns = S->next_stop;
+  if (ns != 0) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       S->done = 1;
-      S->status = conv ? KS_OK : (maxed ? KS_MAXIT : KS_BREAKDOWN);
+      S->status = ns - 1;
     }
     return;
   }
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[2] = {0.0, 0.0};
+  Acc<T> acc[2] = {Acc<T>::zero(), Acc<T>::zero()};
   if (row < *K.nrow) {
     const long long i = K.rows[row];
     T y[B];
@@ -141,34 +264,39 @@ __global__ void __launch_bounds__(KTPB) k_bicg_B(DevGrid G, DevMatrix<T> K, Kryl
 #pragma unroll
     for (int a = 0; a < B; ++a) {
       v.v[i * B + a] = y[a];
-      acc[0] += (double)v.rhat[i * B + a] * (double)y[a];
-      acc[1] += (double)y[a] * (double)y[a];
+      acc[0].add_prod(v.rhat[i * B + a], y[a]);
+      acc[1].add_prod(y[a], y[a]);
     }
   }
-  double* outs[2] = {&S->acc_rv, &S->acc_vv};
-  block_accumulate<2>(acc, outs);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    S->acc_ss = 0.0;
-    S->acc_rs = 0.0;
+  double out[2];
+  if (grid_sum<T, 2>(acc, v.red, &S->ticket, out) && threadIdx.x == 0) {
+    const double rv = out[0], vv = out[1];
+    S->acc_rv = rv;
+    S->acc_vv = vv;
+    // (near) breakdown: rhat and v almost orthogonal, relative to FP32 vectors
+    const bool brk = !(fabs(rv) > 1e-7 * sqrt(vv * S->rhat2));
+    const double alpha = brk ? 0.0 : S->rho / rv;
+    S->c_break = brk ? 1 : 0;
+    S->alpha = alpha;
+    S->alpha_f = (float)alpha;
   }
 }
 
-// C: alpha = rho / (rhat, v); s = r - alpha v; shat = M^-1 s; (s,s), (rhat,s).
+// C: s = r - alpha v; shat = M^-1 s; (s,s), (rhat,s).
 template <int D, class T, int B>
 __global__ void __launch_bounds__(KTPB) k_bicg_C(DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
-  if (S->done) return;
-  const double rv = S->acc_rv;
-  // (near) breakdown: rhat and v almost orthogonal, relative to FP32 vectors
-  if (!(fabs(rv) > 1e-7 * sqrt(S->acc_vv * S->rhat2))) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) { S->done = 1; S->status = KS_BREAKDOWN; }
+  if (bicg_over(S)) return;
+  if (S->c_break) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      S->done = 1;
+      S->status = KS_BREAKDOWN;
+    }
     return;
   }
-  const double rho = S->rho;
-  const double alpha = rho / rv;
-  const T ta = (T)alpha;
+  const T ta = scal<T>(S->alpha, S->alpha_f);
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned live = __ballot_sync(0xffffffffu, row < *K.nrow);
-  double acc[2] = {0.0, 0.0};
+  Acc<T> acc[2] = {Acc<T>::zero(), Acc<T>::zero()};
   if (row < *K.nrow) {
     const long long i = K.rows[row];
     T s[B], z[B];
@@ -177,30 +305,27 @@ __global__ void __launch_bounds__(KTPB) k_bicg_C(DevMatrix<T> K, KrylovVecs<D, T
       const long long d = i * B + a;
       s[a] = v.r[d] - ta * v.v[d];
       v.s[d] = s[a];
-      acc[0] += (double)s[a] * (double)s[a];
-      acc[1] += (double)v.rhat[d] * (double)s[a];
+      acc[0].add_prod(s[a], s[a]);
+      acc[1].add_prod(v.rhat[d], s[a]);
     }
     precond_apply<B, T>(K, row, s, z, live);
 #pragma unroll
     for (int a = 0; a < B; ++a) v.shat[i * B + a] = z[a];
   }
-  double* outs[2] = {&S->acc_ss, &S->acc_rs};
-  block_accumulate<2>(acc, outs);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    S->alpha = alpha;
-    S->rho_old = rho;
-    S->acc_ts = 0.0;
-    S->acc_tt = 0.0;
-    S->acc_rt = 0.0;
+  double out[2];
+  if (grid_sum<T, 2>(acc, v.red, &S->ticket, out) && threadIdx.x == 0) {
+    S->acc_ss = out[0];
+    S->acc_rs = out[1];
   }
 }
 
-// D: t = J shat; (t,s), (t,t), (rhat,t).
+// D: t = J shat; (t,s), (t,t), (rhat,t); omega, rho', ||r||^2, beta and the
+// stop decision for the next iteration.
 template <int D, class T, int B>
 __global__ void __launch_bounds__(KTPB) k_bicg_D(DevGrid G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
-  if (S->done) return;
+  if (bicg_over(S)) return;
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[3] = {0.0, 0.0, 0.0};
+  Acc<T> acc[3] = {Acc<T>::zero(), Acc<T>::zero(), Acc<T>::zero()};
   if (row < *K.nrow) {
     const long long i = K.rows[row];
     T y[B];
@@ -209,32 +334,40 @@ __global__ void __launch_bounds__(KTPB) k_bicg_D(DevGrid G, DevMatrix<T> K, Kryl
     for (int a = 0; a < B; ++a) {
       const long long d = i * B + a;
       v.t[d] = y[a];
-      acc[0] += (double)y[a] * (double)v.s[d];
-      acc[1] += (double)y[a] * (double)y[a];
-      acc[2] += (double)v.rhat[d] * (double)y[a];
+      acc[0].add_prod(y[a], v.s[d]);
+      acc[1].add_prod(y[a], y[a]);
+      acc[2].add_prod(v.rhat[d], y[a]);
     }
   }
-  double* outs[3] = {&S->acc_ts, &S->acc_tt, &S->acc_rt};
-  block_accumulate<3>(acc, outs);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    S->acc_rv = 0.0;
-    S->acc_vv = 0.0;
-    S->iter = S->iter + 1;
+  double out[3];
+  if (grid_sum<T, 3>(acc, v.red, &S->ticket, out) && threadIdx.x == 0) {
+    const double ts = out[0], tt = out[1], rt = out[2];
+    S->acc_ts = ts;
+    S->acc_tt = tt;
+    S->acc_rt = rt;
+    const double omega = (tt > 0.0) ? ts / tt : 0.0;
+    const double rho = S->rho, alpha = S->alpha;
+    const double rho_new = S->acc_rs - omega * rt;
+    const double rr = fmax(S->acc_ss - 2.0 * omega * ts + omega * omega * tt, 0.0);
+    const double beta = (omega != 0.0 && rho != 0.0) ? (rho_new / rho) * (alpha / omega) : 0.0;
+    const int it = S->iter + 1;
+    S->iter = it;
+    S->omega = omega;
+    S->rho = rho_new;
+    S->rr_last = rr;
+    S->beta = beta;
+    S->omega_f = (float)omega;
+    S->beta_f = (float)beta;
+    S->next_stop = stop_code(rr, it, S->maxit, S->tol2, rho_new == 0.0 || omega == 0.0);
   }
 }
 
-// A: omega; x and r updates; rho', ||r||^2 from the reduced products; the
-// next search direction p and phat.
+// A: x and r updates; the next search direction p and phat.
 template <int D, class T, int B>
 __global__ void __launch_bounds__(KTPB) k_bicg_A(DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
-  if (S->done) return;
-  const double tt = S->acc_tt, ts = S->acc_ts;
-  const double omega = (tt > 0.0) ? ts / tt : 0.0;
-  const double alpha = S->alpha, rho_old = S->rho_old;
-  const double rho_new = S->acc_rs - omega * S->acc_rt;
-  const double rr = fmax(S->acc_ss - 2.0 * omega * ts + omega * omega * tt, 0.0);
-  const double beta = (omega != 0.0 && rho_old != 0.0) ? (rho_new / rho_old) * (alpha / omega) : 0.0;
-  const T ta = (T)alpha, tw = (T)omega, tb = (T)beta;
+  if (bicg_over(S)) return;
+  const T ta = scal<T>(S->alpha, S->alpha_f), tw = scal<T>(S->omega, S->omega_f),
+          tb = scal<T>(S->beta, S->beta_f);
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned live = __ballot_sync(0xffffffffu, row < *K.nrow);
   if (row < *K.nrow) {
@@ -253,11 +386,6 @@ __global__ void __launch_bounds__(KTPB) k_bicg_A(DevMatrix<T> K, KrylovVecs<D, T
 #pragma unroll
     for (int a = 0; a < B; ++a) v.phat[i * B + a] = z[a];
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    S->omega = omega;
-    S->rho = rho_new;
-    S->rr_last = rr;
-  }
 }
 
 // restart from the current x: r = b - J x (the true residual), rhat = r,
@@ -268,7 +396,7 @@ __global__ void __launch_bounds__(KTPB) k_bicg_restart(DevGrid G, DevMatrix<T> K
                                                        KrylovScalars* S, double tol2, int maxit) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned live = __ballot_sync(0xffffffffu, row < *K.nrow);
-  double acc = 0.0;
+  Acc<T> acc[1] = {Acc<T>::zero()};
   if (row < *K.nrow) {
     const long long i = K.rows[row];
     T y[B], r[B], z[B];
@@ -281,15 +409,14 @@ __global__ void __launch_bounds__(KTPB) k_bicg_restart(DevGrid G, DevMatrix<T> K
       v.r[d] = r[a];
       v.rhat[d] = r[a];
       v.p[d] = r[a];
-      acc += (double)r[a] * (double)r[a];
+      acc[0].add_prod(r[a], r[a]);
     }
     precond_apply<B, T>(K, row, r, z, live);
 #pragma unroll
     for (int a = 0; a < B; ++a) v.phat[i * B + a] = z[a];
   }
-  double acc3[3] = {acc, acc, acc};
-  double* outs[3] = {&S->rr_last, &S->rho, &S->rhat2};
-  block_accumulate<3>(acc3, outs);
+  double out[1];
+  const bool last = grid_sum<T, 1>(acc, v.red, &S->ticket, out);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     S->alpha = 1.0;
     S->omega = 1.0;
@@ -298,6 +425,12 @@ __global__ void __launch_bounds__(KTPB) k_bicg_restart(DevGrid G, DevMatrix<T> K
     S->iter = 0;
     S->done = 0;
     S->status = KS_OK;
+  }
+  if (last && threadIdx.x == 0) {
+    S->rr_last = out[0];
+    S->rho = out[0];
+    S->rhat2 = out[0];
+    S->next_stop = stop_code(out[0], 0, maxit, tol2, false);
   }
 }
 
