@@ -108,8 +108,9 @@ struct mpm_scene {
   void* d_KT = nullptr;            // adjoint: transposed Jacobian scratch
   unsigned* d_pmask = nullptr;     // per-row slot-presence bits of the Jacobian pattern
   double* d_red = nullptr;         // Krylov reduction slots (krylov_red_slots(cap))
-  int* d_tri = nullptr;            // 3D assembly: first active row of each x-aligned row triple
-  int* d_ntri = nullptr;           // number of entries of d_tri (device scalar)
+  int* d_cellpos = nullptr;        // position of each occupied cell in d_cells (exclusive scan)
+  void* d_cblk = nullptr;          // 3D assembly: 27 x 27 x 9 block values per occupied cell
+  long long cblk_cap = 0;          // cells d_cblk has room for
   int kt_cap = -1;
   int adj_kit = 0;                 // Krylov iterations of the last adjoint solve
   // geometric multigrid preconditioner (MPM_PC_MG): levels 1.. of the
@@ -223,11 +224,13 @@ size_t footprint(const mpm_scene_desc* d, int np) {
   }
   // active rows are bounded by the nodes the particles can reach; the
   // block-Jacobi inverses take one B x B block per row, or four for the
-  // 4-row segments (the u-p default); per row also the presence mask, the
-  // 3D row-triple list and (under a byte) the Krylov reduction slots
+  // 4-row segments (the u-p default); per row also the presence mask and
+  // (under a byte) the Krylov reduction slots; in 3D the blocks of the
+  // occupied cells (at most one per particle, 27 x 27 x 9 values each)
   long long rows = std::min<long long>(nn, (long long)np * (D == 2 ? 9 : 27));
   const int seg = (d->precond == MPM_PC_SEG4 || (d->precond == MPM_PC_AUTO && B > D)) ? 4 : 1;
-  size_t mat = (size_t)rows * ((stencil_slots(D) + seg) * B * B * T + pmask_words(D) * 4 + (D == 3 ? 4 : 0) + 1);
+  size_t mat = (size_t)rows * ((stencil_slots(D) + seg) * B * B * T + pmask_words(D) * 4 + 1);
+  if (D == 3) mat += (size_t)std::min<long long>(nn, np) * CELL_BLOCK_VALUES * T + (size_t)nn * 4;
   // multigrid: coarse matrices (a quarter per level in 2D, an eighth in 3D),
   // coarse grids and vectors, two level-0 scratch vectors
   size_t mg = 0;
@@ -264,16 +267,13 @@ void ensure_capacity(mpm_scene* s, int nrow) {
   s->dfree(s->d_K);
   s->dfree(s->d_dinv);
   s->dfree(s->d_pmask);
-  s->dfree(s->d_tri);
   s->dfree(s->d_red);
   s->d_K = nullptr;
   s->d_dinv = nullptr;
   s->d_pmask = nullptr;
-  s->d_tri = nullptr;
   s->d_red = nullptr;
   const size_t S = stencil_slots(s->D), DD = (size_t)s->B * s->B;
   s->d_pmask = s->dalloc<unsigned>((size_t)cap * pmask_words(s->D));
-  if (s->D == 3) s->d_tri = s->dalloc<int>((size_t)cap);
   s->d_red = s->dalloc<double>((size_t)krylov_red_slots(cap));
   if (s->mixed) {
     s->d_K = s->dalloc<float>((size_t)cap * S * DD);
@@ -394,9 +394,9 @@ void begin_step_impl(mpm_scene* s, mpm_newton_report* rep) {
   std::swap(s->P, s->Q);
   // occupied cells
   ck(launch_flag_positive(s->d_count, s->d_flag, nn + 1, st), "flags");
-  ck(scan_exclusive(s->d_flag, s->d_pos, (int)(nn + 1), s->d_scan_tmp, st), "scan");
-  ck(launch_compact(s->d_flag, s->d_pos, s->d_cells, nn, st), "compact");
-  ck(cudaMemcpyAsync(s->h_int + 0, s->d_pos + nn, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
+  ck(scan_exclusive(s->d_flag, s->d_cellpos, (int)(nn + 1), s->d_scan_tmp, st), "scan");
+  ck(launch_compact(s->d_flag, s->d_cellpos, s->d_cells, nn, st), "compact");
+  ck(cudaMemcpyAsync(s->h_int + 0, s->d_cellpos + nn, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
   // nodal mass and active rows
   ck(cudaMemsetAsync(s->d_M, 0, nn * sizeof(double), st), "memset");
   ck(launch_mass<D>(s->P, s->G, s->d_M, st), "mass");
@@ -416,10 +416,12 @@ void begin_step_impl(mpm_scene* s, mpm_newton_report* rep) {
   ck(launch_pattern_bits<D>(s->G, s->d_rows, s->nrow, s->d_node2row, s->d_count, s->d_pmask, st),
      "pattern bits");
   s->launches += 1;
-  if (D == 3 && B == 3) {
-    ck(cudaMemsetAsync(s->d_ntri, 0, sizeof(int), st), "memset");
-    ck(launch_triple_leaders(s->G, s->d_rows, s->nrow, s->d_node2row, s->d_tri, s->d_ntri, st), "triples");
-    s->launches += 1;
+  if (D == 3 && s->ncell > s->cblk_cap) {
+    s->dfree(s->d_cblk);
+    s->d_cblk = nullptr;
+    const long long cap = (long long)(s->ncell * 1.1) + 64;
+    s->d_cblk = s->dalloc<unsigned char>((size_t)cap * CELL_BLOCK_VALUES * (s->mixed ? 4 : 8));
+    s->cblk_cap = cap;
   }
   if (s->mg) mg_structure<D, B>(s);
   // prescribed increments and r^0 (with the tangent for the first iteration)
@@ -656,8 +658,8 @@ void assemble_impl(mpm_scene* s, bool with_mg = true) {
   cudaStream_t st = s->st;
   DevMatrix<T> K = matview<T>(s);
   // every block of every active row is stored by the assembly (no zero fill)
-  ck(launch_assemble<D, T, B>(s->P, s->G, s->d_cstart, s->d_node2row, (const T*)s->d_A, K, s->nrow, s->d_tri,
-                              s->d_ntri, st),
+  const Asm3<T> a3{s->d_cells, s->ncell, s->d_count, s->d_cellpos, (T*)s->d_cblk};
+  ck(launch_assemble<D, T, B>(s->P, s->G, s->d_cstart, s->d_node2row, (const T*)s->d_A, K, s->nrow, &a3, st),
      "assemble");
   ck(launch_bc_matrix<D, T, B>(s->G, K, s->d_fixed, s->d_node2row, s->nrow, st), "bc matrix");
   ck(launch_block_jacobi<D, T, B>(s->G, K, s->nrow, s->d_err, st), "block jacobi");
@@ -1399,11 +1401,11 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
     s->d_flag = s->dalloc<int>(nn + 1);
     s->d_pos = s->dalloc<int>(nn + 1);
     s->d_cells = s->dalloc<int>(nn);
+    s->d_cellpos = s->dalloc<int>(nn + 1);
     s->d_node2row = s->dalloc<int>(nn);
     s->d_rows = s->dalloc<int>(nn);
     s->d_scan_tmp = s->dalloc<int>(scan_tmp_ints((int)(nn + 1)));
     s->d_nrow = s->dalloc<int>(1);
-    s->d_ntri = s->dalloc<int>(1);
     s->d_err = s->dalloc<int>(2);
     s->d_nplastic = s->d_err + 1;
     s->d_M = s->dalloc<double>(nn);

@@ -264,22 +264,31 @@ template <int D>
 cudaError_t launch_stress_out(const DevParticles& P, const DevGrid& G, const MatC* mats, double* tau9,
                               cudaStream_t st);
 
-// tri / ntri: the 3D row-triple list of launch_triple_leaders (unused in 2D)
+// Values per cell block of the 3D assembly: 27 x 27 node pairs x 9, padded
+// to a multiple of 16 bytes.
+constexpr int CELL_BLOCK_VALUES = 6564;
+// Occupied cells and their block buffer for the 3D two-phase assembly:
+// cells[0..ncell) the occupied cells (base nodes) in index order, count the
+// particles per cell, cellpos[cell] the cell's position in that list, blk
+// room for ncell x CELL_BLOCK_VALUES values.
+template <class T>
+struct Asm3 {
+  const int* cells;
+  int ncell;
+  const int* count;
+  const int* cellpos;
+  T* blk;
+};
+// a3: the 3D cell data (unused in 2D, may be null there)
 template <int D, class T, int B = D>
 cudaError_t launch_assemble(const DevParticles& P, const DevGrid& G, const int* cstart, const int* node2row,
-                            const T* A, DevMatrix<T> K, int nrow_host, const int* tri, const int* ntri,
-                            cudaStream_t st);
-// 3D single-phase rows, one warp per triple of x-neighbouring rows
-// (mpm_assemble3d.cu); the triples are those of launch_triple_leaders
+                            const T* A, DevMatrix<T> K, int nrow_host, const Asm3<T>* a3, cudaStream_t st);
+// 3D single-phase rows: cell block products, then a gather per row
+// (mpm_assemble_cells.cu)
 template <class T>
-cudaError_t launch_assemble_rows3(const DevParticles& P, const DevGrid& G, const int* cstart, const int* node2row,
-                                  const T* A, DevMatrix<T> K, int nrow_host, const int* tri, const int* ntri,
-                                  cudaStream_t st);
-// rows that open an x-aligned triple of nodes (ix0 = 3 m, the first active
-// row among ix0, ix0 + 1, ix0 + 2 at the same y and z), appended to list;
-// *count (zeroed by the caller) receives their number
-cudaError_t launch_triple_leaders(const DevGrid& G, const int* rows, int nrow_host, const int* node2row, int* list,
-                                  int* count, cudaStream_t st);
+cudaError_t launch_assemble_cells3(const DevParticles& P, const DevGrid& G, const Asm3<T>& a3, const int* cstart,
+                                   const int* node2row, const T* A, DevMatrix<T> K, int nrow_host,
+                                   cudaStream_t st);
 template <int D, class T, int B = D>
 cudaError_t launch_bc_matrix(const DevGrid& G, DevMatrix<T> K, const uint8_t* fixed, const int* node2row,
                              int nrow_host, cudaStream_t st);

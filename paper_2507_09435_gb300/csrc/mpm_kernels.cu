@@ -511,7 +511,7 @@ __global__ void __launch_bounds__(ASM_TPB) k_assemble(DevParticles P, DevGrid G,
   using L = AsmSmem<D, T, B>;
   constexpr int TX = L::TX, TY = L::TY, TZ = L::TZ, CHP = L::CHP, NN = L::NN, S = L::S;
   constexpr int D2 = L::D2, D4 = L::D4, NT = L::NT, AST = L::AST, NPHI = L::NPHI;
-  static_assert(D == 2, "3D rows are assembled by k_assemble_rows3");
+  static_assert(D == 2, "3D rows are assembled by launch_assemble_cells3");
   extern __shared__ __align__(16) unsigned char smem[];
   T* acc = reinterpret_cast<T*>(smem + L::acc);    // [NT][S][D2]
   T* sA = reinterpret_cast<T*>(smem + L::sA);      // [CHP][AST]
@@ -674,11 +674,11 @@ __global__ void __launch_bounds__(ASM_TPB) k_assemble(DevParticles P, DevGrid G,
 
 template <int D, class T, int B>
 cudaError_t launch_assemble(const DevParticles& P, const DevGrid& G, const int* cstart, const int* node2row,
-                            const T* A, DevMatrix<T> K, int nrow_host, const int* tri, const int* ntri,
-                            cudaStream_t st) {
+                            const T* A, DevMatrix<T> K, int nrow_host, const Asm3<T>* a3, cudaStream_t st) {
   if constexpr (D == 3) {
     static_assert(B == 3, "3D assembly is written for the single-phase blocks");
-    return launch_assemble_rows3<T>(P, G, cstart, node2row, A, K, nrow_host, tri, ntri, st);
+    if (!a3) return cudaErrorInvalidValue;
+    return launch_assemble_cells3<T>(P, G, *a3, cstart, node2row, A, K, nrow_host, st);
   } else {
   using L = AsmSmem<D, T, B>;
   if (P.np == 0) return cudaSuccess;
@@ -959,8 +959,7 @@ MPM_INST_DT(3, double)
 
 #define MPM_INST_DTB(D, T, B)                                                                           \
   template cudaError_t launch_assemble<D, T, B>(const DevParticles&, const DevGrid&, const int*, const int*, \
-                                                const T*, DevMatrix<T>, int, const int*, const int*,      \
-                                                cudaStream_t);                                           \
+                                                const T*, DevMatrix<T>, int, const Asm3<T>*, cudaStream_t); \
   template cudaError_t launch_bc_matrix<D, T, B>(const DevGrid&, DevMatrix<T>, const uint8_t*, const int*, \
                                                  int, cudaStream_t);                                     \
   template cudaError_t launch_block_jacobi<D, T, B>(const DevGrid&, DevMatrix<T>, int, int*, cudaStream_t);
