@@ -533,7 +533,7 @@ def serving_scene(d, consolidation: str = "layer") -> Tuple[Scene, list]:
     """The scene and load steps of one serving request descriptor.
     elastic block: square grid of ~cells cells, block on a quarter of it,
     1 % strain over the steps; footing: nx = 2 ny with nx*ny ~ cells, h = 0.1,
-    B = nx h / 12.8, nu = 0.35, at-rest prestress, settlement 0.0005 B per step after the geostatic step; Terzaghi: a
+    B = nx h / 12.8, nu = 0.35, at-rest prestress, settlement 0.0003 B per step after the geostatic step; Terzaghi: a
     column 16 cells wide, k = 1e-9 m/s, and
     * consolidation="full": N = cells/16 clipped to [64, 512] cells high, the
       load steps spanning T = c_v t / H^2 in [0, 1] (c_v dt / h^2 = N^2 /
@@ -548,10 +548,11 @@ def serving_scene(d, consolidation: str = "layer") -> Tuple[Scene, list]:
         return sc, sc.steps
     if kind == "dp_footing":
         # footing width in the proportions of the 256 x 128 footing
-        # (B = domain width / 12.8); 0.0005 B per step keeps the 40-step
+        # (B = domain width / 12.8); 0.0003 B per step keeps the 40-step
         # requests short of the bearing-capacity plateau (at 0.001 B per step
-        # the narrower footings reach it after about 30 steps and Newton
-        # stalls there on the GPU and in the oracle).  nu = 0.35: with
+        # the narrower footings reach it after about 30 steps, at 0.0005 B a
+        # few of the larger ones after 14 to 23 steps, and Newton stalls
+        # there on the GPU and in the oracle alike).  nu = 0.35: with
         # nu = 0.3 the at-rest state (K0 = nu / (1 - nu) = 0.43) lies outside
         # the Drucker-Prager cone below about 6.5 m, so the geostatic step
         # leaves half of a deep request plastic, and the first footing
@@ -563,7 +564,7 @@ def serving_scene(d, consolidation: str = "layer") -> Tuple[Scene, list]:
         # particle's stencil
         ny = max(16, int(round(np.sqrt(cells / 2.0))))
         B = 2 * ny * 0.1 / 12.8
-        sc = footing(nx=2 * ny, ny=ny, h=0.1, nsteps=ns - 1, B=B, settle_frac=0.0005 * (ns - 1), nu=0.35,
+        sc = footing(nx=2 * ny, ny=ny, h=0.1, nsteps=ns - 1, B=B, settle_frac=0.0003 * (ns - 1), nu=0.35,
                      prestress=True)
         return sc, sc.steps
     full = consolidation == "full"
