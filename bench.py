@@ -119,11 +119,11 @@ FP64_FLOP_PER_PARTICLE = {
 # precision / preconditioner (bytes; the profile that gives each is named
 # beside it); None where no capture of the current kernels exists
 TRAFFIC = {
-    # profiles/k_bicg_column3d_393k_mixed.md: 553.9 MB per iteration measured
-    # on the 393k column (1.037 x its algorithmic bytes); the 2M column
-    # scaled by its algorithmic bytes (2.543 GB -> 2.637 GB)
-    ("column3d_stated", "mixed", "auto"): 553.9e6,
-    ("column3d", "mixed", "auto"): 2.637e9,
+    # profiles/k_bicg_column3d_393k_mixed.md: 554.3 MB per iteration measured
+    # on the 393k column (1.038 x its algorithmic bytes); the 2M column
+    # scaled by its algorithmic bytes (2.543 GB -> 2.639 GB)
+    ("column3d_stated", "mixed", "auto"): 554.3e6,
+    ("column3d", "mixed", "auto"): 2.639e9,
 }
 
 WORKLOADS = {
@@ -753,7 +753,7 @@ def main():
     asm_tf = 2.0 * fma_asm * sc.np * n_asm / max(t_asm_s, 1e-12) / 1e12
     alu = {"fp64_tflops": fma64, "fp32_tflops": fma32,
            "how": "mpm_fma_peak: 8 independent FMA chains per thread, 8 blocks of 256 per SM, CUDA events",
-           "assembly": {"kernel": "k_assemble_rows3" if sc.dim == 3 else "k_assemble", "bound": "alu",
+           "assembly": {"kernel": "k_cell_blocks + k_gather_rows" if sc.dim == 3 else "k_assemble", "bound": "alu",
                         "achieved_tflops": asm_tf,
                         "peak_tflops": fma32 if args.precision == "mixed" else fma64,
                         "frac": asm_tf / (fma32 if args.precision == "mixed" else fma64),
