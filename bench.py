@@ -85,6 +85,8 @@ def parse():
                     help="the last N timed load steps are solved again by the plain FP64 GPU path from the "
                          "same committed state (0: none)")
     ap.add_argument("--no-footing", action="store_true", help="skip the 2D footing line beside the main one")
+    ap.add_argument("--jacobian-reuse", type=int, default=2,
+                    help="modified-Newton arm on the FP64 arm's steps: reassemble every k-th iteration (<= 1: off)")
     ap.add_argument("--serving", type=int, default=512,
                     help="requests of the serving stream measured beside the main line (0: none); "
                          "--workload serving runs the 512-request stream alone")
@@ -591,6 +593,46 @@ def fp64_arm(sc, schedule, s0, k_end, snap, x_mixed_end, mixed_recs, args, strea
     return out
 
 
+def reuse_arm(sc, schedule, s0, k_end, snap, x_mixed_end, mixed_recs, args, stream, flush, reuse):
+    """The same load steps s0..k_end-1, mixed precision, with modified Newton:
+    the Jacobian (and its preconditioner) assembled at iterations 0, reuse,
+    2 reuse, ... of each load step and reused in between
+    (`jacobian_reuse`); from the mixed run's committed state at step s0, one
+    untimed solve of step s0 first.  Time per load step against full Newton
+    on the same steps is the comparison (Newton it/s is not: modified Newton
+    takes more, cheaper iterations)."""
+    from paper_2507_09435_gb300 import mpm
+    pc = {"auto": mpm.MPM_PC_AUTO, "node": mpm.MPM_PC_NODE, "seg4": mpm.MPM_PC_SEG4,
+          "mg": mpm.MPM_PC_MG}[args.precond]
+    kry = mpm.MPM_BICGSTAB if args.krylov == "bicgstab" else mpm.MPM_GMRES
+    gr = mpm.GpuScene(sc, precision=mpm.MPM_MIXED, krylov=kry, stream=stream.cuda_stream, newton_tol=1e-8,
+                      newton_maxit=32, precond=pc, krylov_maxit=50000, jacobian_reuse=reuse)
+    try:
+        mpm.mpm_set_state(gr.h, x=snap["x"], be=snap["be"], pc=snap["pc"], F=snap["F"])
+        gr.solve_step(schedule(s0))
+        mpm.mpm_set_state(gr.h, x=snap["x"], be=snap["be"], pc=snap["pc"], F=snap["F"])
+        recs = [_events_step(gr, schedule(k), stream, flush) for k in range(s0, k_end)]
+        xr = gr.particles(be=False, pc=False, F=False, tau=False)["x"]
+    except mpm.MPMError as exc:
+        gr.close()
+        return {"jacobian_reuse": int(reuse), "steps": [int(s0), int(k_end - 1)], "converged": False,
+                "error": str(exc)}
+    gr.close()
+    out = _summary(recs)
+    mix = _summary(mixed_recs[s0:k_end])
+    disp = float(np.abs(x_mixed_end - snap["x"]).max())
+    out.update({
+        "jacobian_reuse": int(reuse),
+        "converged": True,
+        "steps": [int(s0), int(k_end - 1)],
+        "full_newton_ms_per_step": mix["ms_per_step"],
+        "full_newton_iters_per_step": mix["newton_iters_per_step"],
+        "time_per_load_step_vs_full_newton": mix["ms_per_step"] and out["ms_per_step"] / mix["ms_per_step"],
+        "x_diff_vs_full_newton_relative": float(np.abs(xr - x_mixed_end).max()) / max(disp, 1e-300),
+    })
+    return out
+
+
 def footing_extra(args, stream, flush, nwarm=2, nsteps=8):
     """The C2 footing (256x128, 128,016 particles, NH + Drucker-Prager, mixed,
     V-cycle preconditioned BiCGStab): geostatic step and one increment
@@ -774,6 +816,11 @@ def main():
     fp64 = None
     if n64 and snap is not None:
         fp64 = fp64_arm(sc, schedule, s0, args.steps, snap, x_mixed_end, recs, args, stream, flush)
+    # ---- modified Newton (Jacobian reuse) on the same steps --------------------
+    modified = None
+    if n64 and snap is not None and args.jacobian_reuse > 1:
+        modified = reuse_arm(sc, schedule, s0, args.steps, snap, x_mixed_end, recs, args, stream, flush,
+                             args.jacobian_reuse)
 
     # ---- end to end through the C ABI with host buffers ----------------------
     e2e = None
@@ -837,6 +884,7 @@ def main():
                 "phase_ms_per_step": {"setup": phase[0] / args.steps, "residual": phase[1] / args.steps,
                                       "assembly": phase[2] / args.steps, "krylov": phase[3] / args.steps},
                 "gpu_launches": int(launches), "roofline": roof, "alu_roofline": alu, "fp64": fp64,
+                "modified_newton": modified,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks, "footing": footing, "serving": serving}
         print(json.dumps(line), flush=True)

@@ -107,6 +107,13 @@ typedef struct {
                               P^T J P, damped block-Jacobi smoothing, dense
                               coarsest level); BiCGStab only (MPM_GMRES with
                               MPM_PC_MG is MPM_ERR_INVALID_ARG)               */
+  int jacobian_reuse;      /* 0 or 1: the Jacobian is assembled at every Newton
+                              iteration (Newton's method, Sec. 2.2); k > 1: at
+                              the first iteration of a load step and then at
+                              every k-th one, the iterations between reusing
+                              the last assembled Jacobian and its
+                              preconditioner (modified Newton); negative:
+                              MPM_ERR_INVALID_ARG                              */
 } mpm_scene_desc;
 
 typedef struct {

@@ -190,6 +190,7 @@ void validate_desc(const mpm_scene_desc* d) {
     fail(MPM_ERR_INVALID_ARG, "bad precond");
   if (d->precond == MPM_PC_MG && d->krylov != MPM_BICGSTAB)
     fail(MPM_ERR_INVALID_ARG, "the multigrid preconditioner is built for BiCGStab");
+  if (d->jacobian_reuse < 0) fail(MPM_ERR_INVALID_ARG, "jacobian_reuse must be >= 0");
   if (d->formulation == MPM_UP) {
     if (d->dim != 2) fail(MPM_ERR_INVALID_ARG, "the u-p formulation is built for dim 2");
     if (!(d->dt > 0)) fail(MPM_ERR_INVALID_ARG, "u-p needs dt > 0");
@@ -816,7 +817,10 @@ void newton_impl(mpm_scene* s, mpm_newton_report* rep) {
   cudaStream_t st = s->st;
   DevMatrix<T> K = matview<T>(s);
   cudaEventRecord(s->ev[0], st);
-  assemble_impl<D, T, B>(s);
+  // modified Newton (jacobian_reuse = k > 1): the Jacobian of the load
+  // step's iteration 0, k, 2k, ... serves the iterations after it
+  const int reuse = s->desc.jacobian_reuse;
+  if (reuse <= 1 || s->k % reuse == 0) assemble_impl<D, T, B>(s);
   // linear tolerance: fixed, or Eisenstat-Walker choice 2 (gamma 0.9,
   // alpha 2) capped at ETA_MAX = 1e-2: with the classical cap of 0.1 loose
   // steps through the plastic zone made Newton diverge on footing problems.

@@ -37,7 +37,7 @@ class mpm_scene_desc(ctypes.Structure):
                 ("gmres_restart", ctypes.c_int), ("newton_tol", ctypes.c_double),
                 ("newton_maxit", ctypes.c_int), ("forcing", ctypes.c_int), ("krylov_rtol", ctypes.c_double),
                 ("krylov_maxit", ctypes.c_int), ("formulation", ctypes.c_int), ("dt", ctypes.c_double),
-                ("p_scale", ctypes.c_double), ("precond", ctypes.c_int)]
+                ("p_scale", ctypes.c_double), ("precond", ctypes.c_int), ("jacobian_reuse", ctypes.c_int)]
 
 
 class mpm_material(ctypes.Structure):
@@ -202,7 +202,7 @@ def _check(rc, handle=None):
 
 def make_desc(dim, n, h, origin=(0.0, 0.0, 0.0), precision=MPM_FP64, krylov=MPM_BICGSTAB, gmres_restart=30,
               newton_tol=1e-8, newton_maxit=25, forcing=None, krylov_rtol=None, krylov_maxit=20000,
-              formulation=MPM_SOLID, dt=0.0, p_scale=0.0, precond=MPM_PC_AUTO):
+              formulation=MPM_SOLID, dt=0.0, p_scale=0.0, precond=MPM_PC_AUTO, jacobian_reuse=0):
     d = mpm_scene_desc()
     d.dim = dim
     for a in range(3):
@@ -225,6 +225,7 @@ def make_desc(dim, n, h, origin=(0.0, 0.0, 0.0), precision=MPM_FP64, krylov=MPM_
     d.dt = float(dt)
     d.p_scale = float(p_scale)
     d.precond = int(precond)
+    d.jacobian_reuse = int(jacobian_reuse)
     return d
 
 

@@ -47,6 +47,9 @@ def test_host_only_calls():
     bad = mpm.make_desc(2, (2, 32), 1 / 32)
     with pytest.raises(mpm.MPMError):
         mpm.mpm_footprint_bytes(bad, 10)
+    with pytest.raises(mpm.MPMError):
+        mpm.mpm_footprint_bytes(mpm.make_desc(2, (32, 32), 1 / 32, jacobian_reuse=-1), 10)
+    assert mpm.mpm_footprint_bytes(mpm.make_desc(2, (32, 32), 1 / 32, jacobian_reuse=3), 1024) == fp
 
 
 def test_footprint_counts_the_krylov_and_preconditioner_storage():
