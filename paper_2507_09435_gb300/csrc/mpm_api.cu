@@ -108,6 +108,9 @@ struct mpm_scene {
   void* d_KT = nullptr;            // adjoint: transposed Jacobian scratch
   unsigned* d_pmask = nullptr;     // per-row slot-presence bits of the Jacobian pattern
   double* d_red = nullptr;         // Krylov reduction slots (krylov_red_slots(cap))
+  double* d_fp = nullptr;          // per-particle residual contributions (3^dim nodes x B per particle)
+  double* d_norm_part = nullptr;   // residual-norm block sums (norm_part_slots(cap))
+  unsigned* d_norm_ticket = nullptr;
   int* d_cellpos = nullptr;        // position of each occupied cell in d_cells (exclusive scan)
   void* d_cblk = nullptr;          // 3D assembly: 27 x 27 x 9 block values per occupied cell
   long long cblk_cap = 0;          // cells d_cblk has room for
@@ -213,7 +216,8 @@ size_t footprint(const mpm_scene_desc* d, int np) {
   const long long nn = nnode_of(d), ndof = nn * B;
   const int nbe = D == 2 ? 4 : 6, nF = D * D;
   const int up_extra = (B > D) ? 2 : 0;   // kdt, pp
-  size_t part = (size_t)np * (2 * (D + 2 + 2 + nbe + 1 + nF + up_extra) * 8 + 2 * 2 * 4 + 3 * 4);
+  size_t part = (size_t)np * (2 * (D + 2 + 2 + nbe + 1 + nF + up_extra) * 8 + 2 * 2 * 4 + 3 * 4 +
+                              (D == 3 ? 27 : 9) * B * 8);   // + the residual contributions
   size_t grid = (size_t)nn * (7 * 4 + 8) + (size_t)ndof * (4 * 8 + 1);
   size_t tang = (size_t)np * B * NPHI * B * NPHI * T;
   long long pad = 2 + 2LL * (d->n[0] + 1) + (D == 3 ? 2LL * (d->n[0] + 1) * (d->n[1] + 1) : 0);
@@ -269,13 +273,16 @@ void ensure_capacity(mpm_scene* s, int nrow) {
   s->dfree(s->d_dinv);
   s->dfree(s->d_pmask);
   s->dfree(s->d_red);
+  s->dfree(s->d_norm_part);
   s->d_K = nullptr;
   s->d_dinv = nullptr;
   s->d_pmask = nullptr;
   s->d_red = nullptr;
+  s->d_norm_part = nullptr;
   const size_t S = stencil_slots(s->D), DD = (size_t)s->B * s->B;
   s->d_pmask = s->dalloc<unsigned>((size_t)cap * pmask_words(s->D));
   s->d_red = s->dalloc<double>((size_t)krylov_red_slots(cap));
+  s->d_norm_part = s->dalloc<double>((size_t)norm_part_slots(cap));
   if (s->mixed) {
     s->d_K = s->dalloc<float>((size_t)cap * S * DD);
     s->d_dinv = s->dalloc<float>((size_t)(cap + 4) * DD * s->seg);
@@ -336,23 +343,26 @@ GatherArrays gather_list(mpm_scene* s, const DevParticles& src, DevParticles& ds
 template <int D, class T, int B>
 void launch_particle_pass(mpm_scene* s, int mode, int* nplastic) {
   if constexpr (B > D)
-    ck(launch_particles_up<D, T>(s->P, s->G, s->d_mats, s->d_du, s->d_r, s->d_grav, (T*)s->d_A, mode, s->psc,
+    ck(launch_particles_up<D, T>(s->P, s->G, s->d_mats, s->d_du, s->d_fp, s->d_grav, (T*)s->d_A, mode, s->psc,
                                  s->d_err, nplastic, s->st),
        "u-p particle kernel");
   else
-    ck(launch_particles<D, T>(s->P, s->G, s->d_mats, s->d_du, s->d_r, s->d_grav, (T*)s->d_A, mode, s->d_err,
+    ck(launch_particles<D, T>(s->P, s->G, s->d_mats, s->d_du, s->d_fp, s->d_grav, (T*)s->d_A, mode, s->d_err,
                               nplastic, s->st),
        "particle kernel");
 }
 
 template <int D, class T, int B>
 void residual_pass(mpm_scene* s, int mode) {
-  ck(cudaMemsetAsync(s->d_r, 0, s->ndof * sizeof(double), s->st), "memset r");
   ck(cudaMemsetAsync(s->d_nplastic, 0, sizeof(int), s->st), "memset");
   ck(cudaMemsetAsync(s->d_fail, 0, sizeof(double), s->st), "memset");
   launch_particle_pass<D, T, B>(s, mode, s->d_nplastic);
-  ck(cudaMemsetAsync(s->d_norm, 0, sizeof(double), s->st), "memset");
-  ck(launch_norm_free<B>(s->d_r, s->d_rows, s->nrow, s->d_fixed, s->d_norm, s->st), "norm kernel");
+  // the residual of every node, added in a fixed order from the particles'
+  // contributions
+  ck(launch_gather_residual<D, B>(s->G, s->d_cstart, s->d_fp, s->np, s->d_r, s->nnode, s->st), "gather r");
+  ck(launch_norm_free<B>(s->d_r, s->d_rows, s->nrow, s->d_fixed, s->d_norm, s->d_norm_part, s->d_norm_ticket,
+                         s->st),
+     "norm kernel");
   ck(cudaMemcpyAsync(s->h_dbl, s->d_norm, sizeof(double), cudaMemcpyDeviceToHost, s->st), "copy norm");
   ck(cudaMemcpyAsync(s->h_int + 2, s->d_err, 2 * sizeof(int), cudaMemcpyDeviceToHost, s->st), "copy err");
   s->launches += 2;
@@ -390,6 +400,7 @@ void begin_step_impl(mpm_scene* s, mpm_newton_report* rep) {
   ck(launch_cell_keys<D>(s->P, s->G, s->d_key, s->d_count, s->d_rank, s->d_err, st), "cell keys");
   ck(scan_exclusive(s->d_count, s->d_cstart, (int)(nn + 1), s->d_scan_tmp, st), "scan");
   ck(launch_sort_scatter(s->np, s->d_key, s->d_rank, s->d_cstart, s->d_perm, st), "scatter");
+  ck(launch_sort_cells(s->d_cstart, s->d_perm, nn, st), "sort cells");
   GatherArrays g = gather_list(s, s->P, s->Q);
   ck(launch_gather(s->np, s->d_perm, g, st), "gather");
   std::swap(s->P, s->Q);
@@ -1004,7 +1015,8 @@ void adjoint_impl(mpm_scene* s, const double* dL_dU, const double* dL_dx, double
   }
   ck(launch_adjoint_rhs<D, B>(d_g, d_b, s->ndof, s->up ? s->psc : 1.0, st), "rhs");
   ck(cudaMemsetAsync(s->d_norm, 0, sizeof(double), st), "memset");
-  ck(launch_norm_free<B>(d_b, s->d_rows, s->nrow, s->d_fixed, s->d_norm, st), "norm");
+  ck(launch_norm_free<B>(d_b, s->d_rows, s->nrow, s->d_fixed, s->d_norm, s->d_norm_part, s->d_norm_ticket, st),
+     "norm");
   ck(cudaMemcpyAsync(s->h_dbl + 4, s->d_norm, sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
   ck(cudaStreamSynchronize(st), "sync");
   s->launches += 2;
@@ -1103,7 +1115,8 @@ void adjoint_step_impl(mpm_scene* s, const double* dL_dU, const double* dL_dx, d
      "commit vjp");
   ck(launch_adjoint_rhs<D, B>(d_g, d_b, s->ndof, psc, st), "rhs");
   ck(cudaMemsetAsync(s->d_norm, 0, sizeof(double), st), "memset");
-  ck(launch_norm_free<B>(d_b, s->d_rows, s->nrow, s->d_fixed, s->d_norm, st), "norm");
+  ck(launch_norm_free<B>(d_b, s->d_rows, s->nrow, s->d_fixed, s->d_norm, s->d_norm_part, s->d_norm_ticket, st),
+     "norm");
   ck(cudaMemcpyAsync(s->h_dbl + 4, s->d_norm, sizeof(double), cudaMemcpyDeviceToHost, st), "copy");
   ck(cudaStreamSynchronize(st), "sync");
   s->launches += 6;
@@ -1437,6 +1450,9 @@ mpm_status mpm_create_scene(const mpm_scene_desc* desc, int np, const double* x,
     else s->d_vec = s->dalloc<double>(9 * s->vlen);
     ck(cudaMemsetAsync(s->d_vec, 0, 9 * s->vlen * T, s->st), "memset");
     s->d_S = s->dalloc<KrylovScalars>(1);
+    s->d_norm_ticket = s->dalloc<unsigned>(1);
+    ck(cudaMemsetAsync(s->d_norm_ticket, 0, sizeof(unsigned), s->st), "memset");
+    s->d_fp = s->dalloc<double>((size_t)np * (s->D == 3 ? 27 : 9) * s->B);
     if (s->mg) mg_create(s);
     if (desc->krylov == MPM_GMRES) {
       s->gm = desc->gmres_restart > 0 ? std::min(std::max(desc->gmres_restart, 2), GMRES_MMAX) : 30;

@@ -302,10 +302,21 @@ template <int D>
 cudaError_t launch_pattern_bits(const DevGrid& G, const int* rows, int nrow_host, const int* node2row,
                                 const int* count, unsigned* bits, cudaStream_t st);
 
-// free-DOF residual norm^2 into *out (device double, accumulated)
+// free-DOF residual norm^2 into *out (device double, written; the sum in an
+// order fixed by the grid, through part and ticket: ticket zero on entry,
+// left zero)
 template <int D>
 cudaError_t launch_norm_free(const double* r, const int* rows, int nrow_host, const uint8_t* fixed,
-                             double* out, cudaStream_t st);
+                             double* out, double* part, unsigned* ticket, cudaStream_t st);
+// scratch of launch_norm_free: one double per block of 256 rows
+inline long long norm_part_slots(long long rows) { return (rows + 255) / 256 + 1; }
+// r on every grid node from the particles' contributions fp (B values per
+// node, the k_particles / k_particles_up layout), in a fixed order
+template <int D, int B>
+cudaError_t launch_gather_residual(const DevGrid& G, const int* cstart, const double* fp, int np, double* r,
+                                   long long nn, cudaStream_t st);
+// the particles of every cell in increasing source index (after the scatter)
+cudaError_t launch_sort_cells(const int* cstart, int* perm, long long ncells, cudaStream_t st);
 
 // Geometric multigrid preconditioner (mpm_mg.cu).  One level of the
 // hierarchy: the level's grid (nz1 = 1 in 2D), its stencil-BSR matrix (seg 1

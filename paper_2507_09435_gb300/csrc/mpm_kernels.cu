@@ -250,16 +250,20 @@ cudaError_t launch_apply_bc(const uint8_t* fixed, const double* bcval, const int
 
 // ---------------------------------------------------------------- particle pass
 // One thread per particle (sorted by cell): G2P of du -> dF; constitutive
-// update -> P = V0 tau dF^-T; P2G: r_i += P grad w_ip - w_ip m_p g.
-// MODE 1 also writes the dim^4 consistent-tangent entries of the particle
-// (SoA: A[k*np + p]).  MODE 2 commits the state instead of scattering.
+// update -> P = V0 tau dF^-T; the particle's contributions to the residual,
+// P grad w_ip - w_ip m_p g for the 3^dim nodes i of its stencil, stored as
+// fp[(k*D + a)*np + p] (k = kx + 3 ky + 9 kz; zeros for a particle that
+// contributes nothing), which k_gather_residual adds per node in a fixed
+// order.  MODE 1 also writes the dim^4 consistent-tangent entries of the
+// particle (SoA: A[k*np + p]).  MODE 2 commits the state instead.
 template <int D, class T, int MODE>
 __global__ void __launch_bounds__(128) k_particles(DevParticles P, DevGrid G, const MatC* __restrict__ mats,
-                                                   const double* __restrict__ du, double* r,
+                                                   const double* __restrict__ du, double* fp,
                                                    const double* __restrict__ grav, T* A, int* err,
                                                    int* nplastic) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   bool live = p < P.np;
+  bool wrote = false;
   int plastic = 0;
   Spline1 sp[3];
   if (live) {
@@ -383,19 +387,25 @@ __global__ void __launch_bounds__(128) k_particles(DevParticles P, DevGrid G, co
               g[0] = sp[0].dN[kx] * sp[1].N[ky] * sp[2].N[kz] * G.ih;
               g[1] = sp[0].N[kx] * sp[1].dN[ky] * sp[2].N[kz] * G.ih;
               g[2] = sp[0].N[kx] * sp[1].N[ky] * sp[2].dN[kz] * G.ih;
+              const int kk = kx + 3 * (ky + 3 * kz);
 #pragma unroll
               for (int a = 0; a < D; ++a) {
                 double f = -w * gv[a];
 #pragma unroll
                 for (int c = 0; c < D; ++c) f += st.P[a][c] * g[c];
                 finite = finite && isfinite(f);
-                atomicAdd(&r[node * D + a], f);
+                fp[((long long)kk * D + a) * P.np + p] = f;
               }
             }
+        wrote = true;
         if (!finite) atomicOr(err, ERRF_NONFINITE);
         if (MODE == 1) tangent<D, T>(st, V0, A + p, (long long)P.np);
       }
     }
+  }
+  if (MODE != 2 && p < P.np && !wrote) {
+    constexpr int NS = (D == 3) ? 27 : 9;
+    for (int k = 0; k < NS * D; ++k) fp[(long long)k * P.np + p] = 0.0;
   }
   if (nplastic) {
     unsigned bal = __ballot_sync(0xffffffffu, plastic);
@@ -900,11 +910,15 @@ cudaError_t launch_pattern_bits(const DevGrid& G, const int* rows, int nrow_host
   return cudaGetLastError();
 }
 
-// ||r||^2 over free DOFs of active rows.
+// ||r||^2 over free DOFs of active rows, summed in an order fixed by the
+// grid: each block stores its sum in part[block] and takes a ticket; the
+// block that takes the last one adds the stored sums in block order, writes
+// *out and resets the ticket.
 template <int D>
 __global__ void k_norm_free(const double* __restrict__ r, const int* __restrict__ rows, int nrow,
-                            const uint8_t* __restrict__ fixed, double* out) {
+                            const uint8_t* __restrict__ fixed, double* out, double* part, unsigned* ticket) {
   __shared__ double ws[TPB / 32];
+  __shared__ int last;
   int row = blockIdx.x * blockDim.x + threadIdx.x;
   double s = 0.0;
   if (row < nrow) {
@@ -918,17 +932,95 @@ __global__ void k_norm_free(const double* __restrict__ r, const int* __restrict_
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = (threadIdx.x < TPB / 32) ? ws[threadIdx.x] : 0.0;
-    v = warp_sum(v);
-    if (threadIdx.x == 0) atomicAdd(out, v);
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < TPB / 32; ++w) v += ws[w];
+    part[blockIdx.x] = v;
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double t = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += TPB) t += __ldcg(&part[b]);
+  t = warp_sum(t);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < TPB / 32; ++w) v += ws[w];
+    *out = v;
+    *ticket = 0u;
   }
 }
 template <int D>
 cudaError_t launch_norm_free(const double* r, const int* rows, int nrow_host, const uint8_t* fixed,
-                             double* out, cudaStream_t st) {
-  if (nrow_host == 0) return cudaSuccess;
-  k_norm_free<D><<<nblocks(nrow_host), TPB, 0, st>>>(r, rows, nrow_host, fixed, out);
+                             double* out, double* part, unsigned* ticket, cudaStream_t st) {
+  if (nrow_host == 0) return cudaMemsetAsync(out, 0, sizeof(double), st);
+  k_norm_free<D><<<nblocks(nrow_host), TPB, 0, st>>>(r, rows, nrow_host, fixed, out, part, ticket);
+  return cudaGetLastError();
+}
+
+// r at every grid node: the contributions fp of the particles of the 3^dim
+// cells i - k that reach it, added in cell order (k = kx + 3 ky + 9 kz) and,
+// within a cell, in the particles' sorted order, so that r does not depend
+// on the order in which threads run.  B values per node.
+template <int D, int B>
+__global__ void k_gather_residual(DevGrid G, const int* __restrict__ cstart, const double* __restrict__ fp,
+                                  int np, double* r, long long nn) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= nn) return;
+  const int ix = (int)(i % G.nx1), iy = (int)((i / G.nx1) % G.ny1), iz = (int)(i / ((long long)G.nx1 * G.ny1));
+  constexpr int KZ = (D == 3) ? 3 : 1;
+  double acc[B];
+#pragma unroll
+  for (int a = 0; a < B; ++a) acc[a] = 0.0;
+  for (int kz = 0; kz < KZ; ++kz)
+    for (int ky = 0; ky < 3; ++ky)
+      for (int kx = 0; kx < 3; ++kx) {
+        const int cx = ix - kx, cy = iy - ky, cz = iz - kz;
+        if (cx < 0 || cy < 0 || cz < 0) continue;
+        const long long cell = cx + (long long)G.nx1 * (cy + (long long)G.ny1 * cz);
+        const int p0 = cstart[cell], p1 = cstart[cell + 1];
+        const double* f = fp + (long long)(kx + 3 * (ky + 3 * kz)) * B * np;
+        for (int p = p0; p < p1; ++p)
+#pragma unroll
+          for (int a = 0; a < B; ++a) acc[a] += f[(long long)a * np + p];
+      }
+#pragma unroll
+  for (int a = 0; a < B; ++a) r[i * B + a] = acc[a];
+}
+template <int D, int B>
+cudaError_t launch_gather_residual(const DevGrid& G, const int* cstart, const double* fp, int np, double* r,
+                                   long long nn, cudaStream_t st) {
+  if (nn == 0) return cudaSuccess;
+  k_gather_residual<D, B><<<nblocks(nn), TPB, 0, st>>>(G, cstart, fp, np, r, nn);
+  return cudaGetLastError();
+}
+
+// The particles of each cell in increasing source index (perm[dst] = src):
+// the counting sort places a cell's particles in arrival order, which this
+// makes independent of the order in which threads ran.  One thread per cell,
+// insertion sort (cells hold a few dozen particles at most).
+__global__ void k_sort_cells(const int* __restrict__ cstart, int* perm, long long ncells) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  const int p0 = cstart[c], p1 = cstart[c + 1];
+  for (int a = p0 + 1; a < p1; ++a) {
+    const int v = perm[a];
+    int b = a - 1;
+    while (b >= p0 && perm[b] > v) {
+      perm[b + 1] = perm[b];
+      --b;
+    }
+    perm[b + 1] = v;
+  }
+}
+cudaError_t launch_sort_cells(const int* cstart, int* perm, long long ncells, cudaStream_t st) {
+  if (ncells == 0) return cudaSuccess;
+  k_sort_cells<<<nblocks(ncells), TPB, 0, st>>>(cstart, perm, ncells);
   return cudaGetLastError();
 }
 
@@ -944,9 +1036,15 @@ cudaError_t launch_norm_free(const double* r, const int* rows, int nrow_host, co
   template cudaError_t launch_pattern_bits<D>(const DevGrid&, const int*, int, const int*, const int*,   \
                                               unsigned*, cudaStream_t);                                  \
   template cudaError_t launch_norm_free<D>(const double*, const int*, int, const uint8_t*, double*,      \
-                                           cudaStream_t);
+                                           double*, unsigned*, cudaStream_t);
 MPM_INST_D(2)
 MPM_INST_D(3)
+template cudaError_t launch_gather_residual<2, 2>(const DevGrid&, const int*, const double*, int, double*, long long,
+                                                  cudaStream_t);
+template cudaError_t launch_gather_residual<2, 3>(const DevGrid&, const int*, const double*, int, double*, long long,
+                                                  cudaStream_t);
+template cudaError_t launch_gather_residual<3, 3>(const DevGrid&, const int*, const double*, int, double*, long long,
+                                                  cudaStream_t);
 
 #define MPM_INST_DT(D, T)                                                                               \
   template cudaError_t launch_particles<D, T>(const DevParticles&, const DevGrid&, const MatC*,          \

@@ -30,12 +30,13 @@ constexpr int UP_TPB = 128;
 // K_ij[a][b] = sum_c,e phi_i[c] A[a c b e] phi_j[e], phi = (grad w, w).
 template <int D, class T, int MODE>
 __global__ void __launch_bounds__(UP_TPB) k_particles_up(DevParticles P, DevGrid G, const MatC* __restrict__ mats,
-                                                         const double* __restrict__ U, double* r,
+                                                         const double* __restrict__ U, double* fp,
                                                          const double* __restrict__ grav, T* A, double psc,
                                                          int* err, int* nplastic) {
   constexpr int B = D + 1, NPHI = D + 1;
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   bool live = p < P.np;
+  bool wrote = false;
   int plastic = 0;
   Spline1 sp[3];
   if (live) {
@@ -178,27 +179,28 @@ __global__ void __launch_bounds__(UP_TPB) k_particles_up(DevParticles P, DevGrid
           for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
             for (int kx = 0; kx < 3; ++kx) {
-              const long long node = nb + kx + (long long)G.nx1 * (ky + (long long)G.ny1 * kz);
               const double w = sp[0].N[kx] * sp[1].N[ky] * sp[2].N[kz];
               double g[3];
               g[0] = sp[0].dN[kx] * sp[1].N[ky] * sp[2].N[kz] * G.ih;
               g[1] = sp[0].N[kx] * sp[1].dN[ky] * sp[2].N[kz] * G.ih;
               g[2] = sp[0].N[kx] * sp[1].N[ky] * sp[2].dN[kz] * G.ih;
+              double* fk = fp + (long long)(kx + 3 * (ky + 3 * kz)) * B * P.np + p;
 #pragma unroll
               for (int a = 0; a < D; ++a) {
                 double f = -w * gv[a];
 #pragma unroll
                 for (int c = 0; c < D; ++c) f += Pt[a][c] * g[c];
                 finite = finite && isfinite(f);
-                atomicAdd(&r[node * B + a], f);
+                fk[(long long)a * P.np] = f;
               }
               double q = w * vol;
 #pragma unroll
               for (int c = 0; c < D; ++c) q += fl[c] * g[c];
               q *= psc;
               finite = finite && isfinite(q);
-              atomicAdd(&r[node * B + D], q);
+              fk[(long long)D * P.np] = q;
             }
+        wrote = true;
         if (!finite) atomicOr(err, ERRF_NONFINITE);
         if (MODE == 1) {
           // effective-stress tangent of the single-phase path, then the
@@ -243,6 +245,10 @@ __global__ void __launch_bounds__(UP_TPB) k_particles_up(DevParticles P, DevGrid
         }
       }
     }
+  }
+  if (MODE != 2 && p < P.np && !wrote) {
+    constexpr int NS = (D == 3) ? 27 : 9;
+    for (int k = 0; k < NS * B; ++k) fp[(long long)k * P.np + p] = 0.0;
   }
   if (nplastic) {
     unsigned bal = __ballot_sync(0xffffffffu, plastic);

@@ -5,8 +5,10 @@ the host (no GPU fault):
   caller-owned CUDA tensors exactly what the host getters return (u-p
   pressure in physical units), and mpm_set_dirichlet_dev stages the same step
   as mpm_set_dirichlet;
-* the residual at a given increment is reproducible to FP64 summation order
-  and the FP32 Jacobian to FP32 summation order;
+* the residual at a given increment is reproducible bit for bit (the
+  particles' contributions are added per node in a fixed order), and so are
+  the 3D Jacobian and a whole 3D load step with its Krylov iteration counts;
+  the 2D Jacobian to FP32 summation order;
 * an infinite Young's modulus injected into one particle is reported as
   MPM_ERR_NONFINITE (or MPM_ERR_RETURN_MAP), a Newton limit of one iteration as
   MPM_ERR_NOT_CONVERGED with the particles left uncommitted, and the scene
@@ -71,8 +73,9 @@ def test_dirichlet_dev_stages_the_same_step(k):
             assert rep.converged
         out.append(gs.particles()["x"])
         gs.close()
-    # the two runs differ only by the summation order of FP64 atomics, which
-    # the Newton iterations carry to about their tolerance
+    # the two runs differ only by the summation order of the 2D assembly's
+    # shared-memory sums, which the Newton iterations carry to about their
+    # tolerance
     x0 = np.zeros_like(out[0])
     x0[:, :sc.dim] = sc.x[:, :sc.dim]
     assert np.abs(out[0] - out[1]).max() <= 1e-8 * np.abs(out[0] - x0).max()
@@ -91,17 +94,22 @@ def test_dirichlet_dev_rejects_out_of_range_index():
     gs.close()
 
 
-def test_residual_and_assembly_reproducible():
-    """Two scenes in the same state, the same increment: the residuals agree to
-    FP64 summation order (node sums use atomics) and the assembled FP32
-    Jacobians to FP32 summation order (the assembly has no atomics, but the
-    counting sort places the particles of a cell in arrival order, which the
-    per-node sums follow)."""
-    sc = S.footing(nx=48, ny=24, h=0.5, nsteps=20, settle_frac=0.1)
+@pytest.mark.parametrize("dim", [2, 3])
+def test_residual_and_assembly_reproducible(dim):
+    """Two scenes in the same state, the same increment: the residuals agree
+    bit for bit (the cells' particles in source order, each node's
+    contributions added in cell and particle order); the assembled FP32
+    Jacobians bit for bit in 3D (cell block products, then each row's 27
+    cells in a fixed order) and to FP32 summation order in 2D (the tile
+    kernel adds its particles' blocks in shared memory with atomics)."""
+    if dim == 2:
+        sc, st = S.footing(nx=48, ny=24, h=0.5, nsteps=20, settle_frac=0.1), 1
+    else:
+        sc, st = S.column_collapse_3d(nx=12, ny=12, nz=12, h=0.1, col=(4, 4, 6), nsteps=6, pc_mean=-1.2e4, E=1e6), 0
     res = []
     for _ in range(2):
         gs = mpm.GpuScene(sc, precision=mpm.MPM_MIXED, newton_tol=1e-8)
-        gs.begin(sc.steps[1])
+        gs.begin(sc.steps[st])
         rng = np.random.default_rng(7)
         du = gs.du()
         du = du + 1e-5 * rng.standard_normal(du.shape)
@@ -110,16 +118,39 @@ def test_residual_and_assembly_reproducible():
         res.append((gs.residual(), gs.jacobian_bsr()))
         gs.close()
     (r0, J0), (r1, J1) = res
-    scale = np.abs(r0).max()
-    assert np.abs(r0 - r1).max() <= 1e-13 * scale
+    assert np.array_equal(r0, r1)
     for a, b in zip(J0[:3], J1[:3]):
         assert np.array_equal(a, b)     # the same pattern
     v0, v1 = J0[3], J1[3]
+    if dim == 3:
+        assert np.array_equal(v0, v1)
+        return
     row_of_block = np.repeat(np.arange(len(J0[0])), np.diff(J0[1]))
     row_scale = np.zeros(len(J0[0]))
     np.maximum.at(row_scale, row_of_block, np.abs(v0).reshape(len(v0), -1).max(axis=1))
     err = np.abs(v0 - v1).reshape(len(v0), -1).max(axis=1) / row_scale[row_of_block]
     assert err.max() <= 1e-6, err.max()
+
+
+def test_3d_load_steps_reproducible():
+    """Three load steps of a 3D Cam-Clay column in mixed precision, solved
+    twice on fresh scenes: the same Newton and BiCGStab iteration counts and
+    the same increments bit for bit (the residual, the assembly and the
+    Krylov dot products are all summed in fixed orders)."""
+    sc = S.column_collapse_3d(nx=12, ny=12, nz=12, h=0.1, col=(4, 4, 6), nsteps=6, pc_mean=-1.2e4, E=1e6)
+    runs = []
+    for _ in range(2):
+        gs = mpm.GpuScene(sc, precision=mpm.MPM_MIXED, newton_tol=1e-8)
+        counts = []
+        for stp in sc.steps[:3]:
+            rep = gs.solve_step(stp)
+            assert rep.converged
+            counts.append([rep.krylov_iters[i] for i in range(rep.newton_iters)])
+        runs.append((counts, gs.du(), gs.particles(be=False, pc=False, F=False, tau=False)["x"]))
+        gs.close()
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1], runs[1][1])
+    assert np.array_equal(runs[0][2], runs[1][2])
 
 
 def test_injected_infinite_modulus_is_reported():
