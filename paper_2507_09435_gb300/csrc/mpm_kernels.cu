@@ -269,7 +269,14 @@ __global__ void __launch_bounds__(128) k_particles(DevParticles P, DevGrid G, co
   if (live) {
 #pragma unroll
     for (int a = 0; a < D; ++a) sp[a] = spline1((P.x[a][p] - G.o[a]) / G.h);
-    if (D == 2) { sp[2].base = 0; sp[2].N[0] = 1.0; sp[2].dN[0] = 0.0; }
+    if (D == 2) {
+      sp[2].base = 0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        sp[2].N[k] = (k == 0) ? 1.0 : 0.0;
+        sp[2].dN[k] = 0.0;
+      }
+    }
     bool inside = true;
 #pragma unroll
     for (int a = 0; a < D; ++a) inside = inside && sp[a].base >= 0 && sp[a].base <= G.n[a] - 2;
@@ -286,16 +293,22 @@ __global__ void __launch_bounds__(128) k_particles(DevParticles P, DevGrid G, co
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int c = 0; c < 3; ++c) st.F[a][c] = (a == c) ? 1.0 : 0.0;
+    // B-spline factors with 1/h folded into the derivatives, and the weight
+    // gradient of node (kx, ky, kz) in product form: grad w = (dNx Ny Nz,
+    // Nx dNy Nz, Nx Ny dNz), the y-z products formed once per (ky, kz)
+    double dh[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) dh[a][k] = sp[a].dN[k] * G.ih;
     for (int kz = 0; kz < KZ; ++kz)
 #pragma unroll
-      for (int ky = 0; ky < 3; ++ky)
+      for (int ky = 0; ky < 3; ++ky) {
+        const double nyz = sp[1].N[ky] * sp[2].N[kz], dyz = dh[1][ky] * sp[2].N[kz], ydz = sp[1].N[ky] * dh[2][kz];
 #pragma unroll
         for (int kx = 0; kx < 3; ++kx) {
           const long long node = nb + kx + (long long)G.nx1 * (ky + (long long)G.ny1 * kz);
-          double g[3];
-          g[0] = sp[0].dN[kx] * sp[1].N[ky] * sp[2].N[kz] * G.ih;
-          g[1] = sp[0].N[kx] * sp[1].dN[ky] * sp[2].N[kz] * G.ih;
-          g[2] = sp[0].N[kx] * sp[1].N[ky] * sp[2].dN[kz] * G.ih;
+          const double g[3] = {dh[0][kx] * nyz, sp[0].N[kx] * dyz, sp[0].N[kx] * ydz};
 #pragma unroll
           for (int a = 0; a < D; ++a) {
             double u = du[node * D + a];
@@ -303,6 +316,7 @@ __global__ void __launch_bounds__(128) k_particles(DevParticles P, DevGrid G, co
             for (int c = 0; c < D; ++c) st.F[a][c] += u * g[c];
           }
         }
+      }
     // start-of-step elastic left Cauchy-Green
     if (D == 2) {
       st.bn[0][0] = P.be[0][p]; st.bn[1][1] = P.be[1][p]; st.bn[2][2] = P.be[2][p];
@@ -378,15 +392,13 @@ __global__ void __launch_bounds__(128) k_particles(DevParticles P, DevGrid G, co
         bool finite = true;
         for (int kz = 0; kz < KZ; ++kz)
 #pragma unroll
-          for (int ky = 0; ky < 3; ++ky)
+          for (int ky = 0; ky < 3; ++ky) {
+            const double nyz = sp[1].N[ky] * sp[2].N[kz], dyz = dh[1][ky] * sp[2].N[kz],
+                         ydz = sp[1].N[ky] * dh[2][kz];
 #pragma unroll
             for (int kx = 0; kx < 3; ++kx) {
-              const long long node = nb + kx + (long long)G.nx1 * (ky + (long long)G.ny1 * kz);
-              double w = sp[0].N[kx] * sp[1].N[ky] * sp[2].N[kz];
-              double g[3];
-              g[0] = sp[0].dN[kx] * sp[1].N[ky] * sp[2].N[kz] * G.ih;
-              g[1] = sp[0].N[kx] * sp[1].dN[ky] * sp[2].N[kz] * G.ih;
-              g[2] = sp[0].N[kx] * sp[1].N[ky] * sp[2].dN[kz] * G.ih;
+              const double w = sp[0].N[kx] * nyz;
+              const double g[3] = {dh[0][kx] * nyz, sp[0].N[kx] * dyz, sp[0].N[kx] * ydz};
               const int kk = kx + 3 * (ky + 3 * kz);
 #pragma unroll
               for (int a = 0; a < D; ++a) {
@@ -397,6 +409,7 @@ __global__ void __launch_bounds__(128) k_particles(DevParticles P, DevGrid G, co
                 fp[((long long)kk * D + a) * P.np + p] = f;
               }
             }
+          }
         wrote = true;
         if (!finite) atomicOr(err, ERRF_NONFINITE);
         if (MODE == 1) tangent<D, T>(st, V0, A + p, (long long)P.np);
