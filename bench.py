@@ -111,10 +111,10 @@ def parse():
 # DMUL) on the workload named beside each (profiles/k_particles_*.md); the
 # count depends on the fraction of particles on a return-map branch
 FP64_FLOP_PER_PARTICLE = {
-    # profiles/k_particles_column3d_393k_mixed.md: 891 M per launch on the
+    # profiles/k_particles_column3d_393k_mixed.md: 714 M per launch on the
     # 393k column's first load step (nearly all particles elastic); plastic
     # returns add operations, so later ramp steps are undercounted
-    "column3d": 2266, "column3d_stated": 2266,
+    "column3d": 1815, "column3d_stated": 1815,
 }
 
 # ncu-measured DRAM traffic of one Krylov iteration per workload /
