@@ -384,10 +384,10 @@ cudaError_t launch_dirichlet_in(int n, const long long* dof, const double* value
 template <int D, class T>
 struct KrylovVecs {
   T *x, *r, *rhat, *p, *phat, *v, *s, *shat, *t;
-  double* red;   // reduction slots: 3 per block of the row grid (krylov_red_slots)
+  double* red;   // reduction slots: 5 per block of the row grid (krylov_red_slots)
 };
 // slots of KrylovVecs::red for a matrix of row capacity cap
-inline long long krylov_red_slots(long long cap) { return 3 * ((cap + KRYLOV_TPB - 1) / KRYLOV_TPB); }
+inline long long krylov_red_slots(long long cap) { return 5 * ((cap + KRYLOV_TPB - 1) / KRYLOV_TPB); }
 template <int D, class T, int B = D>
 cudaError_t launch_bicgstab_init(DevMatrix<T> K, const double* res, const uint8_t* fixed, KrylovVecs<D, T> v,
                                  KrylovScalars* S, double tol2, int maxit, int nblk, cudaStream_t st);

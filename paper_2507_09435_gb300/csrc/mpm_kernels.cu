@@ -620,13 +620,15 @@ __global__ void __launch_bounds__(ASM_TPB) k_assemble(DevParticles P, DevGrid G,
           g[3] = (D == 3 && NPHI > D) ? wx[kx] * wy[ky] * wz[kz] : (T)0;
         }
         __syncthreads();
-        // tasks: (tile node i with y/z overlap, x offset kx of i in the cell)
-        const int ntask = TX * ny_ov * nz_ov * 3;
-        for (int task = warp; task < ntask; task += ASM_TPB / 32) {
-          const int kx = task % 3;
-          const int ixl = (task / 3) % TX;
-          const int iyl = (task / (3 * TX)) % ny_ov;
-          const int izl = task / (3 * TX * ny_ov);
+        // tasks: tile nodes i with y/z overlap, one warp each, taking the x
+        // offsets kx of i in the cells in a fixed order (the warp alone adds
+        // into i's blocks: no atomics, the same sums for any warp order)
+        const int ntask = TX * ny_ov * nz_ov;
+        for (int task = warp; task < ntask; task += ASM_TPB / 32)
+        for (int kx = 0; kx < 3; ++kx) {
+          const int ixl = task % TX;
+          const int iyl = (task / TX) % ny_ov;
+          const int izl = task / (TX * ny_ov);
           const int ix = tx0 + ixl, iy = iy_lo + iyl, iz = iz_lo + izl;
           const int cx = ix - kx;
           if (cx < cx_lo || cx > cx_hi) continue;
@@ -674,8 +676,9 @@ __global__ void __launch_bounds__(ASM_TPB) k_assemble(DevParticles P, DevGrid G,
             const int jx = j % 3, jy = j / 3;
             T* blk = arow + slot_of<2>(jx - kx, jy - ky, 0) * D2;
 #pragma unroll
-            for (int e = 0; e < D2; ++e) atomicAdd(blk + e, kb[e]);
+            for (int e = 0; e < D2; ++e) blk[e] += kb[e];
           }
+          __syncwarp();
         }
       }
     }

@@ -113,21 +113,22 @@ __device__ __forceinline__ bool grid_sum(Acc<T> v[NV], double* red_raw, unsigned
   __syncthreads();
   if (!last) return false;
   __threadfence();
+  // one sum at a time, RU of its block sums in flight (few registers: this
+  // code shares the kernel's register allocation)
   Acc<T> t[NV];
 #pragma unroll
-  for (int k = 0; k < NV; ++k) t[k] = Acc<T>::zero();
-  for (int q0 = threadIdx.x; q0 < nb; q0 += KTPB * RU) {
-    Acc<T> l[NV][RU];
+  for (int k = 0; k < NV; ++k) {
+    t[k] = Acc<T>::zero();
+    for (int q0 = threadIdx.x; q0 < nb; q0 += KTPB * RU) {
+      Acc<T> l[RU];
 #pragma unroll
-    for (int u = 0; u < RU; ++u) {
-      const int q = q0 + u * KTPB;
+      for (int u = 0; u < RU; ++u) {
+        const int q = q0 + u * KTPB;
+        l[u] = (q < nb) ? Acc<T>::load_l2(&red[k * nb + q]) : Acc<T>::zero();
+      }
 #pragma unroll
-      for (int k = 0; k < NV; ++k) l[k][u] = (q < nb) ? Acc<T>::load_l2(&red[k * nb + q]) : Acc<T>::zero();
+      for (int u = 0; u < RU; ++u) t[k].add(l[u]);
     }
-#pragma unroll
-    for (int u = 0; u < RU; ++u)
-#pragma unroll
-      for (int k = 0; k < NV; ++k) t[k].add(l[k][u]);
   }
 #pragma unroll
   for (int k = 0; k < NV; ++k)
@@ -282,9 +283,23 @@ __global__ void __launch_bounds__(KTPB) k_bicg_B(DevGrid G, DevMatrix<T> K, Kryl
   }
 }
 
-// C: s = r - alpha v; shat = M^-1 s; (s,s), (rhat,s).
+// C: s = r - alpha v; shat = M^-1 s (elementwise: its dot products (s,s) and
+// (rhat,s) are taken by D, which reads s anyway).  The row's r and v are
+// loaded before the scalars, so that the two latencies overlap.
 template <int D, class T, int B>
 __global__ void __launch_bounds__(KTPB) k_bicg_C(DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nrow = *K.nrow;
+  long long i = 0;
+  T rr_[B], vv_[B];
+  if (row < nrow) {
+    i = K.rows[row];
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+      rr_[a] = v.r[i * B + a];
+      vv_[a] = v.v[i * B + a];
+    }
+  }
   if (bicg_over(S)) return;
   if (S->c_break) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -294,38 +309,27 @@ __global__ void __launch_bounds__(KTPB) k_bicg_C(DevMatrix<T> K, KrylovVecs<D, T
     return;
   }
   const T ta = scal<T>(S->alpha, S->alpha_f);
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  const unsigned live = __ballot_sync(0xffffffffu, row < *K.nrow);
-  Acc<T> acc[2] = {Acc<T>::zero(), Acc<T>::zero()};
-  if (row < *K.nrow) {
-    const long long i = K.rows[row];
-    T s[B], z[B];
+  const unsigned live = __ballot_sync(0xffffffffu, row < nrow);
+  if (row < nrow) {
+    T sv[B], z[B];
 #pragma unroll
     for (int a = 0; a < B; ++a) {
-      const long long d = i * B + a;
-      s[a] = v.r[d] - ta * v.v[d];
-      v.s[d] = s[a];
-      acc[0].add_prod(s[a], s[a]);
-      acc[1].add_prod(v.rhat[d], s[a]);
+      sv[a] = rr_[a] - ta * vv_[a];
+      v.s[i * B + a] = sv[a];
     }
-    precond_apply<B, T>(K, row, s, z, live);
+    precond_apply<B, T>(K, row, sv, z, live);
 #pragma unroll
     for (int a = 0; a < B; ++a) v.shat[i * B + a] = z[a];
   }
-  double out[2];
-  if (grid_sum<T, 2>(acc, v.red, &S->ticket, out) && threadIdx.x == 0) {
-    S->acc_ss = out[0];
-    S->acc_rs = out[1];
-  }
 }
 
-// D: t = J shat; (t,s), (t,t), (rhat,t); omega, rho', ||r||^2, beta and the
-// stop decision for the next iteration.
+// D: t = J shat; (t,s), (t,t), (rhat,t), (s,s), (rhat,s); omega, rho',
+// ||r||^2, beta and the stop decision for the next iteration.
 template <int D, class T, int B>
 __global__ void __launch_bounds__(KTPB) k_bicg_D(DevGrid G, DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
   if (bicg_over(S)) return;
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  Acc<T> acc[3] = {Acc<T>::zero(), Acc<T>::zero(), Acc<T>::zero()};
+  Acc<T> acc[5] = {Acc<T>::zero(), Acc<T>::zero(), Acc<T>::zero(), Acc<T>::zero(), Acc<T>::zero()};
   if (row < *K.nrow) {
     const long long i = K.rows[row];
     T y[B];
@@ -334,21 +338,26 @@ __global__ void __launch_bounds__(KTPB) k_bicg_D(DevGrid G, DevMatrix<T> K, Kryl
     for (int a = 0; a < B; ++a) {
       const long long d = i * B + a;
       v.t[d] = y[a];
-      acc[0].add_prod(y[a], v.s[d]);
+      const T sd = v.s[d], rh = v.rhat[d];
+      acc[0].add_prod(y[a], sd);
       acc[1].add_prod(y[a], y[a]);
-      acc[2].add_prod(v.rhat[d], y[a]);
+      acc[2].add_prod(rh, y[a]);
+      acc[3].add_prod(sd, sd);
+      acc[4].add_prod(rh, sd);
     }
   }
-  double out[3];
-  if (grid_sum<T, 3>(acc, v.red, &S->ticket, out) && threadIdx.x == 0) {
-    const double ts = out[0], tt = out[1], rt = out[2];
+  double out[5];
+  if (grid_sum<T, 5>(acc, v.red, &S->ticket, out) && threadIdx.x == 0) {
+    const double ts = out[0], tt = out[1], rt = out[2], ss = out[3], rs = out[4];
     S->acc_ts = ts;
     S->acc_tt = tt;
     S->acc_rt = rt;
+    S->acc_ss = ss;
+    S->acc_rs = rs;
     const double omega = (tt > 0.0) ? ts / tt : 0.0;
     const double rho = S->rho, alpha = S->alpha;
-    const double rho_new = S->acc_rs - omega * rt;
-    const double rr = fmax(S->acc_ss - 2.0 * omega * ts + omega * omega * tt, 0.0);
+    const double rho_new = rs - omega * rt;
+    const double rr = fmax(ss - 2.0 * omega * ts + omega * omega * tt, 0.0);
     const double beta = (omega != 0.0 && rho != 0.0) ? (rho_new / rho) * (alpha / omega) : 0.0;
     const int it = S->iter + 1;
     S->iter = it;
@@ -365,21 +374,33 @@ __global__ void __launch_bounds__(KTPB) k_bicg_D(DevGrid G, DevMatrix<T> K, Kryl
 // A: x and r updates; the next search direction p and phat.
 template <int D, class T, int B>
 __global__ void __launch_bounds__(KTPB) k_bicg_A(DevMatrix<T> K, KrylovVecs<D, T> v, KrylovScalars* S) {
+  // the row's vectors are loaded before the scalars (the latencies overlap)
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nrow = *K.nrow;
+  long long i = 0;
+  T xs[B], ph[B], sh[B], ss[B], ts[B], ps[B], vs[B];
+  if (row < nrow) {
+    i = K.rows[row];
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+      const long long d = i * B + a;
+      xs[a] = v.x[d]; ph[a] = v.phat[d]; sh[a] = v.shat[d]; ss[a] = v.s[d];
+      ts[a] = v.t[d]; ps[a] = v.p[d]; vs[a] = v.v[d];
+    }
+  }
   if (bicg_over(S)) return;
   const T ta = scal<T>(S->alpha, S->alpha_f), tw = scal<T>(S->omega, S->omega_f),
           tb = scal<T>(S->beta, S->beta_f);
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  const unsigned live = __ballot_sync(0xffffffffu, row < *K.nrow);
-  if (row < *K.nrow) {
-    const long long i = K.rows[row];
+  const unsigned live = __ballot_sync(0xffffffffu, row < nrow);
+  if (row < nrow) {
     T p[B], z[B];
 #pragma unroll
     for (int a = 0; a < B; ++a) {
       const long long d = i * B + a;
-      v.x[d] += ta * v.phat[d] + tw * v.shat[d];
-      const T rn = v.s[d] - tw * v.t[d];
+      v.x[d] = xs[a] + (ta * ph[a] + tw * sh[a]);
+      const T rn = ss[a] - tw * ts[a];
       v.r[d] = rn;
-      p[a] = rn + tb * (v.p[d] - tw * v.v[d]);
+      p[a] = rn + tb * (ps[a] - tw * vs[a]);
       v.p[d] = p[a];
     }
     precond_apply<B, T>(K, row, p, z, live);
