@@ -410,8 +410,7 @@ void begin_step_impl(mpm_scene* s, mpm_newton_report* rep) {
   ck(launch_compact(s->d_flag, s->d_cellpos, s->d_cells, nn, st), "compact");
   ck(cudaMemcpyAsync(s->h_int + 0, s->d_cellpos + nn, sizeof(int), cudaMemcpyDeviceToHost, st), "copy");
   // nodal mass and active rows
-  ck(cudaMemsetAsync(s->d_M, 0, nn * sizeof(double), st), "memset");
-  ck(launch_mass<D>(s->P, s->G, s->d_M, st), "mass");
+  ck(launch_mass<D>(s->P, s->G, s->d_cstart, s->d_fp, s->d_M, nn, st), "mass");
   ck(cudaMemsetAsync(s->d_flag + nn, 0, sizeof(int), st), "memset");
   ck(launch_active(s->d_M, ACTIVE_REL * s->mmax, s->d_flag, nn, st), "active");
   ck(scan_exclusive(s->d_flag, s->d_pos, (int)(nn + 1), s->d_scan_tmp, st), "scan");
@@ -629,7 +628,9 @@ void mg_setup(mpm_scene* s) {
     for (int l = 0; l + 1 < L; ++l) {
       T* va = (l == 0) ? (T*)s->d_mg_v0 + s->vpad : a.lev[l].b;
       T* vb = (l == 0) ? (T*)s->d_mg_v0 + s->vlen + s->vpad : a.lev[l].z;
-      ck(launch_mg_power<D, T, B>(a.lev[l], a.caps[l], va, vb, s->d_mg_nrm + l * P1, MG_POWER_IT, st), "power");
+      ck(launch_mg_power<D, T, B>(a.lev[l], a.caps[l], va, vb, s->d_mg_nrm + l * P1, MG_POWER_IT, s->d_red,
+                                  s->d_norm_ticket, st),
+         "power");
       s->launches += 1 + MG_POWER_IT;
     }
     s->mg_lam = true;

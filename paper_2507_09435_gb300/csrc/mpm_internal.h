@@ -241,7 +241,8 @@ cudaError_t launch_gather(int np, const int* perm, const GatherArrays& g, cudaSt
 cudaError_t launch_flag_positive(const int* count, int* flag, long long n, cudaStream_t st);
 cudaError_t launch_compact(const int* flag, const int* pos, int* list, long long n, cudaStream_t st);
 template <int D>
-cudaError_t launch_mass(const DevParticles& P, const DevGrid& G, double* M, cudaStream_t st);
+cudaError_t launch_mass(const DevParticles& P, const DevGrid& G, const int* cstart, double* fp, double* M,
+                        long long nnode, cudaStream_t st);
 cudaError_t launch_active(const double* M, double thr, int* flag, long long nnode, cudaStream_t st);
 cudaError_t launch_node2row(const int* flag, const int* pos, int* node2row, int* rows, long long nnode,
                             cudaStream_t st);
@@ -360,7 +361,9 @@ cudaError_t launch_mg_galerkin(MgLevel<T> f, MgLevel<T> c, int nrow_c, cudaStrea
 // power iteration on D^-1 A of a level: nrm[k] = ||v_k||^2 (v_k of unit
 // predecessor), so sqrt(nrm[iters]) estimates lambda_max; va, vb scratch
 template <int D, class T, int B>
-cudaError_t launch_mg_power(MgLevel<T> l, int cap, T* va, T* vb, double* nrm, int iters, cudaStream_t st);
+// part: at least ceil(cap / KRYLOV_TPB) doubles, ticket: zero on entry, left zero
+cudaError_t launch_mg_power(MgLevel<T> l, int cap, T* va, T* vb, double* nrm, int iters, double* part,
+                            unsigned* ticket, cudaStream_t st);
 template <class T>
 cudaError_t launch_mg_scale(T* dinv, long long n, const double* nrm, double c, cudaStream_t st);
 template <int D, class T, int B>

@@ -182,33 +182,41 @@ cudaError_t launch_compact(const int* flag, const int* pos, int* list, long long
 }
 
 // ---------------------------------------------------------------- active set
+// Nodal mass contributions w_ip m_p of each particle, fp[k*np + p] for node k
+// = kx + 3 ky + 9 kz of its stencil (zeros for a particle outside the grid
+// interior, which the sort flagged), added per node by k_gather_residual in
+// a fixed order.
 template <int D>
-__global__ void k_mass(DevParticles P, DevGrid G, double* M) {
+__global__ void k_mass(DevParticles P, DevGrid G, double* fp) {
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P.np) return;
   Spline1 sp[3];
 #pragma unroll
   for (int a = 0; a < D; ++a) sp[a] = spline1((P.x[a][p] - G.o[a]) / G.h);
-  if (D == 2) { sp[2].base = 0; sp[2].N[0] = 1.0; }
-  // a particle outside the grid interior was flagged by the sort; skip it
-  for (int a = 0; a < D; ++a)
-    if (sp[a].base < 0 || sp[a].base > G.n[a] - 2) return;
-  const double m = P.mass[p];
+  if (D == 2) {
+    sp[2].base = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sp[2].N[k] = (k == 0) ? 1.0 : 0.0;
+  }
+  bool inside = true;
+  for (int a = 0; a < D; ++a) inside = inside && sp[a].base >= 0 && sp[a].base <= G.n[a] - 2;
+  const double m = inside ? P.mass[p] : 0.0;
   const int KZ = (D == 3) ? 3 : 1;
   for (int kz = 0; kz < KZ; ++kz)
 #pragma unroll
     for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-      for (int kx = 0; kx < 3; ++kx) {
-        long long node = (sp[0].base + kx) + (long long)G.nx1 * ((sp[1].base + ky) + (long long)G.ny1 * (sp[2].base + kz));
-        atomicAdd(&M[node], sp[0].N[kx] * sp[1].N[ky] * sp[2].N[kz] * m);
-      }
+      for (int kx = 0; kx < 3; ++kx)
+        fp[(long long)(kx + 3 * (ky + 3 * kz)) * P.np + p] = sp[0].N[kx] * sp[1].N[ky] * sp[2].N[kz] * m;
 }
 template <int D>
-cudaError_t launch_mass(const DevParticles& P, const DevGrid& G, double* M, cudaStream_t st) {
-  if (P.np == 0) return cudaSuccess;
-  k_mass<D><<<nblocks(P.np), TPB, 0, st>>>(P, G, M);
-  return cudaGetLastError();
+cudaError_t launch_mass(const DevParticles& P, const DevGrid& G, const int* cstart, double* fp, double* M,
+                        long long nnode, cudaStream_t st) {
+  if (P.np == 0) return cudaMemsetAsync(M, 0, nnode * sizeof(double), st);
+  k_mass<D><<<nblocks(P.np), TPB, 0, st>>>(P, G, fp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_gather_residual<D, 1>(G, cstart, fp, P.np, M, nnode, st);
 }
 
 __global__ void k_active(const double* __restrict__ M, double thr, int* flag, long long n) {
@@ -1044,7 +1052,8 @@ cudaError_t launch_sort_cells(const int* cstart, int* perm, long long ncells, cu
 #define MPM_INST_D(D)                                                                                   \
   template cudaError_t launch_cell_keys<D>(const DevParticles&, const DevGrid&, int*, int*, int*, int*,  \
                                            cudaStream_t);                                                \
-  template cudaError_t launch_mass<D>(const DevParticles&, const DevGrid&, double*, cudaStream_t);      \
+  template cudaError_t launch_mass<D>(const DevParticles&, const DevGrid&, const int*, double*, double*, \
+                                      long long, cudaStream_t);                                         \
   template cudaError_t launch_stress_out<D>(const DevParticles&, const DevGrid&, const MatC*, double*,   \
                                             cudaStream_t);                                               \
   template cudaError_t launch_pattern_count<D>(const DevGrid&, const int*, int, const int*, const int*,  \
@@ -1055,6 +1064,10 @@ cudaError_t launch_sort_cells(const int* cstart, int* perm, long long ncells, cu
                                            double*, unsigned*, cudaStream_t);
 MPM_INST_D(2)
 MPM_INST_D(3)
+template cudaError_t launch_gather_residual<2, 1>(const DevGrid&, const int*, const double*, int, double*, long long,
+                                                  cudaStream_t);
+template cudaError_t launch_gather_residual<3, 1>(const DevGrid&, const int*, const double*, int, double*, long long,
+                                                  cudaStream_t);
 template cudaError_t launch_gather_residual<2, 2>(const DevGrid&, const int*, const double*, int, double*, long long,
                                                   cudaStream_t);
 template cudaError_t launch_gather_residual<2, 3>(const DevGrid&, const int*, const double*, int, double*, long long,

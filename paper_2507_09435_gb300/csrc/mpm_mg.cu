@@ -59,16 +59,38 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
-__device__ __forceinline__ void block_add(double v, double* out) {
+// The grid's sum of v written to *out in an order fixed by the grid: each
+// block stores its sum in part[block] and takes a ticket; the block that
+// takes the last one adds the stored sums in block order and resets the
+// ticket.  Every block of the grid calls this once.
+__device__ __forceinline__ void grid_add(double v, double* out, double* part, unsigned* ticket) {
   __shared__ double sh[MTPB / 32];
+  __shared__ int last;
   v = wsum(v);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) sh[w] = v;
   __syncthreads();
-  if (w == 0) {
-    double t = (lane < MTPB / 32) ? sh[lane] : 0.0;
-    t = wsum(t);
-    if (lane == 0 && t != 0.0) atomicAdd(out, t);
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < MTPB / 32; ++q) t += sh[q];
+    part[blockIdx.x] = t;
+    __threadfence();
+    last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double t = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += MTPB) t += __ldcg(&part[b]);
+  t = wsum(t);
+  __syncthreads();
+  if (lane == 0) sh[w] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double u = 0.0;
+    for (int q = 0; q < MTPB / 32; ++q) u += sh[q];
+    *out = u;
+    *ticket = 0u;
   }
 }
 
@@ -224,7 +246,8 @@ __device__ __forceinline__ double hash_unit(unsigned long long x) {
 }
 
 template <int D, class T, int B>
-__global__ void __launch_bounds__(MTPB) k_mg_power_init(MgLevel<T> l, T* v, double* nrm) {
+__global__ void __launch_bounds__(MTPB) k_mg_power_init(MgLevel<T> l, T* v, double* nrm, double* part,
+                                                        unsigned* ticket) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   double acc = 0.0;
   if (row < *l.K.nrow) {
@@ -237,14 +260,14 @@ __global__ void __launch_bounds__(MTPB) k_mg_power_init(MgLevel<T> l, T* v, doub
       acc += (double)x * (double)x;
     }
   }
-  block_add(acc, nrm);
+  grid_add(acc, nrm, part, ticket);
 }
 
 // dst = D^-1 A src / ||src||, accumulating ||dst||^2 (D^-1: the unscaled
 // block-Jacobi inverse, node blocks or row segments)
 template <int D, class T, int B>
 __global__ void __launch_bounds__(MTPB) k_mg_power(MgLevel<T> l, const T* src, T* dst, const double* nin,
-                                                   double* nout) {
+                                                   double* nout, double* part, unsigned* ticket) {
   const int row = blockIdx.x * blockDim.x + threadIdx.x;
   const int nrow = *l.K.nrow;
   const unsigned live = __ballot_sync(0xffffffffu, row < nrow);
@@ -263,7 +286,7 @@ __global__ void __launch_bounds__(MTPB) k_mg_power(MgLevel<T> l, const T* src, T
       acc += (double)t * (double)t;
     }
   }
-  block_add(acc, nout);
+  grid_add(acc, nout, part, ticket);
 }
 
 // dinv *= c / lambda, lambda = sqrt(*nrm) (the last power-iteration norm);
@@ -596,15 +619,16 @@ cudaError_t launch_mg_galerkin(MgLevel<T> f, MgLevel<T> c, int nrow_c, cudaStrea
 }
 
 template <int D, class T, int B>
-cudaError_t launch_mg_power(MgLevel<T> l, int cap, T* va, T* vb, double* nrm, int iters, cudaStream_t st) {
+cudaError_t launch_mg_power(MgLevel<T> l, int cap, T* va, T* vb, double* nrm, int iters, double* part,
+                            unsigned* ticket, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(nrm, 0, (iters + 1) * sizeof(double), st);
   if (e != cudaSuccess) return e;
   const int nb = nblk_rows(cap);
-  k_mg_power_init<D, T, B><<<nb, MTPB, 0, st>>>(l, va, nrm);
+  k_mg_power_init<D, T, B><<<nb, MTPB, 0, st>>>(l, va, nrm, part, ticket);
   for (int k = 0; k < iters; ++k) {
     const T* src = (k & 1) ? vb : va;
     T* dst = (k & 1) ? va : vb;
-    k_mg_power<D, T, B><<<nb, MTPB, 0, st>>>(l, src, dst, nrm + k, nrm + k + 1);
+    k_mg_power<D, T, B><<<nb, MTPB, 0, st>>>(l, src, dst, nrm + k, nrm + k + 1, part, ticket);
   }
   return cudaGetLastError();
 }
@@ -720,7 +744,8 @@ int mg_vcycle_launches(int L, int tail) {
 
 #define MPM_MG_INST(D, T, B)                                                                                   \
   template cudaError_t launch_mg_galerkin<D, T, B>(MgLevel<T>, MgLevel<T>, int, cudaStream_t);                \
-  template cudaError_t launch_mg_power<D, T, B>(MgLevel<T>, int, T*, T*, double*, int, cudaStream_t);         \
+  template cudaError_t launch_mg_power<D, T, B>(MgLevel<T>, int, T*, T*, double*, int, double*, unsigned*,  \
+                                                cudaStream_t);                                           \
   template cudaError_t launch_mg_dense_inverse<D, T, B>(MgLevel<T>, float*, cudaStream_t);                    \
   template cudaError_t launch_mg_vcycle<D, T, B>(const MgApply<T>&, const T*, T*, const int*, cudaStream_t); \
   template int mg_tail_cluster<D, T, B>();

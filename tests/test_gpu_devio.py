@@ -169,3 +169,24 @@ def test_newton_limit_reports_not_converged_and_does_not_commit():
     assert rep.status == 4 and not rep.converged   # MPM_ERR_NOT_CONVERGED
     assert np.array_equal(gs.particles()["x"], x0)
     gs.close()
+
+
+def test_multigrid_load_steps_reproducible():
+    """The coarse plastic footing with the multigrid V-cycle in mixed
+    precision, solved twice on fresh scenes: the same iteration counts and
+    the same increments bit for bit (the smoother's damping estimate, the
+    nodal mass and every other sum in a fixed order)."""
+    sc = S.footing(nx=48, ny=24, h=0.5, nsteps=20, settle_frac=0.1)
+    runs = []
+    for _ in range(2):
+        gs = mpm.GpuScene(sc, precision=mpm.MPM_MIXED, newton_tol=1e-8, precond=mpm.MPM_PC_MG)
+        counts = []
+        for stp in sc.steps[:3]:
+            rep = gs.solve_step(stp)
+            assert rep.converged
+            counts.append([rep.krylov_iters[i] for i in range(rep.newton_iters)])
+        runs.append((counts, gs.du(), gs.particles(be=False, pc=False, F=False, tau=False)["x"]))
+        gs.close()
+    assert runs[0][0] == runs[1][0]
+    assert np.array_equal(runs[0][1], runs[1][1])
+    assert np.array_equal(runs[0][2], runs[1][2])
