@@ -209,7 +209,12 @@ mpm_status mpm_assemble(mpm_scene* s);
 mpm_status mpm_commit_step(mpm_scene* s);
 
 /* Whole load step: begin, Newton to newton_tol (at most newton_maxit), commit.
- * Returns MPM_ERR_NOT_CONVERGED (state not committed) when tol is missed. */
+ * Returns MPM_ERR_NOT_CONVERGED (state not committed) when tol is missed.
+ * Reproducibility: with MPM_BICGSTAB (any preconditioner) every sum of the
+ * step (residual, nodal mass, Jacobian, norms, Krylov dot products) is taken
+ * in an order that depends only on the inputs, so the same scene and steps
+ * give the same results bit for bit, iteration counts included, on the same
+ * GPU model and build; MPM_GMRES sums its dot products with atomics. */
 mpm_status mpm_solve_step(mpm_scene* s, mpm_step_report* rep);
 
 /* FP64 residual of the current iterate on the dense node grid, nnode*B
