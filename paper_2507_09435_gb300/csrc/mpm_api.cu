@@ -132,6 +132,9 @@ struct mpm_scene {
   void* d_mg_v0 = nullptr;         // level 0: residual and power-iteration scratch (2 vectors)
   float* d_mg_inv = nullptr;       // coarsest-level dense inverse, transposed
   double* d_mg_nrm = nullptr;      // power-iteration norms, MG_POWER_IT + 1 per level
+  double* d_mg_part = nullptr;     // power-iteration partial sums, one per block of a launch
+  int mg_part_n = 0;
+  unsigned* d_mg_tickets = nullptr;   // power-iteration sums: one ticket per level
   int* d_mg_err = nullptr;         // singular coarse diagonal blocks (identity used)
   int* h_mgn = nullptr;            // pinned: active rows per level
   bool mg_lam = false;             // smoother damping estimated for the staged step
@@ -481,7 +484,7 @@ void mg_create(mpm_scene* s) {
     m.flag = s->dalloc<int>(m.nnode + 1);
     m.pos = s->dalloc<int>(m.nnode + 1);
     m.nrow_d = s->dalloc<int>(1);
-    m.fixed = s->dalloc<uint8_t>(m.nnode * s->B);
+    m.fixed = s->dalloc<uint8_t>((m.nnode * s->B + 15) & ~15LL);   // whole 16-byte units (tail staging)
     m.vpad = (2 + 2LL * m.nx1 + (s->D == 3 ? 2LL * m.nx1 * m.ny1 : 0)) * s->B;
     m.vlen = m.nnode * s->B + 2 * m.vpad;
     m.vec = s->mixed ? (void*)s->dalloc<float>(3 * m.vlen) : (void*)s->dalloc<double>(3 * m.vlen);
@@ -496,6 +499,8 @@ void mg_create(mpm_scene* s) {
   ck(cudaMemsetAsync(s->d_mg_v0, 0, 2 * s->vlen * T, s->st), "memset");
   s->d_mg_inv = s->dalloc<float>((size_t)MG_DENSE_MAX * MG_DENSE_MAX);
   s->d_mg_nrm = s->dalloc<double>((size_t)MG_MAX_LEVELS * (MG_POWER_IT + 1));
+  s->d_mg_tickets = s->dalloc<unsigned>(MG_MAX_LEVELS);
+  ck(cudaMemsetAsync(s->d_mg_tickets, 0, MG_MAX_LEVELS * sizeof(unsigned), s->st), "memset");
   s->d_mg_err = s->dalloc<int>(1);
   ck(cudaMallocHost(&s->h_mgn, MG_MAX_LEVELS * sizeof(int)), "host alloc");
 }
@@ -597,6 +602,48 @@ MgApply<T> mg_view(mpm_scene* s) {
     c.r = v + 2 * m.vlen + m.vpad;
     a.caps[l] = m.cap;
   }
+  a.fused = (s->D == 2 && a.lev[0].K.seg == 1 && MG_NU0 >= 2) ? 1 : 0;
+  // coarse levels the tail stages in shared memory: from the first level
+  // below the tail from which all levels down to the dense one fit
+  a.staged = a.L;
+  a.smem = a.inv_off = a.inv_len = 0;
+  const int l0 = std::min(std::max(a.tail, 1), a.L - 1);
+  const size_t TS = sizeof(T), BB = (size_t)s->B * s->B, S = stencil_slots(s->D);
+  const auto al16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  for (int ls = l0 + 1; ls <= a.L - 1; ++ls) {
+    MgStage stg[MG_MAX_LEVELS] = {};
+    size_t off = 0;
+    for (int l = ls; l < a.L && off <= (size_t)MG_TAIL_SMEM_MAX; ++l) {
+      const auto& m = s->mgl[l];
+      const bool dense = (l == a.L - 1);
+      const size_t vb = (size_t)m.vlen * TS;
+      // rows, blocks, block inverses, node-to-row map, prescribed flags, b, z, r
+      const size_t len[8] = {(size_t)m.cap * 4,
+                             dense ? 0 : S * (size_t)m.cap * BB * TS,
+                             dense ? 0 : (size_t)m.cap * BB * TS,
+                             dense ? 0 : (size_t)m.nnode * 4,
+                             dense ? 0 : al16((size_t)m.nnode * s->B),
+                             vb,
+                             vb,
+                             dense ? 0 : vb};
+      for (int k = 0; k < 8; ++k) {
+        stg[l].off[k] = len[k] ? (int)std::min(off, (size_t)MG_TAIL_SMEM_MAX) : -1;
+        stg[l].len[k] = (int)std::min(len[k], (size_t)MG_TAIL_SMEM_MAX);
+        off += al16(len[k]);
+      }
+      stg[l].vpad = (int)m.vpad;
+    }
+    const size_t nd = (size_t)std::min(s->mgl[a.L - 1].cap * s->B, MG_DENSE_MAX);
+    const size_t inv = nd * nd * sizeof(float);
+    if (off + al16(inv) <= (size_t)MG_TAIL_SMEM_MAX) {
+      a.staged = ls;
+      a.inv_off = (int)off;
+      a.inv_len = (int)inv;
+      a.smem = (int)(off + al16(inv));
+      for (int l = ls; l < a.L; ++l) a.stg[l] = stg[l];
+      break;
+    }
+  }
   return a;
 }
 
@@ -625,14 +672,21 @@ void mg_setup(mpm_scene* s) {
   }
   const int P1 = MG_POWER_IT + 1;
   if (!s->mg_lam) {
+    MgPowerSet<T> ps{};
+    ps.n = L - 1;
     for (int l = 0; l + 1 < L; ++l) {
-      T* va = (l == 0) ? (T*)s->d_mg_v0 + s->vpad : a.lev[l].b;
-      T* vb = (l == 0) ? (T*)s->d_mg_v0 + s->vlen + s->vpad : a.lev[l].z;
-      ck(launch_mg_power<D, T, B>(a.lev[l], a.caps[l], va, vb, s->d_mg_nrm + l * P1, MG_POWER_IT, s->d_red,
-                                  s->d_norm_ticket, st),
-         "power");
-      s->launches += 1 + MG_POWER_IT;
+      ps.lev[l] = a.lev[l];
+      ps.va[l] = (l == 0) ? (T*)s->d_mg_v0 + s->vpad : a.lev[l].b;
+      ps.vb[l] = (l == 0) ? (T*)s->d_mg_v0 + s->vlen + s->vpad : a.lev[l].z;
     }
+    const int nb = mg_power_blocks(a.caps, ps.n);
+    if (nb > s->mg_part_n) {
+      s->dfree(s->d_mg_part);
+      s->d_mg_part = s->dalloc<double>((size_t)nb);
+      s->mg_part_n = nb;
+    }
+    ck(launch_mg_power<D, T, B>(ps, a.caps, s->d_mg_nrm, MG_POWER_IT, s->d_mg_part, s->d_mg_tickets, st), "power");
+    if (ps.n > 0) s->launches += 1 + MG_POWER_IT;
     s->mg_lam = true;
   }
   for (int l = 0; l + 1 < L; ++l) {
@@ -745,17 +799,19 @@ void krylov_solve(mpm_scene* s, double eta, double rnorm, int& kit, int& kstat, 
   MgApply<T> mga{};
   if (use_mg) {
     mga = mg_view<T>(s);
-    mga.cluster = mg_tail_cluster<D, T, B>();
+    bool staging = false;
+    mga.cluster = mg_tail_cluster<D, T, B>(&staging);
+    if (!staging) mga.staged = mga.L;
   }
   const MgApply<T>* mgp = use_mg ? &mga : nullptr;
   int* d_done = &s->d_S->done;
   const int chunk = use_mg ? MG_CHUNK : GRAPH_CHUNK;
-  const int per_iter = 4 + (use_mg ? 2 * mg_vcycle_launches(mga.L, mga.tail) : 0);
+  const int per_iter = 4 + (use_mg ? 2 * mg_vcycle_launches(mga.L, mga.tail, mga.fused) : 0);
   ck(launch_bicgstab_init<D, T, B>(K, s->krhs, s->d_fixed, v, s->d_S, tol2, s->desc.krylov_maxit, nblk, st),
      "krylov init");
   if (use_mg) {
     ck(launch_mg_vcycle<D, T, B>(mga, v.p, v.phat, d_done, st), "v-cycle");
-    s->launches += mg_vcycle_launches(mga.L, mga.tail);
+    s->launches += mg_vcycle_launches(mga.L, mga.tail, mga.fused);
   }
   const int pblk = std::min(s->pblocks, std::max(1, (s->nrow * 4 + 511) / 512));
   if (s->pblocks > 0) {
@@ -812,7 +868,7 @@ void krylov_solve(mpm_scene* s, double eta, double rnorm, int& kit, int& kstat, 
       // restart kernel applied only its first smoothing sweep)
       if (use_mg) {
         ck(launch_mg_vcycle<D, T, B>(mga, v.p, v.phat, d_done, st), "v-cycle");
-        s->launches += mg_vcycle_launches(mga.L, mga.tail);
+        s->launches += mg_vcycle_launches(mga.L, mga.tail, mga.fused);
       }
     }
   } else {

@@ -61,19 +61,22 @@ struct DevMatrix {
 };
 
 // One D x D block of the matrix (contiguous), through the read-only path:
-// a single 16-byte load for 2x2 FP32, two for 2x2 FP64.
-template <int D, class T>
+// a single 16-byte load for 2x2 FP32, two for 2x2 FP64.  GENERIC: ordinary
+// loads through a generic pointer (the block may sit in shared memory).
+template <int D, class T, bool GENERIC = false>
 __device__ __forceinline__ void ld_block(const T* p, T b[D * D]) {
   if constexpr (D == 2 && sizeof(T) == 4) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    const float4* q = reinterpret_cast<const float4*>(p);
+    const float4 v = GENERIC ? *q : __ldg(q);
     b[0] = v.x; b[1] = v.y; b[2] = v.z; b[3] = v.w;
   } else if constexpr (D == 2 && sizeof(T) == 8) {
-    const double2 u = __ldg(reinterpret_cast<const double2*>(p));
-    const double2 w = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    const double2* q = reinterpret_cast<const double2*>(p);
+    const double2 u = GENERIC ? q[0] : __ldg(q);
+    const double2 w = GENERIC ? q[1] : __ldg(q + 1);
     b[0] = u.x; b[1] = u.y; b[2] = w.x; b[3] = w.y;
   } else {
 #pragma unroll
-    for (int k = 0; k < D * D; ++k) b[k] = __ldg(p + k);
+    for (int k = 0; k < D * D; ++k) b[k] = GENERIC ? p[k] : __ldg(p + k);
   }
 }
 
@@ -102,12 +105,13 @@ __device__ __forceinline__ void ld_node(const T* x, long long j, T v[D]) {
 // lanes of one warp (one thread per row, blockDim a multiple of 32, rows
 // aligned to 4), which exchange their values by shuffles.  `live` is the
 // ballot of the lanes that call this (exactly the lanes executing it).
-template <int B, class T>
+// GENERIC: the inverses may sit in shared memory (ordinary loads).
+template <int B, class T, bool GENERIC = false>
 __device__ __forceinline__ void precond_apply(const DevMatrix<T>& K, int row, const T v[B], T z[B],
                                               unsigned live) {
   if (K.seg <= 1) {
     T m[B * B];
-    ld_block<B, T>(&K.dinv[(long long)row * (B * B)], m);
+    ld_block<B, T, GENERIC>(&K.dinv[(long long)row * (B * B)], m);
 #pragma unroll
     for (int a = 0; a < B; ++a) {
       T s = (T)0;
@@ -130,7 +134,7 @@ __device__ __forceinline__ void precond_apply(const DevMatrix<T>& K, int row, co
       const T t = __shfl_sync(live, v[b], base + q);
       const T vb = src ? t : (T)0;
 #pragma unroll
-      for (int a = 0; a < B; ++a) z[a] += __ldg(M + a * W + q * B + b) * vb;
+      for (int a = 0; a < B; ++a) z[a] += (GENERIC ? M[a * W + q * B + b] : __ldg(M + a * W + q * B + b)) * vb;
     }
   }
 }
@@ -139,15 +143,16 @@ __device__ __forceinline__ void precond_apply(const DevMatrix<T>& K, int row, co
 constexpr int pmask_words(int D) { return D == 2 ? 1 : 4; }
 
 // The row's slot-presence words (all ones without a mask).
-template <int D>
+template <int D, bool GENERIC = false>
 __device__ __forceinline__ void load_pmask(const unsigned* pmask, int row, unsigned pm[pmask_words(D)]) {
   constexpr int PW = pmask_words(D);
   if (pmask) {
     if constexpr (PW == 4) {
-      const uint4 v = __ldg(reinterpret_cast<const uint4*>(pmask) + row);
+      const uint4* q = reinterpret_cast<const uint4*>(pmask) + row;
+      const uint4 v = GENERIC ? *q : __ldg(q);
       pm[0] = v.x; pm[1] = v.y; pm[2] = v.z; pm[3] = v.w;
     } else {
-      pm[0] = __ldg(pmask + row);
+      pm[0] = GENERIC ? pmask[row] : __ldg(pmask + row);
     }
   } else {
 #pragma unroll
@@ -159,8 +164,9 @@ __device__ __forceinline__ void load_pmask(const unsigned* pmask, int row, unsig
 // blocks of the row against the neighbours' values of x (x on the padded
 // dense node grid of the matrix's level); slots absent from the row's
 // presence mask are not read.  COHERENT: x was written earlier in the same
-// kernel (ordinary loads instead of the read-only path).
-template <int D, class T, int B, bool COHERENT = false>
+// kernel (ordinary loads instead of the read-only path).  GENERIC: the matrix
+// may sit in shared memory (ordinary loads for it as well).
+template <int D, class T, int B, bool COHERENT = false, bool GENERIC = false>
 __device__ __forceinline__ void stencil_row_product(const DevMatrix<T>& K, int row, long long i, int nx1, int ny1,
                                                     const T* x, T y[B]) {
 #pragma unroll
@@ -168,7 +174,7 @@ __device__ __forceinline__ void stencil_row_product(const DevMatrix<T>& K, int r
   constexpr int ZR = (D == 3) ? 2 : 0;
   const long long cap = K.cap;
   unsigned pm[pmask_words(D)];
-  load_pmask<D>(K.pmask, row, pm);
+  load_pmask<D, GENERIC>(K.pmask, row, pm);
 #pragma unroll
   for (int dz = -ZR; dz <= ZR; ++dz)
 #pragma unroll
@@ -182,8 +188,8 @@ __device__ __forceinline__ void stencil_row_product(const DevMatrix<T>& K, int r
         const long long j = i + dx + (long long)nx1 * (dy + (long long)ny1 * dz);
         T xj[B], kb[B * B];
         if (on) {
-          ld_node<B, T, COHERENT>(x, j, xj);
-          ld_block<B, T>(&K.val[((long long)slot * cap + row) * (B * B)], kb);
+          ld_node<B, T, COHERENT || GENERIC>(x, j, xj);
+          ld_block<B, T, GENERIC>(&K.val[((long long)slot * cap + row) * (B * B)], kb);
         } else {
 #pragma unroll
           for (int b = 0; b < B; ++b) xj[b] = (T)0;
@@ -337,19 +343,40 @@ constexpr int MG_POWER_IT = 8;      // power iterations for lambda_max(D^-1 A)
 constexpr int MG_TAIL_ROWS = 16384; // coarse levels this small run inside one cluster
 constexpr int MG_NU0 = 2;           // smoothing sweeps per side on the finest level
 constexpr int MG_TAIL_TPB = 512;
+// Dynamic shared memory the cluster tail may take per block for the levels it
+// stages (one block per SM at this size).
+constexpr int MG_TAIL_SMEM_MAX = 200 * 1024;
+// Where one staged level sits in the tail's dynamic shared memory: byte
+// offsets of its row list, matrix blocks, block inverses, node-to-row map,
+// prescribed flags and vectors b, z, r (-1: not staged; the dense level
+// stages only its rows, b and z), the bytes copied or zeroed for each, and
+// the vectors' padding in elements.
+struct MgStage {
+  int off[8];
+  int len[8];
+  int vpad;
+};
 // A built hierarchy, for the V-cycle launches: levels 0..L-1 (the last
 // dense); levels tail..L-1 (tail >= 1) run inside one kernel of one
 // thread-block cluster of `cluster` blocks, the levels above it one launch
-// per step.
+// per step.  Levels staged..L-1 (tail < staged; staged == L: none) are small
+// enough for every block of the cluster to copy them into its shared memory
+// (`smem` bytes, the dense inverse's `inv_len` bytes at `inv_off`) and run
+// them in full by itself, between block barriers.
 template <class T>
 struct MgApply {
   MgLevel<T> lev[MG_MAX_LEVELS];
   int caps[MG_MAX_LEVELS];
   int L, tail, cluster;
   const float* invT;
+  int staged, smem, inv_off, inv_len;
+  MgStage stg[MG_MAX_LEVELS];
+  // 2D levels above the tail: residual + restriction and prolongation +
+  // first post-sweep as one tiled launch each (node-block smoother)
+  int fused;
 };
 template <int D, class T, int B>
-int mg_tail_cluster();
+int mg_tail_cluster(bool* staging);
 template <int D>
 cudaError_t launch_mg_flags(int fx, int fy, int fz, const int* n2r_f, int cx, int cy, long long nc, int* flag,
                             cudaStream_t st);
@@ -360,10 +387,24 @@ template <int D, class T, int B>
 cudaError_t launch_mg_galerkin(MgLevel<T> f, MgLevel<T> c, int nrow_c, cudaStream_t st);
 // power iteration on D^-1 A of a level: nrm[k] = ||v_k||^2 (v_k of unit
 // predecessor), so sqrt(nrm[iters]) estimates lambda_max; va, vb scratch
+// The power iterations for lambda_max(D^-1 A) of levels 0..n-1 at once
+// (one launch per step): start vectors in va, scratch vb; start[] is filled
+// by the launcher from the row capacities.
+template <class T>
+struct MgPowerSet {
+  MgLevel<T> lev[MG_MAX_LEVELS];
+  T* va[MG_MAX_LEVELS];
+  T* vb[MG_MAX_LEVELS];
+  int start[MG_MAX_LEVELS + 1];
+  int n;
+};
+// blocks of one power-iteration launch over levels with row capacities caps[0..n-1]
+int mg_power_blocks(const int* caps, int n);
+// nrm: (iters + 1) norms per level; part: mg_power_blocks(caps, n) doubles;
+// tickets: n counters, zero on entry and left zero
 template <int D, class T, int B>
-// part: at least ceil(cap / KRYLOV_TPB) doubles, ticket: zero on entry, left zero
-cudaError_t launch_mg_power(MgLevel<T> l, int cap, T* va, T* vb, double* nrm, int iters, double* part,
-                            unsigned* ticket, cudaStream_t st);
+cudaError_t launch_mg_power(MgPowerSet<T> ps, const int* caps, double* nrm, int iters, double* part,
+                            unsigned* tickets, cudaStream_t st);
 template <class T>
 cudaError_t launch_mg_scale(T* dinv, long long n, const double* nrm, double c, cudaStream_t st);
 template <int D, class T, int B>
@@ -372,7 +413,7 @@ cudaError_t launch_mg_dense_inverse(MgLevel<T> c, float* invT, cudaStream_t st);
 // 0..L-1, the last dense; kernels return at once while *done is set
 template <int D, class T, int B>
 cudaError_t launch_mg_vcycle(const MgApply<T>& mg, const T* b0, T* z0, const int* done, cudaStream_t st);
-int mg_vcycle_launches(int L, int tail);
+int mg_vcycle_launches(int L, int tail, int fused);
 
 // device-pointer getters and Dirichlet setter (mpm_devio.cu)
 cudaError_t launch_du_out(const double* du, double* out, long long ndof, int B, int D, double psc,
