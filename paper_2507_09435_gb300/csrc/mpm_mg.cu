@@ -339,7 +339,7 @@ __global__ void k_mg_scale(T* dinv, long long n, const double* nrm, double c) {
 // preconditioner stays defined).  Written transposed:
 // invT[j*n + k] = (A^-1)[k][j].
 __device__ __forceinline__ void gj_select(const float (&a)[4][4], unsigned used, int col, int n,
-                                          float (*fac)[MG_DENSE_MAX], int* prow, float* pval) {
+                                          float (*fac)[MG_DENSE_MAX], int* prow, float* pinv) {
   const int lane = threadIdx.x & 31, sc = col >> 5;
   float best = -1.0f, bval = 0.0f;
   int bi = 1 << 30;
@@ -365,8 +365,10 @@ __device__ __forceinline__ void gj_select(const float (&a)[4][4], unsigned used,
     if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; bval = ov; }
   }
   if (lane == 0) {
+    const float m = fabsf(bval);
+    const bool bad = !(m > 1e-30f) || !(m < 3e38f);
     prow[col] = bi;
-    pval[col] = bval;
+    pinv[col] = bad ? 1.0f : 1.0f / bval;
   }
 }
 
@@ -374,7 +376,7 @@ template <int D, class T, int B>
 __global__ void __launch_bounds__(1024) k_mg_dense_inverse(MgLevel<T> c, float* invT) {
   extern __shared__ float A[];   // A[r * n + k]
   __shared__ float fac[2][MG_DENSE_MAX];
-  __shared__ float pval[MG_DENSE_MAX];
+  __shared__ float pinv[MG_DENSE_MAX];   // 1 / pivot (1 for a vanishing pivot)
   __shared__ int prow[MG_DENSE_MAX], kof[MG_DENSE_MAX];
   const int nrow = *c.K.nrow;
   const int n = nrow * B;
@@ -411,41 +413,54 @@ __global__ void __launch_bounds__(1024) k_mg_dense_inverse(MgLevel<T> c, float* 
       a[q][s] = (r < n && col < n) ? A[r * n + col] : 0.0f;
     }
   }
-  if (w == 0) gj_select(a, used, 0, n, fac, prow, pval);
+  if (w == 0) gj_select(a, used, 0, n, fac, prow, pinv);
   for (int col = 0; col < n; ++col) {
     __syncthreads();
     const int p = prow[col];
-    const float pv = pval[col], m = fabsf(pv);
-    const bool bad = !(m > 1e-30f) || !(m < 3e38f);
-    const float ip = bad ? 1.0f : 1.0f / pv;
-    const int pl = p & 31, pq = p >> 5;
+    const float ip = pinv[col];
+    const int pl = p & 31, pq = p >> 5;   // the same for the whole block
     float f[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int r = lane + 32 * q;
       f[q] = (r < n && r != p) ? fac[col & 1][r] : 0.0f;
     }
+    // the normalised pivot row on this warp's columns (ip on column col)
+    float pr[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
-      float t = 0.0f;
+      float t = a[0][s];
+      if (pq == 1) t = a[1][s];
+      if (pq == 2) t = a[2][s];
+      if (pq == 3) t = a[3][s];
+      t = __shfl_sync(0xffffffffu, t, pl);
+      pr[s] = (w + 32 * s == col) ? ip : t * ip;
+    }
+    // column col leaves the left half; right-half column p takes its place
+    // (zero off the pivot row before the elimination)
+    if (w == (col & 31)) {
+      const int sc = col >> 5;
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        if (q == pq) t = a[q][s];
-      t = __shfl_sync(0xffffffffu, t, pl);
-      const bool pc = (w + 32 * s == col);
-      const float pr = pc ? ip : t * ip;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (lane + 32 * q == p) {
-          a[q][s] = pr;
-        } else {
-          if (pc) a[q][s] = 0.0f;
-          if (f[q] != 0.0f) a[q][s] -= f[q] * pr;
-        }
-      }
+        for (int s = 0; s < 4; ++s)
+          if (s == sc) a[q][s] = 0.0f;
     }
-    if (lane == pl) used |= 1u << pq;
-    if (col + 1 < n && w == ((col + 1) & 31)) gj_select(a, used, col + 1, n, fac, prow, pval);
+    // eliminate (f = 0 on the pivot row, which is then replaced)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int s = 0; s < 4; ++s) a[q][s] -= f[q] * pr[s];
+    if (lane == pl) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q == pq) {
+#pragma unroll
+          for (int s = 0; s < 4; ++s) a[q][s] = pr[s];
+        }
+      used |= 1u << pq;
+    }
+    if (col + 1 < n && w == ((col + 1) & 31)) gj_select(a, used, col + 1, n, fac, prow, pinv);
   }
   __syncthreads();
   for (int k = threadIdx.x; k < n; k += blockDim.x) kof[prow[k]] = k;
