@@ -343,6 +343,14 @@ constexpr int MG_POWER_IT = 8;      // power iterations for lambda_max(D^-1 A)
 constexpr int MG_TAIL_ROWS = 16384; // coarse levels this small run inside one cluster
 constexpr int MG_NU0 = 2;           // smoothing sweeps per side on the finest level
 constexpr int MG_TAIL_TPB = 512;
+// Threads per block of the cluster tail: 1024 for 2D FP32 node blocks (one
+// row per thread for levels of up to 16,384 rows on 16 blocks), else
+// MG_TAIL_TPB (the register budget of the wider blocks).
+constexpr int MG_TAIL_TPB_WIDE = 1024;
+template <class T, int B>
+constexpr int mg_tail_tpb() {
+  return (sizeof(T) == 4 && B == 2) ? MG_TAIL_TPB_WIDE : MG_TAIL_TPB;
+}
 // Dynamic shared memory the cluster tail may take per block for the levels it
 // stages (one block per SM at this size).
 constexpr int MG_TAIL_SMEM_MAX = 200 * 1024;

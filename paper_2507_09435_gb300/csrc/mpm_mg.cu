@@ -890,7 +890,7 @@ __device__ __forceinline__ int row_hi(int n) {
 // smoother needs no warp exchange.  Every block reads the same done flag, so
 // either all return or none does.
 template <int D, class T, int B>
-__global__ void __launch_bounds__(MG_TAIL_TPB) k_mg_tail(const __grid_constant__ MgApply<T> mg, const int* done) {
+__global__ void __launch_bounds__(mg_tail_tpb<T, B>()) k_mg_tail(const __grid_constant__ MgApply<T> mg, const int* done) {
   if (is_done(done)) return;
   cg::cluster_group cl = cg::this_cluster();
   __shared__ float bv[MG_DENSE_MAX];
@@ -1085,7 +1085,7 @@ cudaError_t launch_mg_vcycle(const MgApply<T>& mg, const T* b0, T* z0, const int
   {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)mg.cluster);
-    cfg.blockDim = dim3(MG_TAIL_TPB);
+    cfg.blockDim = dim3(mg_tail_tpb<T, B>());
     cfg.dynamicSmemBytes = (size_t)(mg.staged < L ? mg.smem : 0);
     cfg.stream = st;
     cudaLaunchAttribute at[1];
@@ -1157,7 +1157,7 @@ int mg_tail_cluster(bool* staging) {
   if (cudaFuncSetAttribute(k_mg_tail<D, T, B>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16);
-    cfg.blockDim = dim3(MG_TAIL_TPB);
+    cfg.blockDim = dim3(mg_tail_tpb<T, B>());
     cfg.dynamicSmemBytes = ok ? MG_TAIL_SMEM_MAX : 0;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
