@@ -254,6 +254,17 @@ mpm_status mpm_get_jacobian_bsr(const mpm_scene* s, long long cap, int* row_node
 mpm_status mpm_get_mg_level(const mpm_scene* s, int level, int* levels, int dims[3], int* nrow, int cap,
                             int* nodes, double* vals, unsigned char* fixed, double* lambda_max);
 
+/* One application of the multigrid preconditioner of the last assembly
+ * (MPM_PC_MG): z = M^-1 b, the V-cycle the Krylov solve applies (its first
+ * sweep from zero, the remaining sweeps, the coarse levels and the dense
+ * solve), on the scene's stream and in its precision.  b and z: host arrays
+ * of nnode*B doubles (node-major, x fastest; u-p in solver units, pressure
+ * rows scaled by p_scale); b is rounded to the scene's precision, and z is 0
+ * on nodes without a row.  Synchronises the scene's stream.  MPM_ERR_STATE
+ * without a hierarchy (precond other than MPM_PC_MG, or before an assembly
+ * of the staged step); MPM_ERR_INVALID_ARG for NULL pointers. */
+mpm_status mpm_mg_apply(mpm_scene* s, const double* b, double* z);
+
 /* Device-pointer variants: the caller's DEVICE buffers (for example the data
  * pointers of CUDA tensors on the scene's device), written on the scene's
  * stream without synchronising the host (order later work on that stream, or

@@ -698,6 +698,34 @@ void mg_setup(mpm_scene* s) {
   s->launches += 1;
 }
 
+// z = M^-1 b with the hierarchy of the last assembly (host vectors of ndof
+// doubles, rounded to T on the way in); scratch vectors of the padded
+// level-0 layout are allocated for the call
+template <int D, class T, int B>
+void mg_apply_impl(mpm_scene* s, const double* b, double* z) {
+  if (!s->mg || s->mg_L == 0 || s->nrow == 0)
+    fail(MPM_ERR_STATE, "no multigrid hierarchy (MPM_PC_MG, after an assembly)");
+  cudaStream_t st = s->st;
+  MgApply<T> mga = mg_view<T>(s);
+  bool staging = false;
+  mga.cluster = mg_tail_cluster<D, T, B>(&staging);
+  if (!staging) mga.staged = mga.L;
+  std::vector<T> h((size_t)s->ndof);
+  for (long long d = 0; d < s->ndof; ++d) h[d] = (T)b[d];
+  T* v = s->dalloc<T>(3 * (size_t)s->vlen);
+  ck(cudaMemsetAsync(v, 0, 3 * (size_t)s->vlen * sizeof(T), st), "memset");
+  T* vb = v + s->vpad;
+  T* vzero = v + s->vlen + s->vpad;
+  T* vz = v + 2 * s->vlen + s->vpad;
+  ck(cudaMemcpyAsync(vb, h.data(), (size_t)s->ndof * sizeof(T), cudaMemcpyHostToDevice, st), "upload");
+  ck(launch_mg_apply<D, T, B>(mga, vb, vzero, vz, st), "v-cycle");
+  s->launches += (mga.L >= 2 ? 1 : 0) + mg_vcycle_launches(mga.L, mga.tail, mga.fused);
+  ck(cudaMemcpyAsync(h.data(), vz, (size_t)s->ndof * sizeof(T), cudaMemcpyDeviceToHost, st), "download");
+  ck(cudaStreamSynchronize(st), "sync");
+  s->dfree(v);
+  for (long long d = 0; d < s->ndof; ++d) z[d] = (double)h[d];
+}
+
 template <int D, class T, int B>
 void build_graph(mpm_scene* s, int nblk, const MgApply<T>* mg, int chunk, const std::vector<int>& sig) {
   if (s->gexec) {
@@ -1268,6 +1296,9 @@ template <int D, class T, int B> struct AdjointStepF {
   static void run(mpm_scene* s, const double* a, const double* b, double* sb, double* c, double* d, double* e) {
     adjoint_step_impl<D, T, B>(s, a, b, sb, c, d, e);
   }
+};
+template <int D, class T, int B> struct MgApplyF {
+  static void run(mpm_scene* s, const double* b, double* z) { mg_apply_impl<D, T, B>(s, b, z); }
 };
 template <int D, class T, int B> struct IncrementF {
   static void run(mpm_scene* s, double* o) { particle_increment_impl<D, T, B>(s, o); }
@@ -1870,6 +1901,11 @@ mpm_status mpm_get_mg_level(const mpm_scene* cs, int level, int* levels, int dim
       for (int sl = 0; sl < S; ++sl)
         for (int k = 0; k < BB; ++k) vals[((size_t)r * S + sl) * BB + k] = K[((size_t)sl * m.cap + r) * BB + k];
   });
+}
+
+mpm_status mpm_mg_apply(mpm_scene* s, const double* b, double* z) {
+  if (!s || !b || !z) return MPM_ERR_INVALID_ARG;
+  return guarded(s, [&] { dispatch<MgApplyF>(s, b, z); });
 }
 
 mpm_status mpm_get_particles(const mpm_scene* cs, double* x, double* be, double* pc, double* F, double* tau) {

@@ -422,6 +422,10 @@ cudaError_t launch_mg_dense_inverse(MgLevel<T> c, float* invT, cudaStream_t st);
 template <int D, class T, int B>
 cudaError_t launch_mg_vcycle(const MgApply<T>& mg, const T* b0, T* z0, const int* done, cudaStream_t st);
 int mg_vcycle_launches(int L, int tail, int fused);
+// z0 = M^-1 b0 outside a Krylov solve: the first finest-level sweep from the
+// zero vector `zero` (padded, all zero), then the V-cycle
+template <int D, class T, int B>
+cudaError_t launch_mg_apply(const MgApply<T>& mg, const T* b0, const T* zero, T* z0, cudaStream_t st);
 
 // device-pointer getters and Dirichlet setter (mpm_devio.cu)
 cudaError_t launch_du_out(const double* du, double* out, long long ndof, int B, int D, double psc,

@@ -1177,6 +1177,16 @@ int mg_tail_cluster(bool* staging) {
   return size;
 }
 
+template <int D, class T, int B>
+cudaError_t launch_mg_apply(const MgApply<T>& mg, const T* b0, const T* zero, T* z0, cudaStream_t st) {
+  if (mg.L >= 2) {
+    k_mg_smooth<D, T, B><<<nblk_rows(mg.caps[0]), MTPB, 0, st>>>(mg.lev[0], b0, zero, z0, nullptr);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return launch_mg_vcycle<D, T, B>(mg, b0, z0, nullptr, st);
+}
+
 int mg_vcycle_launches(int L, int tail, int fused) {
   if (L <= 1) return 1;
   const int l0 = std::min(std::max(tail, 1), L - 1);
@@ -1189,6 +1199,7 @@ int mg_vcycle_launches(int L, int tail, int fused) {
                                                 cudaStream_t);                                            \
   template cudaError_t launch_mg_dense_inverse<D, T, B>(MgLevel<T>, float*, cudaStream_t);                    \
   template cudaError_t launch_mg_vcycle<D, T, B>(const MgApply<T>&, const T*, T*, const int*, cudaStream_t); \
+  template cudaError_t launch_mg_apply<D, T, B>(const MgApply<T>&, const T*, const T*, T*, cudaStream_t);   \
   template int mg_tail_cluster<D, T, B>(bool*);
 MPM_MG_INST(2, float, 2)
 MPM_MG_INST(2, double, 2)

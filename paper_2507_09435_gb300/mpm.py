@@ -104,7 +104,7 @@ _lib = None
 # every symbol declared in include/mpm.h
 EXPORTS = ["mpm_create_scene", "mpm_set_gravity", "mpm_set_dirichlet", "mpm_begin_step", "mpm_newton_step",
            "mpm_set_du", "mpm_assemble", "mpm_commit_step", "mpm_solve_step", "mpm_get_residual", "mpm_get_du", "mpm_get_mass",
-           "mpm_get_counts", "mpm_get_jacobian_bsr", "mpm_get_mg_level", "mpm_get_particles", "mpm_get_pressure",
+           "mpm_get_counts", "mpm_get_jacobian_bsr", "mpm_get_mg_level", "mpm_mg_apply", "mpm_get_particles", "mpm_get_pressure",
            "mpm_get_du_dev", "mpm_get_residual_dev", "mpm_get_positions_dev", "mpm_set_dirichlet_dev",
            "mpm_set_traction", "mpm_kernel_launches", "mpm_get_newton_counters", "mpm_fma_peak", "mpm_set_params", "mpm_get_particle_increment",
            "mpm_adjoint", "mpm_adjoint_step", "mpm_set_state",
@@ -140,6 +140,7 @@ def lib(build: bool = True):
     L.mpm_get_mass.argtypes = [_P, _D]
     L.mpm_get_counts.argtypes = [_P, _I, _LL]
     L.mpm_get_jacobian_bsr.argtypes = [_P, ctypes.c_longlong, _I, _LL, _I, _D]
+    L.mpm_mg_apply.argtypes = [_P, _D, _D]
     L.mpm_get_mg_level.argtypes = [_P, ctypes.c_int, _I, _I, _I, ctypes.c_int, _I, _D,
                                    ctypes.POINTER(ctypes.c_ubyte), _D]
     L.mpm_get_particles.argtypes = [_P, _D, _D, _D, _D, _D]
@@ -383,6 +384,15 @@ def mpm_get_mg_level(h, level, dim, B):
                 fixed=fixed.astype(bool), lambda_max=lam.value)
 
 
+def mpm_mg_apply(h, b):
+    """z = M^-1 b, one V-cycle of the last assembly's multigrid hierarchy
+    (b: nnode*B doubles; z the same)."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    z = np.zeros_like(b)
+    _check(lib().mpm_mg_apply(h, _p(b), _p(z)), h)
+    return z
+
+
 def mpm_get_jacobian_bsr(h, dim):
     na, nb = mpm_get_counts(h)
     row_node = np.zeros(na, dtype=np.int32)
@@ -602,6 +612,11 @@ class GpuScene:
 
     def mg_level(self, level):
         return mpm_get_mg_level(self.h, level, self.dim, self.B)
+
+    def mg_apply(self, b):
+        if len(b) != self.ndof:
+            raise ValueError(f"b has {len(b)} entries, the scene {self.ndof} DOFs")
+        return mpm_mg_apply(self.h, b)
 
     # device-tensor variants (work on the scene's stream, no host sync)
     def du_into(self, out):

@@ -308,3 +308,71 @@ def test_multigrid_rejects_gmres():
     sc = S.block_compression(nsteps=1)
     with pytest.raises(mpm.MPMError):
         mpm.GpuScene(sc, krylov=mpm.MPM_GMRES, precond=mpm.MPM_PC_MG)
+
+
+def test_vcycle_matches_oracle():
+    """One application of the GPU's V-cycle (`mpm_mg_apply`) against the
+    reference V-cycle of oracle/mg_oracle.py, built from the oracle's own
+    Jacobian of the coarse footing's first load step (FP64, the GPU at
+    FP64): the same hierarchy depth, the same smoother damping estimates
+    (both sides run the power iteration from the SplitMix64 start vector),
+    and the same z element by element.  The GPU's one FP32 step in FP64 mode
+    is the dense coarsest level (FP32 inverse, FP32 right-hand side and
+    sums); the tolerance is the standard error bound of that solve,
+    (2n + 2) kappa u + u with u = 2^-24, plus the Jacobian's FP64 parity bar
+    (1e-10) times kappa, carried to the finest level through the infinity
+    norm of the up leg's linear part, and 1e-8 of the result for the FP64
+    rounding of the other steps."""
+    from oracle import mg_oracle as G
+
+    sc = S.footing(nx=48, ny=24, h=0.5, nsteps=20, settle_frac=0.1)
+    st = sc.steps[0]
+    B = sc.B
+    gs = mpm.GpuScene(sc, precision=mpm.MPM_FP64, precond=mpm.MPM_PC_MG)
+    gs.begin(st)
+    gs.assemble()
+    orc = O.OracleScene.from_scene(sc)
+    orc.gravity = np.asarray(st.gravity, dtype=np.float64)
+    du0 = np.zeros(sc.nnode * B)
+    du0[np.asarray(st.dof, dtype=np.int64)] = st.value
+    _, M, _ = orc.residual(du0, with_scale=True)
+    act = M > O.ACTIVE_REL * orc.m.max()
+    fixed = fixed_mask(sc, st)
+    keep = (~fixed).astype(float)
+    J = orc.jacobian(du0)
+    A0 = (sp.diags(keep) @ J @ sp.diags(keep) + sp.diags(fixed.astype(float))).tocsr()
+    dims = [sc.n[0] + 1, sc.n[1] + 1]
+    H = G.Hierarchy(A0, act, fixed, dims, B)
+
+    assert H.L == gs.mg_level(0)["levels"] and H.L >= 3
+    assert abs(gs.mg_level(0)["lambda_max"] - H.lam[0]) <= 1e-8 * H.lam[0]
+    for l in range(1, H.L - 1):
+        assert abs(gs.mg_level(l)["lambda_max"] - H.lam[l]) <= 1e-8 * H.lam[l], l
+
+    rng = np.random.default_rng(2507_09435)
+    on = np.repeat(act, B) & ~fixed
+    b = np.where(on, rng.standard_normal(sc.nnode * B), 0.0)
+    z_g = gs.mg_apply(b)
+    z_o = H.vcycle(b)
+
+    bs, _ = H.down(b)
+    zd = H.dense_solve(bs[-1])
+    idx = H.dense_idx
+    Ad = H.A[-1][idx][:, idx].toarray()
+    kappa = float(np.linalg.cond(Ad, np.inf))
+    n = len(idx)
+    u = 2.0 ** -24
+    dzd = ((2 * n + 2) * kappa * u + u + kappa * 1e-10) * float(np.abs(zd).max())
+    U = np.empty((sc.nnode * B, n))
+    for k, j in enumerate(idx):
+        e = np.zeros(len(zd))
+        e[j] = 1.0
+        U[:, k] = H.up_linear(e)
+    normU = float(np.abs(U).sum(axis=1).max())
+    zmax = float(np.abs(z_o).max())
+    tol = normU * dzd + 1e-8 * zmax
+    rows = np.repeat(act, B)
+    err = float(np.abs(z_g[rows] - z_o[rows]).max())
+    assert err <= tol and err <= 1e-3 * zmax, (err, tol, zmax, kappa, normU)
+    assert np.all(z_g[~rows] == 0.0)
+    gs.close()
