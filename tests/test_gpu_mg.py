@@ -345,8 +345,21 @@ def _vcycle_parity(sc):
 
     assert H.L == gs.mg_level(0)["levels"] and H.L >= 3
     assert abs(gs.mg_level(0)["lambda_max"] - H.lam[0]) <= 1e-8 * H.lam[0]
-    for l in range(1, H.L - 1):
-        assert abs(gs.mg_level(l)["lambda_max"] - H.lam[l]) <= 1e-8 * H.lam[l], l
+    for l in range(1, H.L):
+        lev = gs.mg_level(l)
+        if l < H.L - 1:
+            assert abs(lev["lambda_max"] - H.lam[l]) <= 1e-8 * H.lam[l], l
+        # the coarse operators against the oracle's own P^T A P: each is a
+        # sum of at most 81 (2D) or 729 (3D) weighted fine blocks, each within
+        # the FP64 Jacobian bar of 1e-10 of its row's largest block
+        assert set(lev["nodes"].tolist()) == set(np.nonzero(H.act[l])[0].tolist()), l
+        cd = [int(x) for x in lev["dims"]]
+        rows = (lev["nodes"][:, None] * B + np.arange(B)[None, :]).ravel()
+        Ad = H.A[l][rows].toarray()
+        Gd = _level_to_csr(lev, cd, B, d)[rows].toarray()
+        scale = np.abs(Ad).max(axis=1, keepdims=True) + 1e-300
+        nterm = 81 if d == 2 else 729
+        assert float((np.abs(Gd - Ad) / scale).max()) <= nterm * 1e-10, l
 
     rng = np.random.default_rng(2507_09435)
     on = np.repeat(act, B) & ~fixed
