@@ -334,8 +334,8 @@ __global__ void k_mg_scale(T* dinv, long long n, const double* nrm, double c) {
 // as on [A | I]).  At the end [A | I] has become [P | R] with P e_k = e_{p_k},
 // so (A^-1)[k][j] = R[p_k][j], and R[r][p_c] sits in column c.  The warp that
 // owns column k + 1 picks its pivot right after eliminating column k and
-// stages the column in shared memory (double-buffered), so one block barrier
-// per column suffices.  A pivot that vanishes is replaced by 1 (the
+// stages the column (double-buffered), the pivot row and the pivot's
+// reciprocal ip in shared memory, so one block barrier per column suffices.  A pivot that vanishes is replaced by 1 (the
 // preconditioner stays defined).  Written transposed:
 // invT[j*n + k] = (A^-1)[k][j].
 __device__ __forceinline__ void gj_select(const float (&a)[4][4], unsigned used, int col, int n,
