@@ -140,3 +140,35 @@ def test_vcycle_contracts_on_poisson():
         factors.append(rate)
         assert rate < 0.35, (n, rate)
     assert abs(factors[0] - factors[1]) < 0.15, factors
+
+
+def test_block_vcycle_of_decoupled_components():
+    """Two uncoupled copies of the 2D Laplacian as one operator with 2x2 node
+    blocks (component fastest): the block V-cycle is the scalar V-cycle of
+    each component, which pins the node-block indexing of the smoother,
+    and the prolongation per component."""
+    n = 33
+    dims = [n, n]
+    fixed1 = _boundary(dims)
+    A1 = _laplacian(dims, fixed1)
+    A2 = sp.kron(A1, sp.eye(2)).tocsr()
+    fixed2 = np.repeat(fixed1, 2)
+    act = np.ones(n * n, dtype=bool)
+    H1 = G.Hierarchy(A1, act, fixed1, dims, 1)
+    rng = np.random.default_rng(11)
+    b1 = np.where(fixed1, 0.0, rng.standard_normal(n * n))
+    b2 = np.zeros(2 * n * n)
+    b2[0::2] = b1
+    # the same depth (twice the unknowns per node, twice the dense bound) and
+    # the same damping on both sides: the block hierarchy's estimate comes
+    # from a different start vector, so its smoother takes H1's damping
+    H2c = G.Hierarchy(A2, act, fixed2, dims, 2, dense_max=2 * (H1.act[-1].sum()))
+    assert H2c.L == H1.L
+    for l in range(H1.L - 1):
+        w1 = 1.2 / H1.lam[l] if 1e-3 <= H1.lam[l] < 1e30 else 0.5
+        w2 = 1.2 / H2c.lam[l] if 1e-3 <= H2c.lam[l] < 1e30 else 0.5
+        H2c.Dinv[l] = H2c.Dinv[l] * (w1 / w2)
+    z2 = H2c.vcycle(b2)
+    z1 = H1.vcycle(b1)
+    assert np.allclose(z2[0::2], z1, rtol=0, atol=1e-12 * np.abs(z1).max())
+    assert np.all(z2[1::2] == 0.0)
